@@ -1,0 +1,703 @@
+/*
+ * FP64 CPU oracle for batched complex basis pursuit denoising (BPDN).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * execute this file; only tests/, __graft_entry__.smoke() and the CPU-baseline
+ * leg of bench.py use it.  It shares no code with the CUDA implementation.
+ *
+ * Problem (Eq. 1 / Eq. 6):  min_x F(x) = ||A x - g||_2^2 + lambda * sum_l |x_l|
+ * with x in C^L and |.| the complex modulus (the SOCP remark of Sec. III-A makes the
+ * L1 norm of a complex vector the sum of moduli).
+ *
+ * Operator (Eq. 5 and the definitions after Eq. 2): A_nl = exp(-j 2 pi xi_n s_l),
+ * xi_n = 2 b_n / (wavelength * range), s_l uniform on [s_min, s_max] with both
+ * end points included.
+ *
+ * Everything is plain double-precision loops in the order the definitions are
+ * written; no blocking, no fusion.  Complex numbers use C99 `double complex`.
+ *
+ * Contents
+ *   orc_grid / orc_operator / orc_gram_toeplitz / orc_aah   : the operator (Eq. 5)
+ *   orc_soft                                                 : complex soft threshold (Eq. 10)
+ *   orc_rbpg                                                 : Algorithm 1 (RBPG with backtracking)
+ *   orc_cd                                                   : cyclic coordinate descent (exact minimiser)
+ *   orc_newton_polish                                        : Newton on the smooth optimality
+ *                                                              system restricted to a support
+ *   orc_kkt                                                  : optimality certificate (Eq. 6)
+ *   orc_*_batch                                              : OpenMP loops over pixels
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+#define ORC_NOT_CONVERGED 1
+#define ORC_BT_LIMIT 2
+#define ORC_NONFINITE 4
+#define ORC_ZERO_SOLUTION 32
+
+static const double ORC_PI = 3.14159265358979323846264338327950288;
+
+/* ---------------------------------------------------------------- operator */
+
+/* s_l = s_min + l * (s_max - s_min) / (L - 1), l = 0..L-1 (Eq. 5: "uniformly sampled"). */
+void orc_grid(double s_min, double s_max, int L, double *s)
+{
+    for (int l = 0; l < L; ++l)
+        s[l] = (L > 1) ? s_min + (double)l * (s_max - s_min) / (double)(L - 1) : s_min;
+}
+
+/* xi_n = 2 b_n / (wavelength * range)   (Sec. II, after Eq. 2) */
+void orc_xi(const double *b, int N, double wavelength, double range, double *xi)
+{
+    for (int n = 0; n < N; ++n)
+        xi[n] = 2.0 * b[n] / (wavelength * range);
+}
+
+/* A (row-major N x L): A_nl = exp(-j 2 pi xi_n s_l)   (Eq. 5) */
+void orc_operator(const double *b, int N, double wavelength, double range,
+                  double s_min, double s_max, int L, cplx *A)
+{
+    double *s = (double *)malloc(sizeof(double) * (size_t)L);
+    double *xi = (double *)malloc(sizeof(double) * (size_t)N);
+    orc_grid(s_min, s_max, L, s);
+    orc_xi(b, N, wavelength, range, xi);
+    for (int n = 0; n < N; ++n)
+        for (int l = 0; l < L; ++l)
+            A[(size_t)n * L + l] = cexp(-2.0 * ORC_PI * I * xi[n] * s[l]);
+    free(s);
+    free(xi);
+}
+
+/* Toeplitz generator of the Gram matrix on a uniform grid:
+ * (A^H A)_{lm} = sum_n exp(j 2 pi xi_n (s_l - s_m)) = h(l - m),
+ * h(d) = sum_n exp(j 2 pi xi_n d ds), stored as h[d + L - 1], d = -(L-1)..(L-1). */
+void orc_gram_toeplitz(const double *xi, int N, double ds, int L, cplx *h)
+{
+    for (int d = -(L - 1); d <= L - 1; ++d) {
+        cplx acc = 0.0;
+        for (int n = 0; n < N; ++n)
+            acc += cexp(2.0 * ORC_PI * I * xi[n] * (double)d * ds);
+        h[d + L - 1] = acc;
+    }
+}
+
+/* A A^H (N x N), by the plain sum over the grid. */
+void orc_aah(const cplx *A, int N, int L, cplx *M)
+{
+    for (int n = 0; n < N; ++n)
+        for (int m = 0; m < N; ++m) {
+            cplx acc = 0.0;
+            for (int l = 0; l < L; ++l)
+                acc += A[(size_t)n * L + l] * conj(A[(size_t)m * L + l]);
+            M[(size_t)n * N + m] = acc;
+        }
+}
+
+/* ------------------------------------------------------------- primitives */
+
+/* Complex soft threshold, the proximal map of tau*|.| (Eq. 10 read for complex v):
+ * S_tau(v) = v * max(0, 1 - tau/|v|);  |v| <= tau -> 0 (closed middle case). */
+cplx orc_soft(cplx v, double tau)
+{
+    double a = cabs(v);
+    if (!(a > tau))
+        return 0.0;
+    return v * (1.0 - tau / a);
+}
+
+void orc_soft_vec(const cplx *v, int n, double tau, cplx *out)
+{
+    for (int i = 0; i < n; ++i)
+        out[i] = orc_soft(v[i], tau);
+}
+
+static void matvec(const cplx *A, int N, int L, const cplx *x, cplx *out) /* out = A x */
+{
+    for (int n = 0; n < N; ++n) {
+        cplx acc = 0.0;
+        for (int l = 0; l < L; ++l)
+            acc += A[(size_t)n * L + l] * x[l];
+        out[n] = acc;
+    }
+}
+
+static void matvec_h(const cplx *A, int N, int L, const cplx *r, cplx *out) /* out = A^H r */
+{
+    for (int l = 0; l < L; ++l) {
+        cplx acc = 0.0;
+        for (int n = 0; n < N; ++n)
+            acc += conj(A[(size_t)n * L + l]) * r[n];
+        out[l] = acc;
+    }
+}
+
+static double norm2sq(const cplx *v, int n)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i)
+        s += creal(v[i]) * creal(v[i]) + cimag(v[i]) * cimag(v[i]);
+    return s;
+}
+
+static double l1(const cplx *v, int n)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i)
+        s += cabs(v[i]);
+    return s;
+}
+
+/* F(x) = ||A x - g||^2 + lambda ||x||_1   (Eq. 6) */
+double orc_objective(const cplx *A, int N, int L, const cplx *g, double lam, const cplx *x)
+{
+    cplx *r = (cplx *)malloc(sizeof(cplx) * (size_t)N);
+    matvec(A, N, L, x, r);
+    for (int n = 0; n < N; ++n)
+        r[n] -= g[n];
+    double F = norm2sq(r, N) + lam * l1(x, L);
+    free(r);
+    return F;
+}
+
+static int all_finite(const cplx *v, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!isfinite(creal(v[i])) || !isfinite(cimag(v[i])))
+            return 0;
+    return 1;
+}
+
+/* --------------------------------------------------------- Algorithm 1 */
+
+/*
+ * RBPG with backtracking (Algorithm 1, Eqs. 11-15) for one pixel, FP64.
+ *
+ * Block = the pixel's whole x (the patch objective is separable over pixels;
+ * with equal block Lipschitz constants the sampling of Eq. 14 is uniform, so
+ * each pixel's iterate sequence is the one written here).
+ *
+ * Readings of the points the paper leaves open:
+ *   - Nesterov weight theta_k = 2/(k+1) (after Eq. 12), so the extrapolation
+ *     factor theta_k (1/theta_{k-1} - 1) = (k-2)/(k+1); with x^{0} = x^{-1} = 0
+ *     the k = 1 term vanishes.  The counter k never resets.
+ *   - f(x) = ||A x - g||^2, grad f(y) = 2 A^H (A y - g) (Wirtinger gradient).
+ *   - Eq. 10 read as the complex soft threshold with tau = alpha_k * lambda.
+ *   - Backtracking (Eq. 15) loops while the condition does NOT hold; for the
+ *     quadratic f, Eq. 15 at base point y is ||A (x' - y)||^2 <= ||x' - y||^2 / (2 alpha).
+ *     alpha starts at alpha0 and is carried from iteration to iteration
+ *     (non-increasing), shrunk by C_alpha on each failure.
+ *   - Monotone step: x^{k+1} = xbar if F(xbar) <= F(x^k), else x^k (ties accept).
+ *   - Stop when the candidate step is small, ||xbar - x^k|| <= tol * max(||xbar||, 1e-30)
+ *     (accepted or not: on acceptance this is ||x^{k+1} - x^k||; a rejected candidate
+ *     that close to x^k means x^k is a fixed point up to rounding), or after
+ *     max_iter iterations (status NOT_CONVERGED).  x = xbar = 0 at k = 1 stops at once.
+ *
+ * trace arrays (length >= max_iter, may be NULL): alpha after backtracking,
+ * accept flag, number of step reductions, F(xbar) and the smallest relative
+ * margin of any discrete decision taken in the iteration (prox thresholds,
+ * line-search test, accept test).
+ */
+int orc_rbpg(const cplx *A, int N, int L, const cplx *g, double lam, double alpha0,
+             double c_alpha, double tol, int max_iter, int max_bt, cplx *x_out,
+             int *iters_out, double *tr_alpha, int *tr_acc, int *tr_nbt, double *tr_F,
+             double *tr_margin)
+{
+    int status = 0;
+    size_t Lz = (size_t)L, Nz = (size_t)N;
+    cplx *x = (cplx *)calloc(Lz, sizeof(cplx));
+    cplx *xp = (cplx *)calloc(Lz, sizeof(cplx));
+    cplx *y = (cplx *)calloc(Lz, sizeof(cplx));
+    cplx *grad = (cplx *)calloc(Lz, sizeof(cplx));
+    cplx *v = (cplx *)calloc(Lz, sizeof(cplx));
+    cplx *xb = (cplx *)calloc(Lz, sizeof(cplx));
+    cplx *Ay = (cplx *)calloc(Nz, sizeof(cplx));
+    cplx *r = (cplx *)calloc(Nz, sizeof(cplx));
+    cplx *Axb = (cplx *)calloc(Nz, sizeof(cplx));
+    cplx *tmp = (cplx *)calloc(Nz, sizeof(cplx));
+    int k = 0;
+
+    if (!all_finite(g, N)) {
+        status = ORC_NONFINITE;
+        goto done;
+    }
+
+    double alpha = alpha0;
+    double Fx = norm2sq(g, N); /* F(0) */
+    int stopped = 0;
+    for (k = 1; k <= max_iter; ++k) {
+        double beta = (double)(k - 2) / (double)(k + 1);
+        for (int l = 0; l < L; ++l)
+            y[l] = x[l] + beta * (x[l] - xp[l]);
+        matvec(A, N, L, y, Ay);
+        for (int n = 0; n < N; ++n)
+            r[n] = Ay[n] - g[n];
+        matvec_h(A, N, L, r, grad);
+        for (int l = 0; l < L; ++l)
+            grad[l] *= 2.0;
+
+        int nbt = 0;
+        double margin = INFINITY;
+        for (;;) {
+            double tau = alpha * lam;
+            double pm = INFINITY;
+            for (int l = 0; l < L; ++l) {
+                v[l] = y[l] - alpha * grad[l];
+                xb[l] = orc_soft(v[l], tau);
+                double mm = fabs(cabs(v[l]) - tau) / tau;
+                if (mm < pm)
+                    pm = mm;
+            }
+            matvec(A, N, L, xb, Axb);
+            for (int n = 0; n < N; ++n)
+                tmp[n] = Axb[n] - Ay[n];
+            double lhs = norm2sq(tmp, N);
+            double dd = 0.0;
+            for (int l = 0; l < L; ++l) {
+                cplx d = xb[l] - y[l];
+                dd += creal(d) * creal(d) + cimag(d) * cimag(d);
+            }
+            double rhs = dd / (2.0 * alpha);
+            double bm = (lhs + rhs > 0.0) ? fabs(rhs - lhs) / fmax(lhs, rhs) : INFINITY;
+            margin = fmin(pm, bm);
+            if (lhs <= rhs)
+                break;
+            if (nbt >= max_bt) {
+                status |= ORC_BT_LIMIT;
+                break;
+            }
+            alpha *= c_alpha;
+            ++nbt;
+        }
+        for (int n = 0; n < N; ++n)
+            tmp[n] = Axb[n] - g[n];
+        double Fb = norm2sq(tmp, N) + lam * l1(xb, L);
+        double am = fabs(Fb - Fx) / fmax(fabs(Fx), 1e-300);
+        margin = fmin(margin, am);
+
+        int accepted = (Fb <= Fx);
+        /* x^{k} becomes x_prev; x^{k+1} is xbar (accept) or x^{k} (reject).
+         * The stopping test measures the candidate step ||xbar - x^k|| against ||xbar||. */
+        double dnorm = 0.0, xnorm = 0.0;
+        for (int l = 0; l < L; ++l) {
+            cplx xk = x[l];
+            cplx d = xb[l] - xk;
+            dnorm += creal(d) * creal(d) + cimag(d) * cimag(d);
+            xnorm += creal(xb[l]) * creal(xb[l]) + cimag(xb[l]) * cimag(xb[l]);
+            xp[l] = xk;
+            if (accepted)
+                x[l] = xb[l];
+        }
+        if (accepted)
+            Fx = Fb;
+        if (tr_alpha)
+            tr_alpha[k - 1] = alpha;
+        if (tr_acc)
+            tr_acc[k - 1] = accepted;
+        if (tr_nbt)
+            tr_nbt[k - 1] = nbt;
+        if (tr_F)
+            tr_F[k - 1] = Fb;
+        if (tr_margin)
+            tr_margin[k - 1] = margin;
+        if (sqrt(dnorm) <= tol * fmax(sqrt(xnorm), 1e-30)) {
+            stopped = 1;
+            break;
+        }
+    }
+    if (!stopped) {
+        status |= ORC_NOT_CONVERGED;
+        k = max_iter;
+    }
+    {
+        int nz = 0;
+        for (int l = 0; l < L; ++l)
+            nz |= (x[l] != 0.0);
+        if (!nz)
+            status |= ORC_ZERO_SOLUTION;
+    }
+done:
+    for (int l = 0; l < L; ++l)
+        x_out[l] = x[l];
+    if (iters_out)
+        *iters_out = k;
+    free(x); free(xp); free(y); free(grad); free(v); free(xb);
+    free(Ay); free(r); free(Axb); free(tmp);
+    return status;
+}
+
+/* ------------------------------------------------------ exact minimiser */
+
+/*
+ * Cyclic coordinate descent for Eq. 6 (an algorithm unrelated to RBPG; used
+ * only to find the minimiser).  Minimising F over x_l alone with the others
+ * fixed gives x_l = S_{lambda/2}(a_l^H (g - A x + a_l x_l)) / ||a_l||^2.
+ * q = A^H (g - A x) is kept up to date and recomputed from scratch every 64
+ * sweeps.  Stops when max_l |dx_l| <= tol * max(1, max_l |x_l|).
+ * Returns 0 on convergence, 1 if max_sweeps was reached.
+ */
+int orc_cd(const cplx *A, int N, int L, const cplx *g, double lam, double tol,
+           long max_sweeps, cplx *x, long *sweeps_out)
+{
+    size_t Lz = (size_t)L;
+    cplx *G = (cplx *)malloc(sizeof(cplx) * Lz * Lz);
+    cplx *c = (cplx *)malloc(sizeof(cplx) * Lz);
+    cplx *q = (cplx *)malloc(sizeof(cplx) * Lz);
+    /* G = A^H A, c = A^H g */
+    for (int l = 0; l < L; ++l)
+        for (int m = 0; m < L; ++m) {
+            cplx acc = 0.0;
+            for (int n = 0; n < N; ++n)
+                acc += conj(A[(size_t)n * L + l]) * A[(size_t)n * L + m];
+            G[(size_t)l * L + m] = acc;
+        }
+    matvec_h(A, N, L, g, c);
+    for (int l = 0; l < L; ++l)
+        x[l] = 0.0;
+    long sw;
+    int rc = 1;
+    for (sw = 0; sw < max_sweeps; ++sw) {
+        if (sw % 64 == 0) {
+            for (int l = 0; l < L; ++l) {
+                cplx acc = c[l];
+                for (int m = 0; m < L; ++m)
+                    acc -= G[(size_t)l * L + m] * x[m];
+                q[l] = acc;
+            }
+        }
+        double maxd = 0.0, maxx = 0.0;
+        for (int l = 0; l < L; ++l) {
+            double Gll = creal(G[(size_t)l * L + l]);
+            cplx old = x[l];
+            cplx vv = q[l] + Gll * old;
+            cplx nw = orc_soft(vv, 0.5 * lam) / Gll;
+            cplx dlt = nw - old;
+            if (dlt != 0.0) {
+                for (int m = 0; m < L; ++m)
+                    q[m] -= G[(size_t)m * L + l] * dlt;
+                x[l] = nw;
+                double ad = cabs(dlt);
+                if (ad > maxd)
+                    maxd = ad;
+            }
+            double ax = cabs(x[l]);
+            if (ax > maxx)
+                maxx = ax;
+        }
+        if (maxd <= tol * fmax(1.0, maxx)) {
+            rc = 0;
+            ++sw;
+            break;
+        }
+    }
+    if (sweeps_out)
+        *sweeps_out = sw;
+    free(G); free(c); free(q);
+    return rc;
+}
+
+/* Solve the real n x n system M z = rhs by Gaussian elimination with partial
+ * pivoting (M and rhs are overwritten).  Returns 0 on success. */
+static int solve_real(double *M, double *rhs, int n)
+{
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        double best = fabs(M[(size_t)k * n + k]);
+        for (int i = k + 1; i < n; ++i)
+            if (fabs(M[(size_t)i * n + k]) > best) {
+                best = fabs(M[(size_t)i * n + k]);
+                p = i;
+            }
+        if (!(best > 0.0))
+            return 1;
+        if (p != k) {
+            for (int j = 0; j < n; ++j) {
+                double t = M[(size_t)k * n + j];
+                M[(size_t)k * n + j] = M[(size_t)p * n + j];
+                M[(size_t)p * n + j] = t;
+            }
+            double t = rhs[k];
+            rhs[k] = rhs[p];
+            rhs[p] = t;
+        }
+        for (int i = k + 1; i < n; ++i) {
+            double f = M[(size_t)i * n + k] / M[(size_t)k * n + k];
+            for (int j = k; j < n; ++j)
+                M[(size_t)i * n + j] -= f * M[(size_t)k * n + j];
+            rhs[i] -= f * rhs[k];
+        }
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        double s = rhs[k];
+        for (int j = k + 1; j < n; ++j)
+            s -= M[(size_t)k * n + j] * rhs[j];
+        rhs[k] = s / M[(size_t)k * n + k];
+    }
+    return 0;
+}
+
+/* restricted objective F_S(z) = ||A_S z - g||^2 + lambda sum |z_i| */
+static double restricted_F(const cplx *AS, int N, int m, const cplx *g, double lam, const cplx *z)
+{
+    double s = 0.0;
+    for (int n = 0; n < N; ++n) {
+        cplx acc = -g[n];
+        for (int i = 0; i < m; ++i)
+            acc += AS[(size_t)n * m + i] * z[i];
+        s += creal(acc) * creal(acc) + cimag(acc) * cimag(acc);
+    }
+    for (int i = 0; i < m; ++i)
+        s += lam * cabs(z[i]);
+    return s;
+}
+
+/* Phi(z) = 2 (G z - c) + lambda z/|z|: the gradient of F_S where no z_i is 0. */
+static void restricted_phi(const cplx *G, const cplx *c, int m, double lam, const cplx *z, cplx *phi)
+{
+    for (int i = 0; i < m; ++i) {
+        cplx acc = -c[i];
+        for (int j = 0; j < m; ++j)
+            acc += G[(size_t)i * m + j] * z[j];
+        phi[i] = 2.0 * acc + lam * z[i] / cabs(z[i]);
+    }
+}
+
+/*
+ * Newton's method for the optimality system of Eq. 6 restricted to the index
+ * set S (all |z_i| > 0):  Phi(z) = 2 A_S^H (A_S z - g) + lambda z/|z| = 0.
+ * In real coordinates (Re z_i, Im z_i) the Jacobian is
+ *     J = 2 [[Re G, -Im G], [Im G, Re G]] (per 2x2 block) + lambda/|z_i| (I - u u^T),
+ * u = (Re z_i, Im z_i)/|z_i|, G = A_S^H A_S; it is the Hessian of F_S.  Steps are
+ * halved until F_S or ||Phi|| decreases and no component reaches zero.
+ * z: in = starting point (all nonzero), out = solution.  Returns 0 when
+ * max_i |Phi_i| <= ftol * lambda, 1 otherwise.  *res_out = final max |Phi_i| / lambda.
+ */
+int orc_newton_polish(const cplx *A, int N, int L, const cplx *g, double lam, int m,
+                      const int *S, cplx *z, int max_it, double ftol, double *res_out)
+{
+    (void)L;
+    int rc = 1;
+    size_t mz = (size_t)m;
+    cplx *AS = (cplx *)malloc(sizeof(cplx) * (size_t)N * mz);
+    cplx *G = (cplx *)malloc(sizeof(cplx) * mz * mz);
+    cplx *c = (cplx *)malloc(sizeof(cplx) * mz);
+    cplx *phi = (cplx *)malloc(sizeof(cplx) * mz);
+    cplx *zt = (cplx *)malloc(sizeof(cplx) * mz);
+    cplx *pt = (cplx *)malloc(sizeof(cplx) * mz);
+    double *J = (double *)malloc(sizeof(double) * 4 * mz * mz);
+    double *rhs = (double *)malloc(sizeof(double) * 2 * mz);
+    double res = INFINITY;
+    for (int n = 0; n < N; ++n)
+        for (int i = 0; i < m; ++i)
+            AS[(size_t)n * m + i] = A[(size_t)n * L + S[i]];
+    for (int i = 0; i < m; ++i) {
+        cplx acc = 0.0;
+        for (int n = 0; n < N; ++n)
+            acc += conj(AS[(size_t)n * m + i]) * g[n];
+        c[i] = acc;
+        for (int j = 0; j < m; ++j) {
+            cplx a2 = 0.0;
+            for (int n = 0; n < N; ++n)
+                a2 += conj(AS[(size_t)n * m + i]) * AS[(size_t)n * m + j];
+            G[(size_t)i * m + j] = a2;
+        }
+    }
+    for (int i = 0; i < m; ++i)
+        if (z[i] == 0.0)
+            goto out;
+    for (int it = 0; it <= max_it; ++it) {
+        restricted_phi(G, c, m, lam, z, phi);
+        res = 0.0;
+        double nphi = 0.0;
+        for (int i = 0; i < m; ++i) {
+            double a = cabs(phi[i]);
+            res = fmax(res, a);
+            nphi += a * a;
+        }
+        if (res <= ftol * lam) {
+            rc = 0;
+            break;
+        }
+        if (it == max_it)
+            break;
+        int n2 = 2 * m;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                double gr = creal(G[(size_t)i * m + j]), gi = cimag(G[(size_t)i * m + j]);
+                J[(size_t)(2 * i) * n2 + 2 * j] = 2.0 * gr;
+                J[(size_t)(2 * i) * n2 + 2 * j + 1] = -2.0 * gi;
+                J[(size_t)(2 * i + 1) * n2 + 2 * j] = 2.0 * gi;
+                J[(size_t)(2 * i + 1) * n2 + 2 * j + 1] = 2.0 * gr;
+            }
+        for (int i = 0; i < m; ++i) {
+            double a = cabs(z[i]);
+            double ur = creal(z[i]) / a, ui = cimag(z[i]) / a;
+            double w = lam / a;
+            J[(size_t)(2 * i) * n2 + 2 * i] += w * (1.0 - ur * ur);
+            J[(size_t)(2 * i) * n2 + 2 * i + 1] += w * (-ur * ui);
+            J[(size_t)(2 * i + 1) * n2 + 2 * i] += w * (-ui * ur);
+            J[(size_t)(2 * i + 1) * n2 + 2 * i + 1] += w * (1.0 - ui * ui);
+            rhs[2 * i] = -creal(phi[i]);
+            rhs[2 * i + 1] = -cimag(phi[i]);
+        }
+        if (solve_real(J, rhs, n2))
+            break;
+        double F0 = restricted_F(AS, N, m, g, lam, z);
+        double t = 1.0;
+        int ok = 0;
+        for (int h = 0; h < 60; ++h, t *= 0.5) {
+            int zero = 0;
+            for (int i = 0; i < m; ++i) {
+                zt[i] = z[i] + t * (rhs[2 * i] + I * rhs[2 * i + 1]);
+                if (zt[i] == 0.0)
+                    zero = 1;
+            }
+            if (zero)
+                continue;
+            double F1 = restricted_F(AS, N, m, g, lam, zt);
+            restricted_phi(G, c, m, lam, zt, pt);
+            double np = 0.0;
+            for (int i = 0; i < m; ++i)
+                np += creal(pt[i]) * creal(pt[i]) + cimag(pt[i]) * cimag(pt[i]);
+            if (F1 < F0 || np < nphi) {
+                ok = 1;
+                break;
+            }
+        }
+        if (!ok)
+            break;
+        for (int i = 0; i < m; ++i)
+            z[i] = zt[i];
+    }
+out:
+    if (res_out)
+        *res_out = res / lam;
+    free(AS); free(G); free(c); free(phi); free(zt); free(pt); free(J); free(rhs);
+    return rc;
+}
+
+/*
+ * Optimality certificate for Eq. 6.  With r = A x - g and z_l = 2 a_l^H r:
+ *   on S = supp(x):   z_l = -lambda x_l/|x_l|       -> on_res = max_S |z_l + lambda x_l/|x_l|| / lambda
+ *   off S:            |z_l| <= lambda               -> off_max = max_{l not in S} |z_l| / lambda
+ * (off_max = 0 when S is everything; on_res = 0 when S is empty.)
+ */
+void orc_kkt(const cplx *A, int N, int L, const cplx *g, double lam, const cplx *x,
+             double *on_res, double *off_max, double *min_abs_on, int *nS)
+{
+    cplx *r = (cplx *)malloc(sizeof(cplx) * (size_t)N);
+    cplx *z = (cplx *)malloc(sizeof(cplx) * (size_t)L);
+    matvec(A, N, L, x, r);
+    for (int n = 0; n < N; ++n)
+        r[n] -= g[n];
+    matvec_h(A, N, L, r, z);
+    double on = 0.0, off = 0.0, mn = INFINITY;
+    int cnt = 0;
+    for (int l = 0; l < L; ++l) {
+        cplx zl = 2.0 * z[l];
+        if (x[l] != 0.0) {
+            double a = cabs(x[l]);
+            on = fmax(on, cabs(zl + lam * x[l] / a) / lam);
+            mn = fmin(mn, a);
+            ++cnt;
+        } else {
+            off = fmax(off, cabs(zl) / lam);
+        }
+    }
+    *on_res = on;
+    *off_max = off;
+    *min_abs_on = cnt ? mn : 0.0;
+    *nS = cnt;
+    free(r);
+    free(z);
+}
+
+/*
+ * Exact minimiser of Eq. 6 for one pixel: coordinate descent, then Newton on
+ * the support CD found (when CD stops, its support is the minimiser's unless
+ * a component sits at a tie), then the certificate.
+ * flags: bit0 CD hit max_sweeps, bit1 Newton did not converge (CD result kept),
+ *        bit2 certificate failed (on_res > 1e-9 or off_max > 1 + 1e-9), bit3 non-finite input.
+ */
+int orc_min(const cplx *A, int N, int L, const cplx *g, double lam, double cd_tol,
+            long max_sweeps, cplx *x, double *on_res, double *off_max, double *min_abs_on,
+            int *nS, long *sweeps)
+{
+    int flags = 0;
+    if (!all_finite(g, N)) {
+        for (int l = 0; l < L; ++l)
+            x[l] = 0.0;
+        *on_res = *off_max = *min_abs_on = 0.0;
+        *nS = 0;
+        if (sweeps)
+            *sweeps = 0;
+        return 8;
+    }
+    if (orc_cd(A, N, L, g, lam, cd_tol, max_sweeps, x, sweeps))
+        flags |= 1;
+    int m = 0;
+    int *S = (int *)malloc(sizeof(int) * (size_t)L);
+    for (int l = 0; l < L; ++l)
+        if (x[l] != 0.0)
+            S[m++] = l;
+    if (m > 0) {
+        cplx *z = (cplx *)malloc(sizeof(cplx) * (size_t)m);
+        for (int i = 0; i < m; ++i)
+            z[i] = x[S[i]];
+        double res;
+        if (orc_newton_polish(A, N, L, g, lam, m, S, z, 50, 1e-13, &res) == 0) {
+            for (int i = 0; i < m; ++i)
+                x[S[i]] = z[i];
+        } else {
+            flags |= 2;
+        }
+        free(z);
+    }
+    free(S);
+    orc_kkt(A, N, L, g, lam, x, on_res, off_max, min_abs_on, nS);
+    if (*on_res > 1e-9 || *off_max > 1.0 + 1e-9)
+        flags |= 4;
+    return flags;
+}
+
+/* ------------------------------------------------------------- batches */
+
+void orc_rbpg_batch(const cplx *A, int N, int L, const cplx *g, int64_t P, const double *lam,
+                    double alpha0, double c_alpha, double tol, int max_iter, int max_bt,
+                    cplx *x, int *iters, int *status)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t p = 0; p < P; ++p)
+        status[p] = orc_rbpg(A, N, L, g + (size_t)p * N, lam[p], alpha0, c_alpha, tol, max_iter,
+                             max_bt, x + (size_t)p * L, iters + p, NULL, NULL, NULL, NULL, NULL);
+}
+
+void orc_min_batch(const cplx *A, int N, int L, const cplx *g, int64_t P, const double *lam,
+                   double cd_tol, long max_sweeps, cplx *x, double *on_res, double *off_max,
+                   double *min_abs_on, int *nS, long *sweeps, int *flags)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t p = 0; p < P; ++p)
+        flags[p] = orc_min(A, N, L, g + (size_t)p * N, lam[p], cd_tol, max_sweeps,
+                           x + (size_t)p * L, on_res + p, off_max + p, min_abs_on + p, nS + p,
+                           sweeps + p);
+}
+
+int orc_num_threads(void)
+{
+    int n = 1;
+#pragma omp parallel
+    {
+#pragma omp single
+        {
+#ifdef _OPENMP
+            extern int omp_get_num_threads(void);
+            n = omp_get_num_threads();
+#endif
+        }
+    }
+    return n;
+}

@@ -1,0 +1,208 @@
+"""Seeded synthetic TomoSAR pixel stacks (inputs only).
+
+This module simulates measurements; it holds none of the solver's arithmetic.
+Both the FP64 CPU oracle and the CUDA path take their inputs from here.
+
+Physical model (Sec. II, Eq. 2 with the motion term d = 0, and Eq. 5): a pixel
+observed at N baselines b_n returns
+
+    g_n = sum_k gamma_k * exp(-j*2*pi*xi_n*s_k) + eps_n,   xi_n = 2*b_n/(wavelength*range)
+
+for K point scatterers at continuous (off-grid) elevations s_k.  The sign of
+the exponent follows the steering-matrix convention A_nl = exp(-j2*pi*xi_n*s_l)
+so that a scatterer at s appears at +s on the elevation grid.
+
+Scatterers have unit amplitude and a uniform phase; eps is circular complex
+Gaussian noise of total variance sigma^2 = 10^(-SNR/10) per acquisition.
+The Rayleigh resolution rho_s = wavelength*range/Delta_b is Eq. 16 and the
+normalised separation kappa = s/rho_s is Eq. 17.
+
+The regularisation weight is not given in the paper (it only says lambda is
+fixed).  The workloads use lambda = 2*sigma_ref*sqrt(N*ln L) with a 10 dB
+reference SNR: the level at which a noise-only pixel returns x = 0 with high
+probability.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = [
+    "StackGeometry",
+    "Stack",
+    "default_lambda",
+    "rayleigh_resolution",
+    "make_geometry",
+    "make_stack",
+    "workload_small",
+    "workload_patch",
+    "workload_diff",
+    "workload_ragged",
+    "dft_geometry",
+]
+
+
+@dataclasses.dataclass
+class StackGeometry:
+    """Acquisition geometry of one stack (what bpdn_make_operator takes)."""
+
+    baselines_m: np.ndarray  # float64 [N]
+    wavelength_m: float
+    range_m: float
+    s_min_m: float
+    s_max_m: float
+    L: int
+
+    @property
+    def N(self) -> int:
+        return int(self.baselines_m.shape[0])
+
+
+@dataclasses.dataclass
+class Stack:
+    """One stack of P pixels sharing a geometry."""
+
+    geom: StackGeometry
+    g: np.ndarray  # complex64 [P, N], pixel-major
+    lam: float  # regularisation weight lambda (Eq. 6)
+    gamma_true: np.ndarray | None = None  # complex64 [P, L], scatterers at their nearest bin
+    n_scat: np.ndarray | None = None  # int8 [P]
+    snr_db: np.ndarray | None = None  # float32 [P]
+    s_true: np.ndarray | None = None  # float64 [P, 2] (nan where absent)
+    seed: int = 0
+
+
+def rayleigh_resolution(geom: StackGeometry) -> float:
+    """rho_s = wavelength * range / Delta_b (Eq. 16), Delta_b = aperture extent."""
+    b = geom.baselines_m
+    return geom.wavelength_m * geom.range_m / float(b.max() - b.min())
+
+
+def default_lambda(N: int, L: int, snr_ref_db: float = 10.0) -> float:
+    """lambda = 2*sigma_ref*sqrt(N ln L) at a reference SNR (the paper fixes no value)."""
+    sigma = math.sqrt(10.0 ** (-snr_ref_db / 10.0))
+    return 2.0 * sigma * math.sqrt(N * math.log(L))
+
+
+def make_geometry(rng: np.random.Generator, N: int, L: int, half_aperture_m: float = 250.0,
+                  half_height_m: float = 100.0, wavelength_m: float = 0.031,
+                  range_m: float = 7.0e5) -> StackGeometry:
+    b = rng.uniform(-half_aperture_m, half_aperture_m, N)
+    return StackGeometry(np.asarray(b, np.float64), wavelength_m, range_m,
+                         -half_height_m, half_height_m, L)
+
+
+def _phasors(geom: StackGeometry, s: np.ndarray) -> np.ndarray:
+    """exp(-j 2 pi xi_n s) for an array of elevations s[...] -> [..., N] (simulation only)."""
+    xi = 2.0 * geom.baselines_m / (geom.wavelength_m * geom.range_m)
+    return np.exp(-2j * np.pi * s[..., None] * xi)
+
+
+def make_stack(geom: StackGeometry, P: int, rng: np.random.Generator, *, lam: float,
+               snr_db_range: tuple[float, float] = (10.0, 10.0),
+               k_probs: tuple[float, float, float] = (0.3, 0.5, 0.2),
+               second_at_kappa: tuple[float, float] | None = None,
+               seed: int = 0) -> Stack:
+    """Simulate P pixels.
+
+    K in {0,1,2} scatterers per pixel with probabilities k_probs.  The first
+    scatterer is uniform over the elevation extent.  The second is either
+    independent and uniform (second_at_kappa=None) or placed at s1 +/- kappa*rho_s with
+    kappa ~ U[second_at_kappa], redrawn until it falls inside the extent.
+    """
+    N, L = geom.N, geom.L
+    lo, hi = geom.s_min_m, geom.s_max_m
+    K = rng.choice(3, size=P, p=np.asarray(k_probs))
+    snr = rng.uniform(snr_db_range[0], snr_db_range[1], P)
+    s1 = rng.uniform(lo, hi, P)
+    ph1 = rng.uniform(0.0, 2.0 * np.pi, P)
+    ph2 = rng.uniform(0.0, 2.0 * np.pi, P)
+    if second_at_kappa is None:
+        s2 = rng.uniform(lo, hi, P)
+    else:
+        rho = rayleigh_resolution(geom)
+        s2 = np.full(P, np.nan)
+        todo = np.arange(P)
+        while todo.size:
+            kap = rng.uniform(second_at_kappa[0], second_at_kappa[1], todo.size)
+            sign = np.where(rng.uniform(0.0, 1.0, todo.size) < 0.5, -1.0, 1.0)
+            cand = s1[todo] + sign * kap * rho
+            ok = (cand >= lo) & (cand <= hi)
+            s2[todo[ok]] = cand[ok]
+            todo = todo[~ok]
+    sigma2 = 10.0 ** (-snr / 10.0)
+    noise = (rng.standard_normal((P, N)) + 1j * rng.standard_normal((P, N))) * np.sqrt(sigma2 / 2.0)[:, None]
+
+    g = noise.astype(np.complex128)
+    a1 = np.exp(1j * ph1)
+    a2 = np.exp(1j * ph2)
+    m1 = K >= 1
+    m2 = K >= 2
+    g[m1] += a1[m1, None] * _phasors(geom, s1[m1])
+    g[m2] += a2[m2, None] * _phasors(geom, s2[m2])
+
+    ds = (hi - lo) / (L - 1) if L > 1 else 1.0
+    gamma = np.zeros((P, L), np.complex64)
+    idx1 = np.clip(np.rint((s1 - lo) / ds), 0, L - 1).astype(np.int64)
+    idx2 = np.clip(np.rint((np.nan_to_num(s2) - lo) / ds), 0, L - 1).astype(np.int64)
+    rows = np.arange(P)
+    gamma[rows[m1], idx1[m1]] += a1[m1].astype(np.complex64)
+    gamma[rows[m2], idx2[m2]] += a2[m2].astype(np.complex64)
+    s_true = np.stack([np.where(m1, s1, np.nan), np.where(m2, s2, np.nan)], axis=1)
+    return Stack(geom, np.ascontiguousarray(g.astype(np.complex64)), float(lam), gamma,
+                 K.astype(np.int8), snr.astype(np.float32), s_true, seed)
+
+
+def workload_small(P: int = 256, seed: int = 1) -> Stack:
+    """One stack: N=25, b~U[-250,250] m, 0.031 m, 700 km, L=200 on [-100,100] m, 10 dB."""
+    rng = np.random.default_rng(seed)
+    geom = make_geometry(rng, 25, 200, 250.0, 100.0)
+    return make_stack(geom, P, rng, lam=default_lambda(25, 200), snr_db_range=(10.0, 10.0), seed=seed)
+
+
+def workload_patch(P: int = 1 << 20, seed: int = 2) -> Stack:
+    """Full patch: N=25, L=400 on [-200,200] m, second scatterer at kappa*rho_s with
+    kappa~U[0.5,2], per-pixel SNR~U[0,20] dB."""
+    rng = np.random.default_rng(seed)
+    geom = make_geometry(rng, 25, 400, 250.0, 200.0)
+    return make_stack(geom, P, rng, lam=default_lambda(25, 400), snr_db_range=(0.0, 20.0),
+                      second_at_kappa=(0.5, 2.0), seed=seed)
+
+
+def workload_diff(P: int = 1 << 18, seed: int = 5) -> Stack:
+    """Differentiation workload: N=25, L=400 on [-200,200] m, same scatterer law as the patch."""
+    rng = np.random.default_rng(seed)
+    geom = make_geometry(rng, 25, 400, 250.0, 200.0)
+    return make_stack(geom, P, rng, lam=default_lambda(25, 400), snr_db_range=(0.0, 20.0),
+                      second_at_kappa=(0.5, 2.0), seed=seed)
+
+
+def workload_ragged(n_stacks: int = 64, seed: int = 3, p_log2: tuple[int, int] = (12, 16),
+                    scale_pixels: float = 1.0) -> list[Stack]:
+    """Ragged batch: per stack N~U{10..60}, L~U{100..600}, aperture B~U[200,600] m,
+    elevation half-width h~U[50,300] m, P=2^U{12..16} (times scale_pixels)."""
+    out = []
+    for s in range(n_stacks):
+        rng = np.random.default_rng(1000 * seed + s)
+        N = int(rng.integers(10, 61))
+        L = int(rng.integers(100, 601))
+        B = float(rng.uniform(200.0, 600.0))
+        h = float(rng.uniform(50.0, 300.0))
+        P = max(1, int(round((1 << int(rng.integers(p_log2[0], p_log2[1] + 1))) * scale_pixels)))
+        geom = make_geometry(rng, N, L, B / 2.0, h)
+        out.append(make_stack(geom, P, rng, lam=default_lambda(N, L), snr_db_range=(0.0, 20.0),
+                              second_at_kappa=(0.5, 2.0), seed=1000 * seed + s))
+    return out
+
+
+def dft_geometry(N: int, ds: float = 1.0, wavelength_m: float = 0.031,
+                 range_m: float = 7.0e5) -> StackGeometry:
+    """Geometry whose steering matrix is the N-point DFT (orthogonal columns).
+
+    Grid s_l = l*ds (l = 0..N-1) and xi_n = n/(N*ds), i.e. b_n = xi_n*wavelength*range/2.
+    """
+    xi = np.arange(N, dtype=np.float64) / (N * ds)
+    b = xi * wavelength_m * range_m / 2.0
+    return StackGeometry(b, wavelength_m, range_m, 0.0, (N - 1) * ds, N)

@@ -1,0 +1,328 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test names the passage it pins.  The oracle is checked against hand-derived
+values, closed forms, brute force and invariances -- never against itself.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.bruteforce import bruteforce_min
+from paper_1805_01759_gb300 import synth
+
+WL, RG = 0.031, 7.0e5
+
+
+def _geom(b, s_min, s_max, L, wl=WL, rg=RG):
+    return synth.StackGeometry(np.asarray(b, np.float64), wl, rg, s_min, s_max, L)
+
+
+# ------------------------------------------------------------------ Eq. 5
+
+def test_grid_includes_both_ends():
+    """Eq. 5: gamma sampled uniformly at s_l on the elevation extent (both ends kept)."""
+    s = oracle.grid(-100.0, 100.0, 201)
+    assert s[0] == -100.0 and s[-1] == 100.0
+    np.testing.assert_allclose(np.diff(s), 1.0, rtol=0, atol=1e-12)
+    assert oracle.grid(3.0, 7.0, 1)[0] == 3.0
+
+
+def test_operator_hand_values():
+    """Eq. 5 with xi_n = 2 b_n / (wavelength r) (Sec. II): a baseline with xi = 0.01/m gives
+    A = exp(-j 2 pi 0.01 s): s=25 -> -j, s=50 -> -1, s=-25 -> +j, b=0 -> 1."""
+    b1 = 0.01 * WL * RG / 2.0  # xi = 0.01 per metre
+    geom = _geom([0.0, b1], -100.0, 100.0, 201)  # s_l = -100 + l
+    A = oracle.operator(geom)
+    i = lambda s: int(s + 100)
+    np.testing.assert_allclose(A[0], 1.0, atol=1e-15)
+    np.testing.assert_allclose(A[1, i(25)], -1j, atol=1e-13)
+    np.testing.assert_allclose(A[1, i(50)], -1.0, atol=1e-13)
+    np.testing.assert_allclose(A[1, i(-25)], 1j, atol=1e-13)
+    np.testing.assert_allclose(A[1, i(0)], 1.0, atol=1e-15)
+    np.testing.assert_allclose(np.abs(A), 1.0, atol=1e-14)
+
+
+def test_gram_toeplitz_matches_direct_product():
+    """On the uniform grid of Eq. 5, (A^H A)_{lm} depends on l-m only: h(l-m)."""
+    st = synth.workload_small(P=1)
+    A = oracle.operator(st.geom)
+    h = oracle.gram_toeplitz(st.geom)
+    G = A.conj().T @ A  # numpy product, independent of the oracle's h
+    L = st.geom.L
+    l, m = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    np.testing.assert_allclose(h[l - m + L - 1], G, atol=1e-10)
+    np.testing.assert_allclose(h[L - 1], st.geom.N, atol=1e-12)
+
+
+def test_aah_dirichlet_closed_form():
+    """(A A^H)_{nm} = sum_l exp(-j2pi(xi_n - xi_m)(s0 + l ds)), a geometric series."""
+    st = synth.workload_small(P=1)
+    geom = st.geom
+    A = oracle.operator(geom)
+    M = oracle.aah(A)
+    x = 2.0 * geom.baselines_m / (geom.wavelength_m * geom.range_m)
+    L = geom.L
+    ds = (geom.s_max_m - geom.s_min_m) / (L - 1)
+    dxi = x[:, None] - x[None, :]
+    w = np.exp(-2j * np.pi * dxi * ds)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        geo = np.where(np.abs(dxi) > 0, (1 - w ** L) / (1 - w), L)
+    ref = np.exp(-2j * np.pi * dxi * geom.s_min_m) * geo
+    np.testing.assert_allclose(M, ref, atol=1e-9)
+
+
+def test_lipschitz_closed_forms():
+    """L_f = 2 lambda_max(A^H A): DFT geometry has A^H A = N I (L_f = 2N); one acquisition
+    (N = 1) has A A^H = L (L_f = 2L)."""
+    for N in (4, 16, 25):
+        A = oracle.operator(synth.dft_geometry(N))
+        np.testing.assert_allclose(A.conj().T @ A, N * np.eye(N), atol=1e-10)
+        assert abs(oracle.lipschitz(A) - 2 * N) < 1e-9
+    A1 = oracle.operator(_geom([37.0], -50.0, 50.0, 77))
+    assert abs(oracle.lipschitz(A1) - 2 * 77) < 1e-9
+
+
+# ------------------------------------------------------------------ Eq. 10
+
+def test_soft_threshold_closed_form():
+    """Eq. 10 for complex values: S_tau(v) = v (1 - tau/|v|) if |v| > tau else 0.
+    On the real line it gives Eq. 10's three cases (x - a, 0, x + a)."""
+    out = oracle.soft(np.array([3 + 4j, 3 + 4j, 3 + 4j, 0j, 2.0, -2.0, 0.5, -0.5]), 1.0)
+    np.testing.assert_allclose(out[0], 2.4 + 3.2j, atol=1e-15)
+    np.testing.assert_allclose(out[4:], [1.0, -1.0, 0.0, 0.0], atol=1e-15)
+    assert oracle.soft(3 + 4j, 5.0)[0] == 0  # |v| == tau -> exactly zero
+    assert oracle.soft(3 + 4j, 4.999)[0] != 0
+    assert oracle.soft(0j, 0.1)[0] == 0
+    np.testing.assert_allclose(oracle.soft(1j * 3, 1.0)[0], 2j, atol=1e-15)
+
+
+# ------------------------------------------------------------- Algorithm 1
+
+def test_first_iteration_closed_form():
+    """Algorithm 1 at k=1 from x^0 = 0: y = 0, grad f(0) = -2 A^H g, so
+    xbar = S_{alpha lambda}(2 alpha A^H g) with the alpha left by backtracking (Eq. 15);
+    it is accepted iff F(xbar) <= F(0)."""
+    st = synth.workload_small(P=8)
+    A = oracle.operator(st.geom)
+    a0 = oracle.default_alpha0(A)
+    assert abs(a0 - 1.0 / (2 * st.geom.N)) < 1e-15
+    for p in range(8):
+        g = st.g[p].astype(np.complex128)
+        r = oracle.rbpg(A, g, st.lam, max_iter=1, trace=True)
+        alpha = r["alpha"][0]
+        assert alpha == a0 * 0.5 ** r["n_bt"][0]
+        v = 2.0 * alpha * (A.conj().T @ g)
+        a = np.abs(v)
+        xbar = np.where(a > alpha * st.lam, v * (1 - alpha * st.lam / np.maximum(a, 1e-300)), 0)
+        F0 = float(np.vdot(g, g).real)
+        Fb = float(np.vdot(A @ xbar - g, A @ xbar - g).real + st.lam * np.abs(xbar).sum())
+        np.testing.assert_allclose(r["F"][0], Fb, rtol=1e-12)
+        expect = xbar if Fb <= F0 else np.zeros_like(xbar)
+        np.testing.assert_allclose(r["x"], expect, atol=1e-12)
+        # Eq. 15 with base point y = 0 holds for the alpha that was kept
+        d = xbar
+        assert np.vdot(A @ d, A @ d).real <= np.vdot(d, d).real / (2 * alpha) * (1 + 1e-12)
+
+
+def test_momentum_weight_second_and_third_iteration():
+    """theta_k = 2/(k+1) gives y^{k} = x^k + (k-2)/(k+1) (x^k - x^{k-1}) (Eqs. 11-12):
+    beta = 0 at k=2 and 1/4 at k=3.  Re-run iteration 3 by hand from the oracle's
+    x^1, x^2 and alpha and compare."""
+    st = synth.workload_small(P=16)
+    A = oracle.operator(st.geom)
+    lam = st.lam
+    checked = 0
+    for p in range(16):
+        g = st.g[p].astype(np.complex128)
+        r1 = oracle.rbpg(A, g, lam, max_iter=1, tol=0.0, trace=True)
+        r2 = oracle.rbpg(A, g, lam, max_iter=2, tol=0.0, trace=True)
+        r3 = oracle.rbpg(A, g, lam, max_iter=3, tol=0.0, trace=True)
+        if r3["iters"] < 3 or not (r2["accepted"][1] and r1["accepted"][0]):
+            continue
+        if r3["n_bt"][2] != 0:
+            continue
+        x1, x2 = r1["x"], r2["x"]
+        y = x2 + 0.25 * (x2 - x1)
+        alpha = r3["alpha"][2]
+        v = y - alpha * 2.0 * (A.conj().T @ (A @ y - g))
+        xb = oracle.soft(v, alpha * lam)
+        F2 = r2["F"][1]
+        Fb = float(np.vdot(A @ xb - g, A @ xb - g).real + lam * np.abs(xb).sum())
+        expect = xb if Fb <= F2 else x2
+        np.testing.assert_allclose(r3["x"], expect, atol=1e-11)
+        checked += 1
+    assert checked >= 4
+
+
+def test_orthogonal_columns_closed_form():
+    """DFT geometry (A^H A = N I): x* = S_{lambda/2}(A^H g) / N, reached by Algorithm 1
+    in one step (alpha_0 = 1/(2N) = 1/L_f) and by the exact minimiser."""
+    rng = np.random.default_rng(7)
+    N = 16
+    A = oracle.operator(synth.dft_geometry(N))
+    for _ in range(5):
+        g = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        lam = 0.5 * np.max(np.abs(2 * A.conj().T @ g))
+        c = A.conj().T @ g
+        a = np.abs(c)
+        xs = np.where(a > lam / 2, c * (1 - (lam / 2) / a), 0) / N
+        r = oracle.minimise(A, g, lam)
+        np.testing.assert_allclose(r["x"], xs, atol=1e-12)
+        ra = oracle.rbpg(A, g, lam, tol=1e-12, max_iter=50)
+        np.testing.assert_allclose(ra["x"], xs, atol=1e-12)
+        assert ra["iters"] <= 3
+
+
+def test_single_column_closed_form():
+    """L = 1: x* = S_{lambda/2}(a^H g) / ||a||^2."""
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        N = 7
+        a = np.exp(-2j * np.pi * rng.uniform(0, 1, N))
+        A = a[:, None]
+        g = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        lam = rng.uniform(0.1, 2.0) * abs(a.conj() @ g)
+        c = a.conj() @ g
+        xs = (c * max(0.0, 1 - (lam / 2) / abs(c))) / N
+        r = oracle.minimise(A, g, lam)
+        np.testing.assert_allclose(r["x"][0], xs, atol=1e-13)
+        ra = oracle.rbpg(A, g, lam, tol=1e-13, max_iter=2000)
+        np.testing.assert_allclose(ra["x"][0], xs, atol=1e-12)
+
+
+def test_zero_solution():
+    """lambda >= 2 ||A^H g||_inf  =>  x* = 0; Algorithm 1 returns 0 at k = 1."""
+    st = synth.workload_small(P=4)
+    A = oracle.operator(st.geom)
+    for p in range(4):
+        g = st.g[p].astype(np.complex128)
+        lam = 2.0 * np.max(np.abs(A.conj().T @ g)) * 1.0001
+        r = oracle.minimise(A, g, lam)
+        assert np.all(r["x"] == 0)
+        ra = oracle.rbpg(A, g, lam)
+        assert np.all(ra["x"] == 0) and ra["iters"] == 1
+        assert ra["status"] & oracle.STATUS_ZERO_SOLUTION
+        assert not ra["status"] & oracle.STATUS_NOT_CONVERGED
+
+
+def test_nonfinite_input():
+    st = synth.workload_small(P=1)
+    A = oracle.operator(st.geom)
+    g = st.g[0].astype(np.complex128)
+    g[3] = np.nan
+    ra = oracle.rbpg(A, g, st.lam)
+    assert ra["status"] & oracle.STATUS_NONFINITE and np.all(ra["x"] == 0) and ra["iters"] == 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bruteforce_tiny(seed):
+    """N <= 4, L <= 8: enumerate supports; the minimiser found matches the exact
+    minimiser (CD + Newton) and the end point of Algorithm 1."""
+    rng = np.random.default_rng(100 + seed)
+    N = int(rng.integers(2, 5))
+    L = int(rng.integers(3, 9))
+    b = rng.uniform(-250, 250, N)
+    geom = _geom(b, -60.0, 60.0, L)
+    A = oracle.operator(geom)
+    g = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    lam = rng.uniform(0.2, 0.8) * np.max(np.abs(2 * A.conj().T @ g))
+    xb, Fb = bruteforce_min(A, g, lam)
+    r = oracle.minimise(A, g, lam)
+    np.testing.assert_allclose(r["x"], xb, atol=1e-9)
+    assert np.array_equal(r["x"] != 0, xb != 0)
+    ra = oracle.rbpg(A, g, lam, tol=1e-13, max_iter=100000)
+    np.testing.assert_allclose(ra["x"], xb, atol=1e-5 * max(1.0, np.abs(xb).max()))
+    assert oracle.objective(A, g, lam, ra["x"]) >= Fb - 1e-9
+
+
+def test_certificate_on_workload():
+    """Eq. 6 optimality at every oracle output of the small workload: on the support
+    2 a_l^H (A x - g) = -lambda x_l/|x_l|, off it |2 a_l^H (A x - g)| <= lambda."""
+    st = synth.workload_small(P=64)
+    A = oracle.operator(st.geom)
+    r = oracle.minimise_batch(A, st.g, st.lam)
+    assert np.all(r["on_res"] <= 1e-9)
+    assert np.all(r["off_max"] <= 1.0 + 1e-9)
+    # and the certificate really detects a non-minimiser
+    x = r["x"][np.argmax(r["nS"])].copy()
+    x[np.nonzero(x)[0][0]] *= 1.01
+    on, off, _, _ = oracle.kkt(A, st.g[np.argmax(r["nS"])], st.lam, x)
+    assert on > 1e-4
+
+
+def test_rbpg_and_cd_agree_well_conditioned():
+    """Two unrelated algorithms, one unique minimiser: on a coarse grid (columns far
+    from coherent) Algorithm 1 run to a tight tolerance meets coordinate descent."""
+    rng = np.random.default_rng(11)
+    geom = synth.make_geometry(rng, 25, 9, 250.0, 100.0)  # 25 m bins vs ~45 m resolution
+    A = oracle.operator(geom)
+    for _ in range(4):
+        g = A[:, [2, 6]] @ (rng.standard_normal(2) + 1j * rng.standard_normal(2))
+        g = g + 0.1 * (rng.standard_normal(25) + 1j * rng.standard_normal(25))
+        lam = 0.2 * np.max(np.abs(2 * A.conj().T @ g))
+        r = oracle.minimise(A, g, lam)
+        ra = oracle.rbpg(A, g, lam, tol=1e-12, max_iter=50000)
+        np.testing.assert_allclose(ra["x"], r["x"], atol=1e-7 * np.abs(r["x"]).max())
+
+
+def test_invariances():
+    """Global phase, scale (g, lambda) -> (c g, |c| lambda), row permutation and grid
+    shift (g -> D g with D = diag(exp(-j2pi xi_n s0))) leave the minimiser's
+    structure unchanged (Eq. 6)."""
+    st = synth.workload_small(P=6)
+    geom = st.geom
+    A = oracle.operator(geom)
+    rng = np.random.default_rng(5)
+    for p in range(6):
+        g = st.g[p].astype(np.complex128)
+        lam = st.lam
+        x0 = oracle.minimise(A, g, lam)["x"]
+        ph = np.exp(1j * 0.7)
+        np.testing.assert_allclose(oracle.minimise(A, ph * g, lam)["x"], ph * x0, atol=1e-10)
+        c = 2.5 * np.exp(-1j * 1.1)
+        np.testing.assert_allclose(oracle.minimise(A, c * g, abs(c) * lam)["x"], c * x0,
+                                   atol=1e-9)
+        perm = rng.permutation(geom.N)
+        np.testing.assert_allclose(oracle.minimise(A[perm], g[perm], lam)["x"], x0, atol=1e-10)
+        s0 = 17.0
+        gs = geom.baselines_m
+        geom2 = _geom(gs, geom.s_min_m + s0, geom.s_max_m + s0, geom.L)
+        xi = 2 * gs / (WL * RG)
+        g2 = np.exp(-2j * np.pi * xi * s0) * g
+        np.testing.assert_allclose(oracle.minimise(oracle.operator(geom2), g2, lam)["x"], x0,
+                                   atol=1e-9)
+
+
+def test_monotone_objective_and_step():
+    """Algorithm 1's accept test keeps F(x^k) non-increasing; backtracking only shrinks
+    alpha (Eq. 15), and every kept alpha satisfies it."""
+    st = synth.workload_small(P=8)
+    A = oracle.operator(st.geom)
+    for p in range(8):
+        r = oracle.rbpg(A, st.g[p], st.lam, max_iter=300, trace=True)
+        F_acc = []
+        Fx = float(np.vdot(st.g[p], st.g[p]).real)
+        for k in range(r["iters"]):
+            if r["accepted"][k]:
+                assert r["F"][k] <= Fx
+                Fx = r["F"][k]
+            F_acc.append(Fx)
+        assert np.all(np.diff(F_acc) <= 0)
+        assert np.all(np.diff(r["alpha"]) <= 0)
+
+
+def test_newton_polish_one_component_closed_form():
+    """|S| = 1: the restricted optimality system has x = u (|a^H g| - lambda/2)/N,
+    u the phase of a^H g."""
+    st = synth.workload_small(P=1)
+    A = oracle.operator(st.geom)
+    g = st.g[0].astype(np.complex128)
+    l = 57
+    c = A[:, l].conj() @ g
+    lam = abs(c)  # < 2|c|, so the one-column solution is nonzero
+    expect = (c / abs(c)) * (abs(c) - lam / 2) / st.geom.N
+    z, rc, res = oracle.newton_polish(A, g, lam, [l], [c / st.geom.N])
+    assert rc == 0
+    np.testing.assert_allclose(z[0], expect, atol=1e-13)

@@ -1,0 +1,67 @@
+"""Planted mistakes in the oracle (CPU only): each plausible slip in the C source --
+a flipped sign, a dropped factor, a shifted index, a missing conjugate -- must make
+at least one of the oracle's pins fail.  The mutant is compiled from a patched copy
+of the C file into a temporary library; the oracle under test is left untouched."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import tests.test_oracle as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "bpdn_oracle.c")
+
+MUTANTS = {
+    "operator_sign": ("cexp(-2.0 * ORC_PI * I * xi[n] * s[l])", "cexp(2.0 * ORC_PI * I * xi[n] * s[l])"),
+    "grid_spacing": ("(double)l * (s_max - s_min) / (double)(L - 1)", "(double)l * (s_max - s_min) / (double)L"),
+    "xi_factor": ("xi[n] = 2.0 * b[n] / (wavelength * range);", "xi[n] = b[n] / (wavelength * range);"),
+    "soft_half": ("return v * (1.0 - tau / a);", "return v * (1.0 - 0.5 * tau / a);"),
+    "grad_factor": ("grad[l] *= 2.0;", "grad[l] *= 1.0;"),
+    "adjoint_no_conj": ("acc += conj(A[(size_t)n * L + l]) * r[n];", "acc += A[(size_t)n * L + l] * r[n];"),
+    "momentum_index": ("double beta = (double)(k - 2) / (double)(k + 1);", "double beta = (double)(k - 1) / (double)(k + 2);"),
+    "accept_reversed": ("int accepted = (Fb <= Fx);", "int accepted = (Fb >= Fx);"),
+    "linesearch_factor": ("double rhs = dd / (2.0 * alpha);", "double rhs = dd / alpha;"),
+    "cd_threshold": ("cplx nw = orc_soft(vv, 0.5 * lam) / Gll;", "cplx nw = orc_soft(vv, lam) / Gll;"),
+    "newton_residual_sign": ("phi[i] = 2.0 * acc + lam * z[i] / cabs(z[i]);", "phi[i] = 2.0 * acc - lam * z[i] / cabs(z[i]);"),
+    "kkt_factor": ("cplx zl = 2.0 * z[l];", "cplx zl = z[l];"),
+}
+
+PINS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_")]
+
+
+def _build(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / f"lib{name}.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", str(so),
+                    str(path), "-lm"], check=True)
+    return oracle._configure(ctypes.CDLL(str(so)))
+
+
+def _run_pin(fn):
+    import inspect
+    params = inspect.signature(fn).parameters
+    if "seed" in params:
+        for seed in range(6):
+            fn(seed)
+    else:
+        fn()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, monkeypatch, name):
+    old, new = MUTANTS[name]
+    lib = _build(tmp_path, name, old, new)
+    monkeypatch.setattr(oracle, "_lib", lib)
+    caught = []
+    for fn in PINS:
+        try:
+            _run_pin(fn)
+        except Exception:  # noqa: BLE001 - any failure of a pin counts
+            caught.append(fn.__name__)
+            break
+    assert caught, f"mutant {name} passed every pin"
