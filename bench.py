@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Throughput of the batched BPDN hot path on GB300 (pixels/s at 1e-4 vs the FP64 oracle).
+
+Workload: one stack, N=25 acquisitions (baselines U[-250,250] m), wavelength 0.031 m,
+range 700 km, elevation grid L=400 on [-200,200] m, P=2^20 pixels per GPU, K in
+{0,1,2} scatterers (second at kappa*rho_s, kappa~U[0.5,2]), SNR~U[0,20] dB, seeded
+synthetic data.  One step = the whole hot path over the batch: Algorithm 1 on every
+pixel (iteration kernel) followed by the FP64 refit and certificate (refit kernel).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own 2^20 pixels
+of the same stack (weak scaling, no collective on the data path; a barrier and a
+max-reduction of the timings only).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pixels/s to 1e-4 rel err vs FP64 oracle: plain FP32 vs BF16+FP64-refit"
+UNIT = "pixels/s"
+N_ACQ, L_GRID = 25, 400
+FP32_LANES_PER_SM = 128
+
+
+# ------------------------------------------------------------ distributed helpers
+
+def dist_env() -> tuple[int, int, int]:
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def shard_part(rank: int) -> int:
+    """Pixel set of a rank: rank 0 takes the base draw, rank r the r-th extra draw."""
+    return rank
+
+
+def reduce_max(value: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(device=None) -> None:
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [r[0] for r in rows]
+        load = [r for r in rows if r[2] > 200.0] or rows
+        out["sm_mhz"] = statistics.median(r[0] for r in load)
+        out["sm_max_mhz"] = max(r[1] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = set()
+        for r in rows:
+            for n, v in zip(names, r[3]):
+                if v.lower().startswith("active"):
+                    seen.add(n)
+        out["reasons"] = sorted(seen)
+        out["samples"] = len(sm)
+        out["power_w_max"] = max(r[2] for r in rows)
+        return out
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args) -> None:
+    """The FP64 CPU oracle (Algorithm 1 as the paper states it) on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1805_01759_gb300 import synth
+    sample = args.ref_sample
+    st = synth.workload_patch(P=sample, seed=2)
+    A = oracle.operator(st.geom)
+    oracle.rbpg_batch(A, st.g[:32], st.lam)  # load + warm the library
+    times = []
+    for _ in range(max(1, args.warmup)):
+        oracle.rbpg_batch(A, st.g[:64], st.lam)
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        oracle.rbpg_batch(A, st.g, st.lam, tol=1e-6, max_iter=500)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    value = sample / t
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"one stack N={N_ACQ}, L={L_GRID} on [-200,200] m; "
+                               f"bounded sample of {sample} pixels of the 2^20-pixel patch",
+                   "P_sample": sample, "N": N_ACQ, "L": L_GRID},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} pixels of the patch, Algorithm 1 in FP64, "
+                                   f"tol 1e-6, max 500 iterations, OpenMP over pixels"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def _kernel_hash() -> str:
+    src = os.path.join(ROOT, "paper_1805_01759_gb300", "csrc", "rbpg.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def _traffic_per_launch(pixel_iters: float) -> float | None:
+    """DRAM bytes of one iteration-kernel launch from the committed ncu summary, scaled
+    by the pixel-iterations it processed -- only while the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "rbpg_fp32_counters.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+    except ValueError:
+        return None
+    if rec.get("kernel_sha256_16") != _kernel_hash():
+        return None
+    return float(rec["dram_bytes_per_pixel_iter"]) * pixel_iters
+
+
+def cpu_baseline_leg(sample: int) -> dict:
+    import oracle
+    from paper_1805_01759_gb300 import synth
+    st = synth.workload_patch(P=sample, seed=2)
+    A = oracle.operator(st.geom)
+    oracle.rbpg_batch(A, st.g[:32], st.lam)
+    t0 = time.perf_counter()
+    oracle.rbpg_batch(A, st.g, st.lam, tol=1e-6, max_iter=500)
+    t = time.perf_counter() - t0
+    return {"value": sample / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{sample} pixels of the patch: Algorithm 1 in FP64 (tol 1e-6, max 500 "
+                      f"iterations), OpenMP over pixels, {t:.1f} s"}
+
+
+def accuracy_sample(st, x, status, n_sample: int, seed: int = 20) -> dict:
+    """Exact minimiser (oracle) on a seeded sample of pixels vs the GPU result."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(st.g.shape[0], size=n_sample, replace=False))
+    A = oracle.operator(st.geom)
+    ref = oracle.minimise_batch(A, st.g[idx], st.lam)
+    xs = x[idx].astype(np.complex128)
+    cert = (status[idx] & 64) != 0
+    degen = (ref["margin"] < 1e-6) | ((ref["nS"] > 0) & (ref["min_abs_on"] < 1e-6 * np.abs(ref["x"]).max(1)))
+    nr = np.linalg.norm(ref["x"], axis=1)
+    err = np.linalg.norm(xs - ref["x"], axis=1) / np.where(nr > 0, nr, 1.0)
+    supp_ok = np.all((xs != 0) == (ref["x"] != 0), axis=1) | degen
+    ok = cert & (err <= 1e-4) & supp_ok
+    return {"n": int(n_sample), "certified": int(cert.sum()), "ok": int(ok.sum()),
+            "cert_and_wrong": int((cert & ~ok).sum()), "max_err_certified": float(err[cert].max()) if cert.any() else None,
+            "degenerate": int(degen.sum())}
+
+
+def run_ours(args) -> None:
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1 and not dist.is_initialized():
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1805_01759_gb300 import _lib, api, synth
+    lib = _lib.load()
+
+    P = args.pixels
+    st = synth.workload_patch(P=P, seed=2, part=shard_part(rank))
+    op = api.Operator.from_geometry(st.geom)
+    N, L = op.N, op.L
+    stream = torch.cuda.current_stream(dev)
+    g_dev = torch.from_numpy(st.g).to(dev)
+    lam_t = torch.tensor([st.lam], dtype=torch.float32, device=dev)
+    opt_solve = _lib.default_options(refit=0, precision=0)
+    opt_refit = _lib.default_options()
+    x = torch.empty((P, L), dtype=torch.complex64, device=dev)
+    status = torch.empty(P, dtype=torch.int32, device=dev)
+    iters = torch.empty(P, dtype=torch.int32, device=dev)
+    nbt = torch.empty(P, dtype=torch.int32, device=dev)
+    nsupp = torch.empty(P, dtype=torch.int32, device=dev)
+    support = torch.empty((P, opt_refit.s_max), dtype=torch.int32, device=dev)
+    ws_bytes = lib.bpdn_solve_workspace_bytes(op.handle, P, ctypes.byref(opt_solve))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    s_ptr = stream.cuda_stream
+
+    def step():
+        _lib.check(lib.bpdn_solve(op.handle, g_dev.data_ptr(), P, lam_t.data_ptr(), 0,
+                                  ctypes.byref(opt_solve), x.data_ptr(), None, nsupp.data_ptr(),
+                                  status.data_ptr(), iters.data_ptr(), nbt.data_ptr(),
+                                  ws.data_ptr(), ws_bytes, s_ptr))
+        ev_mid = torch.cuda.Event(enable_timing=True)
+        ev_mid.record(stream)
+        _lib.check(lib.bpdn_refit(op.handle, g_dev.data_ptr(), P, lam_t.data_ptr(), 0,
+                                  ctypes.byref(opt_refit), x.data_ptr(), x.data_ptr(),
+                                  support.data_ptr(), nsupp.data_ptr(), status.data_ptr(), s_ptr))
+        return ev_mid
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, inputs resident in HBM (and larger than L2)
+    launches = 0
+    with ClockSampler(dev.index) as clk:
+        barrier(dev)
+        torch.cuda.synchronize()
+        evs = []
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            em = step()
+            e1 = torch.cuda.Event(enable_timing=True)
+            e1.record(stream)
+            evs.append((e0, em, e1))
+            launches += 2
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier(dev)
+    total_ms = t_start.elapsed_time(t_end)
+    rbpg_ms = [a.elapsed_time(b) for a, b, _ in evs]
+    refit_ms = [b.elapsed_time(c) for _, b, c in evs]
+    ms_step = reduce_max(total_ms / args.steps, dev)
+
+    it_np = iters.cpu().numpy()
+    st_np = status.cpu().numpy()
+    nbt_np = nbt.cpu().numpy()
+    x_np = x.cpu().numpy()
+    pixel_iters = float(it_np.astype(np.int64).sum())
+    certified = int(((st_np & 64) != 0).sum())
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    g_host = torch.from_numpy(st.g).pin_memory()
+    x_host = torch.empty((P, L), dtype=torch.complex64).pin_memory()
+    st_host = torch.empty(P, dtype=torch.int32).pin_memory()
+    h2d = g_host.numel() * g_host.element_size()
+    d2h = x_host.numel() * x_host.element_size() + st_host.numel() * 4
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    barrier(dev)
+    e_a = torch.cuda.Event(enable_timing=True)
+    e_b = torch.cuda.Event(enable_timing=True)
+    e_a.record(stream)
+    for _ in range(e2e_steps):
+        g_dev.copy_(g_host, non_blocking=True)
+        step()
+        launches += 2
+        x_host.copy_(x, non_blocking=True)
+        st_host.copy_(status, non_blocking=True)
+    e_b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(e_a.elapsed_time(e_b) / e2e_steps, dev)
+
+    # ---- accuracy gate on a seeded sample (rank 0's pixels), and the CPU baseline
+    acc = None
+    cpu = None
+    if rank == 0:
+        acc = accuracy_sample(st, x_np, st_np, args.sample)
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline_leg(args.cpu_sample)
+    good_frac = (certified / P) * (acc["ok"] / max(acc["certified"], 1) if acc else 1.0)
+    pixels_total = P * world
+    value = pixels_total * good_frac / (ms_step / 1e3)
+    e2e_value = pixels_total * good_frac / (e2e_ms / 1e3)
+
+    clocks = clk.summary()
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    # algorithmic work of the iteration kernel: the dense gradient contraction
+    # 2 A^H (A y - g) of every pixel-iteration, 8 N L real flops (complex N x L product)
+    rbpg_avg_s = statistics.mean(rbpg_ms) / 1e3
+    flops_launch = pixel_iters * 8.0 * N * L
+    achieved = flops_launch / rbpg_avg_s / 1e12
+    traffic = _traffic_per_launch(pixel_iters)
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": f"one stack N={N}, L={L} on [-200,200] m, P=2^{int(np.log2(P))} pixels per GPU, "
+                        "K in {0,1,2} (second at kappa*rho_s, kappa~U[0.5,2]), SNR~U[0,20] dB",
+            "path": "plain FP32 Algorithm 1 + FP64 refit/certificate",
+            "P_per_gpu": P, "N": N, "L": L, "lambda": st.lam, "max_iter": 500, "tol": 1e-6,
+            "l2": "inputs larger than L2 (g 210 MB, x 3.4 GB per GPU); no flush",
+            "parallelism": f"pixels sharded over {world} GPU(s), no collective",
+        },
+        "accuracy": {"certified_frac": certified / P, "sample": acc, "good_frac": good_frac,
+                     "pixels_per_s_all": pixels_total / (ms_step / 1e3),
+                     "mean_iters": float(it_np.mean()), "frac_max_iter": float((it_np >= 500).mean()),
+                     "mean_step_cuts": float(nbt_np.mean())},
+        "kernels_ms": {"rbpg_fp32": statistics.mean(rbpg_ms), "refit_fp64": statistics.mean(refit_ms)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": traffic,
+                     "kernel": "k_rbpg_fp32",
+                     "note": f"FP32 FMA peak = {n_sm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
+                             "(derived from unit counts and the max SM clock); algorithmic flops = "
+                             "8 N L per pixel-iteration (dense A^H r)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
+                   "reasons": clocks.get("reasons"), "power_w_max": clocks.get("power_w_max")},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None) -> None:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--pixels", type=int, default=1 << 20, help="pixels per GPU (workload: 2^20)")
+    ap.add_argument("--sample", type=int, default=256, help="pixels checked against the oracle")
+    ap.add_argument("--cpu-sample", type=int, default=2048, help="pixels of the CPU baseline leg")
+    ap.add_argument("--ref-sample", type=int, default=1024, help="pixels per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * bpdn.h -- C ABI of libbpdn: batched complex basis pursuit denoising on GB300 (sm_103a).
+ *
+ * Each pixel of a SAR stack solves (Eq. 1 / Eq. 6, Sec. I and III-A)
+ *
+ *     x* = argmin_x  ||A x - g||_2^2 + lambda * sum_l |x_l|,    x in C^L, g in C^N,
+ *
+ * with the steering matrix of the discrete tomographic model (Eq. 5, Sec. II)
+ *
+ *     A_nl = exp(-j 2 pi xi_n s_l),   xi_n = 2 b_n / (wavelength * range),
+ *     s_l  = s_min + l (s_max - s_min)/(L - 1),  l = 0..L-1.
+ *
+ * The solver is Algorithm 1 (randomized blockwise proximal gradient with Nesterov
+ * extrapolation, Eqs. 11-13, backtracking, Eq. 15, and the monotone accept step),
+ * one block per pixel, followed by an optional FP64 refit on the detected support.
+ *
+ * Conventions for every entry point
+ *   - Device buffers are owned by the caller (e.g. torch tensors passed by data
+ *     pointer).  The library never allocates or frees device memory and never
+ *     synchronises the stream in bpdn_solve / bpdn_refit / bpdn_backward.
+ *   - Complex arrays are interleaved (re, im) float32 pairs ("c64") or float64
+ *     pairs ("c128"), row-major, pixel-major (row p holds pixel p).
+ *   - cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ *   - A negative return value means nothing was launched; bpdn_last_error() then
+ *     returns a message (thread-local).  Per-pixel numerical outcomes are never
+ *     errors: they are reported as status bits.
+ */
+#ifndef BPDN_H
+#define BPDN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bpdn_op *bpdn_op_t; /* opaque host handle of one stack's operator */
+
+enum bpdn_status {
+    BPDN_OK = 0,
+    BPDN_EINVAL = -1, /* bad argument (null pointer, non-finite or out-of-range value)  */
+    BPDN_ECUDA = -2,  /* a CUDA call failed; message in bpdn_last_error()             */
+    BPDN_ESIZE = -3,  /* N, L, P or a workspace size outside the supported range      */
+    BPDN_EALIGN = -4, /* a device pointer is not aligned as documented                */
+    BPDN_ESTATE = -5  /* wrong device current, destroyed handle, ...                  */
+};
+
+/* per-pixel status bits (int32 written to d_status) */
+#define BPDN_PX_NOT_CONVERGED 1     /* max_iter reached before the stopping test held  */
+#define BPDN_PX_BT_LIMIT 2          /* an iteration needed more than max_bt step cuts   */
+#define BPDN_PX_NONFINITE 4         /* g held NaN/Inf; x = 0, iters = 0                 */
+#define BPDN_PX_SUPPORT_OVERFLOW 8  /* refit skipped: |supp x| > s_max                  */
+#define BPDN_PX_KKT_FAIL 16         /* refit ran but could not certify optimality       */
+#define BPDN_PX_ZERO_SOLUTION 32    /* returned x is exactly 0                          */
+#define BPDN_PX_CERTIFIED 64        /* refit certified x as the minimiser of Eq. 6      */
+
+/* limits */
+#define BPDN_MAX_N 64
+#define BPDN_MAX_L 1024
+#define BPDN_MAX_SMAX 16
+
+typedef struct {
+    int32_t max_iter;     /* N_K of Algorithm 1 (default 500)                                  */
+    float tol;            /* stop when ||xbar - x^k|| <= tol ||xbar|| (default 1e-6)            */
+    float c_alpha;        /* step reduction factor C_alpha of Eq. 15, in (0,1) (default 0.5)    */
+    float alpha0_scale;   /* alpha_0 = alpha0_scale / (2N)  (default 1)                         */
+    int32_t precision;    /* 0: FP32 contraction (CUDA cores); 1: BF16 operands, FP32 accumulate */
+    int32_t refit;        /* 0: none; 1: FP64 restricted solve on the support + certificate     */
+    int32_t s_max;        /* largest support the refit handles (<= BPDN_MAX_SMAX, default 16)   */
+    int32_t max_bt;       /* step cuts allowed per iteration before BT_LIMIT (default 64)        */
+    int32_t tile_pixels;  /* pixels per CTA (0 = library choice)                                 */
+    int32_t refit_rounds; /* working-set rounds of the refit (default 4)                         */
+    int32_t reserved[6];
+} bpdn_options;
+
+/* Fill *opt with the defaults above. */
+void bpdn_default_options(bpdn_options *opt);
+
+/* ---------------------------------------------------------------- operator */
+
+/* Bytes of device workspace an operator with N acquisitions and L grid points
+ * needs (A in the layouts the kernels read, A in FP64, the Toeplitz generator of
+ * A^H A, A A^H and scalars).  0 if N or L is out of range. */
+size_t bpdn_op_workspace_bytes(int32_t N, int32_t L);
+
+/*
+ * Build the operator of one stack on the device (Eq. 5 and the definitions after
+ * Eq. 2): A_nl = exp(-j 2 pi xi_n s_l) with xi_n = 2 b_n/(wavelength range), the
+ * Toeplitz generator h(d) = sum_n exp(j 2 pi xi_n d ds) of A^H A, A A^H, and the
+ * Lipschitz constant L_f = 2 lambda_max(A^H A) that the remark after Eq. 14 names
+ * (computed in FP64 on the device).
+ *
+ * baselines_m   host pointer, N finite values (metres)
+ * N             1..BPDN_MAX_N;  L  1..BPDN_MAX_L (L = 1 needs s_min == s_max)
+ * wavelength_m, range_m  > 0;   s_min_m <= s_max_m (metres)
+ * d_workspace   device, >= bpdn_op_workspace_bytes(N, L) bytes, 256-byte aligned;
+ *               owned by the caller and must outlive the handle
+ * cuda_stream   stream for the set-up kernels.  The call synchronises this
+ *               stream once (to read lambda_max back); do not capture it.
+ * out           receives a host handle; free it with bpdn_destroy_operator().
+ */
+int bpdn_make_operator(const double *baselines_m, int32_t N, double wavelength_m, double range_m,
+                       double s_min_m, double s_max_m, int32_t L, void *d_workspace,
+                       size_t workspace_bytes, void *cuda_stream, bpdn_op_t *out);
+
+/* Free the host handle (the caller's workspace is not touched). NULL is ignored. */
+void bpdn_destroy_operator(bpdn_op_t op);
+
+/* N, L and grid spacing of an operator; L_f = 2 lambda_max(A^H A) (FP64) and
+ * alpha_0 = 1/(2N).  Return BPDN_EINVAL on a NULL handle. */
+int bpdn_op_info(bpdn_op_t op, int32_t *N, int32_t *L, double *ds_m, double *lipschitz);
+double bpdn_op_lipschitz(bpdn_op_t op);
+
+/* Copy one of the operator's device tables into a caller buffer (for inspection):
+ *   what = 0: A as c64, N x L           (dst_bytes >= 8 N L)
+ *          1: A as c128, N x L          (16 N L)
+ *          2: h(d), c128, d = -(L-1)..L-1 stored at [d + L - 1]   (16 (2L-1))
+ *          3: A A^H as c128, N x N      (16 N N)
+ * Asynchronous on cuda_stream. */
+int bpdn_op_export(bpdn_op_t op, int32_t what, void *d_dst, size_t dst_bytes, void *cuda_stream);
+
+/* ------------------------------------------------------------------- solve */
+
+/* Bytes of device workspace bpdn_solve needs for P pixels (a work counter and
+ * per-launch scratch; independent of the data).  256-byte aligned buffer. */
+size_t bpdn_solve_workspace_bytes(bpdn_op_t op, int64_t P, const bpdn_options *opt);
+
+/*
+ * Solve P pixels that share the operator (Algorithm 1 per pixel, then the refit
+ * when opt->refit != 0).  Asynchronous on cuda_stream; no host synchronisation.
+ *
+ * d_g        device c64 [P, N]   pixel vectors g (8-byte aligned)
+ * d_lambda   device float32 [1] (lambda_per_pixel = 0) or [P] (= 1); lambda > 0
+ * d_x        device c64 [P, L]   out: x (8-byte aligned)
+ * d_support  device int32 [P, s_max] out (may be NULL): ascending support indices,
+ *            -1 padded (written only when opt->refit != 0)
+ * d_nsupp    device int32 [P] out (may be NULL): number of nonzeros of x
+ * d_status   device int32 [P] out: BPDN_PX_* bits
+ * d_iters    device int32 [P] out: iterations of Algorithm 1 run
+ * d_nbt      device int32 [P] out (may be NULL): total step cuts (Eq. 15 failures)
+ * d_workspace  >= bpdn_solve_workspace_bytes(op, P, opt) bytes, 256-byte aligned
+ * The operator's workspace must be resident on the current device.
+ */
+int bpdn_solve(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda,
+               int32_t lambda_per_pixel, const bpdn_options *opt, void *d_x, int32_t *d_support,
+               int32_t *d_nsupp, int32_t *d_status, int32_t *d_iters, int32_t *d_nbt,
+               void *d_workspace, size_t workspace_bytes, void *cuda_stream);
+
+/*
+ * Support extraction and FP64 refit on its own (the refinement that follows
+ * Algorithm 1; SL1MMER step (3) "parameter estimation", Sec. III-A):
+ * W = {l : x_in[l] != 0}; minimise ||A_W z - g||^2 + lambda sum |z_i| exactly in
+ * FP64 over z in C^W, then certify Eq. 6's optimality conditions over the whole
+ * grid; grid points that violate them are added to W and the solve repeated
+ * (at most opt->refit_rounds rounds).  Certified pixels get BPDN_PX_CERTIFIED
+ * and x = the minimiser; the others keep x_in and get KKT_FAIL or
+ * SUPPORT_OVERFLOW.  Status bits already in d_status are kept (OR-ed).
+ * d_x_in and d_x_out may alias.  Other arguments as in bpdn_solve.
+ */
+int bpdn_refit(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda,
+               int32_t lambda_per_pixel, const bpdn_options *opt, const void *d_x_in,
+               void *d_x_out, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
+               void *cuda_stream);
+
+/* Thread-local message of the last failed call ("" if none). */
+const char *bpdn_last_error(void);
+
+/* Library version string. */
+const char *bpdn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPDN_H */

@@ -1,0 +1,123 @@
+"""ctypes binding of libbpdn (include/bpdn.h): argument marshalling only.
+
+Every computation happens in the CUDA library; if the library has not been built
+(or fails to load) the import of the solver API raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+BPDN_OK = 0
+STATUS_NAMES = {-1: "EINVAL", -2: "ECUDA", -3: "ESIZE", -4: "EALIGN", -5: "ESTATE"}
+
+PX_NOT_CONVERGED = 1
+PX_BT_LIMIT = 2
+PX_NONFINITE = 4
+PX_SUPPORT_OVERFLOW = 8
+PX_KKT_FAIL = 16
+PX_ZERO_SOLUTION = 32
+PX_CERTIFIED = 64
+
+MAX_N = 64
+MAX_L = 1024
+MAX_SMAX = 16
+
+EXPORTED = [
+    "bpdn_default_options", "bpdn_op_workspace_bytes", "bpdn_make_operator",
+    "bpdn_destroy_operator", "bpdn_op_info", "bpdn_op_lipschitz", "bpdn_op_export",
+    "bpdn_solve_workspace_bytes", "bpdn_solve", "bpdn_refit", "bpdn_last_error", "bpdn_version",
+]
+
+
+class Options(ctypes.Structure):
+    """Mirror of bpdn_options."""
+    _fields_ = [
+        ("max_iter", ctypes.c_int32),
+        ("tol", ctypes.c_float),
+        ("c_alpha", ctypes.c_float),
+        ("alpha0_scale", ctypes.c_float),
+        ("precision", ctypes.c_int32),
+        ("refit", ctypes.c_int32),
+        ("s_max", ctypes.c_int32),
+        ("max_bt", ctypes.c_int32),
+        ("tile_pixels", ctypes.c_int32),
+        ("refit_rounds", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
+    ]
+
+
+class BPDNError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"bpdn error {code} ({STATUS_NAMES.get(code, '?')}): {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libbpdn.so (raises if it is missing and build_if_missing is False)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libbpdn is not built ({path} missing): run "
+                               "`python -m paper_1805_01759_gb300.build` (needs nvcc)")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, sz, i32, i64, dbl = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    op_t = ctypes.c_void_p
+    optp = ctypes.POINTER(Options)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    dblp = ctypes.POINTER(ctypes.c_double)
+    lib.bpdn_default_options.argtypes = [optp]
+    lib.bpdn_default_options.restype = None
+    lib.bpdn_op_workspace_bytes.argtypes = [i32, i32]
+    lib.bpdn_op_workspace_bytes.restype = sz
+    lib.bpdn_make_operator.argtypes = [dblp, i32, dbl, dbl, dbl, dbl, i32, vp, sz, vp,
+                                       ctypes.POINTER(op_t)]
+    lib.bpdn_make_operator.restype = ctypes.c_int
+    lib.bpdn_destroy_operator.argtypes = [op_t]
+    lib.bpdn_destroy_operator.restype = None
+    lib.bpdn_op_info.argtypes = [op_t, i32p, i32p, dblp, dblp]
+    lib.bpdn_op_info.restype = ctypes.c_int
+    lib.bpdn_op_lipschitz.argtypes = [op_t]
+    lib.bpdn_op_lipschitz.restype = dbl
+    lib.bpdn_op_export.argtypes = [op_t, i32, vp, sz, vp]
+    lib.bpdn_op_export.restype = ctypes.c_int
+    lib.bpdn_solve_workspace_bytes.argtypes = [op_t, i64, optp]
+    lib.bpdn_solve_workspace_bytes.restype = sz
+    lib.bpdn_solve.argtypes = [op_t, vp, i64, vp, i32, optp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.bpdn_solve.restype = ctypes.c_int
+    lib.bpdn_refit.argtypes = [op_t, vp, i64, vp, i32, optp, vp, vp, vp, vp, vp, vp]
+    lib.bpdn_refit.restype = ctypes.c_int
+    lib.bpdn_last_error.argtypes = []
+    lib.bpdn_last_error.restype = ctypes.c_char_p
+    lib.bpdn_version.argtypes = []
+    lib.bpdn_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def check(rc: int) -> None:
+    if rc != BPDN_OK:
+        raise BPDNError(rc, load().bpdn_last_error().decode())
+
+
+def default_options(**overrides) -> Options:
+    opt = Options()
+    load().bpdn_default_options(ctypes.byref(opt))
+    for k, v in overrides.items():
+        if not hasattr(opt, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(opt, k, v)
+    return opt

@@ -1,0 +1,162 @@
+"""Python API over libbpdn: torch tensors supply device memory and streams.
+
+    op = Operator(baselines_m, wavelength_m, range_m, s_min_m, s_max_m, L)
+    res = solve(op, g, lam)            # g: complex64 [P, N] on the GPU
+    res.x, res.status, res.iters, ...
+
+Only argument marshalling happens here; every step of the solve runs in the CUDA
+library.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream: torch.cuda.Stream | None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+class Operator:
+    """The steering operator of one stack (Eq. 5), resident on the current GPU."""
+
+    def __init__(self, baselines_m, wavelength_m: float, range_m: float, s_min_m: float,
+                 s_max_m: float, L: int, *, device: torch.device | str | None = None,
+                 stream: torch.cuda.Stream | None = None):
+        lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        b = np.ascontiguousarray(baselines_m, dtype=np.float64)
+        self.N, self.L = int(b.size), int(L)
+        nbytes = lib.bpdn_op_workspace_bytes(self.N, self.L)
+        if nbytes == 0:
+            raise _lib.BPDNError(-3, f"N = {self.N}, L = {self.L} outside the supported range")
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            h = ctypes.c_void_p()
+            _lib.check(lib.bpdn_make_operator(
+                b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.N, float(wavelength_m),
+                float(range_m), float(s_min_m), float(s_max_m), self.L, self.workspace.data_ptr(),
+                nbytes, _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.baselines_m = b
+        self.wavelength_m, self.range_m = float(wavelength_m), float(range_m)
+        self.s_min_m, self.s_max_m = float(s_min_m), float(s_max_m)
+        N, Lc, ds, lip = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+        _lib.check(lib.bpdn_op_info(self._h, ctypes.byref(N), ctypes.byref(Lc), ctypes.byref(ds),
+                                    ctypes.byref(lip)))
+        self.ds_m, self.lipschitz = ds.value, lip.value
+
+    @classmethod
+    def from_geometry(cls, geom, **kw) -> "Operator":
+        return cls(geom.baselines_m, geom.wavelength_m, geom.range_m, geom.s_min_m, geom.s_max_m,
+                   geom.L, **kw)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def export(self, what: str) -> torch.Tensor:
+        """Device tables: 'A' (complex64 N x L), 'A64', 'h' (complex128 2L-1), 'AAH'."""
+        code, shape, dt = {"A": (0, (self.N, self.L), torch.complex64),
+                           "A64": (1, (self.N, self.L), torch.complex128),
+                           "h": (2, (2 * self.L - 1,), torch.complex128),
+                           "AAH": (3, (self.N, self.N), torch.complex128)}[what]
+        out = torch.empty(shape, dtype=dt, device=self.device)
+        _lib.check(_lib.load().bpdn_op_export(self._h, code, out.data_ptr(),
+                                              out.numel() * out.element_size(), _stream(None)))
+        return out
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                _lib.load().bpdn_destroy_operator(h)
+            except Exception:  # pragma: no cover - interpreter shutdown
+                pass
+            self._h = ctypes.c_void_p()
+
+
+@dataclasses.dataclass
+class SolveResult:
+    x: torch.Tensor          # complex64 [P, L]
+    status: torch.Tensor     # int32 [P]
+    iters: torch.Tensor      # int32 [P]
+    nbt: torch.Tensor        # int32 [P]
+    nsupp: torch.Tensor      # int32 [P]
+    support: torch.Tensor | None  # int32 [P, s_max]
+
+
+def _lambda_tensor(lam, P: int, device) -> tuple[torch.Tensor, int]:
+    if isinstance(lam, torch.Tensor):
+        t = lam.to(device=device, dtype=torch.float32).contiguous()
+        if t.numel() == 1:
+            return t.reshape(1), 0
+        if t.numel() != P:
+            raise ValueError("lambda must have 1 or P entries")
+        return t.reshape(P), 1
+    return torch.tensor([float(lam)], dtype=torch.float32, device=device), 0
+
+
+def _check_g(op: Operator, g: torch.Tensor) -> torch.Tensor:
+    if g.dtype != torch.complex64 or g.device.type != "cuda":
+        raise TypeError("g must be a complex64 CUDA tensor")
+    if g.dim() != 2 or g.shape[1] != op.N:
+        raise ValueError(f"g must be [P, {op.N}]")
+    return g.contiguous()
+
+
+def solve(op: Operator, g: torch.Tensor, lam, *, out: SolveResult | None = None,
+          stream: torch.cuda.Stream | None = None, **options) -> SolveResult:
+    """Algorithm 1 (+ the FP64 refit unless refit=0) for every row of g."""
+    lib = _lib.load()
+    g = _check_g(op, g)
+    P = g.shape[0]
+    opt = _lib.default_options(**options)
+    lam_t, pp = _lambda_tensor(lam, P, g.device)
+    dev = g.device
+    if out is None:
+        out = SolveResult(
+            x=torch.empty((P, op.L), dtype=torch.complex64, device=dev),
+            status=torch.zeros(P, dtype=torch.int32, device=dev),
+            iters=torch.empty(P, dtype=torch.int32, device=dev),
+            nbt=torch.empty(P, dtype=torch.int32, device=dev),
+            nsupp=torch.empty(P, dtype=torch.int32, device=dev),
+            support=(torch.empty((P, opt.s_max), dtype=torch.int32, device=dev) if opt.refit else None),
+        )
+    ws_bytes = lib.bpdn_solve_workspace_bytes(op.handle, P, ctypes.byref(opt))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    _lib.check(lib.bpdn_solve(op.handle, g.data_ptr(), P, lam_t.data_ptr(), pp, ctypes.byref(opt),
+                              out.x.data_ptr(), _ptr(out.support), _ptr(out.nsupp),
+                              out.status.data_ptr(), out.iters.data_ptr(), _ptr(out.nbt),
+                              ws.data_ptr(), ws_bytes, _stream(stream)))
+    out._keepalive = (ws, lam_t, g)  # type: ignore[attr-defined]
+    return out
+
+
+def refit(op: Operator, g: torch.Tensor, lam, x_in: torch.Tensor, *, status: torch.Tensor | None = None,
+          stream: torch.cuda.Stream | None = None, **options):
+    """Support extraction + FP64 refit of x_in on its own.  Returns (x, support, nsupp, status)."""
+    lib = _lib.load()
+    g = _check_g(op, g)
+    P = g.shape[0]
+    opt = _lib.default_options(**options)
+    lam_t, pp = _lambda_tensor(lam, P, g.device)
+    x_in = x_in.contiguous()
+    x = torch.empty_like(x_in)
+    support = torch.empty((P, opt.s_max), dtype=torch.int32, device=g.device)
+    nsupp = torch.empty(P, dtype=torch.int32, device=g.device)
+    st = torch.zeros(P, dtype=torch.int32, device=g.device) if status is None else status.clone()
+    _lib.check(lib.bpdn_refit(op.handle, g.data_ptr(), P, lam_t.data_ptr(), pp, ctypes.byref(opt),
+                              x_in.data_ptr(), x.data_ptr(), support.data_ptr(), nsupp.data_ptr(),
+                              st.data_ptr(), _stream(stream)))
+    return x, support, nsupp, st

@@ -1,0 +1,421 @@
+// C ABI of libbpdn (declared in include/bpdn.h): argument checks, workspace
+// layout, and kernel launches on the caller's stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "bpdn_internal.h"
+
+namespace bpdn {
+
+static thread_local char g_err[512] = "";
+
+int set_error(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int check_cuda(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess)
+        return BPDN_OK;
+    return set_error(BPDN_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+OpLayout op_layout(int N, int L)
+{
+    OpLayout o;
+    const int Lpad = round_up(L, 32);
+    const int lda = Lpad + 1;
+    size_t off = 0;
+    o.A_re = off; off = a256(off + sizeof(float) * (size_t)N * lda);
+    o.A_im = off; off = a256(off + sizeof(float) * (size_t)N * lda);
+    o.A64 = off;  off = a256(off + sizeof(double2) * (size_t)N * L);
+    o.h = off;    off = a256(off + sizeof(double2) * (size_t)(2 * L - 1));
+    o.aah = off;  off = a256(off + sizeof(double2) * (size_t)N * N);
+    o.xi = off;   off = a256(off + sizeof(double) * (size_t)N);
+    o.scal = off; off = a256(off + sizeof(double) * 8);
+    o.total = off;
+    return o;
+}
+
+static int current_device(int *dev)
+{
+    cudaError_t e = cudaGetDevice(dev);
+    return check_cuda(e, "cudaGetDevice");
+}
+
+static bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+static int check_op(bpdn_op_t h, OpHandle **out)
+{
+    OpHandle *op = reinterpret_cast<OpHandle *>(h);
+    if (!op || op->magic != kOpMagic)
+        return set_error(BPDN_EINVAL, "invalid operator handle");
+    int dev = -1;
+    int rc = current_device(&dev);
+    if (rc)
+        return rc;
+    if (dev != op->device)
+        return set_error(BPDN_ESTATE, "operator lives on device %d but device %d is current",
+                         op->device, dev);
+    *out = op;
+    return BPDN_OK;
+}
+
+static int num_sms(int dev)
+{
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+        v = 1;
+    return v;
+}
+
+static int max_smem_optin(int dev)
+{
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        v = 48 * 1024;
+    return v;
+}
+
+static int check_options(const bpdn_options *o)
+{
+    if (!o)
+        return set_error(BPDN_EINVAL, "options pointer is NULL");
+    if (o->max_iter < 0)
+        return set_error(BPDN_EINVAL, "max_iter must be >= 0");
+    if (!(o->tol >= 0.f) || !isfinite(o->tol))
+        return set_error(BPDN_EINVAL, "tol must be finite and >= 0");
+    if (!(o->c_alpha > 0.f && o->c_alpha < 1.f))
+        return set_error(BPDN_EINVAL, "c_alpha must lie in (0, 1)");
+    if (!(o->alpha0_scale > 0.f) || !isfinite(o->alpha0_scale))
+        return set_error(BPDN_EINVAL, "alpha0_scale must be finite and > 0");
+    if (o->precision != 0 && o->precision != 1)
+        return set_error(BPDN_EINVAL, "precision must be 0 (FP32) or 1 (BF16)");
+    if (o->refit != 0 && o->refit != 1)
+        return set_error(BPDN_EINVAL, "refit must be 0 or 1");
+    if (o->s_max < 1 || o->s_max > BPDN_MAX_SMAX)
+        return set_error(BPDN_EINVAL, "s_max must lie in [1, %d]", BPDN_MAX_SMAX);
+    if (o->max_bt < 0)
+        return set_error(BPDN_EINVAL, "max_bt must be >= 0");
+    if (o->refit_rounds < 0 || o->refit_rounds > 64)
+        return set_error(BPDN_EINVAL, "refit_rounds must lie in [0, 64]");
+    return BPDN_OK;
+}
+
+}  // namespace bpdn
+
+using namespace bpdn;
+
+extern "C" {
+
+const char *bpdn_last_error(void) { return g_err; }
+
+const char *bpdn_version(void) { return "bpdn-gb300 0.1 (sm_103a)"; }
+
+void bpdn_default_options(bpdn_options *opt)
+{
+    if (!opt)
+        return;
+    memset(opt, 0, sizeof(*opt));
+    opt->max_iter = 500;
+    opt->tol = 1e-6f;
+    opt->c_alpha = 0.5f;
+    opt->alpha0_scale = 1.0f;
+    opt->precision = 0;
+    opt->refit = 1;
+    opt->s_max = BPDN_MAX_SMAX;
+    opt->max_bt = 64;
+    opt->tile_pixels = 0;
+    opt->refit_rounds = 4;
+}
+
+size_t bpdn_op_workspace_bytes(int32_t N, int32_t L)
+{
+    if (N < 1 || N > BPDN_MAX_N || L < 1 || L > BPDN_MAX_L)
+        return 0;
+    return op_layout(N, L).total;
+}
+
+int bpdn_make_operator(const double *baselines_m, int32_t N, double wavelength_m, double range_m,
+                       double s_min_m, double s_max_m, int32_t L, void *d_workspace,
+                       size_t workspace_bytes, void *cuda_stream, bpdn_op_t *out)
+{
+    if (!out)
+        return set_error(BPDN_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!baselines_m || !d_workspace)
+        return set_error(BPDN_EINVAL, "baselines or workspace pointer is NULL");
+    if (N < 1 || N > BPDN_MAX_N)
+        return set_error(BPDN_ESIZE, "N = %d outside [1, %d]", N, BPDN_MAX_N);
+    if (L < 1 || L > BPDN_MAX_L)
+        return set_error(BPDN_ESIZE, "L = %d outside [1, %d]", L, BPDN_MAX_L);
+    for (int n = 0; n < N; ++n)
+        if (!isfinite(baselines_m[n]))
+            return set_error(BPDN_EINVAL, "baseline %d is not finite", n);
+    if (!(wavelength_m > 0.0) || !isfinite(wavelength_m) || !(range_m > 0.0) || !isfinite(range_m))
+        return set_error(BPDN_EINVAL, "wavelength and range must be finite and > 0");
+    if (!isfinite(s_min_m) || !isfinite(s_max_m) || s_max_m < s_min_m)
+        return set_error(BPDN_EINVAL, "elevation extent must be finite with s_min <= s_max");
+    if (L > 1 && !(s_max_m > s_min_m))
+        return set_error(BPDN_EINVAL, "L > 1 needs s_max > s_min");
+    const OpLayout lay = op_layout(N, L);
+    if (workspace_bytes < lay.total)
+        return set_error(BPDN_ESIZE, "operator workspace %zu bytes < %zu needed", workspace_bytes,
+                         lay.total);
+    if (!aligned(d_workspace, 256))
+        return set_error(BPDN_EALIGN, "operator workspace must be 256-byte aligned");
+    int dev = 0;
+    int rc = current_device(&dev);
+    if (rc)
+        return rc;
+
+    OpHandle *op = (OpHandle *)calloc(1, sizeof(OpHandle));
+    if (!op)
+        return set_error(BPDN_EINVAL, "out of host memory");
+    op->magic = kOpMagic;
+    op->device = dev;
+    op->N = N;
+    op->L = L;
+    op->Lpad = round_up(L, 32);
+    op->lda = op->Lpad + 1;
+    op->wavelength = wavelength_m;
+    op->range = range_m;
+    op->s_min = s_min_m;
+    op->s_max = s_max_m;
+    op->ds = (L > 1) ? (s_max_m - s_min_m) / (double)(L - 1) : 0.0;
+    char *base = (char *)d_workspace;
+    op->A_re = (float *)(base + lay.A_re);
+    op->A_im = (float *)(base + lay.A_im);
+    op->A64 = (double2 *)(base + lay.A64);
+    op->h = (double2 *)(base + lay.h);
+    op->aah = (double2 *)(base + lay.aah);
+    op->xi = (double *)(base + lay.xi);
+    op->scal = (double *)(base + lay.scal);
+    op->ws_bytes = workspace_bytes;
+
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // the baselines are staged in the xi table; k_xi turns each b_n into xi_n in place
+    double *d_b = op->xi;
+    rc = check_cuda(cudaMemcpyAsync(d_b, baselines_m, sizeof(double) * N, cudaMemcpyHostToDevice, s),
+                    "copy baselines");
+    if (!rc)
+        rc = check_cuda(launch_make_operator(*op, d_b, s), "operator kernels");
+    double lmax = 0.0;
+    if (!rc)
+        rc = check_cuda(cudaMemcpyAsync(&lmax, op->scal, sizeof(double), cudaMemcpyDeviceToHost, s),
+                        "read lambda_max");
+    if (!rc)
+        rc = check_cuda(cudaStreamSynchronize(s), "synchronise operator stream");
+    if (rc) {
+        free(op);
+        return rc;
+    }
+    op->lambda_max = lmax;
+    op->lipschitz = 2.0 * lmax;
+    *out = reinterpret_cast<bpdn_op_t>(op);
+    return BPDN_OK;
+}
+
+void bpdn_destroy_operator(bpdn_op_t h)
+{
+    OpHandle *op = reinterpret_cast<OpHandle *>(h);
+    if (!op || op->magic != kOpMagic)
+        return;
+    op->magic = 0;
+    free(op);
+}
+
+int bpdn_op_info(bpdn_op_t h, int32_t *N, int32_t *L, double *ds_m, double *lipschitz)
+{
+    OpHandle *op = reinterpret_cast<OpHandle *>(h);
+    if (!op || op->magic != kOpMagic)
+        return set_error(BPDN_EINVAL, "invalid operator handle");
+    if (N)
+        *N = op->N;
+    if (L)
+        *L = op->L;
+    if (ds_m)
+        *ds_m = op->ds;
+    if (lipschitz)
+        *lipschitz = op->lipschitz;
+    return BPDN_OK;
+}
+
+double bpdn_op_lipschitz(bpdn_op_t h)
+{
+    OpHandle *op = reinterpret_cast<OpHandle *>(h);
+    if (!op || op->magic != kOpMagic)
+        return NAN;
+    return op->lipschitz;
+}
+
+int bpdn_op_export(bpdn_op_t h, int32_t what, void *d_dst, size_t dst_bytes, void *cuda_stream)
+{
+    OpHandle *op = nullptr;
+    int rc = check_op(h, &op);
+    if (rc)
+        return rc;
+    if (!d_dst)
+        return set_error(BPDN_EINVAL, "destination is NULL");
+    size_t need = 0;
+    switch (what) {
+    case 0: need = 8 * (size_t)op->N * op->L; break;
+    case 1: need = 16 * (size_t)op->N * op->L; break;
+    case 2: need = 16 * (size_t)(2 * op->L - 1); break;
+    case 3: need = 16 * (size_t)op->N * op->N; break;
+    default: return set_error(BPDN_EINVAL, "unknown table %d", what);
+    }
+    if (dst_bytes < need)
+        return set_error(BPDN_ESIZE, "destination %zu bytes < %zu needed", dst_bytes, need);
+    if (!aligned(d_dst, what == 0 ? 8 : 16))
+        return set_error(BPDN_EALIGN, "destination misaligned");
+    return check_cuda(launch_export(*op, what, d_dst, (cudaStream_t)cuda_stream), "export");
+}
+
+size_t bpdn_solve_workspace_bytes(bpdn_op_t h, int64_t P, const bpdn_options *opt)
+{
+    (void)h;
+    (void)P;
+    (void)opt;
+    return 256;  // one 64-bit work counter, padded
+}
+
+static int check_solve_buffers(const OpHandle *op, const void *d_g, int64_t P, const float *d_lambda,
+                               const void *d_x, const int32_t *d_status)
+{
+    if (P < 0)
+        return set_error(BPDN_EINVAL, "P must be >= 0");
+    if (P > ((int64_t)1 << 40))
+        return set_error(BPDN_ESIZE, "P = %lld too large", (long long)P);
+    if (P == 0)
+        return BPDN_OK;
+    if (!d_g || !d_lambda || !d_x || !d_status)
+        return set_error(BPDN_EINVAL, "g, lambda, x and status pointers must be non-NULL");
+    if (!aligned(d_g, 8) || !aligned(d_x, 8) || !aligned(d_lambda, 4) || !aligned(d_status, 4))
+        return set_error(BPDN_EALIGN, "g and x must be 8-byte aligned, lambda and status 4-byte");
+    (void)op;
+    return BPDN_OK;
+}
+
+int bpdn_solve(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda,
+               int32_t lambda_per_pixel, const bpdn_options *opt, void *d_x, int32_t *d_support,
+               int32_t *d_nsupp, int32_t *d_status, int32_t *d_iters, int32_t *d_nbt,
+               void *d_workspace, size_t workspace_bytes, void *cuda_stream)
+{
+    OpHandle *op = nullptr;
+    int rc = check_op(h, &op);
+    if (rc)
+        return rc;
+    rc = check_options(opt);
+    if (rc)
+        return rc;
+    rc = check_solve_buffers(op, d_g, P, d_lambda, d_x, d_status);
+    if (rc)
+        return rc;
+    if (P == 0)
+        return BPDN_OK;
+    if (!d_iters)
+        return set_error(BPDN_EINVAL, "iters pointer must be non-NULL");
+    if (!d_workspace || workspace_bytes < bpdn_solve_workspace_bytes(h, P, opt))
+        return set_error(BPDN_ESIZE, "solve workspace too small");
+    if (!aligned(d_workspace, 256))
+        return set_error(BPDN_EALIGN, "solve workspace must be 256-byte aligned");
+    if (opt->refit && d_support && !aligned(d_support, 4))
+        return set_error(BPDN_EALIGN, "support must be 4-byte aligned");
+    if (opt->precision != 0)
+        return set_error(BPDN_EINVAL, "precision 1 (BF16) is not available in this build");
+    if (op->Lpad > 512)
+        return set_error(BPDN_ESIZE, "L = %d: the FP32 iteration kernel handles L <= 512", op->L);
+    int dev = op->device;
+    if ((int)rbpg_smem_bytes(*op) > max_smem_optin(dev))
+        return set_error(BPDN_ESIZE, "N = %d, L = %d needs %zu bytes of shared memory (> %d)",
+                         op->N, op->L, rbpg_smem_bytes(*op), max_smem_optin(dev));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    unsigned long long *counter = (unsigned long long *)d_workspace;
+    rc = check_cuda(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s), "reset work counter");
+    if (rc)
+        return rc;
+    SolveLaunch a;
+    a.g = (const float2 *)d_g;
+    a.P = P;
+    a.lam = d_lambda;
+    a.lam_pp = lambda_per_pixel ? 1 : 0;
+    a.x = (float2 *)d_x;
+    a.nsupp = d_nsupp;
+    a.status = d_status;
+    a.iters = d_iters;
+    a.nbt = d_nbt;
+    a.counter = counter;
+    a.max_iter = opt->max_iter;
+    a.tol = opt->tol;
+    a.c_alpha = opt->c_alpha;
+    a.alpha0 = (float)(opt->alpha0_scale / (2.0 * op->N));
+    a.max_bt = opt->max_bt;
+    a.precision = opt->precision;
+    rc = check_cuda(launch_rbpg(*op, a, num_sms(dev), s), "iteration kernel");
+    if (rc)
+        return rc;
+    if (opt->refit) {
+        RefitLaunch r;
+        r.g = a.g;
+        r.P = P;
+        r.lam = d_lambda;
+        r.lam_pp = a.lam_pp;
+        r.x_in = a.x;
+        r.x_out = a.x;
+        r.support = d_support;
+        r.nsupp = d_nsupp;
+        r.status = d_status;
+        r.s_max = opt->s_max;
+        r.rounds = opt->refit_rounds;
+        rc = check_cuda(launch_refit(*op, r, s), "refit kernel");
+    }
+    return rc;
+}
+
+int bpdn_refit(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda,
+               int32_t lambda_per_pixel, const bpdn_options *opt, const void *d_x_in,
+               void *d_x_out, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
+               void *cuda_stream)
+{
+    OpHandle *op = nullptr;
+    int rc = check_op(h, &op);
+    if (rc)
+        return rc;
+    rc = check_options(opt);
+    if (rc)
+        return rc;
+    rc = check_solve_buffers(op, d_g, P, d_lambda, d_x_out, d_status);
+    if (rc)
+        return rc;
+    if (P == 0)
+        return BPDN_OK;
+    if (!d_x_in || !aligned(d_x_in, 8))
+        return set_error(d_x_in ? BPDN_EALIGN : BPDN_EINVAL, "x_in must be non-NULL and 8-byte aligned");
+    RefitLaunch r;
+    r.g = (const float2 *)d_g;
+    r.P = P;
+    r.lam = d_lambda;
+    r.lam_pp = lambda_per_pixel ? 1 : 0;
+    r.x_in = (const float2 *)d_x_in;
+    r.x_out = (float2 *)d_x_out;
+    r.support = d_support;
+    r.nsupp = d_nsupp;
+    r.status = d_status;
+    r.s_max = opt->s_max;
+    r.rounds = opt->refit_rounds;
+    return check_cuda(launch_refit(*op, r, (cudaStream_t)cuda_stream), "refit kernel");
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Internal declarations shared by the libbpdn translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bpdn.h"
+
+namespace bpdn {
+
+constexpr uint32_t kOpMagic = 0xB9D4A11Cu;
+constexpr int kTilePixels = 16;   // pixel slots per CTA of the iteration kernel
+constexpr int kRefitMax = BPDN_MAX_SMAX;
+
+// Host handle of one stack's operator.  All device pointers point into the
+// caller's workspace.
+struct OpHandle {
+    uint32_t magic;
+    int device;
+    int N, L;
+    int Lpad;     // L rounded up to a multiple of 32 (= threads of the iteration CTA)
+    int lda;      // row stride (floats) of the planar FP32 tables: Lpad + 1 (odd, bank spread)
+    double wavelength, range, s_min, s_max, ds;
+    double lambda_max, lipschitz;
+    // device tables
+    float *A_re, *A_im;  // [N][lda], zero for l >= L
+    double2 *A64;        // [N][L]
+    double2 *h;          // [2L-1], h[d + L - 1]
+    double2 *aah;        // [N][N]
+    double *xi;          // [N]
+    double *scal;        // [8] device scalars (lambda_max, ...)
+    size_t ws_bytes;
+};
+
+// Workspace layout of an operator (offsets in bytes, 256-aligned sections).
+struct OpLayout {
+    size_t A_re, A_im, A64, h, aah, xi, scal, total;
+};
+OpLayout op_layout(int N, int L);
+
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Set the thread-local error message; returns code.
+int set_error(int code, const char *fmt, ...);
+int check_cuda(cudaError_t e, const char *what);
+
+// ---- launches (each returns a cudaError_t from the launch) ----
+cudaError_t launch_make_operator(const OpHandle &op, const double *d_b, cudaStream_t s);
+cudaError_t launch_export(const OpHandle &op, int what, void *dst, cudaStream_t s);
+
+struct SolveLaunch {
+    const float2 *g;
+    int64_t P;
+    const float *lam;
+    int lam_pp;
+    float2 *x;
+    int32_t *nsupp, *status, *iters, *nbt;
+    unsigned long long *counter;
+    int max_iter;
+    float tol;
+    float c_alpha;
+    float alpha0;
+    int max_bt;
+    int precision;
+};
+cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
+size_t rbpg_smem_bytes(const OpHandle &op);
+
+struct RefitLaunch {
+    const float2 *g;
+    int64_t P;
+    const float *lam;
+    int lam_pp;
+    const float2 *x_in;
+    float2 *x_out;
+    int32_t *support, *nsupp, *status;
+    int s_max;
+    int rounds;
+};
+cudaError_t launch_refit(const OpHandle &op, const RefitLaunch &a, cudaStream_t s);
+
+}  // namespace bpdn

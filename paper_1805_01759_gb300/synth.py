@@ -151,7 +151,9 @@ def make_stack(geom: StackGeometry, P: int, rng: np.random.Generator, *, lam: fl
     gamma[rows[m1], idx1[m1]] += a1[m1].astype(np.complex64)
     gamma[rows[m2], idx2[m2]] += a2[m2].astype(np.complex64)
     s_true = np.stack([np.where(m1, s1, np.nan), np.where(m2, s2, np.nan)], axis=1)
-    return Stack(geom, np.ascontiguousarray(g.astype(np.complex64)), float(lam), gamma,
+    # lambda is handed to the solver as float32: keep it exactly representable so
+    # every consumer (oracle included) sees the same value
+    return Stack(geom, np.ascontiguousarray(g.astype(np.complex64)), float(np.float32(lam)), gamma,
                  K.astype(np.int8), snr.astype(np.float32), s_true, seed)
 
 
@@ -162,11 +164,14 @@ def workload_small(P: int = 256, seed: int = 1) -> Stack:
     return make_stack(geom, P, rng, lam=default_lambda(25, 200), snr_db_range=(10.0, 10.0), seed=seed)
 
 
-def workload_patch(P: int = 1 << 20, seed: int = 2) -> Stack:
+def workload_patch(P: int = 1 << 20, seed: int = 2, part: int = 0) -> Stack:
     """Full patch: N=25, L=400 on [-200,200] m, second scatterer at kappa*rho_s with
-    kappa~U[0.5,2], per-pixel SNR~U[0,20] dB."""
+    kappa~U[0.5,2], per-pixel SNR~U[0,20] dB.  `part` > 0 draws another set of pixels
+    of the same stack (same geometry), e.g. one per GPU."""
     rng = np.random.default_rng(seed)
     geom = make_geometry(rng, 25, 400, 250.0, 200.0)
+    if part:
+        rng = np.random.default_rng([seed, part])
     return make_stack(geom, P, rng, lam=default_lambda(25, 400), snr_db_range=(0.0, 20.0),
                       second_at_kappa=(0.5, 2.0), seed=seed)
 
