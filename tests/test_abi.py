@@ -1,0 +1,79 @@
+"""The C ABI library (CPU only): it loads, exports every function include/bpdn.h
+declares, and rejects bad arguments with error codes before touching the GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1805_01759_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bpdn.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(bpdn_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return _lib.load(build_if_missing=True)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_lib.EXPORTED), set(names) ^ set(_lib.EXPORTED)
+
+
+def test_options_struct_layout(lib):
+    opt = _lib.default_options()
+    assert ctypes.sizeof(_lib.Options) == 64
+    assert opt.max_iter == 500 and abs(opt.tol - 1e-6) < 1e-12 and opt.c_alpha == 0.5
+    assert opt.refit == 1 and opt.s_max == 16 and opt.precision == 0
+
+
+def test_workspace_sizes(lib):
+    assert lib.bpdn_op_workspace_bytes(25, 400) > 25 * 400 * 16
+    assert lib.bpdn_op_workspace_bytes(0, 400) == 0
+    assert lib.bpdn_op_workspace_bytes(25, 0) == 0
+    assert lib.bpdn_op_workspace_bytes(65, 400) == 0
+    assert lib.bpdn_op_workspace_bytes(25, 1025) == 0
+    assert lib.bpdn_op_workspace_bytes(25, 400) % 256 == 0
+
+
+def test_argument_errors_without_gpu(lib):
+    out = ctypes.c_void_p()
+    b = np.zeros(25)
+    dp = b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    # NULL output / workspace / baselines
+    assert lib.bpdn_make_operator(dp, 25, 0.031, 7e5, -1.0, 1.0, 10, None, 0, None, None) == -1
+    assert lib.bpdn_make_operator(dp, 25, 0.031, 7e5, -1.0, 1.0, 10, None, 0, None, ctypes.byref(out)) == -1
+    assert b"NULL" in lib.bpdn_last_error()
+    fake_ws = ctypes.c_void_p(256)
+    assert lib.bpdn_make_operator(dp, 0, 0.031, 7e5, -1.0, 1.0, 10, fake_ws, 1 << 20, None, ctypes.byref(out)) == -3
+    assert lib.bpdn_make_operator(dp, 25, -1.0, 7e5, -1.0, 1.0, 10, fake_ws, 1 << 20, None, ctypes.byref(out)) == -1
+    assert lib.bpdn_make_operator(dp, 25, 0.031, 7e5, 1.0, -1.0, 10, fake_ws, 1 << 20, None, ctypes.byref(out)) == -1
+    assert lib.bpdn_make_operator(dp, 25, 0.031, 7e5, -1.0, 1.0, 10, fake_ws, 16, None, ctypes.byref(out)) == -3
+    assert lib.bpdn_make_operator(dp, 25, 0.031, 7e5, -1.0, 1.0, 10, ctypes.c_void_p(264), 1 << 20, None,
+                                  ctypes.byref(out)) == -4
+    b2 = b.copy()
+    b2[3] = np.nan
+    assert lib.bpdn_make_operator(b2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 25, 0.031, 7e5,
+                                  -1.0, 1.0, 10, fake_ws, 1 << 20, None, ctypes.byref(out)) == -1
+    # an invalid handle is rejected before any CUDA call
+    opt = _lib.default_options()
+    assert lib.bpdn_solve(None, None, 1, None, 0, ctypes.byref(opt), None, None, None, None, None, None,
+                          None, 0, None) == -1
+    assert lib.bpdn_refit(None, None, 1, None, 0, ctypes.byref(opt), None, None, None, None, None, None) == -1
+    assert lib.bpdn_op_info(None, None, None, None, None) == -1
+    assert np.isnan(lib.bpdn_op_lipschitz(None))
+    lib.bpdn_destroy_operator(None)  # ignored
+    assert lib.bpdn_version().startswith(b"bpdn-gb300")
