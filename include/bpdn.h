@@ -163,6 +163,26 @@ int bpdn_refit(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda,
                void *d_x_out, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
                void *cuda_stream);
 
+/*
+ * bpdn_solve without a workspace, for callers that cannot allocate device memory
+ * (for example a processing chain whose host application owns every GPU buffer
+ * and forbids its modules to call cudaMalloc).  The paper has no counterpart: it
+ * is a deployment variant of bpdn_solve, with the same arguments minus the
+ * workspace and the same results.
+ *
+ * The iteration kernel's scratch (a work counter) lives in a file-scope device
+ * array of 256 bytes that every GPU loading the library keeps until the process
+ * exits.  The first call on a device looks up its address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array and
+ * each clears what it uses, so calls whose work overlaps on the GPU race and must
+ * be serialised by the caller.  A solve whose scratch would exceed 256 bytes is
+ * rejected with BPDN_ESIZE.  No device memory is allocated or freed.
+ */
+int bpdn_solve_noalloc(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda,
+                       int32_t lambda_per_pixel, const bpdn_options *opt, void *d_x,
+                       int32_t *d_support, int32_t *d_nsupp, int32_t *d_status, int32_t *d_iters,
+                       int32_t *d_nbt, void *cuda_stream);
+
 /* Thread-local message of the last failed call ("" if none). */
 const char *bpdn_last_error(void);
 

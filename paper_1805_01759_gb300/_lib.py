@@ -29,6 +29,7 @@ EXPORTED = [
     "bpdn_default_options", "bpdn_op_workspace_bytes", "bpdn_make_operator",
     "bpdn_destroy_operator", "bpdn_op_info", "bpdn_op_lipschitz", "bpdn_op_export",
     "bpdn_solve_workspace_bytes", "bpdn_solve", "bpdn_refit", "bpdn_last_error", "bpdn_version",
+    "bpdn_solve_noalloc",
 ]
 
 
@@ -100,6 +101,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.bpdn_solve.restype = ctypes.c_int
     lib.bpdn_refit.argtypes = [op_t, vp, i64, vp, i32, optp, vp, vp, vp, vp, vp, vp]
     lib.bpdn_refit.restype = ctypes.c_int
+    lib.bpdn_solve_noalloc.argtypes = [op_t, vp, i64, vp, i32, optp, vp, vp, vp, vp, vp, vp, vp]
+    lib.bpdn_solve_noalloc.restype = ctypes.c_int
     lib.bpdn_last_error.argtypes = []
     lib.bpdn_last_error.restype = ctypes.c_char_p
     lib.bpdn_version.argtypes = []
