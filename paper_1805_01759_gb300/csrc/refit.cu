@@ -1,21 +1,27 @@
 // Support extraction and FP64 refit (the refinement after Algorithm 1; SL1MMER
 // step (3), Sec. III-A), one warp per pixel.
 //
-//   1. W = {l : x_in[l] != 0}, ascending (warp ballots over the grid).
-//   2. Exact minimiser of the problem of Eq. 6 restricted to W,
-//          min_z  z^H G z - 2 Re(c^H z) + lambda sum_i |z_i|,   G = A_W^H A_W, c = A_W^H g,
-//      in FP64 (G from the Toeplitz generator h, c from the FP64 operator).
-//      Each round alternates one sweep of exact one-coordinate minimisations
-//      (which can switch a coordinate on or off) with one damped Newton step on
-//      the coordinates that are nonzero.  The Newton system is the Hessian in real
-//      coordinates, 2 [[Re G, -Im G],[Im G, Re G]] + lambda/|z_i| (I - u_i u_i^T);
-//      the step is kept where the objective is smooth (no modulus falls below a
-//      tenth of its value along the step) and must lower the objective or the
-//      gradient norm.  Done when 2 (G z - c)_i + lambda z_i/|z_i| = 0 on the nonzeros
-//      and |2 (G z - c)_i| <= lambda on the zeros of W.
-//   3. Certificate over the whole grid: |2 a_l^H (A z - g)| <= lambda for l not in W
-//      (FP32 products against an FP64 residual, relative slack 1e-5).  Violating grid
-//      points join W (largest first) and step 2 repeats, for at most `rounds` rounds.
+//   1. W = {l : x_in[l] != 0}, ascending (warp ballots over the grid); the s_max
+//      largest moduli when x_in has more nonzeros.
+//   2. The exact minimiser of Eq. 6 restricted to W,
+//          min_z  z^H G z - 2 Re(c^H z) + lambda sum_i |z_i|,   G = A_W^H A_W, c = A_W^H g
+//      (G from the Toeplitz generator h, c from the FP64 operator).  A solve is
+//      coordinate sweeps (exact one-coordinate minimisations, which switch
+//      coordinates on and off) alternating with Newton steps on the nonzero
+//      coordinates; the Newton system is the Hessian in real coordinates,
+//      2 [[Re G, -Im G],[Im G, Re G]] + lambda/|z_i| (I - u_i u_i^T).  A step is kept
+//      where the objective is smooth (no modulus falls below a tenth of its value
+//      along it); a coordinate that a full step carries through zero is set to zero
+//      and the step recomputed.  If that does not converge, damped Newton on the
+//      smoothed objective (|z| -> sqrt(|z|^2 + eps^2), strictly convex) for a
+//      decreasing eps finds the support first.
+//      Precision: the support is found in FP32 (residual <= 1e-4 lambda); the
+//      answer is then finished and checked in FP64 (residual <= 1e-12 lambda),
+//      falling back to an all-FP64 solve when the FP32 support was wrong.
+//   3. Certificate over the grid: |2 a_l^H (A_W z - g)| <= lambda for l not in W
+//      (FP32 products; grid points within 1e-4 of the bound recomputed in FP64
+//      against 1e-9).  Violators join W, largest first, and step 2 repeats
+//      (at most `rounds` rounds).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -26,300 +32,366 @@ namespace bpdn {
 
 namespace {
 
-constexpr int KW = kRefitMax;       // working-set capacity (<= 16, so 2|W| <= 32 lanes)
-constexpr int WARPS = 4;            // pixels per block
-constexpr int kFastRounds = 15;
-constexpr double kOptTol = 1e-12;  // optimality residual relative to lambda
+constexpr int KW = kRefitMax;  // working-set capacity (<= 16, so 2|W| <= 32 lanes)
+constexpr int kFastRounds32 = 15;
+constexpr int kFastRounds64 = 8;
+constexpr int kFallbackRounds = 20;
 
-struct WarpSmem {
-    double2 G[KW][KW];
-    double J[2 * KW][2 * KW + 1];
-    double rhs[2 * KW];
-    double2 z[KW], c[KW], zt[KW], dz[KW], gam[KW];
-    double2 r[BPDN_MAX_N];   // g (FP64)
-    double2 rr[BPDN_MAX_N];  // A_W z - g (FP64)
-    float2 rf[BPDN_MAX_N];   // A_W z - g (FP32 copy)
-    int W[KW];
-    int T[KW];
-    int m, nt;
+template <typename T>
+struct C2 {
+    T x, y;
 };
-
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+template <typename T>
+__device__ __forceinline__ C2<T> mk(T x, T y)
 {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    C2<T> r;
+    r.x = x;
+    r.y = y;
+    return r;
 }
-__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+template <typename T>
+__device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b)
+{
+    return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ T cabs2(C2<T> a) { return a.x * a.x + a.y * a.y; }
+template <typename T>
+__device__ __forceinline__ bool cnz(C2<T> a) { return a.x != T(0) || a.y != T(0); }
 
-__device__ __forceinline__ double warp_sum(double v)
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
 {
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1)
         v += __shfl_xor_sync(0xffffffffu, v, off);
     return v;
 }
-
-// (G z)_i for lane i < m
-__device__ __forceinline__ double2 gz_row(const WarpSmem &S, int i, int m, const double2 *z)
+template <typename T>
+__device__ __forceinline__ T warp_max(T v)
 {
-    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1)
+        v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+// Working storage of one restricted solve in precision T.
+template <typename T>
+struct Solve {
+    C2<T> G[KW][KW];
+    T J[2 * KW][2 * KW + 1];  // Newton system, right-hand side in column n2
+    T inv[2 * KW];            // reciprocal pivots
+    C2<T> z[KW], c[KW], zt[KW], dz[KW], gam[KW];
+    T q[KW], u0[KW], u1[KW];  // per variable: (smoothed) modulus and unit vector
+    int T_[KW];
+};
+
+// Everything one pixel (one warp) keeps in shared memory.  The FP32 and FP64
+// solves never run at the same time and share storage.
+struct PixelSmem {
+    union {
+        Solve<double> s64;
+        Solve<float> s32;
+    };
+    double2 g[BPDN_MAX_N];   // g in FP64
+    double2 rr[BPDN_MAX_N];  // A_W z - g (FP64)
+    float2 rf[BPDN_MAX_N];   // its FP32 copy
+    double2 zkeep[KW];       // z between the precisions (FP64)
+    int W[KW];
+    int m;
+};
+
+constexpr int WARPS = 1;  // pixels (warps) per block
+
+// G_ij = h(l_i - l_j), c_i = a_{l_i}^H g in precision T
+template <typename T>
+__device__ void load_Gc(Solve<T> &S, const PixelSmem &P, const double2 *__restrict__ A64,
+                        const double2 *__restrict__ h, int N, int L, int lane)
+{
+    const int m = P.m;
+    for (int e = lane; e < m * m; e += 32) {
+        const int i = e / m, j = e - (e / m) * m;
+        const double2 v = h[P.W[i] - P.W[j] + L - 1];
+        S.G[i][j] = mk<T>((T)v.x, (T)v.y);
+    }
+    if (lane < m) {
+        const int l = P.W[lane];
+        double ax = 0.0, ay = 0.0;
+        for (int n = 0; n < N; ++n) {
+            const double2 av = A64[(size_t)n * L + l], gv = P.g[n];
+            ax += av.x * gv.x + av.y * gv.y;
+            ay += av.x * gv.y - av.y * gv.x;
+        }
+        S.c[lane] = mk<T>((T)ax, (T)ay);
+    }
+    __syncwarp();
+}
+
+// (G z)_i
+template <typename T>
+__device__ __forceinline__ C2<T> gz_row(const Solve<T> &S, int i, int m, const C2<T> *z)
+{
+    C2<T> acc = mk<T>(T(0), T(0));
     for (int j = 0; j < m; ++j)
         acc = cadd(acc, cmul(S.G[i][j], z[j]));
     return acc;
 }
 
-// gam_i = 2 (G z - c)_i for i < m (into S.gam); returns the optimality residual
-// max( max_{z_i != 0} |gam_i + lam u_i| / lam,  max_{z_i == 0} (|gam_i|/lam - 1) )
-__device__ double optimality(WarpSmem &S, int m, double lam, int lane)
+// objective over W (|z| smoothed by eps; eps = 0 is exact), without the constant ||g||^2
+template <typename T>
+__device__ T objective(const Solve<T> &S, int m, const C2<T> *z, T lam, T eps, int lane)
 {
-    double res = 0.0;
+    T v = T(0);
     if (lane < m) {
-        double2 gz = gz_row(S, lane, m, S.z);
-        double2 gm = make_double2(2.0 * (gz.x - S.c[lane].x), 2.0 * (gz.y - S.c[lane].y));
+        const C2<T> gz = gz_row(S, lane, m, z);
+        const C2<T> zi = z[lane];
+        v = (zi.x * gz.x + zi.y * gz.y) - T(2) * (S.c[lane].x * zi.x + S.c[lane].y * zi.y) +
+            lam * sqrt(cabs2(zi) + eps * eps);
+    }
+    return warp_sum(v);
+}
+
+// gam = 2 (G z - c); returns the optimality residual
+//   max( max_{z_i != 0} |gam_i + lam u_i| / lam,  max_{z_i = 0} (|gam_i| / lam - 1) )
+template <typename T>
+__device__ T optimality(Solve<T> &S, int m, T lam, int lane)
+{
+    T res = T(0);
+    if (lane < m) {
+        const C2<T> gz = gz_row(S, lane, m, S.z);
+        const C2<T> gm = mk<T>(T(2) * (gz.x - S.c[lane].x), T(2) * (gz.y - S.c[lane].y));
         S.gam[lane] = gm;
-        double2 zi = S.z[lane];
-        double a = sqrt(cabs2(zi));
-        if (a > 0.0) {
-            double ex = gm.x + lam * zi.x / a, ey = gm.y + lam * zi.y / a;
+        const C2<T> zi = S.z[lane];
+        const T a = sqrt(cabs2(zi));
+        if (a > T(0)) {
+            const T ex = gm.x + lam * zi.x / a, ey = gm.y + lam * zi.y / a;
             res = sqrt(ex * ex + ey * ey) / lam;
         } else {
-            res = sqrt(cabs2(gm)) / lam - 1.0;
+            res = sqrt(cabs2(gm)) / lam - T(1);
         }
     }
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1)
-        res = fmax(res, __shfl_xor_sync(0xffffffffu, res, off));
+    res = warp_max(res);
     __syncwarp();
     return res;
 }
 
-// Solve S.J[0..n2) x = S.rhs in place (symmetric positive definite: Gaussian
-// elimination without pivoting, lanes over columns).  Returns false on a
-// non-positive pivot.  The solution is left in S.rhs.
-__device__ bool solve_spd(WarpSmem &S, int n2, int lane)
-{
-    for (int k = 0; k < n2; ++k) {
-        const double piv = S.J[k][k];
-        if (!(piv > 0.0))
-            return false;
-        for (int i = k + 1; i < n2; ++i) {
-            const double f = S.J[i][k] / piv;
-            __syncwarp();
-            if (lane >= k && lane < n2)
-                S.J[i][lane] -= f * S.J[k][lane];
-            if (lane == 0)
-                S.rhs[i] -= f * S.rhs[k];
-            __syncwarp();
-        }
-    }
-    if (lane == 0) {
-        for (int k = n2 - 1; k >= 0; --k) {
-            double sacc = S.rhs[k];
-            for (int j = k + 1; j < n2; ++j)
-                sacc -= S.J[k][j] * S.rhs[j];
-            S.rhs[k] = sacc / S.J[k][k];
-        }
-    }
-    __syncwarp();
-    return true;
-}
-
-// One exact coordinate-minimisation sweep over W:
+// One sweep of exact coordinate minimisations:
 //   z_i <- S_{lam/2}(c_i - sum_{j != i} G_ij z_j) / G_ii
-__device__ void cd_sweep(WarpSmem &S, int m, double lam, int lane)
+template <typename T>
+__device__ void cd_sweep(Solve<T> &S, int m, T lam, int lane)
 {
     for (int i = 0; i < m; ++i) {
-        double2 t = make_double2(0.0, 0.0);
+        C2<T> t = mk<T>(T(0), T(0));
         if (lane < m && lane != i)
             t = cmul(S.G[i][lane], S.z[lane]);
-        double qx = warp_sum(t.x), qy = warp_sum(t.y);
+        const T qx = S.c[i].x - warp_sum(t.x), qy = S.c[i].y - warp_sum(t.y);
         if (lane == 0) {
-            qx = S.c[i].x - qx;
-            qy = S.c[i].y - qy;
-            const double a = sqrt(qx * qx + qy * qy);
-            const double th = 0.5 * lam;
-            const double gii = S.G[i][i].x;
+            const T a = sqrt(qx * qx + qy * qy);
+            const T th = T(0.5) * lam;
             if (a > th) {
-                const double sc = (1.0 - th / a) / gii;
-                S.z[i] = make_double2(qx * sc, qy * sc);
+                const T sc = (T(1) - th / a) / S.G[i][i].x;
+                S.z[i] = mk<T>(qx * sc, qy * sc);
             } else {
-                S.z[i] = make_double2(0.0, 0.0);
+                S.z[i] = mk<T>(T(0), T(0));
             }
         }
         __syncwarp();
     }
 }
 
-// Newton direction for the objective restricted to the nonzero coordinates of
-// `z` (exact modulus, eps = 0) or for the smoothed objective over all of W
-// (|z_i| replaced by sqrt(|z_i|^2 + eps^2), eps > 0).  Writes S.dz (zero off
-// the variable set) and returns the directional derivative (negative for a
-// descent direction), or +1 when the system could not be solved.
-__device__ double newton_dir(WarpSmem &S, int m, const double2 *z, double lam, double eps, int lane)
+// Solve J[0..n2) x = J[.][n2] (symmetric positive definite): elimination without
+// pivoting with lanes over columns (one reciprocal per pivot), then column-wise
+// back substitution with lanes over rows.  Lane i returns x_i.  `ok` is false on
+// a non-positive pivot.
+template <typename T>
+__device__ T solve_spd(Solve<T> &S, int n2, int lane, bool &ok)
 {
-    if (lane == 0) {
-        int nt = 0;
-        for (int i = 0; i < m; ++i)
-            if (eps > 0.0 || z[i].x != 0.0 || z[i].y != 0.0)
-                S.T[nt++] = i;
-        S.nt = nt;
+    const int rc = (n2 < 32) ? n2 : 0;  // lane that owns the right-hand-side column
+    ok = true;
+    for (int k = 0; k < n2; ++k) {
+        __syncwarp();
+        const T piv = S.J[k][k];
+        if (!(piv > T(0))) {
+            ok = false;
+            return T(0);
+        }
+        const T ip = T(1) / piv;
+        const T pk = (lane > k && lane < n2) ? S.J[k][lane] : T(0);
+        const T pr = (lane == rc) ? S.J[k][n2] : T(0);
+        if (lane == 0)
+            S.inv[k] = ip;
+        for (int i = k + 1; i < n2; ++i) {
+            const T f = S.J[i][k] * ip;
+            if (lane > k && lane < n2)
+                S.J[i][lane] -= f * pk;
+            if (lane == rc)
+                S.J[i][n2] -= f * pr;
+        }
     }
     __syncwarp();
-    const int nt = S.nt, n2 = 2 * nt;
-    if (nt == 0)
-        return 1.0;
-    // gradient of the (smoothed) objective: 2 (G z - c)_i + lam z_i / q_i
+    T b = (lane < n2) ? S.J[lane][n2] : T(0);
+    for (int k = n2 - 1; k >= 0; --k) {
+        const T xk = __shfl_sync(0xffffffffu, b, k) * S.inv[k];
+        if (lane < k)
+            b -= S.J[lane][k] * xk;
+        else if (lane == k)
+            b = xk;
+    }
+    return b;
+}
+
+// Newton direction for the objective restricted to the nonzero coordinates of z
+// (eps = 0) or for the smoothed objective over all of W (eps > 0).  Writes S.dz
+// (zero off the variables) and returns the directional derivative (negative for
+// a descent direction), or +1 when the system could not be solved.
+template <typename T>
+__device__ T newton_dir(Solve<T> &S, int m, const C2<T> *z, T lam, T eps, int lane)
+{
+    const bool use = (lane < m) && (eps > T(0) || cnz(z[lane]));
+    const unsigned bal = __ballot_sync(0xffffffffu, use);
+    const int nt = __popc(bal), n2 = 2 * nt;
+    if (use)
+        S.T_[__popc(bal & ((1u << lane) - 1u))] = lane;
     if (lane < m) {
-        double2 gz = gz_row(S, lane, m, z);
-        S.gam[lane] = make_double2(2.0 * (gz.x - S.c[lane].x), 2.0 * (gz.y - S.c[lane].y));
+        const C2<T> gz = gz_row(S, lane, m, z);
+        S.gam[lane] = mk<T>(T(2) * (gz.x - S.c[lane].x), T(2) * (gz.y - S.c[lane].y));
+    }
+    __syncwarp();
+    if (nt == 0)
+        return T(1);
+    if (lane < nt) {
+        const C2<T> zi = z[S.T_[lane]];
+        const T q = sqrt(cabs2(zi) + eps * eps);
+        const T iq = T(1) / q;
+        S.q[lane] = q;
+        S.u0[lane] = zi.x * iq;
+        S.u1[lane] = zi.y * iq;
     }
     __syncwarp();
     for (int rI = 0; rI < n2; ++rI) {
         const int a = rI >> 1, ra = rI & 1;
-        const int ia = S.T[a];
         if (lane < n2) {
             const int b = lane >> 1, cb = lane & 1;
-            const int ib = S.T[b];
-            const double2 g = S.G[ia][ib];
-            double v = (ra == 0) ? (cb == 0 ? g.x : -g.y) : (cb == 0 ? g.y : g.x);
-            v *= 2.0;
+            const C2<T> g = S.G[S.T_[a]][S.T_[b]];
+            T v = (ra == 0) ? (cb == 0 ? g.x : -g.y) : (cb == 0 ? g.y : g.x);
+            v *= T(2);
             if (a == b) {
-                const double2 zi = z[ia];
-                const double q = sqrt(cabs2(zi) + eps * eps);
-                const double w0 = zi.x / q, w1 = zi.y / q;
-                const double wr = ra ? w1 : w0, wc = cb ? w1 : w0;
-                v += lam / q * ((ra == cb ? 1.0 : 0.0) - wr * wc);
+                const T wr = ra ? S.u1[a] : S.u0[a], wc = cb ? S.u1[a] : S.u0[a];
+                v += lam / S.q[a] * ((ra == cb ? T(1) : T(0)) - wr * wc);
             }
             S.J[rI][lane] = v;
         }
     }
-    double slope_part = 0.0;
+    T gcomp = T(0);
     if (lane < n2) {
-        const int ia = S.T[lane >> 1];
-        const double2 zi = z[ia];
-        const double q = sqrt(cabs2(zi) + eps * eps);
-        const double gcomp = (lane & 1) ? (S.gam[ia].y + lam * zi.y / q) : (S.gam[ia].x + lam * zi.x / q);
-        S.rhs[lane] = -gcomp;
-        slope_part = gcomp;  // times d below
+        const int a = lane >> 1;
+        const int ia = S.T_[a];
+        const T w = (lane & 1) ? S.u1[a] : S.u0[a];
+        gcomp = ((lane & 1) ? S.gam[ia].y : S.gam[ia].x) + lam * w;
+        S.J[lane][n2] = -gcomp;
     }
-    __syncwarp();
-    if (!solve_spd(S, n2, lane))
-        return 1.0;
+    bool ok;
+    const T d = solve_spd(S, n2, lane, ok);
+    if (!ok)
+        return T(1);
     if (lane < m)
-        S.dz[lane] = make_double2(0.0, 0.0);
+        S.dz[lane] = mk<T>(T(0), T(0));
     __syncwarp();
-    double sl = 0.0;
-    if (lane < n2)
-        sl = slope_part * S.rhs[lane];
+    // gather (re, im) pairs: lane a takes rows 2a and 2a+1
+    const T dre = __shfl_sync(0xffffffffu, d, (2 * lane) & 31);
+    const T dim = __shfl_sync(0xffffffffu, d, (2 * lane + 1) & 31);
     if (lane < nt)
-        S.dz[S.T[lane]] = make_double2(S.rhs[2 * lane], S.rhs[2 * lane + 1]);
+        S.dz[S.T_[lane]] = mk<T>(dre, dim);
     __syncwarp();
-    return warp_sum(sl);
-}
-
-// objective over W with |z| smoothed by eps (eps = 0: exact)
-__device__ double objective_W(const WarpSmem &S, int m, const double2 *z, double lam, double eps, int lane)
-{
-    double v = 0.0;
-    if (lane < m) {
-        const double2 gz = gz_row(S, lane, m, z);
-        const double2 zi = z[lane];
-        v = (zi.x * gz.x + zi.y * gz.y) - 2.0 * (S.c[lane].x * zi.x + S.c[lane].y * zi.y) +
-            lam * sqrt(cabs2(zi) + eps * eps);
-    }
-    return warp_sum(v);
+    return warp_sum((lane < n2) ? gcomp * d : T(0));
 }
 
 // does the segment z_i + s dz_i, s in [0, t], come within a tenth of |z_i| of zero?
-__device__ __forceinline__ bool passes_zero(double2 zi, double2 d, double t)
+template <typename T>
+__device__ __forceinline__ bool passes_zero(C2<T> zi, C2<T> d, T t)
 {
-    const double dd = cabs2(d);
-    if (!(dd > 0.0) || (zi.x == 0.0 && zi.y == 0.0))
+    const T dd = cabs2(d);
+    if (!(dd > T(0)) || !cnz(zi))
         return false;
-    double s = -(zi.x * d.x + zi.y * d.y) / dd;
-    s = fmin(fmax(s, 0.0), t);
-    const double2 p = make_double2(zi.x + s * d.x, zi.y + s * d.y);
-    return cabs2(p) < 0.01 * cabs2(zi);
+    T s = -(zi.x * d.x + zi.y * d.y) / dd;
+    s = fmin(fmax(s, T(0)), t);
+    const C2<T> p = mk<T>(zi.x + s * d.x, zi.y + s * d.y);
+    return cabs2(p) < T(0.01) * cabs2(zi);
 }
 
-// Fast path of step 2: coordinate sweeps alternating with Newton steps on the
-// nonzero coordinates.  A coordinate that a full Newton step would carry through
-// zero is set to zero and the step recomputed; the swap is kept when the
-// objective falls.  Returns true on convergence.
-__device__ bool solve_fast(WarpSmem &S, double lam, int lane, int max_outer)
+// coordinate sweeps alternating with Newton steps (see the file header)
+template <typename T>
+__device__ bool fast_path(Solve<T> &S, int m, T lam, int lane, int max_outer, T tol)
 {
-    const int m = S.m;
     for (int outer = 0; outer < max_outer; ++outer) {
         cd_sweep(S, m, lam, lane);
-        double res = optimality(S, m, lam, lane);
-        if (res <= kOptTol)
+        const T res = optimality(S, m, lam, lane);
+        if (res <= tol)
             return true;
-        const double F0 = objective_W(S, m, S.z, lam, 0.0, lane);
-        double slope = newton_dir(S, m, S.z, lam, 0.0, lane);
-        if (slope > 0.0)
+        const T F0 = objective(S, m, S.z, lam, T(0), lane);
+        T slope = newton_dir(S, m, S.z, lam, T(0), lane);
+        if (slope > T(0))
             continue;
-        // coordinates the full step carries through zero
-        bool blk = (lane < m) && passes_zero(S.z[lane], S.dz[lane], 1.0);
-        const unsigned bmask = __ballot_sync(0xffffffffu, blk);
-        if (bmask) {
-            double2 zkeep = (lane < m) ? S.z[lane] : make_double2(0.0, 0.0);
+        const bool blk = (lane < m) && passes_zero(S.z[lane], S.dz[lane], T(1));
+        if (__any_sync(0xffffffffu, blk)) {
+            const C2<T> zk = (lane < m) ? S.z[lane] : mk<T>(T(0), T(0));
             if (lane < m)
-                S.zt[lane] = blk ? make_double2(0.0, 0.0) : zkeep;
+                S.zt[lane] = blk ? mk<T>(T(0), T(0)) : zk;
             __syncwarp();
-            const double sl2 = newton_dir(S, m, S.zt, lam, 0.0, lane);
-            bool ok2 = sl2 < 0.0;
+            const T sl2 = newton_dir(S, m, S.zt, lam, T(0), lane);
+            bool ok2 = sl2 < T(0);
             if (ok2) {
-                bool blk2 = (lane < m) && passes_zero(S.zt[lane], S.dz[lane], 1.0);
+                const bool blk2 = (lane < m) && passes_zero(S.zt[lane], S.dz[lane], T(1));
                 ok2 = !__any_sync(0xffffffffu, blk2);
             }
             if (ok2) {
                 if (lane < m)
-                    S.zt[lane] = make_double2(S.zt[lane].x + S.dz[lane].x, S.zt[lane].y + S.dz[lane].y);
+                    S.zt[lane] = cadd(S.zt[lane], S.dz[lane]);
                 __syncwarp();
-                const double F2 = objective_W(S, m, S.zt, lam, 0.0, lane);
-                if (F2 < F0) {
+                if (objective(S, m, S.zt, lam, T(0), lane) < F0) {
                     if (lane < m)
                         S.z[lane] = S.zt[lane];
                     __syncwarp();
-                    if (optimality(S, m, lam, lane) <= kOptTol)
+                    if (optimality(S, m, lam, lane) <= tol)
                         return true;
                     continue;
                 }
             }
-            // recompute the plain direction for the damped step below
-            slope = newton_dir(S, m, S.z, lam, 0.0, lane);
-            if (slope > 0.0)
+            slope = newton_dir(S, m, S.z, lam, T(0), lane);
+            if (slope > T(0))
                 continue;
         }
-        // damped step kept inside the smooth region
-        double t = 1.0;
-        for (int h = 0; h < 60; ++h) {
+        T t = T(1);
+        for (int hh = 0; hh < 60; ++hh) {
             const bool bad = (lane < m) && passes_zero(S.z[lane], S.dz[lane], t);
             if (!__any_sync(0xffffffffu, bad))
                 break;
-            t *= 0.5;
+            t *= T(0.5);
         }
-        const double2 keep = (lane < m) ? S.z[lane] : make_double2(0.0, 0.0);
+        const C2<T> keep = (lane < m) ? S.z[lane] : mk<T>(T(0), T(0));
         bool accepted = false;
-        for (int h = 0; h < 50 && t > 1e-14; ++h, t *= 0.5) {
+        for (int hh = 0; hh < 50 && t > T(1e-14); ++hh, t *= T(0.5)) {
             if (lane < m)
-                S.zt[lane] = make_double2(keep.x + t * S.dz[lane].x, keep.y + t * S.dz[lane].y);
+                S.zt[lane] = mk<T>(keep.x + t * S.dz[lane].x, keep.y + t * S.dz[lane].y);
             __syncwarp();
-            const double F1 = objective_W(S, m, S.zt, lam, 0.0, lane);
-            if (F1 <= F0 + 1e-4 * t * slope) {
+            if (objective(S, m, S.zt, lam, T(0), lane) <= F0 + T(1e-4) * t * slope) {
                 accepted = true;
                 break;
             }
-            if (h == 0) {
-                // near the minimiser the objective no longer resolves the decrease
+            if (hh == 0) {
+                // near the minimiser the objective no longer resolves the decrease:
+                // take the step if it halves the optimality residual instead
                 if (lane < m)
                     S.z[lane] = S.zt[lane];
                 __syncwarp();
-                const double r1 = optimality(S, m, lam, lane);
+                const T r1 = optimality(S, m, lam, lane);
                 if (lane < m)
                     S.z[lane] = keep;
                 __syncwarp();
-                if (r1 < 0.5 * res) {
+                if (r1 < T(0.5) * res) {
                     accepted = true;
                     break;
                 }
@@ -328,61 +400,105 @@ __device__ bool solve_fast(WarpSmem &S, double lam, int lane, int max_outer)
         if (accepted && lane < m)
             S.z[lane] = S.zt[lane];
         __syncwarp();
-        if (optimality(S, m, lam, lane) <= kOptTol)
+        if (optimality(S, m, lam, lane) <= tol)
             return true;
     }
     return false;
 }
 
-// Fallback of step 2: damped Newton on the smoothed objective (|z| replaced by
-// sqrt(|z|^2 + eps^2): smooth and strictly convex, so damped Newton converges
-// from any start) for eps = 1e-1, 1e-2, ..., 1e-13 times the scale of z, each
-// level warm-started from the last; then coordinates below 1e-6 of the scale are
-// set to zero and exact Newton steps on the rest finish.  Returns true on convergence.
-__device__ bool solve_continuation(WarpSmem &S, double lam, int lane)
+// damped Newton on the smoothed objective for eps = e0, e0/10, ..., e1 (times the
+// scale of z), at most maxit steps per level; then coordinates below 1e-6 of the
+// scale are set to zero
+template <typename T>
+__device__ void continuation(Solve<T> &S, int m, T lam, int lane, T e0, T e1, int maxit)
 {
-    const int m = S.m;
-    double sc = (lane < m) ? sqrt(cabs2(S.z[lane])) : 0.0;
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1)
-        sc = fmax(sc, __shfl_xor_sync(0xffffffffu, sc, off));
-    sc = fmax(sc, 1e-3);
-    for (double eps = 1e-1 * sc; eps >= 1e-13 * sc; eps *= 0.1) {
-        for (int it = 0; it < 40; ++it) {
-            const double slope = newton_dir(S, m, S.z, lam, eps, lane);
-            if (!(slope < 0.0) || -slope <= 1e-28 * fmax(1.0, sc * sc))
+    T sc = warp_max((lane < m) ? sqrt(cabs2(S.z[lane])) : T(0));
+    sc = fmax(sc, T(1e-3));
+    for (T eps = e0 * sc; eps >= T(0.999) * e1 * sc; eps *= T(0.1)) {
+        for (int it = 0; it < maxit; ++it) {
+            const T slope = newton_dir(S, m, S.z, lam, eps, lane);
+            if (!(slope < T(0)) || -slope <= T(1e-28) * fmax(T(1), sc * sc))
                 break;
-            const double F0 = objective_W(S, m, S.z, lam, eps, lane);
-            const double2 keep = (lane < m) ? S.z[lane] : make_double2(0.0, 0.0);
-            double t = 1.0;
-            for (int h = 0; h < 45; ++h, t *= 0.5) {
+            const T F0 = objective(S, m, S.z, lam, eps, lane);
+            const C2<T> keep = (lane < m) ? S.z[lane] : mk<T>(T(0), T(0));
+            T t = T(1);
+            for (int hh = 0; hh < 40; ++hh, t *= T(0.5)) {
                 if (lane < m)
-                    S.zt[lane] = make_double2(keep.x + t * S.dz[lane].x, keep.y + t * S.dz[lane].y);
+                    S.zt[lane] = mk<T>(keep.x + t * S.dz[lane].x, keep.y + t * S.dz[lane].y);
                 __syncwarp();
-                if (objective_W(S, m, S.zt, lam, eps, lane) <= F0 + 1e-4 * t * slope)
+                if (objective(S, m, S.zt, lam, eps, lane) <= F0 + T(1e-4) * t * slope)
                     break;
             }
             if (lane < m)
                 S.z[lane] = S.zt[lane];
             __syncwarp();
-            if (-slope < 1e-20 * fmax(1.0, fabs(F0)))
+            if (-slope < T(1e-12) * fmax(T(1), fabs(F0)))
                 break;
         }
     }
-    if (lane < m && sqrt(cabs2(S.z[lane])) <= 1e-6 * sc)
-        S.z[lane] = make_double2(0.0, 0.0);
+    if (lane < m && sqrt(cabs2(S.z[lane])) <= T(1e-6) * sc)
+        S.z[lane] = mk<T>(T(0), T(0));
     __syncwarp();
-    for (int it = 0; it < 20; ++it) {
-        if (optimality(S, m, lam, lane) <= kOptTol)
-            return true;
-        const double slope = newton_dir(S, m, S.z, lam, 0.0, lane);
-        if (slope > 0.0)
-            break;
+}
+
+// Step 2 on the current W from the start values in P.zkeep: FP32 support search,
+// FP64 finish.  The FP64 answer is left in P.zkeep.  Returns true on convergence.
+__device__ bool restricted_minimiser(PixelSmem &P, const double2 *A64, const double2 *h, int N,
+                                     int L, double lam, int lane)
+{
+    const int m = P.m;
+    if (m == 0)
+        return true;
+    double2 start = (lane < m) ? P.zkeep[lane] : make_double2(0.0, 0.0);
+    {
+        Solve<float> &S = P.s32;
+        load_Gc(S, P, A64, h, N, L, lane);
         if (lane < m)
-            S.z[lane] = make_double2(S.z[lane].x + S.dz[lane].x, S.z[lane].y + S.dz[lane].y);
+            S.z[lane] = mk<float>((float)start.x, (float)start.y);
+        __syncwarp();
+        const float lf = (float)lam;
+        if (!fast_path(S, m, lf, lane, kFastRounds32, 1e-4f)) {
+            continuation(S, m, lf, lane, 1e-2f, 1e-6f, 8);
+            fast_path(S, m, lf, lane, kFastRounds32, 1e-4f);
+        }
+        if (lane < m)
+            P.zkeep[lane] = make_double2((double)S.z[lane].x, (double)S.z[lane].y);
         __syncwarp();
     }
-    return optimality(S, m, lam, lane) <= kOptTol;
+    Solve<double> &S = P.s64;
+    load_Gc(S, P, A64, h, N, L, lane);
+    if (lane < m)
+        S.z[lane] = mk<double>(P.zkeep[lane].x, P.zkeep[lane].y);
+    __syncwarp();
+    bool ok = fast_path(S, m, lam, lane, kFastRounds64, 1e-12);
+    if (!ok) {
+        // the FP32 support was wrong: solve in FP64 from the start values
+        if (lane < m)
+            S.z[lane] = mk<double>(start.x, start.y);
+        __syncwarp();
+        continuation(S, m, lam, lane, 1e-2, 1e-8, 8);
+        ok = fast_path(S, m, lam, lane, kFallbackRounds, 1e-12);
+    }
+    if (lane < m)
+        P.zkeep[lane] = make_double2(S.z[lane].x, S.z[lane].y);
+    __syncwarp();
+    return ok;
+}
+
+__device__ void sort_W(PixelSmem &P)
+{
+    for (int i = 1; i < P.m; ++i) {
+        const int w = P.W[i];
+        const double2 zz = P.zkeep[i];
+        int j = i - 1;
+        while (j >= 0 && P.W[j] > w) {
+            P.W[j + 1] = P.W[j];
+            P.zkeep[j + 1] = P.zkeep[j];
+            --j;
+        }
+        P.W[j + 1] = w;
+        P.zkeep[j + 1] = zz;
+    }
 }
 
 __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict__ A64,
@@ -393,7 +509,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict_
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSmem &S = ((WarpSmem *)smem_raw)[warp];
+    PixelSmem &P = ((PixelSmem *)smem_raw)[warp];
     const long long p = (long long)blockIdx.x * WARPS + warp;
     if (p >= a.P)
         return;
@@ -402,7 +518,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict_
     const float2 *gp = a.g + (size_t)p * N;
     const double lam = (double)(a.lam_pp ? a.lam[p] : a.lam[0]);
 
-    // 1. working set W: the nonzeros of x_in (ascending), or the s_max largest of them
+    // 1. working set W
     int nnz = 0;
     for (int l0 = 0; l0 < L; l0 += 32) {
         const int l = l0 + lane;
@@ -417,18 +533,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict_
             const float2 v = (l < L) ? xin[l] : make_float2(0.f, 0.f);
             const bool nz = (v.x != 0.f || v.y != 0.f);
             const unsigned bal = __ballot_sync(0xffffffffu, nz);
-            const int pos = m + __popc(bal & ((1u << lane) - 1u));
-            if (nz) {
-                S.W[pos] = l;
-                S.z[pos] = make_double2((double)v.x, (double)v.y);
-            }
+            if (nz)
+                P.W[m + __popc(bal & ((1u << lane) - 1u))] = l;
             m += __popc(bal);
         }
         if (lane == 0)
-            S.m = m;
+            P.m = m;
     } else {
-        // s_max rounds of a warp arg-max over |x_l|^2, excluding grid points taken
-        uint32_t taken = 0;  // bit j: l = lane + 32 j already in W (L <= 1024)
+        // s_max rounds of a warp arg-max over |x_l|^2 excluding points already taken
+        uint32_t taken = 0;  // bit j: l = lane + 32 j taken (L <= 1024)
         for (int k = 0; k < smax; ++k) {
             float best = -1.f;
             int bl = -1;
@@ -455,86 +568,67 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict_
                 break;  // cannot happen: more than s_max grid points are nonzero
             if ((bl & 31) == lane)
                 taken |= 1u << (bl >> 5);
-            if (lane == 0) {
-                const float2 v = xin[bl];
-                S.W[k] = bl;
-                S.z[k] = make_double2((double)v.x, (double)v.y);
-            }
+            if (lane == 0)
+                P.W[k] = bl;
         }
         __syncwarp();
         if (lane == 0) {
-            S.m = smax;
-            for (int i = 1; i < smax; ++i) {
-                const int w = S.W[i];
-                const double2 zz = S.z[i];
+            P.m = smax;
+            for (int i = 1; i < smax; ++i) {  // ascending
+                const int w = P.W[i];
                 int j = i - 1;
-                while (j >= 0 && S.W[j] > w) {
-                    S.W[j + 1] = S.W[j];
-                    S.z[j + 1] = S.z[j];
+                while (j >= 0 && P.W[j] > w) {
+                    P.W[j + 1] = P.W[j];
                     --j;
                 }
-                S.W[j + 1] = w;
-                S.z[j + 1] = zz;
+                P.W[j + 1] = w;
             }
         }
     }
     const int status = a.status[p];
     for (int n = lane; n < N; n += 32) {
         const float2 gg = gp[n];
-        S.r[n] = make_double2((double)gg.x, (double)gg.y);
+        P.g[n] = make_double2((double)gg.x, (double)gg.y);
+    }
+    __syncwarp();
+    if (lane < P.m) {
+        const float2 v = xin[P.W[lane]];
+        P.zkeep[lane] = make_double2((double)v.x, (double)v.y);
     }
     __syncwarp();
 
     bool certified = false, noroom = false;
     for (int round = 0; round <= a.rounds; ++round) {
-        const int m = S.m;
-        // G_ij = h(l_i - l_j), c_i = a_{l_i}^H g
-        for (int e = lane; e < m * m; e += 32) {
-            const int i = e / m, j = e % m;
-            S.G[i][j] = h[S.W[i] - S.W[j] + L - 1];
-        }
-        if (lane < m) {
-            const int l = S.W[lane];
-            double2 acc = make_double2(0.0, 0.0);
-            for (int n = 0; n < N; ++n) {
-                const double2 av = A64[(size_t)n * L + l], gv = S.r[n];
-                acc.x += av.x * gv.x + av.y * gv.y;
-                acc.y += av.x * gv.y - av.y * gv.x;
-            }
-            S.c[lane] = acc;
-        }
-        __syncwarp();
         // 2. exact minimiser over W
-        bool conv = solve_fast(S, lam, lane, kFastRounds);
-        if (!conv)
-            conv = solve_continuation(S, lam, lane);
-        if (!conv)
+        if (!restricted_minimiser(P, A64, h, N, L, lam, lane))
             break;
+        const int m = P.m;
         // residual A_W z - g in FP64 and its FP32 copy
         for (int n = lane; n < N; n += 32) {
-            double2 acc = make_double2(-S.r[n].x, -S.r[n].y);
-            for (int i = 0; i < m; ++i)
-                acc = cadd(acc, cmul(A64[(size_t)n * L + S.W[i]], S.z[i]));
-            S.rr[n] = acc;
-            S.rf[n] = make_float2((float)acc.x, (float)acc.y);
+            double2 acc = make_double2(-P.g[n].x, -P.g[n].y);
+            for (int i = 0; i < m; ++i) {
+                const double2 av = A64[(size_t)n * L + P.W[i]], zi = P.zkeep[i];
+                acc.x += av.x * zi.x - av.y * zi.y;
+                acc.y += av.x * zi.y + av.y * zi.x;
+            }
+            P.rr[n] = acc;
+            P.rf[n] = make_float2((float)acc.x, (float)acc.y);
         }
         __syncwarp();
-        // 3. certificate off W: |2 a_l^H r| <= lambda.  FP32 products first; grid
-        // points within 1e-4 of the bound are recomputed in FP64 and must satisfy
-        // it to 1e-9.
+        // 3. certificate off W
         const float near = (float)lam * (1.0f - 1e-4f);
         double worst = 0.0;
         int worst_l = -1;
         for (int l = lane; l < L; l += 32) {
             bool inW = false;
             for (int i = 0; i < m; ++i)
-                inW |= (S.W[i] == l);
+                inW |= (P.W[i] == l);
             if (inW)
                 continue;
             float ux = 0.f, uy = 0.f;
             for (int n = 0; n < N; ++n) {
                 const float ar = A_re[n * lda + l], ai = A_im[n * lda + l];
-                const float2 rv = S.rf[n];
+                const float2 rv = P.rf[n];
                 ux = fmaf(ar, rv.x, fmaf(ai, rv.y, ux));
                 uy = fmaf(ar, rv.y, fmaf(-ai, rv.x, uy));
             }
@@ -542,7 +636,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict_
                 continue;
             double vx = 0.0, vy = 0.0;
             for (int n = 0; n < N; ++n) {
-                const double2 av = A64[(size_t)n * L + l], rv = S.rr[n];
+                const double2 av = A64[(size_t)n * L + l], rv = P.rr[n];
                 vx += av.x * rv.x + av.y * rv.y;
                 vy += av.x * rv.y - av.y * rv.x;
             }
@@ -573,8 +667,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict_
                 break;
             }
             if (lane == 0) {
-                S.W[m + added] = bl;
-                S.z[m + added] = make_double2(0.0, 0.0);
+                P.W[m + added] = bl;
+                P.zkeep[m + added] = make_double2(0.0, 0.0);
             }
             ++added;
             if (worst_l == bl) {
@@ -589,21 +683,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict_
             certified = !noroom;
             break;
         }
-        // keep W ascending (insertion sort, lane 0)
         if (lane == 0) {
-            S.m = m + added;
-            for (int i = 1; i < S.m; ++i) {
-                const int w = S.W[i];
-                const double2 zz = S.z[i];
-                int j = i - 1;
-                while (j >= 0 && S.W[j] > w) {
-                    S.W[j + 1] = S.W[j];
-                    S.z[j + 1] = S.z[j];
-                    --j;
-                }
-                S.W[j + 1] = w;
-                S.z[j + 1] = zz;
-            }
+            P.m = m + added;
+            sort_W(P);
         }
         __syncwarp();
         if (noroom)
@@ -612,20 +694,19 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict_
 
     float2 *xo = a.x_out + (size_t)p * L;
     if (certified) {
-        const int m = S.m;
-        // x = z on W (zeros of z stay zero), 0 elsewhere
+        const int m = P.m;
         for (int l = lane; l < L; l += 32) {
             float2 v = make_float2(0.f, 0.f);
             for (int i = 0; i < m; ++i)
-                if (S.W[i] == l)
-                    v = make_float2((float)S.z[i].x, (float)S.z[i].y);
+                if (P.W[i] == l)
+                    v = make_float2((float)P.zkeep[i].x, (float)P.zkeep[i].y);
             xo[l] = v;
         }
         int ns = 0;
         for (int i = 0; i < m; ++i) {
-            const bool nz = (S.z[i].x != 0.0 || S.z[i].y != 0.0);
+            const bool nz = (P.zkeep[i].x != 0.0 || P.zkeep[i].y != 0.0);
             if (a.support && lane == 0 && nz)
-                a.support[(size_t)p * smax + ns] = S.W[i];
+                a.support[(size_t)p * smax + ns] = P.W[i];
             ns += nz;
         }
         if (a.support)
@@ -673,7 +754,7 @@ cudaError_t launch_refit(const OpHandle &op, const RefitLaunch &a, cudaStream_t 
 {
     if (a.P <= 0)
         return cudaSuccess;
-    const size_t smem = WARPS * sizeof(WarpSmem);
+    const size_t smem = WARPS * sizeof(PixelSmem);
     cudaError_t e = cudaFuncSetAttribute(k_refit, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess)
