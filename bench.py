@@ -6,6 +6,9 @@ range 700 km, elevation grid L=400 on [-200,200] m, P=2^20 pixels per GPU, K in
 {0,1,2} scatterers (second at kappa*rho_s, kappa~U[0.5,2]), SNR~U[0,20] dB, seeded
 synthetic data.  One step = the whole hot path over the batch: Algorithm 1 on every
 pixel (iteration kernel) followed by the FP64 refit and certificate (refit kernel).
+Both paths of the metric are timed -- the plain FP32 contraction and the BF16
+tensor-core contraction, each followed by the FP64 refit -- and the BF16 path is
+the headline value; pixels count only when certified and the oracle sample agrees.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -176,22 +179,23 @@ def run_reference(args) -> None:
 
 # ------------------------------------------------------------------ our arm
 
-def _kernel_hash() -> str:
-    src = os.path.join(ROOT, "paper_1805_01759_gb300", "csrc", "rbpg.cu")
+def _kernel_hash(name: str) -> str:
+    src = os.path.join(ROOT, "paper_1805_01759_gb300", "csrc", name)
     return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
 
-def _traffic_per_launch(pixel_iters: float) -> float | None:
-    """DRAM bytes of one iteration-kernel launch from the committed ncu summary, scaled
+def _traffic_per_launch(pixel_iters: float, path_name: str) -> float | None:
+    """DRAM bytes of one iteration-kernel launch from the committed ncu counters, scaled
     by the pixel-iterations it processed -- only while the kernel source is unchanged."""
-    path = os.path.join(ROOT, "profiles", "rbpg_fp32_counters.json")
+    src = "rbpg_tc.cu" if path_name == "bf16" else "rbpg.cu"
+    path = os.path.join(ROOT, "profiles", f"counters_{path_name}.json")
     if not os.path.exists(path):
         return None
     try:
         rec = json.load(open(path))
     except ValueError:
         return None
-    if rec.get("kernel_sha256_16") != _kernel_hash():
+    if rec.get("kernel_sha256_16") != _kernel_hash(src):
         return None
     return float(rec["dram_bytes_per_pixel_iter"]) * pixel_iters
 
@@ -229,6 +233,68 @@ def accuracy_sample(st, x, status, n_sample: int, seed: int = 20) -> dict:
             "degenerate": int(degen.sum())}
 
 
+class PathRunner:
+    """One configuration of the hot path (iteration kernel + refit) on resident inputs."""
+
+    def __init__(self, lib, _lib, op, g_dev, lam_t, P, precision, tol, stream):
+        import torch
+        self.lib, self._lib, self.op, self.g_dev, self.lam_t, self.P = lib, _lib, op, g_dev, lam_t, P
+        dev = g_dev.device
+        self.opt_solve = _lib.default_options(refit=0, precision=precision, tol=tol)
+        self.opt_refit = _lib.default_options()
+        L = op.L
+        self.x = torch.empty((P, L), dtype=torch.complex64, device=dev)
+        self.status = torch.empty(P, dtype=torch.int32, device=dev)
+        self.iters = torch.empty(P, dtype=torch.int32, device=dev)
+        self.nbt = torch.empty(P, dtype=torch.int32, device=dev)
+        self.nsupp = torch.empty(P, dtype=torch.int32, device=dev)
+        self.support = torch.empty((P, self.opt_refit.s_max), dtype=torch.int32, device=dev)
+        self.ws_bytes = lib.bpdn_solve_workspace_bytes(op.handle, P, ctypes.byref(self.opt_solve))
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.stream = stream
+        self.precision, self.tol = precision, tol
+
+    def step(self):
+        """bpdn_solve (Algorithm 1) then bpdn_refit; returns the event between the two."""
+        import torch
+        lib, _lib, s = self.lib, self._lib, self.stream.cuda_stream
+        _lib.check(lib.bpdn_solve(self.op.handle, self.g_dev.data_ptr(), self.P, self.lam_t.data_ptr(), 0,
+                                  ctypes.byref(self.opt_solve), self.x.data_ptr(), None,
+                                  self.nsupp.data_ptr(), self.status.data_ptr(), self.iters.data_ptr(),
+                                  self.nbt.data_ptr(), self.ws.data_ptr(), self.ws_bytes, s))
+        ev_mid = torch.cuda.Event(enable_timing=True)
+        ev_mid.record(self.stream)
+        _lib.check(lib.bpdn_refit(self.op.handle, self.g_dev.data_ptr(), self.P, self.lam_t.data_ptr(), 0,
+                                  ctypes.byref(self.opt_refit), self.x.data_ptr(), self.x.data_ptr(),
+                                  self.support.data_ptr(), self.nsupp.data_ptr(), self.status.data_ptr(), s))
+        return ev_mid
+
+    def timed(self, steps: int, warmup: int, dev):
+        import torch
+        for _ in range(warmup):
+            self.step()
+        torch.cuda.synchronize()
+        barrier(dev)
+        torch.cuda.synchronize()
+        evs = []
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(self.stream)
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            em = self.step()
+            e1 = torch.cuda.Event(enable_timing=True)
+            e1.record(self.stream)
+            evs.append((e0, em, e1))
+        t1.record(self.stream)
+        torch.cuda.synchronize()
+        barrier(dev)
+        return {"total_ms": t0.elapsed_time(t1),
+                "rbpg_ms": [a.elapsed_time(b) for a, b, _ in evs],
+                "refit_ms": [b.elapsed_time(c) for _, b, c in evs]}
+
+
 def run_ours(args) -> None:
     import torch
     import torch.distributed as dist
@@ -250,67 +316,50 @@ def run_ours(args) -> None:
     stream = torch.cuda.current_stream(dev)
     g_dev = torch.from_numpy(st.g).to(dev)
     lam_t = torch.tensor([st.lam], dtype=torch.float32, device=dev)
-    opt_solve = _lib.default_options(refit=0, precision=0)
-    opt_refit = _lib.default_options()
-    x = torch.empty((P, L), dtype=torch.complex64, device=dev)
-    status = torch.empty(P, dtype=torch.int32, device=dev)
-    iters = torch.empty(P, dtype=torch.int32, device=dev)
-    nbt = torch.empty(P, dtype=torch.int32, device=dev)
-    nsupp = torch.empty(P, dtype=torch.int32, device=dev)
-    support = torch.empty((P, opt_refit.s_max), dtype=torch.int32, device=dev)
-    ws_bytes = lib.bpdn_solve_workspace_bytes(op.handle, P, ctypes.byref(opt_solve))
-    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
-    s_ptr = stream.cuda_stream
 
-    def step():
-        _lib.check(lib.bpdn_solve(op.handle, g_dev.data_ptr(), P, lam_t.data_ptr(), 0,
-                                  ctypes.byref(opt_solve), x.data_ptr(), None, nsupp.data_ptr(),
-                                  status.data_ptr(), iters.data_ptr(), nbt.data_ptr(),
-                                  ws.data_ptr(), ws_bytes, s_ptr))
-        ev_mid = torch.cuda.Event(enable_timing=True)
-        ev_mid.record(stream)
-        _lib.check(lib.bpdn_refit(op.handle, g_dev.data_ptr(), P, lam_t.data_ptr(), 0,
-                                  ctypes.byref(opt_refit), x.data_ptr(), x.data_ptr(),
-                                  support.data_ptr(), nsupp.data_ptr(), status.data_ptr(), s_ptr))
-        return ev_mid
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    # ---- timed region: K steps, inputs resident in HBM (and larger than L2)
+    paths = {"fp32": (0, args.tol_fp32), "bf16": (1, args.tol_bf16)}
+    if args.precision != "both":
+        paths = {args.precision: paths[args.precision]}
+    results = {}
     launches = 0
     with ClockSampler(dev.index) as clk:
-        barrier(dev)
-        torch.cuda.synchronize()
-        evs = []
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_start.record(stream)
-        for _ in range(args.steps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            em = step()
-            e1 = torch.cuda.Event(enable_timing=True)
-            e1.record(stream)
-            evs.append((e0, em, e1))
-            launches += 2
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_end.record(stream)
-        torch.cuda.synchronize()
-        barrier(dev)
-    total_ms = t_start.elapsed_time(t_end)
-    rbpg_ms = [a.elapsed_time(b) for a, b, _ in evs]
-    refit_ms = [b.elapsed_time(c) for _, b, c in evs]
-    ms_step = reduce_max(total_ms / args.steps, dev)
+        for name, (prec, tol) in paths.items():
+            runner = PathRunner(lib, _lib, op, g_dev, lam_t, P, prec, tol, stream)
+            tm = runner.timed(args.steps, args.warmup, dev)
+            launches += 2 * args.steps
+            results[name] = (runner, tm)
 
-    it_np = iters.cpu().numpy()
-    st_np = status.cpu().numpy()
-    nbt_np = nbt.cpu().numpy()
-    x_np = x.cpu().numpy()
-    pixel_iters = float(it_np.astype(np.int64).sum())
-    certified = int(((st_np & 64) != 0).sum())
+    # headline path: BF16 + FP64 refit when timed, else the one that ran
+    head = "bf16" if "bf16" in results else next(iter(results))
+    out_paths = {}
+    acc_head = None
+    good_head = None
+    ms_head = None
+    for name, (runner, tm) in results.items():
+        ms_step = reduce_max(tm["total_ms"] / args.steps, dev)
+        it_np = runner.iters.cpu().numpy()
+        st_np = runner.status.cpu().numpy()
+        nbt_np = runner.nbt.cpu().numpy()
+        x_np = runner.x.cpu().numpy()
+        certified = int(((st_np & 64) != 0).sum())
+        acc = accuracy_sample(st, x_np, st_np, args.sample) if rank == 0 else None
+        good = (certified / P) * (acc["ok"] / max(acc["certified"], 1) if acc else 1.0)
+        pixel_iters = float(it_np.astype(np.int64).sum())
+        rbpg_avg_s = statistics.mean(tm["rbpg_ms"]) / 1e3
+        out_paths[name] = {
+            "value": P * world * good / (ms_step / 1e3), "ms_per_step": ms_step,
+            "kernels_ms": {"iteration": statistics.mean(tm["rbpg_ms"]), "refit_fp64": statistics.mean(tm["refit_ms"])},
+            "tol": runner.tol, "certified_frac": certified / P, "good_frac": good, "sample": acc,
+            "mean_iters": float(it_np.mean()), "frac_max_iter": float((it_np >= 500).mean()),
+            "mean_step_cuts": float(nbt_np.mean()),
+            "contraction_tflops": pixel_iters * 8.0 * N * L / rbpg_avg_s / 1e12,
+        }
+        if name == head:
+            acc_head, good_head, ms_head = acc, good, ms_step
+            head_runner, head_tm, head_iters = runner, tm, pixel_iters
 
-    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    runner = head_runner
     g_host = torch.from_numpy(st.g).pin_memory()
     x_host = torch.empty((P, L), dtype=torch.complex64).pin_memory()
     st_host = torch.empty(P, dtype=torch.int32).pin_memory()
@@ -324,63 +373,57 @@ def run_ours(args) -> None:
     e_a.record(stream)
     for _ in range(e2e_steps):
         g_dev.copy_(g_host, non_blocking=True)
-        step()
+        runner.step()
         launches += 2
-        x_host.copy_(x, non_blocking=True)
-        st_host.copy_(status, non_blocking=True)
+        x_host.copy_(runner.x, non_blocking=True)
+        st_host.copy_(runner.status, non_blocking=True)
     e_b.record(stream)
     torch.cuda.synchronize()
     e2e_ms = reduce_max(e_a.elapsed_time(e_b) / e2e_steps, dev)
 
-    # ---- accuracy gate on a seeded sample (rank 0's pixels), and the CPU baseline
-    acc = None
     cpu = None
-    if rank == 0:
-        acc = accuracy_sample(st, x_np, st_np, args.sample)
-        if not args.no_cpu_baseline:
-            cpu = cpu_baseline_leg(args.cpu_sample)
-    good_frac = (certified / P) * (acc["ok"] / max(acc["certified"], 1) if acc else 1.0)
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_leg(args.cpu_sample)
     pixels_total = P * world
-    value = pixels_total * good_frac / (ms_step / 1e3)
-    e2e_value = pixels_total * good_frac / (e2e_ms / 1e3)
+    value = pixels_total * good_head / (ms_head / 1e3)
+    e2e_value = pixels_total * good_head / (e2e_ms / 1e3)
 
     clocks = clk.summary()
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    # algorithmic work of the iteration kernel: the dense gradient contraction
-    # 2 A^H (A y - g) of every pixel-iteration, 8 N L real flops (complex N x L product)
-    rbpg_avg_s = statistics.mean(rbpg_ms) / 1e3
-    flops_launch = pixel_iters * 8.0 * N * L
-    achieved = flops_launch / rbpg_avg_s / 1e12
-    traffic = _traffic_per_launch(pixel_iters)
+    # the dominant kernel of the headline path is its iteration kernel; its algorithmic
+    # work is the dense gradient contraction 8 N L per pixel-iteration
+    rbpg_avg_s = statistics.mean(head_tm["rbpg_ms"]) / 1e3
+    achieved = head_iters * 8.0 * N * L / rbpg_avg_s / 1e12
+    traffic = _traffic_per_launch(head_iters, head)
 
     if rank != 0:
         return
+    kname = "k_rbpg_bf16" if head == "bf16" else "k_rbpg_fp32"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": ms_head, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
         "config": {
             "workload": f"one stack N={N}, L={L} on [-200,200] m, P=2^{int(np.log2(P))} pixels per GPU, "
                         "K in {0,1,2} (second at kappa*rho_s, kappa~U[0.5,2]), SNR~U[0,20] dB",
-            "path": "plain FP32 Algorithm 1 + FP64 refit/certificate",
-            "P_per_gpu": P, "N": N, "L": L, "lambda": st.lam, "max_iter": 500, "tol": 1e-6,
+            "path": ("BF16 tensor-core contraction (FP32 accumulate, FP32 iterate) + FP64 refit/certificate"
+                     if head == "bf16" else "plain FP32 Algorithm 1 + FP64 refit/certificate"),
+            "P_per_gpu": P, "N": N, "L": L, "lambda": st.lam, "max_iter": 500,
             "l2": "inputs larger than L2 (g 210 MB, x 3.4 GB per GPU); no flush",
             "parallelism": f"pixels sharded over {world} GPU(s), no collective",
         },
-        "accuracy": {"certified_frac": certified / P, "sample": acc, "good_frac": good_frac,
-                     "pixels_per_s_all": pixels_total / (ms_step / 1e3),
-                     "mean_iters": float(it_np.mean()), "frac_max_iter": float((it_np >= 500).mean()),
-                     "mean_step_cuts": float(nbt_np.mean())},
-        "kernels_ms": {"rbpg_fp32": statistics.mean(rbpg_ms), "refit_fp64": statistics.mean(refit_ms)},
+        "paths": out_paths,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": traffic,
-                     "kernel": "k_rbpg_fp32",
-                     "note": f"FP32 FMA peak = {n_sm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
-                             "(derived from unit counts and the max SM clock); algorithmic flops = "
-                             "8 N L per pixel-iteration (dense A^H r)"},
+                     "frac": achieved / peak_tflops, "traffic": traffic, "kernel": kname,
+                     "note": f"peak = FP32 FMA rate, {n_sm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
+                             "(unit counts and the max SM clock); achieved = the contraction's "
+                             "algorithmic 8 N L flops per pixel-iteration over the iteration kernel's time "
+                             "(on the BF16 path the contraction runs on the tensor cores and the kernel is "
+                             "bound by its FP32 elementwise work, so this is an equivalent rate)"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -401,6 +444,9 @@ def main(argv=None) -> None:
     ap.add_argument("--cpu-sample", type=int, default=2048, help="pixels of the CPU baseline leg")
     ap.add_argument("--ref-sample", type=int, default=1024, help="pixels per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "both"], default="both")
+    ap.add_argument("--tol-fp32", type=float, default=1e-6)
+    ap.add_argument("--tol-bf16", type=float, default=1e-4)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

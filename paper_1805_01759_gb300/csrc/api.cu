@@ -288,7 +288,7 @@ size_t bpdn_solve_workspace_bytes(bpdn_op_t h, int64_t P, const bpdn_options *op
     (void)h;
     (void)P;
     (void)opt;
-    return 256;  // one 64-bit work counter, padded
+    return 256;  // a 64-bit work counter and an error word, padded
 }
 
 static int check_solve_buffers(const OpHandle *op, const void *d_g, int64_t P, const float *d_lambda,
@@ -333,17 +333,19 @@ int bpdn_solve(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda,
         return set_error(BPDN_EALIGN, "solve workspace must be 256-byte aligned");
     if (opt->refit && d_support && !aligned(d_support, 4))
         return set_error(BPDN_EALIGN, "support must be 4-byte aligned");
-    if (opt->precision != 0)
-        return set_error(BPDN_EINVAL, "precision 1 (BF16) is not available in this build");
     if (op->Lpad > 512)
-        return set_error(BPDN_ESIZE, "L = %d: the FP32 iteration kernel handles L <= 512", op->L);
+        return set_error(BPDN_ESIZE, "L = %d: the iteration kernels handle L <= 512", op->L);
     int dev = op->device;
     if ((int)rbpg_smem_bytes(*op) > max_smem_optin(dev))
         return set_error(BPDN_ESIZE, "N = %d, L = %d needs %zu bytes of shared memory (> %d)",
                          op->N, op->L, rbpg_smem_bytes(*op), max_smem_optin(dev));
+    if (opt->precision == 1 && !rbpg_tc_supported(*op, max_smem_optin(dev)))
+        return set_error(BPDN_ESIZE, "precision 1 (BF16 tensor cores) needs 2N <= 64 and L <= 512 "
+                         "(N = %d, L = %d)", op->N, op->L);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     unsigned long long *counter = (unsigned long long *)d_workspace;
-    rc = check_cuda(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s), "reset work counter");
+    // work counter (8 bytes) and the kernel's error word (4 bytes)
+    rc = check_cuda(cudaMemsetAsync(counter, 0, 16, s), "reset work counter");
     if (rc)
         return rc;
     SolveLaunch a;
@@ -363,7 +365,10 @@ int bpdn_solve(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda,
     a.alpha0 = (float)(opt->alpha0_scale / (2.0 * op->N));
     a.max_bt = opt->max_bt;
     a.precision = opt->precision;
-    rc = check_cuda(launch_rbpg(*op, a, num_sms(dev), s), "iteration kernel");
+    a.err = (int *)((char *)d_workspace + 8);
+    rc = check_cuda(opt->precision == 1 ? launch_rbpg_tc(*op, a, num_sms(dev), s)
+                                        : launch_rbpg(*op, a, num_sms(dev), s),
+                    "iteration kernel");
     if (rc)
         return rc;
     if (opt->refit) {

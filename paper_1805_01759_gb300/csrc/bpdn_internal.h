@@ -62,9 +62,13 @@ struct SolveLaunch {
     float alpha0;
     int max_bt;
     int precision;
+    int *err;  // set to 1 if a bounded wait ran out (may be NULL)
 };
 cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
 size_t rbpg_smem_bytes(const OpHandle &op);
+// the BF16 tensor-core variant: 2N <= 64 and L <= 512
+bool rbpg_tc_supported(const OpHandle &op, int max_smem);
+cudaError_t launch_rbpg_tc(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
 
 struct RefitLaunch {
     const float2 *g;

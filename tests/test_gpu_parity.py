@@ -87,12 +87,14 @@ def test_first_iterations_match_algorithm_1(api, small, k):
     assert checked >= (100 if k <= 3 else 50), checked
 
 
-def test_solve_refit_small_workload(api, small, small_oracle):
-    """Full path (Algorithm 1 + FP64 refit) against the exact minimiser, N=25, L=200, P=256."""
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_refit_small_workload(api, small, small_oracle, precision):
+    """Full path (Algorithm 1 + FP64 refit) against the exact minimiser, N=25, L=200, P=256,
+    with the gradient contraction in FP32 (precision 0) or BF16 tensor cores (precision 1)."""
     A, ref = small_oracle
     op = api.Operator.from_geometry(small.geom)
     g = torch.from_numpy(small.g).cuda()
-    res = api.solve(op, g, small.lam)
+    res = api.solve(op, g, small.lam, precision=precision)
     x = res.x.cpu().numpy().astype(np.complex128)
     st = res.status.cpu().numpy()
     cert = (st & 64) != 0
@@ -162,16 +164,55 @@ def test_refit_standalone_on_exact_support(api, small, small_oracle):
     assert _rel(x, ref["x"]).max() <= 1e-6
 
 
-def test_bitwise_deterministic_across_runs(api):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_bitwise_deterministic_across_runs(api, precision):
     """Slot assignment depends on timing; the arithmetic of a pixel must not: two solves
     of the same inputs give identical bits (patch workload, enough pixels to refill slots)."""
     st = synth.workload_patch(P=4096, seed=2)
     op = api.Operator.from_geometry(st.geom)
     g = torch.from_numpy(st.g).cuda()
-    r1 = api.solve(op, g, st.lam, max_iter=120)
-    r2 = api.solve(op, g, st.lam, max_iter=120)
+    r1 = api.solve(op, g, st.lam, max_iter=120, precision=precision)
+    r2 = api.solve(op, g, st.lam, max_iter=120, precision=precision)
     torch.cuda.synchronize()
     assert torch.equal(r1.status, r2.status)
     assert torch.equal(r1.iters, r2.iters)
     assert torch.equal(r1.nbt, r2.nbt)
     assert torch.equal(torch.view_as_real(r1.x), torch.view_as_real(r2.x))
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_bf16_first_iterations(api, small, k):
+    """Algorithm 1 with the gradient from BF16 operands (FP32 accumulation) against the
+    FP64 oracle after k iterations.  BF16 keeps 8 significant bits (unit roundoff 2^-9);
+    a gradient entry sums 2N = 50 products of two rounded operands, so its relative
+    error is a few 1e-3, and prox entries within that distance of the threshold may
+    switch on or off with a modulus of the same order.  Bounds on the relative error
+    ||x - x_oracle|| / ||x_oracle|| over the nonzero pixels: median 1e-2, 90th
+    percentile 3e-2."""
+    A = oracle.operator(small.geom)
+    op = api.Operator.from_geometry(small.geom)
+    g = torch.from_numpy(small.g).cuda()
+    res = api.solve(op, g, small.lam, max_iter=k, tol=0.0, refit=0, precision=1)
+    x = res.x.cpu().numpy()
+    errs = []
+    for p in range(small.g.shape[0]):
+        r = oracle.rbpg(A, small.g[p], small.lam, max_iter=k, tol=0.0)
+        nr = np.linalg.norm(r["x"])
+        if nr == 0:
+            continue
+        errs.append(np.linalg.norm(x[p] - r["x"]) / nr)
+    errs = np.array(errs)
+    assert errs.size >= 100
+    assert np.median(errs) <= 1e-2, np.median(errs)
+    assert np.percentile(errs, 90) <= 3e-2, np.percentile(errs, 90)
+
+
+def test_bf16_rejects_unsupported_sizes(api):
+    """The tensor-core path holds 2N <= 64 contraction terms; larger N is refused up front."""
+    from paper_1805_01759_gb300 import _lib
+    geom = synth.make_geometry(np.random.default_rng(0), 40, 100)
+    op = api.Operator.from_geometry(geom)
+    g = torch.zeros((4, 40), dtype=torch.complex64, device="cuda")
+    with pytest.raises(_lib.BPDNError) as ei:
+        api.solve(op, g, 1.0, precision=1)
+    assert ei.value.code == -3
