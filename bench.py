@@ -184,20 +184,23 @@ def _kernel_hash(name: str) -> str:
     return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
 
-def _traffic_per_launch(pixel_iters: float, path_name: str) -> float | None:
-    """DRAM bytes of one iteration-kernel launch from the committed ncu counters, scaled
-    by the pixel-iterations it processed -- only while the kernel source is unchanged."""
+def _traffic_per_launch(pixels: int, path_name: str) -> float | None:
+    """DRAM bytes of one iteration-kernel launch from the committed ncu counters
+    (profiles/counters_<path>.txt, taken on a smaller patch), scaled by the pixels the
+    launch processes -- the traffic is the per-pixel read of g and write of x -- and
+    only while the kernel source is the one the counters were taken on."""
     src = "rbpg_tc.cu" if path_name == "bf16" else "rbpg.cu"
-    path = os.path.join(ROOT, "profiles", f"counters_{path_name}.json")
+    path = os.path.join(ROOT, "profiles", f"counters_{path_name}.txt")
     if not os.path.exists(path):
         return None
-    try:
-        rec = json.load(open(path))
-    except ValueError:
+    rec = {}
+    for line in open(path):
+        parts = line.split()
+        if len(parts) == 2 and not line.startswith("#"):
+            rec[parts[0]] = parts[1]
+    if rec.get("kernel_sha256_16") != _kernel_hash(src) or "dram_bytes_per_pixel" not in rec:
         return None
-    if rec.get("kernel_sha256_16") != _kernel_hash(src):
-        return None
-    return float(rec["dram_bytes_per_pixel_iter"]) * pixel_iters
+    return float(rec["dram_bytes_per_pixel"]) * pixels
 
 
 def cpu_baseline_leg(sample: int) -> dict:
@@ -397,7 +400,7 @@ def run_ours(args) -> None:
     # work is the dense gradient contraction 8 N L per pixel-iteration
     rbpg_avg_s = statistics.mean(head_tm["rbpg_ms"]) / 1e3
     achieved = head_iters * 8.0 * N * L / rbpg_avg_s / 1e12
-    traffic = _traffic_per_launch(head_iters, head)
+    traffic = _traffic_per_launch(P, head)
 
     if rank != 0:
         return
