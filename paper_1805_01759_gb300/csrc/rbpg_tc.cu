@@ -1,21 +1,33 @@
 // Persistent iteration kernel with the gradient contraction on the tensor cores:
 // Algorithm 1 (RBPG with backtracking) for many pixels that share one operator,
 // with sum_n conj(A_nl) r_n computed by tcgen05 MMAs from BF16 operands into FP32
-// accumulators in tensor memory; everything else (iterate, prox, line search,
-// accept and stopping tests, A xbar) stays in FP32 exactly as in the CUDA-core
-// kernel (rbpg.cu).
+// accumulators in tensor memory; the iterate, prox, line search (Eq. 15), accept
+// and stopping tests and A xbar stay in FP32.
 //
-// The contraction, per group of 8 pixel slots and per 128-row tile of the grid:
-//   D_re[l, p] = sum_k Aop_re[l, k] R[p, k],   D_im[l, p] = sum_k Aop_im[l, k] R[p, k]
-// with K = 64 (2N <= 64, zero padded), R[p, :] = (Re r_p, Im r_p) in BF16 written by the
-// decision phase into shared memory (canonical K-major layout, no swizzle), and the
-// constant operator rows
-//   Aop_re[l, :] = ( Re A[:, l],  Im A[:, l]),   Aop_im[l, :] = (-Im A[:, l], Re A[:, l])
-// in BF16 held in tensor memory for the whole launch.  M = 128, N = 16 (rows 8..15 of
-// R are zero).  One thread per group issues the MMAs and commits them to the group's
-// mbarrier; every thread then reads its own row (TMEM lane = l mod 128) with
-// tcgen05.ld.  Warps are interleaved between groups four at a time so that the warp
-// holding rows 32q..32q+31 of a tile has index = q mod 4, as tensor-memory access needs.
+// Contraction, per group of 8 pixel slots and per 128-row tile of the grid:
+//   D[l, j] = sum_k Aop[l, k] B[j, k],  K = 64 (2N <= 64, zero padded), N = 16,
+// with the constant operator rows Aop[l, :] = (Re A[:, l], Im A[:, l]) (BF16, in
+// tensor memory for the whole launch) and the residual rows
+//   B[p, :] = (Re r_p, Im r_p),  B[8 + p, :] = (Im r_p, -Re r_p)     (BF16, shared memory)
+// so that D[l, p] = Re sum_n conj(A_nl) r_n and D[l, 8 + p] = Im sum_n conj(A_nl) r_n.
+//
+// Per-pixel state lives in tensor memory as well: thread l keeps x^k in registers and
+// x^{k-1}, xbar in its own tensor-memory lane.  One sweep of a group:
+//   transition  apply the previous decisions (x^{k-1} <- x^k, x^k <- xbar, write out
+//               finished pixels, zero refilled slots) while the MMAs run;
+//   C           wait for the MMAs, read the gradient, prox (Eq. 12) per slot, partial
+//               sums over the warp's 32 grid points and the warp's share of A xbar
+//               (ascending l over the nonzeros the ballot finds);
+//   DE          one warp per slot: A xbar and the sums over warps in a fixed order,
+//               Eq. 15, monotone accept, stopping test, next residual r = A y - g in
+//               N space, and the refill of finished slots from the work counter.
+// A slot whose step fails Eq. 15 runs the next sweep with the smaller step and the
+// same residual (the MMAs recompute the same gradient).  Two group barriers per sweep.
+//
+// Warps are assigned to (group, tile, lane quadrant) so that a warp only touches the
+// tensor-memory lanes 32 (w mod 4) .. 32 (w mod 4) + 31 it may access; the partial last
+// tile of group g sits at quadrants s_g .. (the operator rows are duplicated there), so
+// two groups of L = 416 take 26 warps.
 //
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -27,33 +39,35 @@ namespace bpdn {
 
 namespace {
 
-constexpr int TPG = 8;          // pixel slots per group
-constexpr int kMaxGroups = 2;   // groups per CTA (named barriers 1..kMaxGroups)
-constexpr int kMaxThreads = 928;  // 29 warps: two groups of L = 416 interleaved by 4 warps
-constexpr int kK = 64;          // contraction length 2N padded to a multiple of 16
-constexpr int kTmemCols = 512;  // D: 128 columns per group; operator rows: 256 columns
-constexpr int kSparseMax = 24;  // A xbar by gathering when xbar has at most this many nonzeros
-constexpr int kChunks = 4;      // ranges of l per slot in the dense A xbar pass (fixed, so the
-                                // summation order depends on nothing but the pixel)
+constexpr int TPG = 8;           // pixel slots per group
+constexpr int kMaxGroups = 2;    // groups per CTA (named barriers 1..kMaxGroups)
+constexpr int kMaxThreads = 832; // 26 warps: two groups of L = 416
+constexpr int kK = 64;           // contraction length 2N padded to a multiple of 16
+constexpr int kTmemCols = 512;
+constexpr int kColAop = 0;       // operator rows: 32 columns per tile
+constexpr int kColD = 128;       // + 64 g: gradient, 16 columns per tile
+constexpr int kColXp = 256;      // + 64 g: x^{k-1}, 16 columns per tile (slot p at 2p, 2p+1)
+constexpr int kColXb = 384;      // + 64 g: xbar
+constexpr int kMaxNW = 16;       // warps (32-point blocks of the grid) per group: Lpad <= 512
 
-// slot flags
-constexpr int F_ACTIVE = 1, F_ACC = 2, F_FIN = 4;
+// transition bits, applied at the start of a sweep
+constexpr int T_ACTIVE = 1;  // the slot holds a pixel during this sweep
+constexpr int T_ACC = 2;     // x^k <- xbar (the last evaluation was accepted)
+constexpr int T_SHIFT = 4;   // x^{k-1} <- x^k (an iteration ended)
+constexpr int T_OUT = 8;     // write x^k (after T_ACC) to the output row of pix_out
+constexpr int T_RESET = 16;  // x^k = x^{k-1} = 0: a new pixel starts in this sweep
 
 struct SlotState {
-    long long pix[TPG];
-    int k[TPG], nbt[TPG], nbt_it[TPG], status[TPG], nnz[TPG], flags[TPG];
-    int need[2][TPG];  // [iteration parity][slot]: evaluate the slot in this sweep / retry round
-    int cnt[2][TPG];   // [sweep parity][slot]: nonzeros of xbar
-    int dense[TPG];    // slots whose A xbar comes from the dense pass this sweep
+    long long pix[TPG];      // pixel in the slot, -1 when none
+    long long pix_out[TPG];  // pixel whose x the next transition writes out
+    float4 par[TPG];         // (beta, 2 alpha, alpha lambda, transition bits)
     float alpha[TPG], Fx[TPG], lam[TPG];
-    float4 par[TPG];   // (beta, 2 alpha, alpha lambda, unused)
-    int retry[3];      // by retry round mod 3: reset two barriers after its last read
-    int ndense, nfin, nactive;
+    int k[TPG], nbt[TPG], nbt_it[TPG], status[TPG], nnz[TPG];
 };
 
-// shared-memory layout: A once, then one block of arrays per group
+// shared-memory layout: A^T once, then one block per group
 struct GroupLayout {
-    size_t Bop, mbar, Xb, Xp, mask, G, Ax, Axp, Ay, red, part, st, bytes;
+    size_t Bop, mbar, G, Ax, Axp, Ay, mask, red, part, st, bytes;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -63,23 +77,90 @@ __host__ __device__ inline GroupLayout group_layout(int N, int Lpad)
     GroupLayout s;
     const int NW = Lpad / 32;
     size_t o = 0;
-    s.Bop = o;  o = align16(o + 16 * kK * 2);   // R: 16 rows x K bf16, core-matrix layout
+    s.Bop = o;  o = align16(o + 16 * kK * 2);  // B: 16 rows x K bf16, core-matrix layout
     s.mbar = o; o = align16(o + 8);
-    s.Xb = o;   o = align16(o + sizeof(float2) * (size_t)TPG * Lpad);
-    s.Xp = o;   o = align16(o + sizeof(float2) * (size_t)TPG * Lpad);
-    s.mask = o; o = align16(o + sizeof(uint32_t) * (size_t)TPG * NW);
     s.G = o;    o = align16(o + sizeof(float2) * (size_t)TPG * N);
     s.Ax = o;   o = align16(o + sizeof(float2) * (size_t)TPG * N);
     s.Axp = o;  o = align16(o + sizeof(float2) * (size_t)TPG * N);
     s.Ay = o;   o = align16(o + sizeof(float2) * (size_t)TPG * N);
-    s.red = o;  o = align16(o + sizeof(float) * (size_t)NW * TPG * 4);
-    s.part = o; o = align16(o + sizeof(float2) * (size_t)TPG * kChunks * N);
+    s.mask = o; o = align16(o + sizeof(uint32_t) * (size_t)TPG * NW);
+    s.red = o;  o = align16(o + sizeof(float4) * (size_t)NW * TPG);
+    s.part = o; o = align16(o + sizeof(float2) * (size_t)TPG * NW * N);
     s.st = o;   o = align16(o + sizeof(SlotState));
     s.bytes = o;
     return s;
 }
 
-__host__ __device__ inline size_t a_bytes(int N, int lda) { return align16(sizeof(float2) * (size_t)N * lda); }
+// A^T as float2 [Lpad][N]: lanes n of a warp read one grid point's column without conflicts
+__host__ __device__ inline size_t at_bytes(int N, int Lpad) { return align16(sizeof(float2) * (size_t)N * Lpad); }
+
+// ---- warp roles ----
+// Tiles T = ceil(Lpad / 128); the last one holds qlast blocks of 32 grid points.  Group g
+// places the blocks of a partial last tile at quadrants s_g .. s_g + qlast - 1.
+struct TileShape {
+    int T, F, qlast, partial;  // tiles, full tiles, blocks in the last tile, has a partial tile
+};
+
+__host__ __device__ inline TileShape tile_shape(int Lpad)
+{
+    TileShape s;
+    s.T = (Lpad + 127) / 128;
+    s.qlast = (Lpad - 128 * (s.T - 1)) / 32;
+    s.partial = s.qlast < 4;
+    s.F = s.partial ? s.T - 1 : s.T;
+    return s;
+}
+
+__host__ __device__ inline int partial_start(const TileShape &s, int G, int g)
+{
+    return (G * s.qlast <= 4) ? g * s.qlast : 0;
+}
+
+// role of warp w: group, block of 32 grid points (l = 32 blk + lane) and tile; false = idle
+__host__ __device__ inline bool warp_role(int w, int G, int Lpad, int *grp, int *blk, int *tile)
+{
+    const TileShape s = tile_shape(Lpad);
+    const int q = w & 3, i = w >> 2;
+    if (i < G * s.F) {
+        *grp = i / s.F;
+        *tile = i % s.F;
+        *blk = 4 * (*tile) + q;
+        return true;
+    }
+    if (!s.partial)
+        return false;
+    int j = i - G * s.F;
+    for (int g = 0; g < G; ++g) {
+        const int s0 = partial_start(s, G, g);
+        if (q >= s0 && q < s0 + s.qlast) {
+            if (j == 0) {
+                *grp = g;
+                *tile = s.T - 1;
+                *blk = 4 * (s.T - 1) + (q - s0);
+                return true;
+            }
+            --j;
+        }
+    }
+    return false;
+}
+
+int warps_for(int Lpad, int G)
+{
+    const TileShape s = tile_shape(Lpad);
+    int W = 0;
+    for (int q = 0; q < 4; ++q) {
+        int n = G * s.F;
+        if (s.partial)
+            for (int g = 0; g < G; ++g) {
+                const int s0 = partial_start(s, G, g);
+                n += (q >= s0 && q < s0 + s.qlast) ? 1 : 0;
+            }
+        if (n > 0 && 4 * (n - 1) + q + 1 > W)
+            W = 4 * (n - 1) + q + 1;
+    }
+    return W;
+}
 
 struct Params {
     const float *A_re, *A_im;  // global planar tables [N][lda]
@@ -181,7 +262,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
     return false;
 }
 
-// 8 consecutive FP32 columns of this warp's 32 tensor-memory lanes
+// tensor-memory loads and stores of this warp's 32 lanes, consecutive 32-bit columns
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4])
+{
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 {
     uint32_t r[8];
@@ -194,19 +286,34 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
         v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+__device__ __forceinline__ void tmem_st8u(uint32_t taddr, const uint32_t (&v)[8])
 {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
-        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
-        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]));
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
 }
 
-// R row p (BF16): (Re r, Im r) at k = n and k = N + n
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8])
+{
+    uint32_t u[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        u[i] = __float_as_uint(v[i]);
+    tmem_st8u(taddr, u);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// residual row p of B and its rotated copy (row 8 + p), BF16
 __device__ __forceinline__ void put_r(unsigned char *bop, int p, int n, int N, float re, float im)
 {
-    *(__nv_bfloat16 *)(bop + kmaj_off(p, n)) = __float2bfloat16_rn(re);
-    *(__nv_bfloat16 *)(bop + kmaj_off(p, N + n)) = __float2bfloat16_rn(im);
+    const __nv_bfloat16 bre = __float2bfloat16_rn(re), bim = __float2bfloat16_rn(im);
+    const __nv_bfloat16 nre = __float2bfloat16_rn(-re);
+    *(__nv_bfloat16 *)(bop + kmaj_off(p, n)) = bre;
+    *(__nv_bfloat16 *)(bop + kmaj_off(p, N + n)) = bim;
+    *(__nv_bfloat16 *)(bop + kmaj_off(TPG + p, n)) = bim;
+    *(__nv_bfloat16 *)(bop + kmaj_off(TPG + p, N + n)) = nre;
 }
 
 __global__ void __launch_bounds__(kMaxThreads, 1) k_rbpg_bf16(Params prm, int G)
@@ -214,51 +321,35 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_rbpg_bf16(Params prm, int G)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint32_t s_tmem;
     const int N = prm.N, L = prm.L, Lpad = prm.Lpad, lda = prm.lda;
-    const int NW = Lpad / 32;  // warps per group
-    // warp w = 4 (t G + g) + q: tile t of group g, lane quadrant q
+    const int NW = Lpad / 32;  // warps (blocks of 32 grid points) per group
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q4 = w & 3, tg = w >> 2;
-    const int tile = tg / G, grp = tg - tile * G;
-    const int tid = 128 * tile + 32 * q4 + lane;  // grid index l owned by this thread
-    const bool live = tid < Lpad;                 // warps of the last tile beyond Lpad idle
-    const int warp = tid >> 5;                    // warp within the group (l / 32)
+    const int q4 = w & 3;
+    int grp = 0, blk = 0, tile = 0;
+    const bool live = warp_role(w, G, Lpad, &grp, &blk, &tile);
+    const int l = 32 * blk + lane;  // grid index owned by this thread
     const SolveLaunch &a = prm.a;
-    float2 *sA = (float2 *)smem_raw;  // [N][lda] (re, im)
+    float2 *sAT = (float2 *)smem_raw;  // [Lpad][N]
     const GroupLayout lay = group_layout(N, Lpad);
-    unsigned char *gbase = smem_raw + a_bytes(N, lda) + (size_t)grp * lay.bytes;
-    unsigned char *sBop = gbase + lay.Bop;           // R of this group (BF16 operand)
+    unsigned char *gbase = smem_raw + at_bytes(N, Lpad) + (size_t)grp * lay.bytes;
+    unsigned char *sBop = gbase + lay.Bop;
     const uint32_t mbar = smem_u32(gbase + lay.mbar);
-    float2 *sXb = (float2 *)(gbase + lay.Xb);        // [TPG][Lpad]
-    float2 *sXp = (float2 *)(gbase + lay.Xp);        // [TPG][Lpad]
-    uint32_t *sMask = (uint32_t *)(gbase + lay.mask);  // [TPG][NW]
-    float2 *sG = (float2 *)(gbase + lay.G);          // [TPG][N]
+    float2 *sG = (float2 *)(gbase + lay.G);  // [TPG][N]
     float2 *sAx = (float2 *)(gbase + lay.Ax);
     float2 *sAxp = (float2 *)(gbase + lay.Axp);
     float2 *sAy = (float2 *)(gbase + lay.Ay);
-    float *sRed = (float *)(gbase + lay.red);        // [NW][TPG][4]
-    float2 *sPart = (float2 *)(gbase + lay.part);    // [TPG][kChunks][N]
+    uint32_t *sMask = (uint32_t *)(gbase + lay.mask);  // [TPG][NW] ballots of xbar != 0
+    float4 *sRed = (float4 *)(gbase + lay.red);        // [NW][TPG] (dd, l1, dx, xn)
+    float2 *sPart = (float2 *)(gbase + lay.part);      // [TPG][NW][N] A xbar over one block
     SlotState &S = *(SlotState *)(gbase + lay.st);
 
-    for (int i = threadIdx.x; i < N * lda; i += blockDim.x)
-        sA[i] = make_float2(prm.A_re[i], prm.A_im[i]);
-    if (live) {
-        for (int i = tid; i < TPG * Lpad; i += Lpad)
-            sXp[i] = make_float2(0.f, 0.f);
-        for (int i = tid; i < 16 * kK * 2 / 4; i += Lpad)
-            ((uint32_t *)sBop)[i] = 0u;  // rows 8..15 of R stay zero
-        if (tid < TPG) {
-            S.flags[tid] = F_FIN;  // every slot starts empty and asks for a pixel
-            S.need[0][tid] = 0;
-            S.need[1][tid] = 0;
-            S.cnt[0][tid] = 0;
-            S.cnt[1][tid] = 0;
-            S.pix[tid] = -1;
-        }
-        if (tid == 0) {
-            S.retry[0] = S.retry[1] = S.retry[2] = 0;
-            S.nfin = TPG;
-            S.nactive = 0;
-            S.ndense = 0;
+    for (int i = threadIdx.x; i < Lpad * N; i += blockDim.x) {
+        const int ll = i / N, n = i - (i / N) * N;
+        sAT[i] = make_float2(prm.A_re[n * lda + ll], prm.A_im[n * lda + ll]);
+    }
+    if (live && blk == 0) {
+        for (int i = lane; i < 16 * kK * 2 / 4; i += 32)
+            ((uint32_t *)sBop)[i] = 0u;  // K padding of B stays zero
+        if (lane == 0) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar));
             asm volatile("fence.mbarrier_init.release.cluster;");
         }
@@ -272,457 +363,382 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_rbpg_bf16(Params prm, int G)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    // operator rows of this thread's grid index into tensor memory (group 0 writes them
-    // for both groups): columns 256 + 64 tile (+32 for the imaginary-output rows)
-    if (live && grp == 0) {
-        const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 256 + 64 * tile;
-        // Aop_re row at column 0, Aop_im row at column 32; 16 columns (32 elements) at a time
-        for (int part = 0; part < 4; ++part) {
-            const int im_row = part >> 1, c0 = 16 * (part & 1);
-            uint32_t v[16];
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * q4) << 16);
+    const int T = (Lpad + 127) / 128;
+    const uint32_t taD = lane_base + kColD + 64 * grp + 16 * tile;
+    const uint32_t taXp = lane_base + kColXp + 64 * grp + 16 * tile;
+    const uint32_t taXb = lane_base + kColXb + 64 * grp + 16 * tile;
+    if (live) {
+        // operator rows of this thread's grid index into its tensor-memory lane: full
+        // tiles by group 0, the partial tile by every group at its own quadrants
+        if (grp == 0 || tile == T - 1) {
+            const uint32_t ta = lane_base + kColAop + 32 * tile;
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                float e2[2];
+            for (int part = 0; part < 4; ++part) {
+                uint32_t v[8];
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int k = 2 * (c0 + c) + e;
-                    float val = 0.f;
-                    if (k < N)
-                        val = im_row ? -sA[k * lda + tid].y : sA[k * lda + tid].x;
-                    else if (k < 2 * N)
-                        val = im_row ? sA[(k - N) * lda + tid].x : sA[(k - N) * lda + tid].y;
-                    e2[e] = val;
+                for (int c = 0; c < 8; ++c) {
+                    float e2[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int k = 2 * (8 * part + c) + e;
+                        float val = 0.f;
+                        if (k < N)
+                            val = sAT[l * N + k].x;
+                        else if (k < 2 * N)
+                            val = sAT[l * N + k - N].y;
+                        e2[e] = val;
+                    }
+                    v[c] = pack_bf16(e2[0], e2[1]);
                 }
-                v[c] = pack_bf16(e2[0], e2[1]);
+                tmem_st8u(ta + 8 * part, v);
             }
-            tmem_st16(ta + 32 * im_row + c0, v);
         }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        tmem_st8(taXp, z);
+        tmem_st8(taXp + 8, z);
+        tmem_st8(taXb, z);
+        tmem_st8(taXb + 8, z);
+        tmem_wait_st();
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
-    __syncthreads();  // A, operator rows and R padding complete for every group
-    tc_fence_after();
+    __syncthreads();  // operator rows of every tile are in place before any group's MMA
     if (!live) {
-        // idle warp of the last tile: wait for the groups to finish, then leave
+        // idle warp: wait for the groups to finish, then leave
         __syncthreads();
         return;
+    }
+
+    const float alpha0 = a.alpha0;
+    const float tol2 = a.tol * a.tol;
+
+    // refill slot p from the work counter (one warp); returns the transition bits
+    auto refill = [&](int p) -> int {
+        long long q;
+        for (;;) {
+            if (lane == 0)
+                q = (long long)atomicAdd(a.counter, 1ULL);
+            q = __shfl_sync(0xffffffffu, q, 0);
+            if (q >= a.P) {
+                q = -1;
+                break;
+            }
+            const float2 *gq = a.g + (size_t)q * N;
+            const float2 g0 = (lane < N) ? gq[lane] : make_float2(0.f, 0.f);
+            const bool allfin = __all_sync(0xffffffffu, isfinite(g0.x) && isfinite(g0.y));
+            if (!allfin || a.max_iter <= 0) {
+                // non-finite g (or no iteration allowed): x = 0 at once
+                float2 *xq = a.x + (size_t)q * L;
+                for (int ll = lane; ll < L; ll += 32)
+                    xq[ll] = make_float2(0.f, 0.f);
+                if (lane == 0) {
+                    a.status[q] = allfin ? (BPDN_PX_NOT_CONVERGED | BPDN_PX_ZERO_SOLUTION) : BPDN_PX_NONFINITE;
+                    a.iters[q] = 0;
+                    if (a.nbt)
+                        a.nbt[q] = 0;
+                    if (a.nsupp)
+                        a.nsupp[q] = 0;
+                }
+                continue;
+            }
+            // x^0 = x^{-1} = 0: A y = 0 and r = -g for the first iteration
+            if (lane < N) {
+                sG[p * N + lane] = g0;
+                sAx[p * N + lane] = make_float2(0.f, 0.f);
+                sAxp[p * N + lane] = make_float2(0.f, 0.f);
+                sAy[p * N + lane] = make_float2(0.f, 0.f);
+                put_r(sBop, p, lane, N, -g0.x, -g0.y);
+            }
+            float gg2 = g0.x * g0.x + g0.y * g0.y;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1)
+                gg2 += __shfl_xor_sync(0xffffffffu, gg2, off);
+            if (lane == 0) {
+                const float lam = a.lam_pp ? a.lam[q] : a.lam[0];
+                S.k[p] = 1;
+                S.alpha[p] = alpha0;
+                S.Fx[p] = gg2;  // F(0) = ||g||^2
+                S.lam[p] = lam;
+                S.nbt[p] = 0;
+                S.nbt_it[p] = 0;
+                S.status[p] = 0;
+                S.nnz[p] = 0;
+                // (k-2)/(k+1) at k = 1 multiplies x - x_prev = 0
+                S.par[p] = make_float4(-0.5f, 2.f * alpha0, alpha0 * lam, 0.f);
+            }
+            break;
+        }
+        if (lane == 0)
+            S.pix[p] = q;
+        return (q >= 0) ? (T_ACTIVE | T_RESET) : 0;
+    };
+
+    // prologue: fill every slot
+    for (int p = blk; p < TPG; p += NW) {
+        const int bits = refill(p);
+        __syncwarp();
+        if (lane == 0)
+            S.par[p].w = __int_as_float(bits);
     }
     float2 x[TPG];
 #pragma unroll
     for (int p = 0; p < TPG; ++p)
         x[p] = make_float2(0.f, 0.f);
     uint32_t mma_phase = 0;
-    // issue this group's gradient MMAs (one thread per group)
-    auto issue_mma = [&]() {
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t b0 = smem_u32(sBop);
-            const int tiles = (Lpad + 127) / 128;
-            for (int t = 0; t < tiles; ++t)
-                for (int half = 0; half < 2; ++half) {
-                    const uint32_t d = tmem + 128 * grp + 32 * t + 16 * half;
-                    const uint32_t arow = tmem + 256 + 64 * t + 32 * half;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    group_sync(grp, 32 * NW);
+
+    for (;;) {
+        tc_fence_after();
+        // ---------------- issue the gradient MMAs; transition -------------------------------
+        int any = 0;
 #pragma unroll
-                    for (int j = 0; j < kK / 16; ++j)
-                        tc_mma_ts(d, arow + 8 * j, smem_desc(b0 + 256 * j, 128, (kK / 8) * 128), j > 0);
-                }
+        for (int p = 0; p < TPG; ++p)
+            any |= __float_as_int(S.par[p].w);
+        const bool running = (any & T_ACTIVE) != 0;
+        if (running && blk == 0 && lane == 0) {
+            const uint32_t b0 = smem_u32(sBop);
+            for (int t = 0; t < T; ++t) {
+                const uint32_t d = tmem + kColD + 64 * grp + 16 * t;
+                const uint32_t arow = tmem + kColAop + 32 * t;
+#pragma unroll
+                for (int j = 0; j < kK / 16; ++j)
+                    tc_mma_ts(d, arow + 8 * j, smem_desc(b0 + 256 * j, 128, (kK / 8) * 128), j > 0);
+            }
             tc_commit(mbar);
         }
-    };
+        if (any & (T_ACC | T_SHIFT | T_OUT | T_RESET)) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float xb[8], xp[8];
+                tmem_ld8(taXb + 8 * h, xb);
+                tmem_ld8(taXp + 8 * h, xp);
+                tmem_wait_ld();
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) {
+                    const int p = 4 * h + pp;
+                    const int b = __float_as_int(S.par[p].w);
+                    if (b & T_SHIFT) {
+                        xp[2 * pp] = x[p].x;
+                        xp[2 * pp + 1] = x[p].y;
+                    }
+                    if (b & T_ACC)
+                        x[p] = make_float2(xb[2 * pp], xb[2 * pp + 1]);
+                    if ((b & T_OUT) && l < L)
+                        a.x[(size_t)S.pix_out[p] * L + l] = x[p];
+                    if (b & T_RESET) {
+                        x[p] = make_float2(0.f, 0.f);
+                        xp[2 * pp] = 0.f;
+                        xp[2 * pp + 1] = 0.f;
+                    }
+                }
+                tmem_st8(taXp + 8 * h, xp);
+            }
+            tmem_wait_st();
+        }
+        if (!running)
+            break;
 
-    const float alpha0 = a.alpha0;
-    const float tol2 = a.tol * a.tol;
-    int sweep = 0;  // C-DE sweeps so far (iterations and step-size retries)
-
-    for (int iter = 0;; ++iter) {
-        const int cur = iter & 1, nxt = cur ^ 1;
-        // ---------------- H: record finished pixels and refill their slots -----------
-        if (S.nfin) {
-            for (int p = warp; p < TPG; p += NW) {
-                if (!(S.flags[p] & F_FIN))
-                    continue;
-                long long q;
-                for (;;) {
+        // ---------------- C: gradient, prox, partial sums, A xbar over this block --------------
+        if (!mbar_wait(mbar, mma_phase) && a.err)
+            atomicExch(a.err, 1);
+        mma_phase ^= 1u;
+        tc_fence_after();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float gre[4], gim[4], xp[8], xbv[8];
+            tmem_ld4(taD + 4 * h, gre);
+            tmem_ld4(taD + 8 + 4 * h, gim);
+            tmem_ld8(taXp + 8 * h, xp);
+            tmem_wait_ld();
+            float part[16];
+#pragma unroll
+            for (int pp = 0; pp < 4; ++pp) {
+                const int p = 4 * h + pp;
+                float dd = 0.f, l1 = 0.f, dx = 0.f, xn = 0.f;
+                float bx = 0.f, by = 0.f;
+                const float4 par = S.par[p];  // beta, 2 alpha, tau = alpha lambda, bits
+                if (__float_as_int(par.w) & T_ACTIVE) {
+                    const float yx = fmaf(par.x, x[p].x - xp[2 * pp], x[p].x);
+                    const float yy = fmaf(par.x, x[p].y - xp[2 * pp + 1], x[p].y);
+                    const float vx = fmaf(-par.y, gre[pp], yx), vy = fmaf(-par.y, gim[pp], yy);
+                    const float m2 = fmaf(vx, vx, vy * vy);
+                    const float tau = par.z;
+                    // soft threshold (Eq. 12): scale 1 - tau / |v| where that is positive
+                    const float rs = rsqrtf(m2);
+                    const float sc = fmaf(-tau, rs, 1.f);
+                    const bool nz = sc > 0.f;
+                    if (nz) {
+                        bx = vx * sc;
+                        by = vy * sc;
+                        l1 = fmaf(m2, rs, -tau);
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, nz);
                     if (lane == 0)
-                        q = (long long)atomicAdd(a.counter, 1ULL);
-                    q = __shfl_sync(0xffffffffu, q, 0);
-                    if (q >= a.P) {
-                        q = -1;
-                        break;
-                    }
-                    const float2 *gq = a.g + (size_t)q * N;
-                    const float2 g0 = (lane < N) ? gq[lane] : make_float2(0.f, 0.f);
-                    const float2 g1 = (lane + 32 < N) ? gq[lane + 32] : make_float2(0.f, 0.f);
-                    const bool fin = isfinite(g0.x) && isfinite(g0.y) && isfinite(g1.x) && isfinite(g1.y);
-                    const bool allfin = __all_sync(0xffffffffu, fin);
-                    if (!allfin || a.max_iter <= 0) {
-                        // non-finite g (or no iteration allowed): x = 0 at once
-                        float2 *xq = a.x + (size_t)q * L;
-                        for (int l = lane; l < L; l += 32)
-                            xq[l] = make_float2(0.f, 0.f);
-                        if (lane == 0) {
-                            a.status[q] = allfin ? (BPDN_PX_NOT_CONVERGED | BPDN_PX_ZERO_SOLUTION)
-                                                 : BPDN_PX_NONFINITE;
-                            a.iters[q] = 0;
-                            if (a.nbt)
-                                a.nbt[q] = 0;
-                            if (a.nsupp)
-                                a.nsupp[q] = 0;
+                        sMask[p * NW + blk] = bal;
+                    if (bal) {
+                        // this block's share of A xbar, ascending l; lane n owns row n
+                        float2 acc = make_float2(0.f, 0.f);
+                        const float2 *arow = sAT + (size_t)(32 * blk) * N + lane;
+                        unsigned m = bal;
+                        while (m) {
+                            const int j = __ffs(m) - 1;
+                            m &= m - 1;
+                            const float xr = __shfl_sync(0xffffffffu, bx, j);
+                            const float xi = __shfl_sync(0xffffffffu, by, j);
+                            if (lane < N) {
+                                const float2 av = arow[j * N];
+                                acc.x = fmaf(av.x, xr, fmaf(-av.y, xi, acc.x));
+                                acc.y = fmaf(av.x, xi, fmaf(av.y, xr, acc.y));
+                            }
                         }
-                        continue;
+                        if (lane < N)
+                            sPart[(p * NW + blk) * N + lane] = acc;
                     }
-                    // x^0 = x^{-1} = 0: A y = 0 and r = -g for the first iteration
-                    for (int n = lane; n < N; n += 32) {
-                        const float2 gg = (n < 32) ? g0 : g1;
-                        sG[p * N + n] = gg;
-                        sAx[p * N + n] = make_float2(0.f, 0.f);
-                        sAxp[p * N + n] = make_float2(0.f, 0.f);
-                        sAy[p * N + n] = make_float2(0.f, 0.f);
-                        put_r(sBop, p, n, N, -gg.x, -gg.y);
-                    }
-                    float gg2 = g0.x * g0.x + g0.y * g0.y + g1.x * g1.x + g1.y * g1.y;
-#pragma unroll
-                    for (int off = 16; off >= 1; off >>= 1)
-                        gg2 += __shfl_xor_sync(0xffffffffu, gg2, off);
-                    if (lane == 0) {
-                        const float lam = a.lam_pp ? a.lam[q] : a.lam[0];
-                        S.k[p] = 1;
-                        S.alpha[p] = alpha0;
-                        S.Fx[p] = gg2;  // F(0) = ||g||^2
-                        S.lam[p] = lam;
-                        // (k-2)/(k+1) at k = 1 multiplies x - x_prev = 0
-                        S.par[p] = make_float4(-0.5f, 2.f * alpha0, alpha0 * lam, 0.f);
-                        S.nbt[p] = 0;
-                        S.status[p] = 0;
-                        S.nnz[p] = 0;
-                    }
-                    break;
+                    const float ex = bx - yx, ey = by - yy;
+                    dd = fmaf(ex, ex, ey * ey);
+                    const float fx = bx - x[p].x, fy = by - x[p].y;
+                    dx = fmaf(fx, fx, fy * fy);
+                    xn = fmaf(bx, bx, by * by);
                 }
-                if (lane == 0) {
-                    S.pix[p] = q;
-                    S.flags[p] = (q >= 0) ? F_ACTIVE : 0;
-                    S.need[cur][p] = (q >= 0);
-                    S.nbt_it[p] = 0;
-                }
+                part[4 * pp + 0] = dd;
+                part[4 * pp + 1] = l1;
+                part[4 * pp + 2] = dx;
+                part[4 * pp + 3] = xn;
+                xbv[2 * pp] = bx;
+                xbv[2 * pp + 1] = by;
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            group_sync(grp, Lpad);
-            if (tid == 0) {
-                int c = 0;
-                for (int p = 0; p < TPG; ++p)
-                    c += (S.flags[p] & F_ACTIVE) ? 1 : 0;
-                S.nactive = c;
-                S.nfin = 0;
-            }
-            group_sync(grp, Lpad);
-            if (S.nactive == 0)
-                break;
-            issue_mma();  // R of every slot is in place
-        }
-
-        // ---------------- B: gradient sum_n conj(A_nl) r_n for l = tid, from the MMAs -----------
-        float2 gx[TPG / 2], gy[TPG / 2];  // slot pairs (2q, 2q+1): real and imaginary parts
-        {
-            if (!mbar_wait(mbar, mma_phase) && a.err)
-                atomicExch(a.err, 1);
-            mma_phase ^= 1u;
-            tc_fence_after();
-            float vre[8], vim[8];
-            const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 128 * grp + 32 * tile;
-            tmem_ld8(ta, vre);
-            tmem_ld8(ta + 16, vim);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            tc_fence_before();
-#pragma unroll
-            for (int q = 0; q < TPG / 2; ++q) {
-                gx[q] = make_float2(vre[2 * q], vre[2 * q + 1]);
-                gy[q] = make_float2(vim[2 * q], vim[2 * q + 1]);
+            tmem_st8(taXb + 8 * h, xbv);
+            warp_transpose_reduce16(part, lane);
+            // lanes 2i, 2i+1 hold value i: slot 4h + i/4, quantity i%4
+            if ((lane & 1) == 0) {
+                const int v = lane >> 1;
+                ((float *)sRed)[(blk * TPG + 4 * h + (v >> 2)) * 4 + (v & 3)] = part[0];
             }
         }
+        tmem_wait_st();
+        tc_fence_before();
+        group_sync(grp, 32 * NW);
 
-        // ---------------- C, A xbar, DE with backtracking ----------------------------------------
-        for (int round = 0;; ++round) {
-            // C: prox, ballots, partial sums (two passes of 4 slots keep register use low)
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                float part[16];
-#pragma unroll
-                for (int pp = 0; pp < TPG / 2; ++pp) {
-                    const int p = half * (TPG / 2) + pp;
-                    float dd = 0.f, l1 = 0.f, dx = 0.f, xn = 0.f;
-                    if (S.need[cur][p]) {
-                        const float4 par = S.par[p];  // beta, 2 alpha, tau = alpha lambda
-                        const float gre = (p & 1) ? gx[p >> 1].y : gx[p >> 1].x;
-                        const float gim = (p & 1) ? gy[p >> 1].y : gy[p >> 1].x;
-                        const float2 xp = sXp[p * Lpad + tid];
-                        const float yx = fmaf(par.x, x[p].x - xp.x, x[p].x);
-                        const float yy = fmaf(par.x, x[p].y - xp.y, x[p].y);
-                        const float vx = fmaf(-par.y, gre, yx), vy = fmaf(-par.y, gim, yy);
-                        const float m2 = fmaf(vx, vx, vy * vy);
-                        const float tau = par.z;
-                        float bx = 0.f, by = 0.f;
-                        bool nz = false;
-                        if (m2 > tau * tau) {
-                            const float mag = sqrtf(m2);
-                            if (mag > tau) {
-                                const float sc = 1.f - tau / mag;
-                                bx = vx * sc;
-                                by = vy * sc;
-                                l1 = mag - tau;
-                                nz = true;
-                            }
-                        }
-                        sXb[p * Lpad + tid] = make_float2(bx, by);
-                        const unsigned bal = __ballot_sync(0xffffffffu, nz);
-                        if (lane == 0) {
-                            sMask[p * NW + warp] = bal;
-                            if (bal)
-                                atomicAdd(&S.cnt[sweep & 1][p], __popc(bal));
-                        }
-                        const float ex = bx - yx, ey = by - yy;
-                        dd = fmaf(ex, ex, ey * ey);
-                        const float fx = bx - x[p].x, fy = by - x[p].y;
-                        dx = fmaf(fx, fx, fy * fy);
-                        xn = fmaf(bx, bx, by * by);
-                    }
-                    part[4 * pp + 0] = dd;
-                    part[4 * pp + 1] = l1;
-                    part[4 * pp + 2] = dx;
-                    part[4 * pp + 3] = xn;
-                }
-                warp_transpose_reduce16(part, lane);
-                // lanes 2i, 2i+1 hold value i: slot half*4 + i/4, quantity i%4
-                if ((lane & 1) == 0) {
-                    const int v = lane >> 1;
-                    sRed[(warp * TPG + half * (TPG / 2) + (v >> 2)) * 4 + (v & 3)] = part[0];
-                }
-            }
-            if (tid == 0)
-                S.retry[(round + 1) % 3] = 0;
-            group_sync(grp, Lpad);
-
-            // which slots need the dense A xbar pass
-            if (tid == 0) {
-                int nd = 0;
-                for (int p = 0; p < TPG; ++p)
-                    if (S.need[cur][p] && S.cnt[sweep & 1][p] > kSparseMax)
-                        S.dense[nd++] = p;
-                S.ndense = nd;
-            }
-            if (tid < TPG)
-                S.cnt[(sweep + 1) & 1][tid] = 0;  // counts of the next sweep
-            group_sync(grp, Lpad);
-            const int ndense = S.ndense;
-            if (ndense) {
-                const int CH = Lpad / kChunks;  // Lpad is a multiple of 32
-                for (int it = tid; it < ndense * kChunks * N; it += Lpad) {
-                    const int jc = it / N, n = it - (it / N) * N;  // jc = j * kChunks + c
-                    const int j = jc / kChunks, c = jc - (jc / kChunks) * kChunks;
-                    const int p = S.dense[j];
-                    const float2 *xr = sXb + p * Lpad + c * CH;
-                    const float2 *ar = sA + n * lda + c * CH;
-                    float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
-                    for (int l = 0; l < CH; l += 2) {
-                        const float2 x0 = xr[l], a0 = ar[l], x1 = xr[l + 1], a1 = ar[l + 1];
-                        s0.x = fmaf(a0.x, x0.x, fmaf(-a0.y, x0.y, s0.x));
-                        s0.y = fmaf(a0.x, x0.y, fmaf(a0.y, x0.x, s0.y));
-                        s1.x = fmaf(a1.x, x1.x, fmaf(-a1.y, x1.y, s1.x));
-                        s1.y = fmaf(a1.x, x1.y, fmaf(a1.y, x1.x, s1.y));
-                    }
-                    sPart[(p * kChunks + c) * N + n] = make_float2(s0.x + s1.x, s0.y + s1.y);
-                }
-                group_sync(grp, Lpad);
-            }
-
-            // DE: one half-warp per slot (slots 2 pw, 2 pw + 1 on warp pw mod #warps)
-            for (int pw = warp; pw < TPG / 2; pw += NW) {
-                const int p = 2 * pw + (lane >> 4);
-                const int h = lane & 15;
-                const unsigned hmask = (lane < 16) ? 0x0000ffffu : 0xffff0000u;
-                if (!S.need[cur][p])
-                    continue;
-                // A xbar; lane h owns n = h + 16 j
-                float2 axb[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    axb[j] = make_float2(0.f, 0.f);
-                const bool dense = S.cnt[sweep & 1][p] > kSparseMax;
-                if (dense) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int n = h + 16 * j;
-                        if (n < N)
-#pragma unroll
-                            for (int c = 0; c < kChunks; ++c) {
-                                const float2 v = sPart[(p * kChunks + c) * N + n];
-                                axb[j].x += v.x;
-                                axb[j].y += v.y;
-                            }
-                    }
-                } else {
-                    // over the nonzeros of xbar in ascending l, four per trip
-                    for (int w = 0; w < NW; ++w) {
-                        uint32_t msk = sMask[p * NW + w];
-                        while (msk) {
-                            int lq[4];
-                            float2 xq[4];
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                lq[u] = msk ? (w * 32 + __ffs(msk) - 1) : -1;
-                                msk &= msk - 1;
-                                xq[u] = (lq[u] >= 0) ? sXb[p * Lpad + lq[u]] : make_float2(0.f, 0.f);
-                            }
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                const int n = h + 16 * j;
-                                if (n < N) {
-#pragma unroll
-                                    for (int u = 0; u < 4; ++u) {
-                                        if (lq[u] >= 0) {
-                                            const float2 av = sA[n * lda + lq[u]];
-                                            axb[j].x = fmaf(av.x, xq[u].x, fmaf(-av.y, xq[u].y, axb[j].x));
-                                            axb[j].y = fmaf(av.x, xq[u].y, fmaf(av.y, xq[u].x, axb[j].y));
-                                        }
-                                    }
-                                }
-                            }
-                        }
-                    }
-                }
-                float lhs = 0.f, res = 0.f, dd = 0.f, l1 = 0.f, dx = 0.f, xn = 0.f;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int n = h + 16 * j;
-                    if (n < N) {
-                        const float2 ay = sAy[p * N + n], gg = sG[p * N + n];
-                        const float d0 = axb[j].x - ay.x, d1 = axb[j].y - ay.y;
-                        lhs = fmaf(d0, d0, fmaf(d1, d1, lhs));
-                        const float e0 = axb[j].x - gg.x, e1 = axb[j].y - gg.y;
-                        res = fmaf(e0, e0, fmaf(e1, e1, res));
-                    }
-                }
-                if (h < NW) {
-                    const float4 rd = *(const float4 *)(sRed + (h * TPG + p) * 4);
-                    dd = rd.x;
-                    l1 = rd.y;
-                    dx = rd.z;
-                    xn = rd.w;
-                }
-#pragma unroll
-                for (int off = 8; off >= 1; off >>= 1) {
-                    lhs += __shfl_xor_sync(hmask, lhs, off);
-                    res += __shfl_xor_sync(hmask, res, off);
-                    dd += __shfl_xor_sync(hmask, dd, off);
-                    l1 += __shfl_xor_sync(hmask, l1, off);
-                    dx += __shfl_xor_sync(hmask, dx, off);
-                    xn += __shfl_xor_sync(hmask, xn, off);
-                }
-                const float al = S.alpha[p];
-                const bool bt_ok = lhs <= dd / (2.f * al);
-                if (!bt_ok && S.nbt_it[p] < a.max_bt) {
-                    // Eq. 15 failed: shrink the step and redo the prox for this slot
-                    __syncwarp(hmask);
-                    if (h == 0) {
-                        const float an = al * a.c_alpha;
-                        S.alpha[p] = an;
-                        S.par[p].y = 2.f * an;
-                        S.par[p].z = an * S.lam[p];
-                        S.nbt[p] += 1;
-                        S.nbt_it[p] += 1;
-                        atomicAdd(&S.retry[round % 3], 1);
-                    }
-                    continue;
-                }
-                const float Fb = fmaf(S.lam[p], l1, res);
-                const bool accepted = (Fb <= S.Fx[p]);
-                const bool conv = (dx <= tol2 * xn) || (dx == 0.f);
-                const int k = S.k[p];
-                const bool fin = conv || (k >= a.max_iter);
-                // N-space state: A x^{k-1} <- A x^k, A x^{k+1} <- A xbar (accepted); for the
-                // next iteration A y = A x + beta (A x - A x_prev), r = A y - g
-                const float beta_n = (float)(k - 1) / (float)(k + 2);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int n = h + 16 * j;
-                    if (n < N) {
-                        const float2 axo = sAx[p * N + n];
-                        const float2 axn = accepted ? axb[j] : axo;
-                        sAxp[p * N + n] = axo;
-                        sAx[p * N + n] = axn;
-                        if (!fin) {
-                            const float2 ay = make_float2(fmaf(beta_n, axn.x - axo.x, axn.x),
-                                                          fmaf(beta_n, axn.y - axo.y, axn.y));
-                            const float2 gg = sG[p * N + n];
-                            sAy[p * N + n] = ay;
-                            put_r(sBop, p, n, N, ay.x - gg.x, ay.y - gg.y);
-                        }
-                    }
-                }
-                __syncwarp(hmask);
-                if (h == 0) {
-                    int st = S.status[p];
-                    if (!bt_ok)
-                        st |= BPDN_PX_BT_LIMIT;
-                    int nnz = S.nnz[p];
-                    if (accepted) {
-                        S.Fx[p] = Fb;
-                        nnz = 0;
-                        for (int w = 0; w < NW; ++w)
-                            nnz += __popc(sMask[p * NW + w]);
-                        S.nnz[p] = nnz;
-                    }
-                    if (fin && !conv)
-                        st |= BPDN_PX_NOT_CONVERGED;
-                    S.status[p] = st;
-                    S.flags[p] = F_ACTIVE | (accepted ? F_ACC : 0) | (fin ? F_FIN : 0);
-                    S.need[cur][p] = 0;
-                    S.need[nxt][p] = fin ? 0 : 1;
-                    if (fin) {
-                        atomicAdd(&S.nfin, 1);
-                        const long long q = S.pix[p];
-                        a.status[q] = (nnz == 0) ? (st | BPDN_PX_ZERO_SOLUTION) : st;
-                        a.iters[q] = k;
-                        if (a.nbt)
-                            a.nbt[q] = S.nbt[p];
-                        if (a.nsupp)
-                            a.nsupp[q] = nnz;
-                    } else {
-                        S.k[p] = k + 1;
-                        S.par[p].x = beta_n;
-                        S.nbt_it[p] = 0;
-                    }
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // R rows for the MMA
-            group_sync(grp, Lpad);
-            ++sweep;
-            if (S.retry[round % 3] == 0)
-                break;
-        }
-        if (S.nfin == 0)
-            issue_mma();  // no slot to refill: the next gradient overlaps the register update
-
-        // ---------------- G: registers and outputs -------------------------------------------
-#pragma unroll
-        for (int p = 0; p < TPG; ++p) {
-            const int fl = S.flags[p];
-            if (!(fl & F_ACTIVE))
+        // ---------------- DE: one warp per slot ------------------------------------------------
+        for (int p = blk; p < TPG; p += NW) {
+            const int bits = __float_as_int(S.par[p].w);
+            if (!(bits & T_ACTIVE)) {
+                __syncwarp();
+                if (lane == 0)
+                    S.par[p].w = __int_as_float(0);
                 continue;
-            const float2 xo = x[p];
-            if (fl & F_ACC)
-                x[p] = sXb[p * Lpad + tid];
-            if (fl & F_FIN) {
-                if (tid < L)
-                    a.x[(size_t)S.pix[p] * L + tid] = x[p];
-                x[p] = make_float2(0.f, 0.f);
-                sXp[p * Lpad + tid] = make_float2(0.f, 0.f);
-            } else {
-                sXp[p * Lpad + tid] = xo;
+            }
+            // A xbar and nnz over the blocks in ascending order
+            const uint32_t mw = (lane < NW) ? sMask[p * NW + lane] : 0u;
+            const int nnz = (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(mw));
+            unsigned wm = __ballot_sync(0xffffffffu, mw != 0u);
+            float2 axb = make_float2(0.f, 0.f);
+            while (wm) {
+                const int b = __ffs(wm) - 1;
+                wm &= wm - 1;
+                if (lane < N) {
+                    const float2 v = sPart[(p * NW + b) * N + lane];
+                    axb.x += v.x;
+                    axb.y += v.y;
+                }
+            }
+            // sums over the grid: lane b < NW holds block b's partial sums
+            float4 rd = (lane < NW) ? sRed[lane * TPG + p] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float lhs = 0.f, res = 0.f;
+            float2 gg = make_float2(0.f, 0.f);
+            if (lane < N) {
+                const float2 ay = sAy[p * N + lane];
+                gg = sG[p * N + lane];
+                const float d0 = axb.x - ay.x, d1 = axb.y - ay.y;
+                lhs = fmaf(d0, d0, d1 * d1);
+                const float e0 = axb.x - gg.x, e1 = axb.y - gg.y;
+                res = fmaf(e0, e0, e1 * e1);
+            }
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                lhs += __shfl_xor_sync(0xffffffffu, lhs, off);
+                res += __shfl_xor_sync(0xffffffffu, res, off);
+                rd.x += __shfl_xor_sync(0xffffffffu, rd.x, off);
+                rd.y += __shfl_xor_sync(0xffffffffu, rd.y, off);
+                rd.z += __shfl_xor_sync(0xffffffffu, rd.z, off);
+                rd.w += __shfl_xor_sync(0xffffffffu, rd.w, off);
+            }
+            const float dd = rd.x, l1 = rd.y, dx = rd.z, xn = rd.w;
+            const float al = S.alpha[p];
+            const bool bt_ok = lhs <= dd / (2.f * al);
+            const int nbt_it = S.nbt_it[p];
+            __syncwarp();
+            if (!bt_ok && nbt_it < a.max_bt) {
+                // Eq. 15 failed: the next sweep redoes the prox with the smaller step
+                if (lane == 0) {
+                    const float an = al * a.c_alpha;
+                    S.alpha[p] = an;
+                    S.nbt[p] += 1;
+                    S.nbt_it[p] = nbt_it + 1;
+                    S.par[p] = make_float4(S.par[p].x, 2.f * an, an * S.lam[p], __int_as_float(T_ACTIVE));
+                }
+                continue;
+            }
+            const float Fb = fmaf(S.lam[p], l1, res);
+            const bool accepted = (Fb <= S.Fx[p]);
+            const bool conv = (dx <= tol2 * xn) || (dx == 0.f);
+            const int k = S.k[p];
+            const bool fin = conv || (k >= a.max_iter);
+            // N-space state: A x^{k-1} <- A x^k, A x^k <- A xbar (accepted); for the next
+            // iteration A y = A x + beta (A x - A x_prev), r = A y - g
+            const float beta_n = (float)(k - 1) / (float)(k + 2);
+            __syncwarp();  // every lane has read the slot state lane 0 updates below
+            if (lane < N && !fin) {
+                const float2 axo = sAx[p * N + lane];
+                const float2 axn = accepted ? axb : axo;
+                sAxp[p * N + lane] = axo;
+                sAx[p * N + lane] = axn;
+                const float2 ayn = make_float2(fmaf(beta_n, axn.x - axo.x, axn.x), fmaf(beta_n, axn.y - axo.y, axn.y));
+                sAy[p * N + lane] = ayn;
+                put_r(sBop, p, lane, N, ayn.x - gg.x, ayn.y - gg.y);
+            }
+            int nbits = T_SHIFT | (accepted ? T_ACC : 0);
+            if (lane == 0) {
+                int st = S.status[p];
+                if (!bt_ok)
+                    st |= BPDN_PX_BT_LIMIT;
+                if (fin && !conv)
+                    st |= BPDN_PX_NOT_CONVERGED;
+                int nz = S.nnz[p];
+                if (accepted) {
+                    S.Fx[p] = Fb;
+                    nz = nnz;
+                    S.nnz[p] = nz;
+                }
+                S.status[p] = st;
+                if (fin) {
+                    const long long q = S.pix[p];
+                    a.status[q] = (nz == 0) ? (st | BPDN_PX_ZERO_SOLUTION) : st;
+                    a.iters[q] = k;
+                    if (a.nbt)
+                        a.nbt[q] = S.nbt[p];
+                    if (a.nsupp)
+                        a.nsupp[q] = nz;
+                    S.pix_out[p] = q;
+                } else {
+                    S.k[p] = k + 1;
+                    S.nbt_it[p] = 0;
+                    S.par[p] = make_float4(beta_n, S.par[p].y, S.par[p].z, __int_as_float(nbits | T_ACTIVE));
+                }
+            }
+            if (fin) {
+                __syncwarp();
+                nbits |= T_OUT | refill(p);
+                __syncwarp();
+                if (lane == 0)
+                    S.par[p].w = __int_as_float(nbits);
             }
         }
-        if (S.nfin)
-            group_sync(grp, Lpad);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B rows for the MMA
+        tc_fence_before();
+        group_sync(grp, 32 * NW);
     }
     // every group has finished and no MMA is in flight: release tensor memory
     tc_fence_before();
@@ -733,21 +749,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_rbpg_bf16(Params prm, int G)
     }
 }
 
-// warps of a CTA with G groups: 4 per tile and group, the last tile only as many as it needs
-int warps_for(int Lpad, int G)
-{
-    const int T = (Lpad + 127) / 128;
-    const int qlast = (Lpad - 128 * (T - 1)) / 32;
-    return 4 * (T * G - 1) + qlast;
-}
-
 int choose_groups(const OpHandle &op, int max_smem, size_t *smem_out)
 {
     const GroupLayout lay = group_layout(op.N, op.Lpad);
-    const size_t base = a_bytes(op.N, op.lda);
+    const size_t base = at_bytes(op.N, op.Lpad);
     int g = kMaxGroups;
-    while (g > 1 && (32 * warps_for(op.Lpad, g) > kMaxThreads ||
-                     base + (size_t)g * lay.bytes > (size_t)max_smem))
+    while (g > 1 && (32 * warps_for(op.Lpad, g) > kMaxThreads || base + (size_t)g * lay.bytes > (size_t)max_smem))
         --g;
     *smem_out = base + (size_t)g * lay.bytes;
     return g;
@@ -757,7 +764,7 @@ int choose_groups(const OpHandle &op, int max_smem, size_t *smem_out)
 
 bool rbpg_tc_supported(const OpHandle &op, int max_smem)
 {
-    if (2 * op.N > kK || op.Lpad > 512)
+    if (2 * op.N > kK || op.Lpad > 32 * kMaxNW)
         return false;
     size_t smem = 0;
     choose_groups(op, max_smem, &smem);
@@ -783,6 +790,9 @@ cudaError_t launch_rbpg_tc(const OpHandle &op, const SolveLaunch &a, int num_sms
         return e;
     size_t smem = 0;
     const int groups = choose_groups(op, max_smem, &smem);
+    // one CTA per SM: each CTA allocates all 512 tensor-memory columns
+    if (smem < (size_t)max_smem / 2 + 1024)
+        smem = (size_t)max_smem / 2 + 1024;
     e = cudaFuncSetAttribute(k_rbpg_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
