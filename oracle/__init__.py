@@ -88,6 +88,9 @@ def _configure(lib):
                                    c_double, c_int, c_int, dp, ip, ip]
     lib.orc_min_batch.argtypes = [dp, c_int, c_int, dp, c_i64, dp, c_double, c_long, dp, dp,
                                   dp, dp, ip, lp, ip]
+    lib.orc_adjoint.argtypes = [dp, c_int, c_int, c_double, dp, dp, dp, dp]
+    lib.orc_adjoint.restype = c_int
+    lib.orc_adjoint_batch.argtypes = [dp, c_int, c_int, dp, c_i64, dp, dp, dp, dp, ip]
     lib.orc_num_threads.restype = c_int
     return lib
 
@@ -276,3 +279,31 @@ def minimise_batch(A, G, lam, *, cd_tol: float = 1e-14, max_sweeps: int = 200000
                           _dp(x), _dp(on), _dp(off), _dp(mn), _ip(nS), _lp(sw), _ip(fl))
     return {"x": x, "on_res": on, "off_max": off, "margin": 1.0 - off, "min_abs_on": mn,
             "nS": nS, "sweeps": sw, "flags": fl}
+
+
+# ---------------------------------------------------------------- adjoint
+
+def adjoint(A, lam: float, x, dLdx):
+    """Derivatives of the minimiser x of Eq. 6 in (g, lambda) for an upstream gradient
+    dL/dx = dL/dRe x + j dL/dIm x (one pixel), by implicit differentiation of the
+    optimality system on supp(x).  Returns (dL/dg [N] complex, dL/dlambda, flag)."""
+    A, x, dLdx = _c128(A), _c128(x), _c128(dLdx)
+    N, L = A.shape
+    dg = np.zeros(N, np.complex128)
+    dl = np.zeros(1)
+    rc = _load().orc_adjoint(_dp(A), N, L, float(lam), _dp(x), _dp(dLdx), _dp(dg), _dp(dl))
+    return dg, float(dl[0]), int(rc)
+
+
+def adjoint_batch(A, lam, X, dLdX):
+    """adjoint() for every row of X / dLdX (P x L); lam scalar or [P]."""
+    A, X, dLdX = _c128(A), _c128(X), _c128(dLdX)
+    N, L = A.shape
+    P = X.shape[0]
+    lam_v = np.ascontiguousarray(np.broadcast_to(np.asarray(lam, np.float64), (P,)))
+    dg = np.zeros((P, N), np.complex128)
+    dl = np.zeros(P)
+    fl = np.zeros(P, np.int32)
+    _load().orc_adjoint_batch(_dp(A), N, L, _dp(lam_v), P, _dp(X), _dp(dLdX), _dp(dg), _dp(dl),
+                              _ip(fl))
+    return {"dLdg": dg, "dLdlam": dl, "flags": fl}

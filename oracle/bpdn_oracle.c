@@ -24,6 +24,9 @@
  *   orc_newton_polish                                        : Newton on the smooth optimality
  *                                                              system restricted to a support
  *   orc_kkt                                                  : optimality certificate (Eq. 6)
+ *   orc_adjoint                                              : derivatives of the minimiser in
+ *                                                              (g, lambda) by implicit
+ *                                                              differentiation on the support
  *   orc_*_batch                                              : OpenMP loops over pixels
  */
 #include <complex.h>
@@ -663,6 +666,87 @@ int orc_min(const cplx *A, int N, int L, const cplx *g, double lam, double cd_to
     return flags;
 }
 
+/* ----------------------------------------------------------------- adjoint */
+
+/*
+ * Derivatives of the minimiser x of Eq. 6 with respect to g and lambda, for a loss
+ * L(x) whose gradient dL/dx is given as dL/dRe x + j dL/dIm x.
+ *
+ * On the support S = {l : x_l != 0} the optimality condition of Eq. 6 is the smooth
+ * system  Phi(x_S, g, lambda) = 2 A_S^H (A_S x_S - g) + lambda x_S / |x_S| = 0
+ * (componentwise modulus).  With each complex unknown written as (Re, Im), the
+ * Jacobian of Phi in x_S is the real symmetric matrix
+ *     J = 2 realify(A_S^H A_S) + lambda * blockdiag((I - u_l u_l^T) / |x_l|),
+ * u_l = (Re x_l, Im x_l) / |x_l|, realify(M) = [[Re M, -Im M], [Im M, Re M]] per entry.
+ * The support of a strict minimiser does not move under small changes of (g, lambda),
+ * so implicit differentiation gives
+ *     dx_S = J^{-1} (realify(2 A_S^H) dg - u dlambda),   dx = 0 off S,
+ * and with v = J^{-1} c, c = dL/dx on S (J is symmetric):
+ *     dL/dg = 2 A_S v  (v read as a complex vector),   dL/dlambda = -sum_l u_l . v_l.
+ * Returns 1 when J could not be solved, 0 otherwise (x = 0 gives zero derivatives).
+ */
+int orc_adjoint(const cplx *A, int N, int L, double lam, const cplx *x, const cplx *dLdx,
+                cplx *dLdg, double *dLdlam)
+{
+    int m = 0;
+    for (int l = 0; l < L; ++l)
+        if (x[l] != 0.0)
+            ++m;
+    for (int n = 0; n < N; ++n)
+        dLdg[n] = 0.0;
+    *dLdlam = 0.0;
+    if (m == 0)
+        return 0;
+    int *S = (int *)malloc(sizeof(int) * (size_t)m);
+    double *Jm = (double *)malloc(sizeof(double) * 4 * (size_t)m * (size_t)m);
+    double *v = (double *)malloc(sizeof(double) * 2 * (size_t)m);
+    int k = 0;
+    for (int l = 0; l < L; ++l)
+        if (x[l] != 0.0)
+            S[k++] = l;
+    const int n2 = 2 * m;
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            cplx Gij = 0.0;  /* (A_S^H A_S)_ij */
+            for (int n = 0; n < N; ++n)
+                Gij += conj(A[(size_t)n * L + S[i]]) * A[(size_t)n * L + S[j]];
+            Jm[(size_t)(2 * i) * n2 + 2 * j] = 2.0 * creal(Gij);
+            Jm[(size_t)(2 * i) * n2 + 2 * j + 1] = -2.0 * cimag(Gij);
+            Jm[(size_t)(2 * i + 1) * n2 + 2 * j] = 2.0 * cimag(Gij);
+            Jm[(size_t)(2 * i + 1) * n2 + 2 * j + 1] = 2.0 * creal(Gij);
+        }
+    for (int i = 0; i < m; ++i) {
+        const double mod = cabs(x[S[i]]);
+        const double u0 = creal(x[S[i]]) / mod, u1 = cimag(x[S[i]]) / mod;
+        const double curv = lam / mod;  /* curvature of lambda |x_l| across the phase */
+        Jm[(size_t)(2 * i) * n2 + 2 * i] += curv * (1.0 - u0 * u0);
+        Jm[(size_t)(2 * i) * n2 + 2 * i + 1] -= curv * u0 * u1;
+        Jm[(size_t)(2 * i + 1) * n2 + 2 * i] -= curv * u1 * u0;
+        Jm[(size_t)(2 * i + 1) * n2 + 2 * i + 1] += curv * (1.0 - u1 * u1);
+        v[2 * i] = creal(dLdx[S[i]]);
+        v[2 * i + 1] = cimag(dLdx[S[i]]);
+    }
+    int rc = solve_real(Jm, v, n2);
+    if (rc == 0) {
+        for (int n = 0; n < N; ++n) {
+            cplx acc = 0.0;
+            for (int i = 0; i < m; ++i)
+                acc += A[(size_t)n * L + S[i]] * (v[2 * i] + I * v[2 * i + 1]);
+            dLdg[n] = 2.0 * acc;
+        }
+        double dl = 0.0;
+        for (int i = 0; i < m; ++i) {
+            const double mod = cabs(x[S[i]]);
+            dl += (creal(x[S[i]]) * v[2 * i] + cimag(x[S[i]]) * v[2 * i + 1]) / mod;
+        }
+        *dLdlam = -dl;
+    }
+    free(S);
+    free(Jm);
+    free(v);
+    return rc;
+}
+
 /* ------------------------------------------------------------- batches */
 
 void orc_rbpg_batch(const cplx *A, int N, int L, const cplx *g, int64_t P, const double *lam,
@@ -700,4 +784,13 @@ int orc_num_threads(void)
         }
     }
     return n;
+}
+
+void orc_adjoint_batch(const cplx *A, int N, int L, const double *lam, int64_t P, const cplx *x,
+                       const cplx *dLdx, cplx *dLdg, double *dLdlam, int *flags)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t p = 0; p < P; ++p)
+        flags[p] = orc_adjoint(A, N, L, lam[p], x + (size_t)p * L, dLdx + (size_t)p * L,
+                               dLdg + (size_t)p * N, dLdlam + p);
 }

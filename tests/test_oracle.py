@@ -326,3 +326,89 @@ def test_newton_polish_one_component_closed_form():
     z, rc, res = oracle.newton_polish(A, g, lam, [l], [c / st.geom.N])
     assert rc == 0
     np.testing.assert_allclose(z[0], expect, atol=1e-13)
+
+
+# ------------------------------------------------- adjoint (implicit differentiation)
+
+def _loss(c, x):
+    """L(x) = Re <c, x> = sum_l Re(conj(c_l) x_l): dL/dRe x + j dL/dIm x = c."""
+    return float(np.real(np.vdot(c, x)))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_adjoint_matches_finite_differences(seed):
+    """Derivatives of the minimiser of Eq. 6 in g and lambda: central differences of
+    the exact minimiser (CD + Newton, no Jacobian involved) against the adjoint."""
+    rng = np.random.default_rng(300 + seed)
+    N = int(rng.integers(5, 11))
+    L = int(rng.integers(12, 31))
+    geom = _geom(rng.uniform(-250, 250, N), -60.0, 60.0, L)
+    A = oracle.operator(geom)
+    for _ in range(50):
+        g = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        lam = rng.uniform(0.2, 0.6) * np.max(np.abs(2 * A.conj().T @ g))
+        r = oracle.minimise(A, g, lam)
+        if (r["nS"] >= 1 and r["margin"] > 1e-2
+                and r["min_abs_on"] > 1e-2 * np.abs(r["x"]).max()):
+            break
+    else:
+        raise AssertionError("no non-degenerate problem drawn")
+    c = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    dg, dl, rc = oracle.adjoint(A, lam, r["x"], c)
+    assert rc == 0
+    h = 1e-6 * max(1.0, np.abs(g).max())
+    fd = np.zeros(N, np.complex128)
+    for n in range(N):
+        for part, unit in ((0, 1.0), (1, 1j)):
+            gp, gm = g.copy(), g.copy()
+            gp[n] += h * unit
+            gm[n] -= h * unit
+            d = (_loss(c, oracle.minimise(A, gp, lam)["x"]) - _loss(c, oracle.minimise(A, gm, lam)["x"])) / (2 * h)
+            fd[n] += d if part == 0 else 1j * d
+    np.testing.assert_allclose(dg, fd, rtol=0, atol=1e-6 * np.abs(fd).max())
+    hl = 1e-6 * lam
+    fdl = (_loss(c, oracle.minimise(A, g, lam + hl)["x"]) - _loss(c, oracle.minimise(A, g, lam - hl)["x"])) / (2 * hl)
+    assert abs(dl - fdl) <= 1e-6 * max(abs(fdl), np.abs(fd).max() * np.abs(g).max() / lam)
+
+
+def test_adjoint_orthogonal_columns_closed_form():
+    """DFT geometry (A^H A = N I): x_l = w_l (1 - lambda / (2|w_l|)) / N for |w_l| > lambda/2,
+    w = A^H g.  Differentiating that formula by hand: dx_l/dlambda = -u_l / (2N) and
+    dx_l/dw_l = (I - lambda/(2|w_l|) (I - u_l u_l^T)) / N (real 2x2, u_l = w_l/|w_l|), and
+    dL/dg = sum_l a_l (dL/dw_l) since w_l = a_l^H g is complex linear."""
+    rng = np.random.default_rng(11)
+    N = 16
+    A = oracle.operator(synth.dft_geometry(N))
+    for _ in range(4):
+        g = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        w = A.conj().T @ g
+        lam = 0.6 * np.max(np.abs(2 * w))
+        r = oracle.minimise(A, g, lam)
+        c = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        act = np.abs(w) > lam / 2
+        assert np.array_equal(act, r["x"] != 0)
+        dl_ref = 0.0
+        dg_ref = np.zeros(N, np.complex128)
+        for l in np.nonzero(act)[0]:
+            u = np.array([w[l].real, w[l].imag]) / abs(w[l])
+            cl = np.array([c[l].real, c[l].imag])
+            Jx = (np.eye(2) - lam / (2 * abs(w[l])) * (np.eye(2) - np.outer(u, u))) / N
+            dLdw = Jx.T @ cl
+            dg_ref += A[:, l] * (dLdw[0] + 1j * dLdw[1])
+            dl_ref += -(cl @ u) / (2 * N)
+        dg, dl, rc = oracle.adjoint(A, lam, r["x"], c)
+        assert rc == 0
+        np.testing.assert_allclose(dg, dg_ref, rtol=0, atol=1e-10 * np.abs(dg_ref).max())
+        assert abs(dl - dl_ref) <= 1e-10 * max(1.0, abs(dl_ref))
+
+
+def test_adjoint_zero_solution():
+    """x* = 0 (lambda >= 2 ||A^H g||_inf) does not move under small changes: zero derivatives."""
+    st = synth.workload_small(P=2)
+    A = oracle.operator(st.geom)
+    g = st.g[0].astype(np.complex128)
+    lam = 2.5 * np.max(np.abs(A.conj().T @ g))
+    x = oracle.minimise(A, g, lam)["x"]
+    assert np.all(x == 0)
+    dg, dl, rc = oracle.adjoint(A, lam, x, np.ones(st.geom.L, np.complex128))
+    assert rc == 0 and np.all(dg == 0) and dl == 0.0

@@ -26,6 +26,12 @@ MUTANTS = {
     "cd_threshold": ("cplx nw = orc_soft(vv, 0.5 * lam) / Gll;", "cplx nw = orc_soft(vv, lam) / Gll;"),
     "newton_residual_sign": ("phi[i] = 2.0 * acc + lam * z[i] / cabs(z[i]);", "phi[i] = 2.0 * acc - lam * z[i] / cabs(z[i]);"),
     "kkt_factor": ("cplx zl = 2.0 * z[l];", "cplx zl = z[l];"),
+    "adjoint_curvature_sign": ("Jm[(size_t)(2 * i) * n2 + 2 * i] += curv * (1.0 - u0 * u0);",
+                               "Jm[(size_t)(2 * i) * n2 + 2 * i] -= curv * (1.0 - u0 * u0);"),
+    "adjoint_gram_transposed": ("Gij += conj(A[(size_t)n * L + S[i]]) * A[(size_t)n * L + S[j]];",
+                                "Gij += A[(size_t)n * L + S[i]] * conj(A[(size_t)n * L + S[j]]);"),
+    "adjoint_dg_factor": ("dLdg[n] = 2.0 * acc;", "dLdg[n] = acc;"),
+    "adjoint_lambda_sign": ("*dLdlam = -dl;", "*dLdlam = dl;"),
 }
 
 PINS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_")]
