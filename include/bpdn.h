@@ -163,6 +163,51 @@ int bpdn_refit(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda,
                void *d_x_out, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
                void *cuda_stream);
 
+/* ---------------------------------------------------------------- adjoint */
+
+/* Bytes of device workspace bpdn_backward needs for P pixels: 8 P (the per-pixel
+ * dL/dlambda terms summed when lambda is shared), rounded up to 256.  Nothing is
+ * needed when lambda_per_pixel != 0. */
+size_t bpdn_backward_workspace_bytes(bpdn_op_t op, int64_t P);
+
+/*
+ * Derivatives of the BPDN minimiser (Eq. 6) with respect to g and lambda for a loss
+ * L(x) whose gradient dL/dx is given.  On the support S the optimality condition of
+ * Eq. 6, 2 A_S^H (A_S x_S - g) + lambda x_S/|x_S| = 0, is smooth; with J its real
+ * symmetric Jacobian in x_S (each complex unknown as (Re, Im)) and v = J^{-1} (dL/dx)_S,
+ *     dL/dg = 2 A_S v,    dL/dlambda = -sum_{l in S} (x_l/|x_l|) . v_l,
+ * solved in FP64 per pixel.  Meaningful where x is the certified minimiser (the
+ * refit's output) and its support is strict (every dual constraint off S slack):
+ * then S does not move under small changes of g and lambda.
+ *
+ * Complex gradients follow PyTorch's convention for real losses:
+ * grad = dL/dRe + j dL/dIm.
+ *
+ * d_lambda    device float32 [1] (lambda_per_pixel = 0) or [P] (= 1)
+ * d_x         device c64 [P, L]   the solution (bpdn_solve / bpdn_refit output)
+ * d_support   device int32 [P, s_max]  its ascending support (-1 padded), as written
+ *             by bpdn_solve / bpdn_refit with the same s_max
+ * d_nsupp     device int32 [P]    number of nonzeros; entries beyond s_max are ignored,
+ *             as are support entries outside [0, L) or where x is 0
+ * d_status    device int32 [P] (may be NULL): BPDN_PX_* bits of the solve; pixels
+ *             without BPDN_PX_CERTIFIED (x is then not the minimiser) get zero derivatives
+ * s_max       1..BPDN_MAX_SMAX
+ * d_dL_dx     device c64 [P, L]   upstream gradient (entries off the support are unused)
+ * d_dL_dg     device c64 [P, N]   out
+ * d_dL_dlambda device float32 [P] (lambda_per_pixel = 1) or [1] (= 0; the sum over
+ *             pixels, accumulated in FP64 in a fixed order) out
+ * d_workspace >= bpdn_backward_workspace_bytes(op, P) bytes, 256-byte aligned, when
+ *             lambda_per_pixel = 0 (may be NULL otherwise)
+ * A pixel whose system is not positive definite (a degenerate support) gets zero
+ * derivatives.  Asynchronous on cuda_stream; allocates nothing.  The paper
+ * differentiates nothing: this is the adjoint of its solution map for learning lambda.
+ */
+int bpdn_backward(bpdn_op_t op, int64_t P, const float *d_lambda, int32_t lambda_per_pixel,
+                  const void *d_x, const int32_t *d_support, const int32_t *d_nsupp,
+                  const int32_t *d_status, int32_t s_max,
+                  const void *d_dL_dx, void *d_dL_dg, float *d_dL_dlambda, void *d_workspace,
+                  size_t workspace_bytes, void *cuda_stream);
+
 /*
  * bpdn_solve without a workspace, for callers that cannot allocate device memory
  * (for example a processing chain whose host application owns every GPU buffer

@@ -11,6 +11,7 @@ import os
 from . import build as _build
 
 BPDN_OK = 0
+BPDN_EINVAL, BPDN_ECUDA, BPDN_ESIZE, BPDN_EALIGN, BPDN_ESTATE = -1, -2, -3, -4, -5
 STATUS_NAMES = {-1: "EINVAL", -2: "ECUDA", -3: "ESIZE", -4: "EALIGN", -5: "ESTATE"}
 
 PX_NOT_CONVERGED = 1
@@ -29,7 +30,7 @@ EXPORTED = [
     "bpdn_default_options", "bpdn_op_workspace_bytes", "bpdn_make_operator",
     "bpdn_destroy_operator", "bpdn_op_info", "bpdn_op_lipschitz", "bpdn_op_export",
     "bpdn_solve_workspace_bytes", "bpdn_solve", "bpdn_refit", "bpdn_last_error", "bpdn_version",
-    "bpdn_solve_noalloc",
+    "bpdn_solve_noalloc", "bpdn_backward_workspace_bytes", "bpdn_backward",
 ]
 
 
@@ -103,6 +104,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.bpdn_refit.restype = ctypes.c_int
     lib.bpdn_solve_noalloc.argtypes = [op_t, vp, i64, vp, i32, optp, vp, vp, vp, vp, vp, vp, vp]
     lib.bpdn_solve_noalloc.restype = ctypes.c_int
+    lib.bpdn_backward_workspace_bytes.argtypes = [op_t, i64]
+    lib.bpdn_backward_workspace_bytes.restype = sz
+    lib.bpdn_backward.argtypes = [op_t, i64, vp, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp, sz, vp]
+    lib.bpdn_backward.restype = ctypes.c_int
     lib.bpdn_last_error.argtypes = []
     lib.bpdn_last_error.restype = ctypes.c_char_p
     lib.bpdn_version.argtypes = []

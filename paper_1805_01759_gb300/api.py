@@ -10,6 +10,7 @@ library.
 from __future__ import annotations
 
 import ctypes
+import math
 import dataclasses
 
 import numpy as np
@@ -160,3 +161,84 @@ def refit(op: Operator, g: torch.Tensor, lam, x_in: torch.Tensor, *, status: tor
                               x_in.data_ptr(), x.data_ptr(), support.data_ptr(), nsupp.data_ptr(),
                               st.data_ptr(), _stream(stream)))
     return x, support, nsupp, st
+
+
+def backward(op: Operator, x: torch.Tensor, support: torch.Tensor, nsupp: torch.Tensor,
+             dLdx: torch.Tensor, lam, *, status: torch.Tensor | None = None,
+             stream: torch.cuda.Stream | None = None):
+    """Adjoint of the minimiser (bpdn_backward): (dL/dg [P, N] complex64, dL/dlambda).
+
+    dL/dlambda has P entries when lam has P entries, else one (the sum over pixels).
+    With status given, pixels the solve did not certify get zero derivatives."""
+    lib = _lib.load()
+    if x.dtype != torch.complex64 or x.device.type != "cuda" or x.dim() != 2 or x.shape[1] != op.L:
+        raise TypeError(f"x must be a complex64 CUDA tensor [P, {op.L}]")
+    P = x.shape[0]
+    dev = x.device
+    x = x.contiguous()
+    dLdx = dLdx.to(dtype=torch.complex64).contiguous()
+    support = support.to(dtype=torch.int32).contiguous()
+    nsupp = nsupp.to(dtype=torch.int32).contiguous()
+    if dLdx.shape != x.shape or support.dim() != 2 or support.shape[0] != P or nsupp.shape != (P,):
+        raise ValueError("dL/dx, support and nsupp must match x")
+    lam_t, pp = _lambda_tensor(lam, P, dev)
+    if status is not None:
+        status = status.to(dtype=torch.int32).contiguous()
+        if status.shape != (P,):
+            raise ValueError("status must have P entries")
+    dLdg = torch.empty((P, op.N), dtype=torch.complex64, device=dev)
+    dLdlam = torch.empty(P if pp else 1, dtype=torch.float32, device=dev)
+    ws_bytes = 0 if pp else lib.bpdn_backward_workspace_bytes(op.handle, P)
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
+    _lib.check(lib.bpdn_backward(op.handle, P, lam_t.data_ptr(), pp, x.data_ptr(), support.data_ptr(),
+                                 nsupp.data_ptr(), _ptr(status), support.shape[1], dLdx.data_ptr(), dLdg.data_ptr(),
+                                 dLdlam.data_ptr(), ws.data_ptr() if ws_bytes else None, ws_bytes,
+                                 _stream(stream)))
+    return dLdg, dLdlam
+
+
+class BPDNFunction(torch.autograd.Function):
+    """x = argmin ||A x - g||^2 + lambda ||x||_1 (Eq. 6) per pixel as a differentiable map of
+    (g, lambda): forward = bpdn_solve with the refit, backward = bpdn_backward (zero
+    derivatives on pixels the refit did not certify).
+
+    Usage: x = BPDNFunction.apply(g, lam, op, options) with g complex64 [P, N] and lam a
+    float32 tensor of 1 or P entries; options is a dict of solve options (or None)."""
+
+    @staticmethod
+    def forward(ctx, g, lam, op, options=None):
+        opts = dict(options or {})
+        opts["refit"] = 1
+        lam_d = lam.detach()
+        res = solve(op, g.detach(), lam_d, **opts)
+        ctx.op = op
+        ctx.lam_shape = lam.shape
+        ctx.save_for_backward(res.x, res.support, res.nsupp, res.status, lam_d)
+        ctx.mark_non_differentiable(res.status)
+        return res.x, res.status
+
+    @staticmethod
+    def backward(ctx, grad_x, grad_status):
+        x, support, nsupp, status, lam_d = ctx.saved_tensors
+        if grad_x is None:
+            return None, None, None, None
+        dLdg, dLdlam = backward(ctx.op, x, support, nsupp, grad_x, lam_d, status=status)
+        return dLdg, dLdlam.reshape(ctx.lam_shape), None, None
+
+
+def tune_lambda(op: Operator, g: torch.Tensor, gamma_true: torch.Tensor, lam0: float, *,
+                steps: int = 50, lr: float = 0.1, options: dict | None = None):
+    """Learn one lambda by gradient descent on log lambda, minimising the relative squared
+    error sum |x(lambda) - gamma_true|^2 / sum |gamma_true|^2 over pixels and grid points.
+    Returns (lambda, [(lambda, error) per step])."""
+    log_lam = torch.tensor([math.log(lam0)], dtype=torch.float32, device=g.device, requires_grad=True)
+    history = []
+    for _ in range(steps):
+        lam = log_lam.exp()
+        x, _ = BPDNFunction.apply(g, lam, op, options)
+        mse = (x - gamma_true).abs().pow(2).sum() / gamma_true.abs().pow(2).sum().clamp_min(1e-30)
+        (grad,) = torch.autograd.grad(mse, log_lam)
+        history.append((float(lam.item()), float(mse.item())))
+        with torch.no_grad():
+            log_lam -= lr * grad
+    return float(log_lam.exp().item()), history

@@ -423,4 +423,61 @@ int bpdn_refit(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda,
     return check_cuda(launch_refit(*op, r, (cudaStream_t)cuda_stream), "refit kernel");
 }
 
+size_t bpdn_backward_workspace_bytes(bpdn_op_t h, int64_t P)
+{
+    (void)h;
+    return P > 0 ? a256(sizeof(double) * (size_t)P) : 0;
+}
+
+int bpdn_backward(bpdn_op_t h, int64_t P, const float *d_lambda, int32_t lambda_per_pixel,
+                  const void *d_x, const int32_t *d_support, const int32_t *d_nsupp,
+                  const int32_t *d_status, int32_t s_max,
+                  const void *d_dL_dx, void *d_dL_dg, float *d_dL_dlambda, void *d_workspace,
+                  size_t workspace_bytes, void *cuda_stream)
+{
+    OpHandle *op = nullptr;
+    int rc = check_op(h, &op);
+    if (rc)
+        return rc;
+    if (P < 0)
+        return set_error(BPDN_EINVAL, "P must be >= 0");
+    if (s_max < 1 || s_max > BPDN_MAX_SMAX)
+        return set_error(BPDN_EINVAL, "s_max must lie in 1..%d", BPDN_MAX_SMAX);
+    if (!d_lambda || !d_dL_dlambda)
+        return set_error(BPDN_EINVAL, "lambda and dL/dlambda must be non-NULL");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (P == 0) {
+        if (!lambda_per_pixel)
+            return check_cuda(cudaMemsetAsync(d_dL_dlambda, 0, sizeof(float), s), "clear dL/dlambda");
+        return BPDN_OK;
+    }
+    if (!d_x || !d_support || !d_nsupp || !d_dL_dx || !d_dL_dg)
+        return set_error(BPDN_EINVAL, "x, support, nsupp, dL/dx and dL/dg must be non-NULL");
+    if (!aligned(d_x, 8) || !aligned(d_dL_dx, 8) || !aligned(d_dL_dg, 8))
+        return set_error(BPDN_EALIGN, "x, dL/dx and dL/dg must be 8-byte aligned");
+    if (!aligned(d_support, 4) || !aligned(d_nsupp, 4) || !aligned(d_lambda, 4) || !aligned(d_dL_dlambda, 4) ||
+        (d_status && !aligned(d_status, 4)))
+        return set_error(BPDN_EALIGN, "int32 / float32 arrays must be 4-byte aligned");
+    if (!lambda_per_pixel) {
+        if (!d_workspace || workspace_bytes < bpdn_backward_workspace_bytes(h, P))
+            return set_error(BPDN_ESIZE, "backward workspace too small");
+        if (!aligned(d_workspace, 256))
+            return set_error(BPDN_EALIGN, "backward workspace must be 256-byte aligned");
+    }
+    BackwardLaunch a;
+    a.P = P;
+    a.lam = d_lambda;
+    a.lam_pp = lambda_per_pixel ? 1 : 0;
+    a.x = (const float2 *)d_x;
+    a.support = d_support;
+    a.nsupp = d_nsupp;
+    a.status = d_status;
+    a.s_max = s_max;
+    a.dLdx = (const float2 *)d_dL_dx;
+    a.dLdg = (float2 *)d_dL_dg;
+    a.dLdlam = d_dL_dlambda;
+    a.part = (double *)d_workspace;
+    return check_cuda(launch_backward(*op, a, s), "backward kernel");
+}
+
 }  // extern "C"

@@ -83,4 +83,19 @@ struct RefitLaunch {
 };
 cudaError_t launch_refit(const OpHandle &op, const RefitLaunch &a, cudaStream_t s);
 
+struct BackwardLaunch {
+    int64_t P;
+    const float *lam;
+    int lam_pp;
+    const float2 *x;
+    const int32_t *support, *nsupp;
+    const int32_t *status;  // may be NULL
+    int s_max;
+    const float2 *dLdx;
+    float2 *dLdg;
+    float *dLdlam;  // [P] (lam_pp) or [1]
+    double *part;   // [P] per-pixel dL/dlambda terms when lambda is shared
+};
+cudaError_t launch_backward(const OpHandle &op, const BackwardLaunch &a, cudaStream_t s);
+
 }  // namespace bpdn
