@@ -189,7 +189,7 @@ def _traffic_per_launch(pixels: int, path_name: str) -> float | None:
     (profiles/counters_<path>.txt, taken on a smaller patch), scaled by the pixels the
     launch processes -- the traffic is the per-pixel read of g and write of x -- and
     only while the kernel source is the one the counters were taken on."""
-    src = "rbpg_tc.cu" if path_name == "bf16" else "rbpg.cu"
+    src = "rbpg.cu"
     path = os.path.join(ROOT, "profiles", f"counters_{path_name}.txt")
     if not os.path.exists(path):
         return None
@@ -404,7 +404,7 @@ def run_ours(args) -> None:
 
     if rank != 0:
         return
-    kname = "k_rbpg_bf16" if head == "bf16" else "k_rbpg_fp32"
+    kname = "k_rbpg<BF16>" if head == "bf16" else "k_rbpg<FP32>"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_head, "higher_is_better": True,

@@ -333,15 +333,10 @@ int bpdn_solve(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda,
         return set_error(BPDN_EALIGN, "solve workspace must be 256-byte aligned");
     if (opt->refit && d_support && !aligned(d_support, 4))
         return set_error(BPDN_EALIGN, "support must be 4-byte aligned");
-    if (op->Lpad > 512)
-        return set_error(BPDN_ESIZE, "L = %d: the iteration kernels handle L <= 512", op->L);
     int dev = op->device;
-    if ((int)rbpg_smem_bytes(*op) > max_smem_optin(dev))
-        return set_error(BPDN_ESIZE, "N = %d, L = %d needs %zu bytes of shared memory (> %d)",
-                         op->N, op->L, rbpg_smem_bytes(*op), max_smem_optin(dev));
-    if (opt->precision == 1 && !rbpg_tc_supported(*op, max_smem_optin(dev)))
-        return set_error(BPDN_ESIZE, "precision 1 (BF16 tensor cores) needs 2N <= 64 and L <= 512 "
-                         "(N = %d, L = %d)", op->N, op->L);
+    const char *why = rbpg_check(*op, opt->precision, max_smem_optin(dev));
+    if (why[0] != '\0')
+        return set_error(BPDN_ESIZE, "N = %d, L = %d, precision %d: %s", op->N, op->L, opt->precision, why);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     unsigned long long *counter = (unsigned long long *)d_workspace;
     // work counter (8 bytes) and the kernel's error word (4 bytes)
@@ -366,9 +361,7 @@ int bpdn_solve(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda,
     a.max_bt = opt->max_bt;
     a.precision = opt->precision;
     a.err = (int *)((char *)d_workspace + 8);
-    rc = check_cuda(opt->precision == 1 ? launch_rbpg_tc(*op, a, num_sms(dev), s)
-                                        : launch_rbpg(*op, a, num_sms(dev), s),
-                    "iteration kernel");
+    rc = check_cuda(launch_rbpg(*op, a, num_sms(dev), s), "iteration kernel");
     if (rc)
         return rc;
     if (opt->refit) {

@@ -64,11 +64,10 @@ struct SolveLaunch {
     int precision;
     int *err;  // set to 1 if a bounded wait ran out (may be NULL)
 };
+// iteration kernel (a.precision 0: FP32 CUDA cores, 1: BF16 tensor cores)
 cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
-size_t rbpg_smem_bytes(const OpHandle &op);
-// the BF16 tensor-core variant: 2N <= 64 and L <= 512
-bool rbpg_tc_supported(const OpHandle &op, int max_smem);
-cudaError_t launch_rbpg_tc(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
+// "" when the operator's sizes suit the kernel at this precision, else the reason
+const char *rbpg_check(const OpHandle &op, int precision, int max_smem);
 
 struct RefitLaunch {
     const float2 *g;

@@ -1,39 +1,38 @@
-// Persistent iteration kernel: Algorithm 1 (RBPG with backtracking) for many
-// pixels that share one operator.
+// Persistent iteration kernel: Algorithm 1 (RBPG with backtracking) for many pixels
+// that share one operator, one pixel per slot, eight slots per group of warps.
 //
-// Block = one pixel's whole x (the patch objective separates over pixels; with
-// equal block Lipschitz constants the sampling of Eq. 14 is uniform, and each
-// pixel's iterate sequence does not depend on the visiting order), so every
-// resident pixel takes one step of Eqs. 11-13 per sweep.
+// Two variants share everything but the gradient contraction sum_n conj(A_nl) r_n:
+//   FP32  CUDA cores, packed f32x2 FMAs against the FP32 residuals in shared memory;
+//   BF16  tcgen05 MMAs from BF16 operands into FP32 accumulators in tensor memory,
+//         D[l, j] = sum_k Aop[l, k] B[j, k] per 128-row tile of the grid, K = 64
+//         (2N <= 64, zero padded), N = 16, with the constant operator rows
+//         Aop[l, :] = (Re A[:, l], Im A[:, l]) in tensor memory for the whole launch and
+//         B[p, :] = (Re r_p, Im r_p), B[8 + p, :] = (Im r_p, -Re r_p) in shared memory,
+//         so that D[l, p] = Re sum_n conj(A_nl) r_n and D[l, 8 + p] its imaginary part.
+// The iterate, prox, line search (Eq. 15), accept and stopping tests and A xbar run in
+// FP32 in both.  A sits in shared memory when it fits, else it is read from global
+// memory (it stays in L2).
 //
-// Work decomposition (one CTA per SM, persistent):
-//   * A (FP32, complex interleaved) stays in shared memory for the whole launch and
-//     is shared by G independent slot groups; each group has its own Lpad threads,
-//     TPG pixel slots, slot state and named barrier, so the latency-bound phases
-//     of one group overlap the arithmetic of another;
-//   * a slot whose pixel has stopped is refilled from a global work counter
-//     (converged-slot refill);
-//   * thread l of a group owns grid index l of its group's slots: x^k and the
-//     gradient stay in registers, x^{k-1} and xbar in shared memory.
+// Per-pixel state: thread l (one grid point) keeps x^k of its slots in registers and
+// x^{k-1}, xbar in its own tensor-memory lane.  One sweep of a group:
+//   transition  apply the previous decisions (x^{k-1} <- x^k, x^k <- xbar, write out
+//               finished pixels, zero refilled slots), overlapping the MMAs (BF16);
+//   C           gradient, prox (Eq. 12) per slot, partial sums over the warp's 32 grid
+//               points and the warp's share of A xbar (ascending l over the nonzeros
+//               its ballot finds);
+//   DE          one warp per slot: A xbar and the sums over warps in a fixed order,
+//               Eq. 15, monotone accept, stopping test, next residual r = A y - g in
+//               N space, and the refill of finished slots from the work counter.
+// A slot whose step fails Eq. 15 runs the next sweep with the smaller step and the
+// same residual (the gradient is recomputed bit for bit).  Two group barriers per
+// sweep; every sum has a fixed order, so results do not depend on timing.
 //
-// One iteration of a group (readings of the paper in the oracle's header):
-//   B  gradient: sum_n conj(A_nl) r_n, r = A y - g   (dense; packed f32x2 FMA; the
-//                factor 2 of grad f = 2 A^H (A y - g) is folded into the step)
-//   C  prox:     xbar = S_{alpha lambda}(y - alpha grad),  y = x + beta (x - x_prev),
-//                beta = (k-2)/(k+1) (Eq. 10 read as the complex soft threshold), plus
-//                per-slot partial sums ||xbar - y||^2, ||xbar||_1, ||xbar - x||^2, ||xbar||^2
-//   ---- group barrier
-//   A xbar: slots with few nonzeros sum over them in the next phase; slots with
-//                many get a dense pass of the whole group (partial sums over
-//                ranges of l, added in a fixed order) ---- group barrier
-//   DE one half-warp per slot: Eq. 15 ||A xbar - A y||^2 <= ||xbar - y||^2 / (2 alpha),
-//                else alpha *= C_alpha and the slot redoes C-DE; then the monotone
-//                accept test F(xbar) <= F(x^k), the stopping test
-//                ||xbar - x^k|| <= tol ||xbar||, and the next iteration's
-//                r: A y = A x^k + beta (A x^k - A x^{k-1}) (linearity)
-//   ---- group barrier
-//   G  registers: x_prev <- x, x <- xbar (accepted); finished slots write x out
-//   H  (only when a slot finished) record status and take the next pixel
+// Warps are assigned to (group, tile, lane quadrant) so that a warp only touches the
+// tensor-memory lanes 32 (w mod 4) .. 32 (w mod 4) + 31 it may access; the partial last
+// tile of group g sits at quadrants s_g .. (the BF16 operator rows are duplicated there),
+// so two groups of L = 416 take 26 warps.
+//
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -44,74 +43,142 @@ namespace bpdn {
 namespace {
 
 constexpr int TPG = 8;          // pixel slots per group
-constexpr int kMaxGroups = 4;   // groups per CTA (named barriers 1..kMaxGroups)
-constexpr int kMaxThreads = 832;  // threads per CTA: the register budget is 65536 / 832
-constexpr int kSparseMax = 24;  // A xbar by gathering when xbar has at most this many nonzeros
-constexpr int kChunks = 4;      // ranges of l per slot in the dense A xbar pass (fixed, so the
-                                // summation order depends on nothing but the pixel)
+constexpr int kMaxGroups = 2;   // groups per CTA (named barriers 1..kMaxGroups)
+constexpr int kK = 64;          // BF16 contraction length 2N padded to a multiple of 16
+constexpr int kTmemCols = 512;
+constexpr int kMaxNW = 32;      // 32-point blocks of the grid per group: Lpad <= 1024
 
-// slot flags
-constexpr int F_ACTIVE = 1, F_ACC = 2, F_FIN = 4;
+// transition bits, applied at the start of a sweep
+constexpr int T_ACTIVE = 1;  // the slot holds a pixel during this sweep
+constexpr int T_ACC = 2;     // x^k <- xbar (the last evaluation was accepted)
+constexpr int T_SHIFT = 4;   // x^{k-1} <- x^k (an iteration ended)
+constexpr int T_OUT = 8;     // write x^k (after T_ACC) to the output row of pix_out
+constexpr int T_RESET = 16;  // x^k = x^{k-1} = 0: a new pixel starts in this sweep
 
 struct SlotState {
-    long long pix[TPG];
-    int k[TPG], nbt[TPG], nbt_it[TPG], status[TPG], nnz[TPG], flags[TPG];
-    int need[2][TPG];  // [iteration parity][slot]: evaluate the slot in this sweep / retry round
-    int cnt[2][TPG];   // [sweep parity][slot]: nonzeros of xbar
-    int dense[TPG];    // slots whose A xbar comes from the dense pass this sweep
+    long long pix[TPG];      // pixel in the slot, -1 when none
+    long long pix_out[TPG];  // pixel whose x the next transition writes out
+    float4 par[TPG];         // (beta, 2 alpha, alpha lambda, transition bits)
     float alpha[TPG], Fx[TPG], lam[TPG];
-    float4 par[TPG];   // (beta, 2 alpha, alpha lambda, unused)
-    int retry[3];      // by retry round mod 3: reset two barriers after its last read
-    int ndense, nfin, nactive;
+    int k[TPG], nbt[TPG], nbt_it[TPG], status[TPG], nnz[TPG];
 };
 
-// shared-memory layout: A once, then one block of arrays per group
+// shared-memory layout: A (when it fits) once, then one block per group
 struct GroupLayout {
-    size_t Rre, Rim, Xb, Xp, mask, G, Ax, Axp, Ay, red, part, st, bytes;
+    size_t Bop, Rre, Rim, mbar, G, Ax, Axp, Ay, mask, red, part, st, bytes;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline GroupLayout group_layout(int N, int Lpad)
+__host__ __device__ inline GroupLayout group_layout(int N, int Lpad, bool tc)
 {
     GroupLayout s;
     const int NW = Lpad / 32;
     size_t o = 0;
-    s.Rre = o;  o = align16(o + sizeof(float) * (size_t)N * TPG);
-    s.Rim = o;  o = align16(o + sizeof(float) * (size_t)N * TPG);
-    s.Xb = o;   o = align16(o + sizeof(float2) * (size_t)TPG * Lpad);
-    s.Xp = o;   o = align16(o + sizeof(float2) * (size_t)TPG * Lpad);
-    s.mask = o; o = align16(o + sizeof(uint32_t) * (size_t)TPG * NW);
+    s.Bop = s.Rre = s.Rim = s.mbar = 0;
+    if (tc) {
+        s.Bop = o;  o = align16(o + 16 * kK * 2);  // B: 16 rows x K bf16, core-matrix layout
+        s.mbar = o; o = align16(o + 8);
+    } else {
+        s.Rre = o;  o = align16(o + sizeof(float) * (size_t)N * TPG);  // [N][TPG]
+        s.Rim = o;  o = align16(o + sizeof(float) * (size_t)N * TPG);
+    }
     s.G = o;    o = align16(o + sizeof(float2) * (size_t)TPG * N);
     s.Ax = o;   o = align16(o + sizeof(float2) * (size_t)TPG * N);
     s.Axp = o;  o = align16(o + sizeof(float2) * (size_t)TPG * N);
     s.Ay = o;   o = align16(o + sizeof(float2) * (size_t)TPG * N);
-    s.red = o;  o = align16(o + sizeof(float) * (size_t)NW * TPG * 4);
-    s.part = o; o = align16(o + sizeof(float2) * (size_t)TPG * kChunks * N);
+    s.mask = o; o = align16(o + sizeof(uint32_t) * (size_t)TPG * NW);
+    s.red = o;  o = align16(o + sizeof(float4) * (size_t)NW * TPG);
+    s.part = o; o = align16(o + sizeof(float2) * (size_t)TPG * NW * N);
     s.st = o;   o = align16(o + sizeof(SlotState));
     s.bytes = o;
     return s;
 }
 
+// A as float2 [N][lda] (lda = Lpad + 1, odd): lanes over l and lanes over n both
+// read without bank conflicts
 __host__ __device__ inline size_t a_bytes(int N, int lda) { return align16(sizeof(float2) * (size_t)N * lda); }
+
+// ---- warp roles ----
+// Tiles T = ceil(Lpad / 128); the last one holds qlast blocks of 32 grid points.  Group g
+// places the blocks of a partial last tile at quadrants s_g .. s_g + qlast - 1.
+struct TileShape {
+    int T, F, qlast, partial;  // tiles, full tiles, blocks in the last tile, has a partial tile
+};
+
+__host__ __device__ inline TileShape tile_shape(int Lpad)
+{
+    TileShape s;
+    s.T = (Lpad + 127) / 128;
+    s.qlast = (Lpad - 128 * (s.T - 1)) / 32;
+    s.partial = s.qlast < 4;
+    s.F = s.partial ? s.T - 1 : s.T;
+    return s;
+}
+
+__host__ __device__ inline int partial_start(const TileShape &s, int G, int g)
+{
+    return (G * s.qlast <= 4) ? g * s.qlast : 0;
+}
+
+// role of warp w: group, block of 32 grid points (l = 32 blk + lane) and tile; false = idle
+__host__ __device__ inline bool warp_role(int w, int G, int Lpad, int *grp, int *blk, int *tile)
+{
+    const TileShape s = tile_shape(Lpad);
+    const int q = w & 3, i = w >> 2;
+    if (i < G * s.F) {
+        *grp = i / s.F;
+        *tile = i % s.F;
+        *blk = 4 * (*tile) + q;
+        return true;
+    }
+    if (!s.partial)
+        return false;
+    int j = i - G * s.F;
+    for (int g = 0; g < G; ++g) {
+        const int s0 = partial_start(s, G, g);
+        if (q >= s0 && q < s0 + s.qlast) {
+            if (j == 0) {
+                *grp = g;
+                *tile = s.T - 1;
+                *blk = 4 * (s.T - 1) + (q - s0);
+                return true;
+            }
+            --j;
+        }
+    }
+    return false;
+}
+
+int warps_for(int Lpad, int G)
+{
+    const TileShape s = tile_shape(Lpad);
+    int W = 0;
+    for (int q = 0; q < 4; ++q) {
+        int n = G * s.F;
+        if (s.partial)
+            for (int g = 0; g < G; ++g) {
+                const int s0 = partial_start(s, G, g);
+                n += (q >= s0 && q < s0 + s.qlast) ? 1 : 0;
+            }
+        if (n > 0 && 4 * (n - 1) + q + 1 > W)
+            W = 4 * (n - 1) + q + 1;
+    }
+    return W;
+}
+
+// tensor-memory columns: [BF16 operator rows][BF16 accumulators per group][x^{k-1} per
+// group][xbar per group], 16 columns per tile for each per-group table
+__host__ __device__ inline int tmem_cols_used(int T, int G, bool tc)
+{
+    return (tc ? 32 * T + 16 * T * G : 0) + 32 * T * G;
+}
 
 struct Params {
     const float *A_re, *A_im;  // global planar tables [N][lda]
     int N, L, Lpad, lda;
     SolveLaunch a;
 };
-
-// packed FP32 pair FMA: d = a * b + c on both halves (Blackwell f32x2)
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
-{
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;"
-        : "=l"(d)
-        : "l"(*reinterpret_cast<unsigned long long *>(&a)),
-          "l"(*reinterpret_cast<unsigned long long *>(&b)),
-          "l"(*reinterpret_cast<unsigned long long *>(&c)));
-    return *reinterpret_cast<float2 *>(&d);
-}
 
 // barrier of one group (ids 1..kMaxGroups; id 0 is __syncthreads)
 __device__ __forceinline__ void group_sync(int grp, int nthreads)
@@ -139,482 +206,730 @@ __device__ __forceinline__ void warp_transpose_reduce16(float (&v)[16], int lane
     v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-__global__ void __launch_bounds__(kMaxThreads, 1) k_rbpg_fp32(Params prm)
+// packed FP32 pair FMA: d = a * b + c on both halves
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<unsigned long long *>(&a)),
+          "l"(*reinterpret_cast<unsigned long long *>(&b)),
+          "l"(*reinterpret_cast<unsigned long long *>(&c)));
+    return *reinterpret_cast<float2 *>(&d);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *ptr)
+{
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+// two FP32 values -> packed BF16 pair (element 2c in the low half, as tensor memory
+// holds a K-major operand row: element k in column k/2)
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return l | (h << 16);
+}
+
+// byte offset of element (row, k) of a K-major operand with kK columns, no swizzle:
+// core matrices of 8 rows x 16 bytes; the K-adjacent core matrix 128 bytes on (LBO),
+// the next 8-row group kK/8 * 128 bytes on (SBO)
+__host__ __device__ inline int kmaj_off(int row, int k)
+{
+    return (row >> 3) * (kK / 8) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// shared-memory matrix descriptor of tcgen05 (no swizzle)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version
+    return d;
+}
+
+// instruction descriptor: D FP32, A and B BF16, both K-major, N = 16, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D (tmem) [+]= A (tmem) x B (smem descriptor)
+__device__ __forceinline__ void tc_mma_ts(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t accum)
+{
+    asm volatile(
+        "{.reg .pred p; setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;}" ::"r"(d),
+        "r"(a), "l"(bdesc), "r"(kIdesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+// bounded wait for an mbarrier phase; false when the bound ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 26); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{.reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p;}"
+            : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done)
+            return true;
+    }
+    return false;
+}
+
+// tensor-memory loads and stores of this warp's 32 lanes, consecutive 32-bit columns
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4])
+{
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st8u(uint32_t taddr, const uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8])
+{
+    uint32_t u[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        u[i] = __float_as_uint(v[i]);
+    tmem_st8u(taddr, u);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+template <bool TC, bool SA, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_rbpg(Params prm, int G)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint32_t s_tmem;
     const int N = prm.N, L = prm.L, Lpad = prm.Lpad, lda = prm.lda;
-    const int NW = Lpad / 32;  // warps per group
-    const int grp = threadIdx.x / Lpad;
-    const int tid = threadIdx.x - grp * Lpad;  // grid index l owned by this thread
-    const int lane = tid & 31, warp = tid >> 5;  // warp within the group
+    const int NW = Lpad / 32;  // warps (blocks of 32 grid points) per group
+    constexpr int NCH = TC ? 1 : 2;  // rows n = lane + 32 c, c < NCH, per lane (BF16: N <= 32)
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q4 = w & 3;
+    int grp = 0, blk = 0, tile = 0;
+    const bool live = warp_role(w, G, Lpad, &grp, &blk, &tile);
+    const int l = 32 * blk + lane;  // grid index owned by this thread
     const SolveLaunch &a = prm.a;
-    float2 *sA = (float2 *)smem_raw;  // [N][lda] (re, im)
-    const GroupLayout lay = group_layout(N, Lpad);
-    unsigned char *gbase = smem_raw + a_bytes(N, lda) + (size_t)grp * lay.bytes;
-    float *sRre = (float *)(gbase + lay.Rre);        // [N][TPG]
-    float *sRim = (float *)(gbase + lay.Rim);        // [N][TPG]
-    float2 *sXb = (float2 *)(gbase + lay.Xb);        // [TPG][Lpad]
-    float2 *sXp = (float2 *)(gbase + lay.Xp);        // [TPG][Lpad]
-    uint32_t *sMask = (uint32_t *)(gbase + lay.mask);  // [TPG][NW]
-    float2 *sG = (float2 *)(gbase + lay.G);          // [TPG][N]
+    float2 *sA = (float2 *)smem_raw;  // [N][lda] when SA
+    const GroupLayout lay = group_layout(N, Lpad, TC);
+    unsigned char *gbase = smem_raw + (SA ? a_bytes(N, lda) : 0) + (size_t)grp * lay.bytes;
+    unsigned char *sBop = gbase + lay.Bop;  // BF16
+    float *sRre = (float *)(gbase + lay.Rre), *sRim = (float *)(gbase + lay.Rim);  // FP32: [N][TPG]
+    const uint32_t mbar = smem_u32(gbase + lay.mbar);
+    float2 *sG = (float2 *)(gbase + lay.G);  // [TPG][N]
     float2 *sAx = (float2 *)(gbase + lay.Ax);
     float2 *sAxp = (float2 *)(gbase + lay.Axp);
     float2 *sAy = (float2 *)(gbase + lay.Ay);
-    float *sRed = (float *)(gbase + lay.red);        // [NW][TPG][4]
-    float2 *sPart = (float2 *)(gbase + lay.part);    // [TPG][kChunks][N]
+    uint32_t *sMask = (uint32_t *)(gbase + lay.mask);  // [TPG][NW] ballots of xbar != 0
+    float4 *sRed = (float4 *)(gbase + lay.red);        // [NW][TPG] (dd, l1, dx, xn)
+    float2 *sPart = (float2 *)(gbase + lay.part);      // [TPG][NW][N] A xbar over one block
     SlotState &S = *(SlotState *)(gbase + lay.st);
 
-    for (int i = threadIdx.x; i < N * lda; i += blockDim.x)
-        sA[i] = make_float2(prm.A_re[i], prm.A_im[i]);
-    for (int i = tid; i < TPG * Lpad; i += Lpad)
-        sXp[i] = make_float2(0.f, 0.f);
-    for (int i = tid; i < N * TPG; i += Lpad) {
-        sRre[i] = 0.f;
-        sRim[i] = 0.f;
+    // A_{n, ll}
+    auto Aat = [&](int n, int ll) -> float2 {
+        if constexpr (SA)
+            return sA[n * lda + ll];
+        else
+            return make_float2(__ldg(prm.A_re + n * lda + ll), __ldg(prm.A_im + n * lda + ll));
+    };
+    // residual of slot p at row n for the next gradient
+    auto put_r = [&](int p, int n, float re, float im) {
+        if constexpr (TC) {
+            const __nv_bfloat16 bre = __float2bfloat16_rn(re), bim = __float2bfloat16_rn(im);
+            const __nv_bfloat16 nre = __float2bfloat16_rn(-re);
+            *(__nv_bfloat16 *)(sBop + kmaj_off(p, n)) = bre;
+            *(__nv_bfloat16 *)(sBop + kmaj_off(p, N + n)) = bim;
+            *(__nv_bfloat16 *)(sBop + kmaj_off(TPG + p, n)) = bim;
+            *(__nv_bfloat16 *)(sBop + kmaj_off(TPG + p, N + n)) = nre;
+        } else {
+            sRre[n * TPG + p] = re;
+            sRim[n * TPG + p] = im;
+        }
+    };
+
+    if constexpr (SA) {
+        for (int i = threadIdx.x; i < N * lda; i += blockDim.x)
+            sA[i] = make_float2(prm.A_re[i], prm.A_im[i]);
+    }
+    if (live && blk == 0) {
+        if constexpr (TC) {
+            for (int i = lane; i < 16 * kK * 2 / 4; i += 32)
+                ((uint32_t *)sBop)[i] = 0u;  // K padding of B stays zero
+            if (lane == 0) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar));
+                asm volatile("fence.mbarrier_init.release.cluster;");
+            }
+        } else {
+            for (int i = lane; i < N * TPG; i += 32) {
+                sRre[i] = 0.f;
+                sRim[i] = 0.f;
+            }
+        }
+    }
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * q4) << 16);
+    const int T = (Lpad + 127) / 128;
+    const int colD = TC ? 32 * T : 0;
+    const int colXp = colD + (TC ? 16 * T * G : 0);
+    const int colXb = colXp + 16 * T * G;
+    const uint32_t taD = lane_base + colD + 16 * T * grp + 16 * tile;
+    const uint32_t taXp = lane_base + colXp + 16 * T * grp + 16 * tile;
+    const uint32_t taXb = lane_base + colXb + 16 * T * grp + 16 * tile;
+    if (live) {
+        if constexpr (TC) {
+            // operator rows of this thread's grid index into its tensor-memory lane: full
+            // tiles by group 0, the partial tile by every group at its own quadrants
+            if (grp == 0 || tile == T - 1) {
+                const uint32_t ta = lane_base + 32 * tile;
+#pragma unroll
+                for (int part = 0; part < 4; ++part) {
+                    uint32_t v[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        float e2[2];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int k = 2 * (8 * part + c) + e;
+                            float val = 0.f;
+                            if (k < N)
+                                val = Aat(k, l).x;
+                            else if (k < 2 * N)
+                                val = Aat(k - N, l).y;
+                            e2[e] = val;
+                        }
+                        v[c] = pack_bf16(e2[0], e2[1]);
+                    }
+                    tmem_st8u(ta + 8 * part, v);
+                }
+            }
+        }
+        const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        tmem_st8(taXp, z);
+        tmem_st8(taXp + 8, z);
+        tmem_st8(taXb, z);
+        tmem_st8(taXb + 8, z);
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();  // A, operator rows of every tile in place before any group's MMA
+    if (!live) {
+        // idle warp: wait for the groups to finish, then leave
+        __syncthreads();
+        return;
+    }
+
+    const float alpha0 = a.alpha0;
+    const float tol2 = a.tol * a.tol;
+
+    // refill slot p from the work counter (one warp, lane n owns rows n and n + 32);
+    // returns the transition bits
+    auto refill = [&](int p) -> int {
+        long long q;
+        for (;;) {
+            if (lane == 0)
+                q = (long long)atomicAdd(a.counter, 1ULL);
+            q = __shfl_sync(0xffffffffu, q, 0);
+            if (q >= a.P) {
+                q = -1;
+                break;
+            }
+            const float2 *gq = a.g + (size_t)q * N;
+            const float2 g0 = (lane < N) ? gq[lane] : make_float2(0.f, 0.f);
+            const float2 g1 = (NCH > 1 && lane + 32 < N) ? gq[lane + 32] : make_float2(0.f, 0.f);
+            const bool allfin = __all_sync(0xffffffffu, isfinite(g0.x) && isfinite(g0.y) && isfinite(g1.x) &&
+                                                            isfinite(g1.y));
+            if (!allfin || a.max_iter <= 0) {
+                // non-finite g (or no iteration allowed): x = 0 at once
+                float2 *xq = a.x + (size_t)q * L;
+                for (int ll = lane; ll < L; ll += 32)
+                    xq[ll] = make_float2(0.f, 0.f);
+                if (lane == 0) {
+                    a.status[q] = allfin ? (BPDN_PX_NOT_CONVERGED | BPDN_PX_ZERO_SOLUTION) : BPDN_PX_NONFINITE;
+                    a.iters[q] = 0;
+                    if (a.nbt)
+                        a.nbt[q] = 0;
+                    if (a.nsupp)
+                        a.nsupp[q] = 0;
+                }
+                continue;
+            }
+            // x^0 = x^{-1} = 0: A y = 0 and r = -g for the first iteration
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                const int n = lane + 32 * c;
+                if (n < N) {
+                    const float2 gg = c ? g1 : g0;
+                    sG[p * N + n] = gg;
+                    sAx[p * N + n] = make_float2(0.f, 0.f);
+                    sAxp[p * N + n] = make_float2(0.f, 0.f);
+                    sAy[p * N + n] = make_float2(0.f, 0.f);
+                    put_r(p, n, -gg.x, -gg.y);
+                }
+            }
+            float gg2 = g0.x * g0.x + g0.y * g0.y + g1.x * g1.x + g1.y * g1.y;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1)
+                gg2 += __shfl_xor_sync(0xffffffffu, gg2, off);
+            if (lane == 0) {
+                const float lam = a.lam_pp ? a.lam[q] : a.lam[0];
+                S.k[p] = 1;
+                S.alpha[p] = alpha0;
+                S.Fx[p] = gg2;  // F(0) = ||g||^2
+                S.lam[p] = lam;
+                S.nbt[p] = 0;
+                S.nbt_it[p] = 0;
+                S.status[p] = 0;
+                S.nnz[p] = 0;
+                // (k-2)/(k+1) at k = 1 multiplies x - x_prev = 0
+                S.par[p] = make_float4(-0.5f, 2.f * alpha0, alpha0 * lam, 0.f);
+            }
+            break;
+        }
+        if (lane == 0)
+            S.pix[p] = q;
+        return (q >= 0) ? (T_ACTIVE | T_RESET) : 0;
+    };
+
+    // prologue: fill every slot
+    for (int p = blk; p < TPG; p += NW) {
+        const int bits = refill(p);
+        __syncwarp();
+        if (lane == 0)
+            S.par[p].w = __int_as_float(bits);
     }
     float2 x[TPG];
 #pragma unroll
     for (int p = 0; p < TPG; ++p)
         x[p] = make_float2(0.f, 0.f);
-    if (tid < TPG) {
-        S.flags[tid] = F_FIN;  // every slot starts empty and asks for a pixel
-        S.need[0][tid] = 0;
-        S.need[1][tid] = 0;
-        S.cnt[0][tid] = 0;
-        S.cnt[1][tid] = 0;
-        S.pix[tid] = -1;
-    }
-    if (tid == 0) {
-        S.retry[0] = S.retry[1] = S.retry[2] = 0;
-        S.nfin = TPG;
-        S.nactive = 0;
-        S.ndense = 0;
-    }
-    __syncthreads();  // A is complete for every group
+    uint32_t mma_phase = 0;
+    if constexpr (TC)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    group_sync(grp, 32 * NW);
 
-    const float alpha0 = a.alpha0;
-    const float tol2 = a.tol * a.tol;
-    int sweep = 0;  // C-DE sweeps so far (iterations and step-size retries)
-
-    for (int iter = 0;; ++iter) {
-        const int cur = iter & 1, nxt = cur ^ 1;
-        // ---------------- H: record finished pixels and refill their slots -----------
-        if (S.nfin) {
-            for (int p = warp; p < TPG; p += NW) {
-                if (!(S.flags[p] & F_FIN))
-                    continue;
-                long long q;
-                for (;;) {
-                    if (lane == 0)
-                        q = (long long)atomicAdd(a.counter, 1ULL);
-                    q = __shfl_sync(0xffffffffu, q, 0);
-                    if (q >= a.P) {
-                        q = -1;
-                        break;
-                    }
-                    const float2 *gq = a.g + (size_t)q * N;
-                    const float2 g0 = (lane < N) ? gq[lane] : make_float2(0.f, 0.f);
-                    const float2 g1 = (lane + 32 < N) ? gq[lane + 32] : make_float2(0.f, 0.f);
-                    const bool fin = isfinite(g0.x) && isfinite(g0.y) && isfinite(g1.x) && isfinite(g1.y);
-                    const bool allfin = __all_sync(0xffffffffu, fin);
-                    if (!allfin || a.max_iter <= 0) {
-                        // non-finite g (or no iteration allowed): x = 0 at once
-                        float2 *xq = a.x + (size_t)q * L;
-                        for (int l = lane; l < L; l += 32)
-                            xq[l] = make_float2(0.f, 0.f);
-                        if (lane == 0) {
-                            a.status[q] = allfin ? (BPDN_PX_NOT_CONVERGED | BPDN_PX_ZERO_SOLUTION)
-                                                 : BPDN_PX_NONFINITE;
-                            a.iters[q] = 0;
-                            if (a.nbt)
-                                a.nbt[q] = 0;
-                            if (a.nsupp)
-                                a.nsupp[q] = 0;
-                        }
-                        continue;
-                    }
-                    // x^0 = x^{-1} = 0: A y = 0 and r = -g for the first iteration
-                    for (int n = lane; n < N; n += 32) {
-                        const float2 gg = (n < 32) ? g0 : g1;
-                        sG[p * N + n] = gg;
-                        sAx[p * N + n] = make_float2(0.f, 0.f);
-                        sAxp[p * N + n] = make_float2(0.f, 0.f);
-                        sAy[p * N + n] = make_float2(0.f, 0.f);
-                        sRre[n * TPG + p] = -gg.x;
-                        sRim[n * TPG + p] = -gg.y;
-                    }
-                    float gg2 = g0.x * g0.x + g0.y * g0.y + g1.x * g1.x + g1.y * g1.y;
+    for (;;) {
+        tc_fence_after();
+        // ---------------- issue the gradient MMAs (BF16); transition --------------------------
+        int any = 0;
 #pragma unroll
-                    for (int off = 16; off >= 1; off >>= 1)
-                        gg2 += __shfl_xor_sync(0xffffffffu, gg2, off);
-                    if (lane == 0) {
-                        const float lam = a.lam_pp ? a.lam[q] : a.lam[0];
-                        S.k[p] = 1;
-                        S.alpha[p] = alpha0;
-                        S.Fx[p] = gg2;  // F(0) = ||g||^2
-                        S.lam[p] = lam;
-                        // (k-2)/(k+1) at k = 1 multiplies x - x_prev = 0
-                        S.par[p] = make_float4(-0.5f, 2.f * alpha0, alpha0 * lam, 0.f);
-                        S.nbt[p] = 0;
-                        S.status[p] = 0;
-                        S.nnz[p] = 0;
-                    }
-                    break;
-                }
-                if (lane == 0) {
-                    S.pix[p] = q;
-                    S.flags[p] = (q >= 0) ? F_ACTIVE : 0;
-                    S.need[cur][p] = (q >= 0);
-                    S.nbt_it[p] = 0;
-                }
-            }
-            group_sync(grp, Lpad);
-            if (tid == 0) {
-                int c = 0;
-                for (int p = 0; p < TPG; ++p)
-                    c += (S.flags[p] & F_ACTIVE) ? 1 : 0;
-                S.nactive = c;
-                S.nfin = 0;
-            }
-            group_sync(grp, Lpad);
-            if (S.nactive == 0)
-                break;
-        }
-
-        // ---------------- B: gradient sum_n conj(A_nl) r_n for l = tid -------------------
-        float2 gx[TPG / 2], gy[TPG / 2];  // slot pairs (2q, 2q+1): real and imaginary parts
+        for (int p = 0; p < TPG; ++p)
+            any |= __float_as_int(S.par[p].w);
+        const bool running = (any & T_ACTIVE) != 0;
+        if constexpr (TC) {
+            if (running && blk == 0 && lane == 0) {
+                const uint32_t b0 = smem_u32(sBop);
+                for (int t = 0; t < T; ++t) {
+                    const uint32_t d = tmem + colD + 16 * T * grp + 16 * t;
+                    const uint32_t arow = tmem + 32 * t;
 #pragma unroll
-        for (int q = 0; q < TPG / 2; ++q) {
-            gx[q] = make_float2(0.f, 0.f);
-            gy[q] = make_float2(0.f, 0.f);
+                    for (int j = 0; j < kK / 16; ++j)
+                        tc_mma_ts(d, arow + 8 * j, smem_desc(b0 + 256 * j, 128, (kK / 8) * 128), j > 0);
+                }
+                tc_commit(mbar);
+            }
         }
-        {
-            const float2 *pa = sA + tid;
+        if (any & (T_ACC | T_SHIFT | T_OUT | T_RESET)) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float xb[8], xp[8];
+                tmem_ld8(taXb + 8 * h, xb);
+                tmem_ld8(taXp + 8 * h, xp);
+                tmem_wait_ld();
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) {
+                    const int p = 4 * h + pp;
+                    const int b = __float_as_int(S.par[p].w);
+                    if (b & T_SHIFT) {
+                        xp[2 * pp] = x[p].x;
+                        xp[2 * pp + 1] = x[p].y;
+                    }
+                    if (b & T_ACC)
+                        x[p] = make_float2(xb[2 * pp], xb[2 * pp + 1]);
+                    if ((b & T_OUT) && l < L)
+                        a.x[(size_t)S.pix_out[p] * L + l] = x[p];
+                    if (b & T_RESET) {
+                        x[p] = make_float2(0.f, 0.f);
+                        xp[2 * pp] = 0.f;
+                        xp[2 * pp + 1] = 0.f;
+                    }
+                }
+                tmem_st8(taXp + 8 * h, xp);
+            }
+            tmem_wait_st();
+        }
+        if (!running)
+            break;
+
+        // ---------------- gradient sum_n conj(A_nl) r_n -----------------------------------------
+        float2 gx[TPG / 2], gy[TPG / 2];  // FP32 variant: slot pairs (2q, 2q+1), re and im
+        if constexpr (TC) {
+            if (!mbar_wait(mbar, mma_phase) && a.err)
+                atomicExch(a.err, 1);
+            mma_phase ^= 1u;
+            tc_fence_after();
+        } else {
+#pragma unroll
+            for (int q = 0; q < TPG / 2; ++q) {
+                gx[q] = make_float2(0.f, 0.f);
+                gy[q] = make_float2(0.f, 0.f);
+            }
             const float4 *rre = (const float4 *)sRre;
             const float4 *rim = (const float4 *)sRim;
 #pragma unroll 2
             for (int n = 0; n < N; ++n) {
-                const float2 av = pa[n * lda];
+                const float2 av = Aat(n, l);
                 const float2 ar2 = make_float2(av.x, av.x);
                 const float2 ai2 = make_float2(av.y, av.y);
                 const float2 nai2 = make_float2(-av.y, -av.y);
 #pragma unroll
-                for (int q4 = 0; q4 < TPG / 4; ++q4) {
-                    const float4 rx = rre[n * (TPG / 4) + q4];
-                    const float4 ry = rim[n * (TPG / 4) + q4];
+                for (int h4 = 0; h4 < TPG / 4; ++h4) {
+                    const float4 rx = rre[n * (TPG / 4) + h4];
+                    const float4 ry = rim[n * (TPG / 4) + h4];
                     const float2 rx0 = make_float2(rx.x, rx.y), rx1 = make_float2(rx.z, rx.w);
                     const float2 ry0 = make_float2(ry.x, ry.y), ry1 = make_float2(ry.z, ry.w);
                     // Re conj(a) r = ar rx + ai ry ;  Im conj(a) r = ar ry - ai rx
-                    gx[2 * q4] = ffma2(ai2, ry0, ffma2(ar2, rx0, gx[2 * q4]));
-                    gy[2 * q4] = ffma2(nai2, rx0, ffma2(ar2, ry0, gy[2 * q4]));
-                    gx[2 * q4 + 1] = ffma2(ai2, ry1, ffma2(ar2, rx1, gx[2 * q4 + 1]));
-                    gy[2 * q4 + 1] = ffma2(nai2, rx1, ffma2(ar2, ry1, gy[2 * q4 + 1]));
+                    gx[2 * h4] = ffma2(ai2, ry0, ffma2(ar2, rx0, gx[2 * h4]));
+                    gy[2 * h4] = ffma2(nai2, rx0, ffma2(ar2, ry0, gy[2 * h4]));
+                    gx[2 * h4 + 1] = ffma2(ai2, ry1, ffma2(ar2, rx1, gx[2 * h4 + 1]));
+                    gy[2 * h4 + 1] = ffma2(nai2, rx1, ffma2(ar2, ry1, gy[2 * h4 + 1]));
                 }
             }
         }
 
-        // ---------------- C, A xbar, DE with backtracking ----------------------------------------
-        for (int round = 0;; ++round) {
-            // C: prox, ballots, partial sums (two passes of 4 slots keep register use low)
+        // ---------------- C: prox, partial sums, A xbar over this block ---------------------------
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                float part[16];
+        for (int h = 0; h < 2; ++h) {
+            float gre[4], gim[4], xp[8], xbv[8];
+            if constexpr (TC) {
+                tmem_ld4(taD + 4 * h, gre);
+                tmem_ld4(taD + 8 + 4 * h, gim);
+            } else {
 #pragma unroll
-                for (int pp = 0; pp < TPG / 2; ++pp) {
-                    const int p = half * (TPG / 2) + pp;
-                    float dd = 0.f, l1 = 0.f, dx = 0.f, xn = 0.f;
-                    if (S.need[cur][p]) {
-                        const float4 par = S.par[p];  // beta, 2 alpha, tau = alpha lambda
-                        const float gre = (p & 1) ? gx[p >> 1].y : gx[p >> 1].x;
-                        const float gim = (p & 1) ? gy[p >> 1].y : gy[p >> 1].x;
-                        const float2 xp = sXp[p * Lpad + tid];
-                        const float yx = fmaf(par.x, x[p].x - xp.x, x[p].x);
-                        const float yy = fmaf(par.x, x[p].y - xp.y, x[p].y);
-                        const float vx = fmaf(-par.y, gre, yx), vy = fmaf(-par.y, gim, yy);
-                        const float m2 = fmaf(vx, vx, vy * vy);
-                        const float tau = par.z;
-                        float bx = 0.f, by = 0.f;
-                        bool nz = false;
-                        if (m2 > tau * tau) {
-                            const float mag = sqrtf(m2);
-                            if (mag > tau) {
-                                const float sc = 1.f - tau / mag;
-                                bx = vx * sc;
-                                by = vy * sc;
-                                l1 = mag - tau;
-                                nz = true;
-                            }
-                        }
-                        sXb[p * Lpad + tid] = make_float2(bx, by);
-                        const unsigned bal = __ballot_sync(0xffffffffu, nz);
-                        if (lane == 0) {
-                            sMask[p * NW + warp] = bal;
-                            if (bal)
-                                atomicAdd(&S.cnt[sweep & 1][p], __popc(bal));
-                        }
-                        const float ex = bx - yx, ey = by - yy;
-                        dd = fmaf(ex, ex, ey * ey);
-                        const float fx = bx - x[p].x, fy = by - x[p].y;
-                        dx = fmaf(fx, fx, fy * fy);
-                        xn = fmaf(bx, bx, by * by);
-                    }
-                    part[4 * pp + 0] = dd;
-                    part[4 * pp + 1] = l1;
-                    part[4 * pp + 2] = dx;
-                    part[4 * pp + 3] = xn;
-                }
-                warp_transpose_reduce16(part, lane);
-                // lanes 2i, 2i+1 hold value i: slot half*4 + i/4, quantity i%4
-                if ((lane & 1) == 0) {
-                    const int v = lane >> 1;
-                    sRed[(warp * TPG + half * (TPG / 2) + (v >> 2)) * 4 + (v & 3)] = part[0];
+                for (int pp = 0; pp < 4; ++pp) {
+                    const int p = 4 * h + pp;
+                    gre[pp] = (p & 1) ? gx[p >> 1].y : gx[p >> 1].x;
+                    gim[pp] = (p & 1) ? gy[p >> 1].y : gy[p >> 1].x;
                 }
             }
-            if (tid == 0)
-                S.retry[(round + 1) % 3] = 0;
-            group_sync(grp, Lpad);
+            tmem_ld8(taXp + 8 * h, xp);
+            tmem_wait_ld();
+            float part[16];
+#pragma unroll
+            for (int pp = 0; pp < 4; ++pp) {
+                const int p = 4 * h + pp;
+                float dd = 0.f, l1 = 0.f, dx = 0.f, xn = 0.f;
+                float bx = 0.f, by = 0.f;
+                const float4 par = S.par[p];  // beta, 2 alpha, tau = alpha lambda, bits
+                if (__float_as_int(par.w) & T_ACTIVE) {
+                    const float yx = fmaf(par.x, x[p].x - xp[2 * pp], x[p].x);
+                    const float yy = fmaf(par.x, x[p].y - xp[2 * pp + 1], x[p].y);
+                    const float vx = fmaf(-par.y, gre[pp], yx), vy = fmaf(-par.y, gim[pp], yy);
+                    const float m2 = fmaf(vx, vx, vy * vy);
+                    const float tau = par.z;
+                    // soft threshold (Eq. 12): scale 1 - tau / |v| where that is positive
+                    const float rs = rsqrtf(m2);
+                    const float sc = fmaf(-tau, rs, 1.f);
+                    const bool nz = sc > 0.f;
+                    if (nz) {
+                        bx = vx * sc;
+                        by = vy * sc;
+                        l1 = fmaf(m2, rs, -tau);
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, nz);
+                    if (lane == 0)
+                        sMask[p * NW + blk] = bal;
+                    if (bal) {
+                        // this block's share of A xbar, ascending l; lane n owns rows n, n + 32
+                        float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+                        unsigned m = bal;
+                        while (m) {
+                            const int j = __ffs(m) - 1;
+                            m &= m - 1;
+                            const float xr = __shfl_sync(0xffffffffu, bx, j);
+                            const float xi = __shfl_sync(0xffffffffu, by, j);
+                            const int lj = 32 * blk + j;
+                            if (lane < N) {
+                                const float2 av = Aat(lane, lj);
+                                acc0.x = fmaf(av.x, xr, fmaf(-av.y, xi, acc0.x));
+                                acc0.y = fmaf(av.x, xi, fmaf(av.y, xr, acc0.y));
+                            }
+                            if (NCH > 1 && lane + 32 < N) {
+                                const float2 av = Aat(lane + 32, lj);
+                                acc1.x = fmaf(av.x, xr, fmaf(-av.y, xi, acc1.x));
+                                acc1.y = fmaf(av.x, xi, fmaf(av.y, xr, acc1.y));
+                            }
+                        }
+                        if (lane < N)
+                            sPart[(p * NW + blk) * N + lane] = acc0;
+                        if (NCH > 1 && lane + 32 < N)
+                            sPart[(p * NW + blk) * N + lane + 32] = acc1;
+                    }
+                    const float ex = bx - yx, ey = by - yy;
+                    dd = fmaf(ex, ex, ey * ey);
+                    const float fx = bx - x[p].x, fy = by - x[p].y;
+                    dx = fmaf(fx, fx, fy * fy);
+                    xn = fmaf(bx, bx, by * by);
+                }
+                part[4 * pp + 0] = dd;
+                part[4 * pp + 1] = l1;
+                part[4 * pp + 2] = dx;
+                part[4 * pp + 3] = xn;
+                xbv[2 * pp] = bx;
+                xbv[2 * pp + 1] = by;
+            }
+            tmem_st8(taXb + 8 * h, xbv);
+            warp_transpose_reduce16(part, lane);
+            // lanes 2i, 2i+1 hold value i: slot 4h + i/4, quantity i%4
+            if ((lane & 1) == 0) {
+                const int v = lane >> 1;
+                ((float *)sRed)[(blk * TPG + 4 * h + (v >> 2)) * 4 + (v & 3)] = part[0];
+            }
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        group_sync(grp, 32 * NW);
 
-            // which slots need the dense A xbar pass
-            if (tid == 0) {
-                int nd = 0;
-                for (int p = 0; p < TPG; ++p)
-                    if (S.need[cur][p] && S.cnt[sweep & 1][p] > kSparseMax)
-                        S.dense[nd++] = p;
-                S.ndense = nd;
+        // ---------------- DE: one warp per slot ------------------------------------------------
+        for (int p = blk; p < TPG; p += NW) {
+            const int bits = __float_as_int(S.par[p].w);
+            if (!(bits & T_ACTIVE)) {
+                __syncwarp();
+                if (lane == 0)
+                    S.par[p].w = __int_as_float(0);
+                continue;
             }
-            if (tid < TPG)
-                S.cnt[(sweep + 1) & 1][tid] = 0;  // counts of the next sweep
-            group_sync(grp, Lpad);
-            const int ndense = S.ndense;
-            if (ndense) {
-                const int CH = Lpad / kChunks;  // Lpad is a multiple of 32
-                for (int it = tid; it < ndense * kChunks * N; it += Lpad) {
-                    const int jc = it / N, n = it - (it / N) * N;  // jc = j * kChunks + c
-                    const int j = jc / kChunks, c = jc - (jc / kChunks) * kChunks;
-                    const int p = S.dense[j];
-                    const float2 *xr = sXb + p * Lpad + c * CH;
-                    const float2 *ar = sA + n * lda + c * CH;
-                    float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
-                    for (int l = 0; l < CH; l += 2) {
-                        const float2 x0 = xr[l], a0 = ar[l], x1 = xr[l + 1], a1 = ar[l + 1];
-                        s0.x = fmaf(a0.x, x0.x, fmaf(-a0.y, x0.y, s0.x));
-                        s0.y = fmaf(a0.x, x0.y, fmaf(a0.y, x0.x, s0.y));
-                        s1.x = fmaf(a1.x, x1.x, fmaf(-a1.y, x1.y, s1.x));
-                        s1.y = fmaf(a1.x, x1.y, fmaf(a1.y, x1.x, s1.y));
-                    }
-                    sPart[(p * kChunks + c) * N + n] = make_float2(s0.x + s1.x, s0.y + s1.y);
-                }
-                group_sync(grp, Lpad);
-            }
-
-            // DE: one half-warp per slot (slots 2 pw, 2 pw + 1 on warp pw mod #warps)
-            for (int pw = warp; pw < TPG / 2; pw += NW) {
-                const int p = 2 * pw + (lane >> 4);
-                const int h = lane & 15;
-                const unsigned hmask = (lane < 16) ? 0x0000ffffu : 0xffff0000u;
-                if (!S.need[cur][p])
-                    continue;
-                // A xbar; lane h owns n = h + 16 j
-                float2 axb[4];
+            // A xbar and nnz over the blocks in ascending order; lane n owns rows n, n + 32
+            const uint32_t mw = (lane < NW) ? sMask[p * NW + lane] : 0u;
+            const int nnz = (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(mw));
+            unsigned wm = __ballot_sync(0xffffffffu, mw != 0u);
+            float2 axb[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            while (wm) {
+                const int b = __ffs(wm) - 1;
+                wm &= wm - 1;
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    axb[j] = make_float2(0.f, 0.f);
-                const bool dense = S.cnt[sweep & 1][p] > kSparseMax;
-                if (dense) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int n = h + 16 * j;
-                        if (n < N)
-#pragma unroll
-                            for (int c = 0; c < kChunks; ++c) {
-                                const float2 v = sPart[(p * kChunks + c) * N + n];
-                                axb[j].x += v.x;
-                                axb[j].y += v.y;
-                            }
-                    }
-                } else {
-                    // over the nonzeros of xbar in ascending l, four per trip
-                    for (int w = 0; w < NW; ++w) {
-                        uint32_t msk = sMask[p * NW + w];
-                        while (msk) {
-                            int lq[4];
-                            float2 xq[4];
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                lq[u] = msk ? (w * 32 + __ffs(msk) - 1) : -1;
-                                msk &= msk - 1;
-                                xq[u] = (lq[u] >= 0) ? sXb[p * Lpad + lq[u]] : make_float2(0.f, 0.f);
-                            }
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                const int n = h + 16 * j;
-                                if (n < N) {
-#pragma unroll
-                                    for (int u = 0; u < 4; ++u) {
-                                        if (lq[u] >= 0) {
-                                            const float2 av = sA[n * lda + lq[u]];
-                                            axb[j].x = fmaf(av.x, xq[u].x, fmaf(-av.y, xq[u].y, axb[j].x));
-                                            axb[j].y = fmaf(av.x, xq[u].y, fmaf(av.y, xq[u].x, axb[j].y));
-                                        }
-                                    }
-                                }
-                            }
-                        }
-                    }
-                }
-                float lhs = 0.f, res = 0.f, dd = 0.f, l1 = 0.f, dx = 0.f, xn = 0.f;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int n = h + 16 * j;
+                for (int c = 0; c < NCH; ++c) {
+                    const int n = lane + 32 * c;
                     if (n < N) {
-                        const float2 ay = sAy[p * N + n], gg = sG[p * N + n];
-                        const float d0 = axb[j].x - ay.x, d1 = axb[j].y - ay.y;
-                        lhs = fmaf(d0, d0, fmaf(d1, d1, lhs));
-                        const float e0 = axb[j].x - gg.x, e1 = axb[j].y - gg.y;
-                        res = fmaf(e0, e0, fmaf(e1, e1, res));
+                        const float2 v = sPart[(p * NW + b) * N + n];
+                        axb[c].x += v.x;
+                        axb[c].y += v.y;
                     }
                 }
-                if (h < NW) {
-                    const float4 rd = *(const float4 *)(sRed + (h * TPG + p) * 4);
-                    dd = rd.x;
-                    l1 = rd.y;
-                    dx = rd.z;
-                    xn = rd.w;
-                }
+            }
+            // sums over the grid: lane b < NW holds block b's partial sums
+            float4 rd = (lane < NW) ? sRed[lane * TPG + p] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float lhs = 0.f, res = 0.f;
+            float2 gg[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
-                for (int off = 8; off >= 1; off >>= 1) {
-                    lhs += __shfl_xor_sync(hmask, lhs, off);
-                    res += __shfl_xor_sync(hmask, res, off);
-                    dd += __shfl_xor_sync(hmask, dd, off);
-                    l1 += __shfl_xor_sync(hmask, l1, off);
-                    dx += __shfl_xor_sync(hmask, dx, off);
-                    xn += __shfl_xor_sync(hmask, xn, off);
+            for (int c = 0; c < NCH; ++c) {
+                const int n = lane + 32 * c;
+                if (n < N) {
+                    const float2 ay = sAy[p * N + n];
+                    gg[c] = sG[p * N + n];
+                    const float d0 = axb[c].x - ay.x, d1 = axb[c].y - ay.y;
+                    lhs = fmaf(d0, d0, fmaf(d1, d1, lhs));
+                    const float e0 = axb[c].x - gg[c].x, e1 = axb[c].y - gg[c].y;
+                    res = fmaf(e0, e0, fmaf(e1, e1, res));
                 }
-                const float al = S.alpha[p];
-                const bool bt_ok = lhs <= dd / (2.f * al);
-                if (!bt_ok && S.nbt_it[p] < a.max_bt) {
-                    // Eq. 15 failed: shrink the step and redo the prox for this slot
-                    __syncwarp(hmask);
-                    if (h == 0) {
-                        const float an = al * a.c_alpha;
-                        S.alpha[p] = an;
-                        S.par[p].y = 2.f * an;
-                        S.par[p].z = an * S.lam[p];
-                        S.nbt[p] += 1;
-                        S.nbt_it[p] += 1;
-                        atomicAdd(&S.retry[round % 3], 1);
-                    }
-                    continue;
-                }
-                const float Fb = fmaf(S.lam[p], l1, res);
-                const bool accepted = (Fb <= S.Fx[p]);
-                const bool conv = (dx <= tol2 * xn) || (dx == 0.f);
-                const int k = S.k[p];
-                const bool fin = conv || (k >= a.max_iter);
-                // N-space state: A x^{k-1} <- A x^k, A x^{k+1} <- A xbar (accepted); for the
-                // next iteration A y = A x + beta (A x - A x_prev), r = A y - g
-                const float beta_n = (float)(k - 1) / (float)(k + 2);
+            }
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int n = h + 16 * j;
+            for (int off = 16; off >= 1; off >>= 1) {
+                lhs += __shfl_xor_sync(0xffffffffu, lhs, off);
+                res += __shfl_xor_sync(0xffffffffu, res, off);
+                rd.x += __shfl_xor_sync(0xffffffffu, rd.x, off);
+                rd.y += __shfl_xor_sync(0xffffffffu, rd.y, off);
+                rd.z += __shfl_xor_sync(0xffffffffu, rd.z, off);
+                rd.w += __shfl_xor_sync(0xffffffffu, rd.w, off);
+            }
+            const float dd = rd.x, l1 = rd.y, dx = rd.z, xn = rd.w;
+            const float al = S.alpha[p];
+            const bool bt_ok = lhs <= dd / (2.f * al);
+            const int nbt_it = S.nbt_it[p];
+            __syncwarp();
+            if (!bt_ok && nbt_it < a.max_bt) {
+                // Eq. 15 failed: the next sweep redoes the prox with the smaller step
+                if (lane == 0) {
+                    const float an = al * a.c_alpha;
+                    S.alpha[p] = an;
+                    S.nbt[p] += 1;
+                    S.nbt_it[p] = nbt_it + 1;
+                    S.par[p] = make_float4(S.par[p].x, 2.f * an, an * S.lam[p], __int_as_float(T_ACTIVE));
+                }
+                continue;
+            }
+            const float Fb = fmaf(S.lam[p], l1, res);
+            const bool accepted = (Fb <= S.Fx[p]);
+            const bool conv = (dx <= tol2 * xn) || (dx == 0.f);
+            const int k = S.k[p];
+            const bool fin = conv || (k >= a.max_iter);
+            // N-space state: A x^{k-1} <- A x^k, A x^k <- A xbar (accepted); for the next
+            // iteration A y = A x + beta (A x - A x_prev), r = A y - g
+            const float beta_n = (float)(k - 1) / (float)(k + 2);
+            __syncwarp();  // every lane has read the slot state lane 0 updates below
+            if (!fin) {
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    const int n = lane + 32 * c;
                     if (n < N) {
                         const float2 axo = sAx[p * N + n];
-                        const float2 axn = accepted ? axb[j] : axo;
+                        const float2 axn = accepted ? axb[c] : axo;
                         sAxp[p * N + n] = axo;
                         sAx[p * N + n] = axn;
-                        if (!fin) {
-                            const float2 ay = make_float2(fmaf(beta_n, axn.x - axo.x, axn.x),
-                                                          fmaf(beta_n, axn.y - axo.y, axn.y));
-                            const float2 gg = sG[p * N + n];
-                            sAy[p * N + n] = ay;
-                            sRre[n * TPG + p] = ay.x - gg.x;
-                            sRim[n * TPG + p] = ay.y - gg.y;
-                        }
-                    }
-                }
-                __syncwarp(hmask);
-                if (h == 0) {
-                    int st = S.status[p];
-                    if (!bt_ok)
-                        st |= BPDN_PX_BT_LIMIT;
-                    int nnz = S.nnz[p];
-                    if (accepted) {
-                        S.Fx[p] = Fb;
-                        nnz = 0;
-                        for (int w = 0; w < NW; ++w)
-                            nnz += __popc(sMask[p * NW + w]);
-                        S.nnz[p] = nnz;
-                    }
-                    if (fin && !conv)
-                        st |= BPDN_PX_NOT_CONVERGED;
-                    S.status[p] = st;
-                    S.flags[p] = F_ACTIVE | (accepted ? F_ACC : 0) | (fin ? F_FIN : 0);
-                    S.need[cur][p] = 0;
-                    S.need[nxt][p] = fin ? 0 : 1;
-                    if (fin) {
-                        atomicAdd(&S.nfin, 1);
-                        const long long q = S.pix[p];
-                        a.status[q] = (nnz == 0) ? (st | BPDN_PX_ZERO_SOLUTION) : st;
-                        a.iters[q] = k;
-                        if (a.nbt)
-                            a.nbt[q] = S.nbt[p];
-                        if (a.nsupp)
-                            a.nsupp[q] = nnz;
-                    } else {
-                        S.k[p] = k + 1;
-                        S.par[p].x = beta_n;
-                        S.nbt_it[p] = 0;
+                        const float2 ayn = make_float2(fmaf(beta_n, axn.x - axo.x, axn.x),
+                                                       fmaf(beta_n, axn.y - axo.y, axn.y));
+                        sAy[p * N + n] = ayn;
+                        put_r(p, n, ayn.x - gg[c].x, ayn.y - gg[c].y);
                     }
                 }
             }
-            group_sync(grp, Lpad);
-            ++sweep;
-            if (S.retry[round % 3] == 0)
-                break;
-        }
-
-        // ---------------- G: registers and outputs -------------------------------------------
-#pragma unroll
-        for (int p = 0; p < TPG; ++p) {
-            const int fl = S.flags[p];
-            if (!(fl & F_ACTIVE))
-                continue;
-            const float2 xo = x[p];
-            if (fl & F_ACC)
-                x[p] = sXb[p * Lpad + tid];
-            if (fl & F_FIN) {
-                if (tid < L)
-                    a.x[(size_t)S.pix[p] * L + tid] = x[p];
-                x[p] = make_float2(0.f, 0.f);
-                sXp[p * Lpad + tid] = make_float2(0.f, 0.f);
-            } else {
-                sXp[p * Lpad + tid] = xo;
+            int nbits = T_SHIFT | (accepted ? T_ACC : 0);
+            if (lane == 0) {
+                int st = S.status[p];
+                if (!bt_ok)
+                    st |= BPDN_PX_BT_LIMIT;
+                if (fin && !conv)
+                    st |= BPDN_PX_NOT_CONVERGED;
+                int nz = S.nnz[p];
+                if (accepted) {
+                    S.Fx[p] = Fb;
+                    nz = nnz;
+                    S.nnz[p] = nz;
+                }
+                S.status[p] = st;
+                if (fin) {
+                    const long long q = S.pix[p];
+                    a.status[q] = (nz == 0) ? (st | BPDN_PX_ZERO_SOLUTION) : st;
+                    a.iters[q] = k;
+                    if (a.nbt)
+                        a.nbt[q] = S.nbt[p];
+                    if (a.nsupp)
+                        a.nsupp[q] = nz;
+                    S.pix_out[p] = q;
+                } else {
+                    S.k[p] = k + 1;
+                    S.nbt_it[p] = 0;
+                    S.par[p] = make_float4(beta_n, S.par[p].y, S.par[p].z, __int_as_float(nbits | T_ACTIVE));
+                }
+            }
+            if (fin) {
+                __syncwarp();
+                nbits |= T_OUT | refill(p);
+                __syncwarp();
+                if (lane == 0)
+                    S.par[p].w = __int_as_float(nbits);
             }
         }
-        if (S.nfin)
-            group_sync(grp, Lpad);
+        if constexpr (TC)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B rows for the MMA
+        tc_fence_before();
+        group_sync(grp, 32 * NW);
+    }
+    // every group has finished and no MMA is in flight: release tensor memory
+    tc_fence_before();
+    __syncthreads();
+    if (w == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
     }
 }
 
-int choose_groups(const OpHandle &op, int max_smem, size_t *smem_out)
+// launch shape of one solve
+struct Plan {
+    int groups, threads;
+    bool smem_a;
+    size_t smem;
+};
+
+// Pick groups per CTA and where A lives: two groups before one, A in shared memory
+// before A in global memory.  Returns an empty string on success, else the reason.
+const char *make_plan(const OpHandle &op, bool tc, int max_smem, Plan *pl)
 {
-    const GroupLayout lay = group_layout(op.N, op.Lpad);
-    const size_t base = a_bytes(op.N, op.lda);
-    int g = kMaxThreads / op.Lpad;
-    if (g > kMaxGroups)
-        g = kMaxGroups;
-    while (g > 1 && base + (size_t)g * lay.bytes > (size_t)max_smem)
-        --g;
-    *smem_out = base + (size_t)g * lay.bytes;
-    return g;
+    if (op.Lpad > 32 * kMaxNW)
+        return "the iteration kernel handles L <= 1024";
+    if (tc && (2 * op.N > kK || op.Lpad > 512))
+        return "precision 1 (BF16 tensor cores) needs 2N <= 64 and L <= 512";
+    const int T = (op.Lpad + 127) / 128;
+    const GroupLayout lay = group_layout(op.N, op.Lpad, tc);
+    const size_t abytes = a_bytes(op.N, op.lda);
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool sa = (pass == 0);
+        if (!sa && tc)
+            break;
+        for (int g = kMaxGroups; g >= 1; --g) {
+            const int W = warps_for(op.Lpad, g);
+            // the BF16 variant is built for at most 832 threads, the FP32 ones for 1024
+            if (32 * W > (tc ? 832 : 1024) || tmem_cols_used(T, g, tc) > kTmemCols)
+                continue;
+            const size_t smem = (sa ? abytes : 0) + (size_t)g * lay.bytes;
+            if (smem > (size_t)max_smem)
+                continue;
+            pl->groups = g;
+            pl->threads = 32 * W;
+            pl->smem_a = sa;
+            pl->smem = smem;
+            return "";
+        }
+    }
+    return "the iteration kernel's shared memory does not fit (N and L too large)";
+}
+
+template <bool TC, bool SA, int MAXT>
+cudaError_t launch_variant(const Params &prm, const Plan &pl, int grid, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_rbpg<TC, SA, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    k_rbpg<TC, SA, MAXT><<<grid, pl.threads, smem, s>>>(prm, pl.groups);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t rbpg_smem_bytes(const OpHandle &op)
+const char *rbpg_check(const OpHandle &op, int precision, int max_smem)
 {
-    // the smallest configuration (one group)
-    return a_bytes(op.N, op.lda) + group_layout(op.N, op.Lpad).bytes;
+    Plan pl;
+    return make_plan(op, precision == 1, max_smem, &pl);
 }
 
 cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s)
@@ -634,17 +949,26 @@ cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, c
     e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess)
         return e;
-    size_t smem = 0;
-    const int groups = choose_groups(op, max_smem, &smem);
-    e = cudaFuncSetAttribute(k_rbpg_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-        return e;
-    const long long tiles = (a.P + (long long)groups * TPG - 1) / ((long long)groups * TPG);
+    const bool tc = (a.precision == 1);
+    Plan pl;
+    if (make_plan(op, tc, max_smem, &pl)[0] != '\0')
+        return cudaErrorInvalidValue;
+    // one CTA per SM: each CTA allocates all 512 tensor-memory columns
+    size_t smem = pl.smem;
+    if (smem < (size_t)max_smem / 2 + 1024)
+        smem = (size_t)max_smem / 2 + 1024;
+    const long long tiles = (a.P + (long long)pl.groups * TPG - 1) / ((long long)pl.groups * TPG);
     int grid = (int)((tiles < num_sms) ? tiles : num_sms);
     if (grid < 1)
         grid = 1;
-    k_rbpg_fp32<<<grid, groups * op.Lpad, smem, s>>>(prm);
-    return cudaGetLastError();
+    const bool big = pl.threads > 832;
+    if (tc)
+        return launch_variant<true, true, 832>(prm, pl, grid, smem, s);
+    if (pl.smem_a)
+        return big ? launch_variant<false, true, 1024>(prm, pl, grid, smem, s)
+                   : launch_variant<false, true, 832>(prm, pl, grid, smem, s);
+    return big ? launch_variant<false, false, 1024>(prm, pl, grid, smem, s)
+               : launch_variant<false, false, 832>(prm, pl, grid, smem, s);
 }
 
 }  // namespace bpdn

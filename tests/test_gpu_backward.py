@@ -156,20 +156,26 @@ def test_autograd_function_and_lambda_tuning(api):
     torch.cuda.synchronize()
     assert torch.allclose(g.grad, dg, rtol=1e-5, atol=1e-12) and torch.allclose(lam.grad, dl, rtol=1e-5)
     # d(error)/d(lambda) of the whole batch against a central difference of the forward map,
-    # at 1.5 times the default weight (supports small and strict on nearly every pixel)
+    # at 1.5 times the default weight (supports small and strict on nearly every pixel).
+    # The sum runs over the pixels certified at all three weights: elsewhere x is the last
+    # iterate of Algorithm 1, whose changes with lambda the adjoint does not describe.
     gd = g.detach()
     lam0 = 1.5 * st.lam
+    eps = 1e-3
+    rp = api.solve(op, gd, lam0 * (1 + eps))
+    rm = api.solve(op, gd, lam0 * (1 - eps))
+    r0 = api.solve(op, gd, lam0)
+    keep = (((rp.status & rm.status & r0.status) & 64) != 0).unsqueeze(1).to(torch.float32)
+    den = gt.abs().pow(2).sum()
 
-    def rel_err(xx):
-        return (xx - gt).abs().pow(2).sum() / gt.abs().pow(2).sum()
+    def masked_err(xx):
+        return ((xx - gt).abs().pow(2) * keep).sum() / den
 
     lt = torch.tensor([lam0], dtype=torch.float32, device="cuda", requires_grad=True)
     xt, _ = api.BPDNFunction.apply(gd, lt, op, None)
-    (d,) = torch.autograd.grad(rel_err(xt), lt)
-    eps = 1e-3
-    ep = rel_err(api.solve(op, gd, lam0 * (1 + eps)).x).item()
-    em = rel_err(api.solve(op, gd, lam0 * (1 - eps)).x).item()
-    fd = (ep - em) / (2 * eps * lam0)
+    (d,) = torch.autograd.grad(masked_err(xt), lt)
+    fd = (masked_err(rp.x).item() - masked_err(rm.x).item()) / (2 * eps * lam0)
+    assert keep.mean().item() > 0.9
     assert abs(d.item() - fd) <= 0.05 * abs(fd), (d.item(), fd)
     # gradient descent on log lambda (first step 0.1 in log lambda) lowers the error
     lr = 0.1 / abs(d.item() * lam0)

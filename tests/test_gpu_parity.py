@@ -216,3 +216,26 @@ def test_bf16_rejects_unsupported_sizes(api):
     with pytest.raises(_lib.BPDNError) as ei:
         api.solve(op, g, 1.0, precision=1)
     assert ei.value.code == -3
+
+
+@pytest.mark.parametrize("N,L,half_width", [(60, 600, 250.0), (40, 300, 120.0), (12, 1000, 300.0)])
+def test_solve_refit_operator_sizes(api, N, L, half_width):
+    """FP32 path beyond the sizes of the benchmark stack: N > 32 (two rows per lane),
+    L > 512, and an operator too large for shared memory (N=60, L=600: A is read from
+    global memory).  Same bar as the small workload against the exact minimiser."""
+    rng = np.random.default_rng(1000 + N + L)
+    geom = synth.make_geometry(rng, N, L, 250.0, half_width)
+    st = synth.make_stack(geom, 48, rng, lam=synth.default_lambda(N, L), snr_db_range=(5.0, 20.0))
+    A = oracle.operator(st.geom)
+    ref = oracle.minimise_batch(A, st.g, st.lam)
+    op = api.Operator.from_geometry(st.geom)
+    res = api.solve(op, torch.from_numpy(st.g).cuda(), st.lam)
+    x = res.x.cpu().numpy().astype(np.complex128)
+    status = res.status.cpu().numpy()
+    cert = (status & 64) != 0
+    assert cert.mean() >= 0.9, cert.mean()
+    degenerate = (ref["margin"] < 1e-6) | ((ref["nS"] > 0) & (ref["min_abs_on"] < 1e-6 * np.abs(ref["x"]).max(1)))
+    sel = cert & ~degenerate
+    assert sel.sum() >= 30
+    assert np.array_equal(x[sel] != 0, ref["x"][sel] != 0)
+    assert _rel(x[sel], ref["x"][sel]).max() <= 1e-4
