@@ -163,6 +163,42 @@ int bpdn_refit(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda,
                void *d_x_out, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
                void *cuda_stream);
 
+/* ------------------------------------------------------------ ragged batch */
+
+/* One stack of a ragged batch: its operator and the buffers bpdn_solve would take. */
+typedef struct {
+    bpdn_op_t op;
+    const void *d_g;           /* device c64 [P, N] */
+    int64_t P;
+    const float *d_lambda;     /* device float32 [1] or [P] */
+    int32_t lambda_per_pixel;
+    void *d_x;                 /* device c64 [P, L] out */
+    int32_t *d_support;        /* device int32 [P, s_max] out, or NULL */
+    int32_t *d_nsupp;          /* device int32 [P] out, or NULL */
+    int32_t *d_status;         /* device int32 [P] out */
+    int32_t *d_iters;          /* device int32 [P] out */
+    int32_t *d_nbt;            /* device int32 [P] out, or NULL */
+} bpdn_stack;
+
+/* Workspace of bpdn_solve_ragged: 256 bytes per stack. */
+size_t bpdn_solve_ragged_workspace_bytes(int32_t n_stacks);
+
+/*
+ * Solve many stacks, each with its own operator (N, L, grid) and pixel count, in one
+ * call: every stack gets exactly the results bpdn_solve would give it.  Every
+ * stack's arguments are checked first; on any error nothing is launched and the
+ * message names the stack.  The solves are issued largest first (by P N L) on a
+ * few library-owned streams that fork from and join back into cuda_stream through
+ * events, so the end of one stack overlaps the start of the next and the whole
+ * call can be captured into one CUDA graph.  The streams and events are created by
+ * the first call on a device: make that call before any stream capture.  Calls on
+ * the same device are serialised on the host; their GPU work may overlap only
+ * through cuda_stream's own ordering.  Allocates no device memory.
+ * The paper solves one stack at a time; this is the batched form of the same solve.
+ */
+int bpdn_solve_ragged(const bpdn_stack *stacks, int32_t n_stacks, const bpdn_options *opt,
+                      void *d_workspace, size_t workspace_bytes, void *cuda_stream);
+
 /* ---------------------------------------------------------------- adjoint */
 
 /* Bytes of device workspace bpdn_backward needs for P pixels: 8 P (the per-pixel

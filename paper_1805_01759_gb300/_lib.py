@@ -31,6 +31,7 @@ EXPORTED = [
     "bpdn_destroy_operator", "bpdn_op_info", "bpdn_op_lipschitz", "bpdn_op_export",
     "bpdn_solve_workspace_bytes", "bpdn_solve", "bpdn_refit", "bpdn_last_error", "bpdn_version",
     "bpdn_solve_noalloc", "bpdn_backward_workspace_bytes", "bpdn_backward",
+    "bpdn_solve_ragged_workspace_bytes", "bpdn_solve_ragged",
 ]
 
 
@@ -58,6 +59,23 @@ class BPDNError(RuntimeError):
 
 
 _lib = None
+
+
+class Stack(ctypes.Structure):
+    """Mirror of bpdn_stack."""
+    _fields_ = [
+        ("op", ctypes.c_void_p),
+        ("d_g", ctypes.c_void_p),
+        ("P", ctypes.c_int64),
+        ("d_lambda", ctypes.c_void_p),
+        ("lambda_per_pixel", ctypes.c_int32),
+        ("d_x", ctypes.c_void_p),
+        ("d_support", ctypes.c_void_p),
+        ("d_nsupp", ctypes.c_void_p),
+        ("d_status", ctypes.c_void_p),
+        ("d_iters", ctypes.c_void_p),
+        ("d_nbt", ctypes.c_void_p),
+    ]
 
 
 def library_path() -> str:
@@ -108,6 +126,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.bpdn_backward_workspace_bytes.restype = sz
     lib.bpdn_backward.argtypes = [op_t, i64, vp, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp, sz, vp]
     lib.bpdn_backward.restype = ctypes.c_int
+    lib.bpdn_solve_ragged_workspace_bytes.argtypes = [i32]
+    lib.bpdn_solve_ragged_workspace_bytes.restype = sz
+    lib.bpdn_solve_ragged.argtypes = [ctypes.POINTER(Stack), i32, optp, vp, sz, vp]
+    lib.bpdn_solve_ragged.restype = ctypes.c_int
     lib.bpdn_last_error.argtypes = []
     lib.bpdn_last_error.restype = ctypes.c_char_p
     lib.bpdn_version.argtypes = []

@@ -242,3 +242,70 @@ def tune_lambda(op: Operator, g: torch.Tensor, gamma_true: torch.Tensor, lam0: f
         with torch.no_grad():
             log_lam -= lr * grad
     return float(log_lam.exp().item()), history
+
+
+class RaggedSolver:
+    """Many stacks, each with its own operator and pixel count, through bpdn_solve_ragged.
+
+    items: list of (Operator, g [P_s, N_s] complex64 CUDA tensor, lambda).  Outputs are
+    allocated once (`results`, one SolveResult per stack).  run() launches on the current
+    (or given) stream; capture() records one call into a CUDA graph and replay()
+    relaunches it: the graph reads the same g tensors, so new data is copied into them."""
+
+    def __init__(self, items, **options):
+        lib = _lib.load()
+        self.opt = _lib.default_options(**options)
+        self.items = []
+        self.results = []
+        self._keep = []
+        arr = (_lib.Stack * len(items))()
+        for i, (op, g, lam) in enumerate(items):
+            g = _check_g(op, g)
+            P = g.shape[0]
+            dev = g.device
+            lam_t, pp = _lambda_tensor(lam, P, dev)
+            res = SolveResult(
+                x=torch.empty((P, op.L), dtype=torch.complex64, device=dev),
+                status=torch.zeros(P, dtype=torch.int32, device=dev),
+                iters=torch.empty(P, dtype=torch.int32, device=dev),
+                nbt=torch.empty(P, dtype=torch.int32, device=dev),
+                nsupp=torch.empty(P, dtype=torch.int32, device=dev),
+                support=(torch.empty((P, self.opt.s_max), dtype=torch.int32, device=dev)
+                         if self.opt.refit else None),
+            )
+            arr[i] = _lib.Stack(op.handle.value, g.data_ptr(), P, lam_t.data_ptr(), pp, res.x.data_ptr(),
+                                _ptr(res.support), res.nsupp.data_ptr(), res.status.data_ptr(),
+                                res.iters.data_ptr(), res.nbt.data_ptr())
+            self.items.append((op, g, lam_t))
+            self.results.append(res)
+        self._arr = arr
+        self.ws_bytes = lib.bpdn_solve_ragged_workspace_bytes(len(items))
+        dev = self.items[0][1].device if self.items else torch.device("cuda")
+        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        self.graph = None
+
+    def run(self, stream: torch.cuda.Stream | None = None) -> list:
+        lib = _lib.load()
+        _lib.check(lib.bpdn_solve_ragged(self._arr, len(self.items), ctypes.byref(self.opt),
+                                         self.ws.data_ptr(), self.ws_bytes, _stream(stream)))
+        return self.results
+
+    def capture(self) -> "torch.cuda.CUDAGraph":
+        self.run()  # the first call creates the library's streams outside the capture
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.run()
+        self.graph = graph
+        return graph
+
+    def replay(self) -> list:
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        self.graph.replay()
+        return self.results
+
+
+def solve_ragged(items, *, stream: torch.cuda.Stream | None = None, **options) -> list:
+    """Solve every (Operator, g, lambda) stack of `items` in one bpdn_solve_ragged call."""
+    return RaggedSolver(items, **options).run(stream)

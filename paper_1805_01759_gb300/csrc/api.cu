@@ -117,6 +117,102 @@ static int check_options(const bpdn_options *o)
 
 using namespace bpdn;
 
+namespace bpdn {
+static int check_solve_buffers(const OpHandle *op, const void *d_g, int64_t P, const float *d_lambda,
+                               const void *d_x, const int32_t *d_status)
+{
+    if (P < 0)
+        return set_error(BPDN_EINVAL, "P must be >= 0");
+    if (P > ((int64_t)1 << 40))
+        return set_error(BPDN_ESIZE, "P = %lld too large", (long long)P);
+    if (P == 0)
+        return BPDN_OK;
+    if (!d_g || !d_lambda || !d_x || !d_status)
+        return set_error(BPDN_EINVAL, "g, lambda, x and status pointers must be non-NULL");
+    if (!aligned(d_g, 8) || !aligned(d_x, 8) || !aligned(d_lambda, 4) || !aligned(d_status, 4))
+        return set_error(BPDN_EALIGN, "g and x must be 8-byte aligned, lambda and status 4-byte");
+    (void)op;
+    return BPDN_OK;
+}
+
+// Checks every argument of a solve; launches it when `launch` is true.
+int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, int32_t lambda_per_pixel,
+               const bpdn_options *opt, void *d_x, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
+               int32_t *d_iters, int32_t *d_nbt, void *d_workspace, size_t workspace_bytes, void *cuda_stream,
+               bool launch)
+{
+    OpHandle *op = nullptr;
+    int rc = check_op(h, &op);
+    if (rc)
+        return rc;
+    rc = check_options(opt);
+    if (rc)
+        return rc;
+    rc = check_solve_buffers(op, d_g, P, d_lambda, d_x, d_status);
+    if (rc)
+        return rc;
+    if (P == 0)
+        return BPDN_OK;
+    if (!d_iters)
+        return set_error(BPDN_EINVAL, "iters pointer must be non-NULL");
+    if (!d_workspace || workspace_bytes < bpdn_solve_workspace_bytes(h, P, opt))
+        return set_error(BPDN_ESIZE, "solve workspace too small");
+    if (!aligned(d_workspace, 256))
+        return set_error(BPDN_EALIGN, "solve workspace must be 256-byte aligned");
+    if (opt->refit && d_support && !aligned(d_support, 4))
+        return set_error(BPDN_EALIGN, "support must be 4-byte aligned");
+    int dev = op->device;
+    const char *why = rbpg_check(*op, opt->precision, max_smem_optin(dev));
+    if (why[0] != '\0')
+        return set_error(BPDN_ESIZE, "N = %d, L = %d, precision %d: %s", op->N, op->L, opt->precision, why);
+    if (!launch)
+        return BPDN_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    unsigned long long *counter = (unsigned long long *)d_workspace;
+    // work counter (8 bytes) and the kernel's error word (4 bytes)
+    rc = check_cuda(cudaMemsetAsync(counter, 0, 16, s), "reset work counter");
+    if (rc)
+        return rc;
+    SolveLaunch a;
+    a.g = (const float2 *)d_g;
+    a.P = P;
+    a.lam = d_lambda;
+    a.lam_pp = lambda_per_pixel ? 1 : 0;
+    a.x = (float2 *)d_x;
+    a.nsupp = d_nsupp;
+    a.status = d_status;
+    a.iters = d_iters;
+    a.nbt = d_nbt;
+    a.counter = counter;
+    a.max_iter = opt->max_iter;
+    a.tol = opt->tol;
+    a.c_alpha = opt->c_alpha;
+    a.alpha0 = (float)(opt->alpha0_scale / (2.0 * op->N));
+    a.max_bt = opt->max_bt;
+    a.precision = opt->precision;
+    a.err = (int *)((char *)d_workspace + 8);
+    rc = check_cuda(launch_rbpg(*op, a, num_sms(dev), s), "iteration kernel");
+    if (rc)
+        return rc;
+    if (opt->refit) {
+        RefitLaunch r;
+        r.g = a.g;
+        r.P = P;
+        r.lam = d_lambda;
+        r.lam_pp = a.lam_pp;
+        r.x_in = a.x;
+        r.x_out = a.x;
+        r.support = d_support;
+        r.nsupp = d_nsupp;
+        r.status = d_status;
+        r.s_max = opt->s_max;
+        r.rounds = opt->refit_rounds;
+        rc = check_cuda(launch_refit(*op, r, s), "refit kernel");
+    }
+    return rc;
+}
+}  // namespace bpdn
+
 extern "C" {
 
 const char *bpdn_last_error(void) { return g_err; }
@@ -291,95 +387,14 @@ size_t bpdn_solve_workspace_bytes(bpdn_op_t h, int64_t P, const bpdn_options *op
     return 256;  // a 64-bit work counter and an error word, padded
 }
 
-static int check_solve_buffers(const OpHandle *op, const void *d_g, int64_t P, const float *d_lambda,
-                               const void *d_x, const int32_t *d_status)
-{
-    if (P < 0)
-        return set_error(BPDN_EINVAL, "P must be >= 0");
-    if (P > ((int64_t)1 << 40))
-        return set_error(BPDN_ESIZE, "P = %lld too large", (long long)P);
-    if (P == 0)
-        return BPDN_OK;
-    if (!d_g || !d_lambda || !d_x || !d_status)
-        return set_error(BPDN_EINVAL, "g, lambda, x and status pointers must be non-NULL");
-    if (!aligned(d_g, 8) || !aligned(d_x, 8) || !aligned(d_lambda, 4) || !aligned(d_status, 4))
-        return set_error(BPDN_EALIGN, "g and x must be 8-byte aligned, lambda and status 4-byte");
-    (void)op;
-    return BPDN_OK;
-}
 
 int bpdn_solve(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda,
                int32_t lambda_per_pixel, const bpdn_options *opt, void *d_x, int32_t *d_support,
                int32_t *d_nsupp, int32_t *d_status, int32_t *d_iters, int32_t *d_nbt,
                void *d_workspace, size_t workspace_bytes, void *cuda_stream)
 {
-    OpHandle *op = nullptr;
-    int rc = check_op(h, &op);
-    if (rc)
-        return rc;
-    rc = check_options(opt);
-    if (rc)
-        return rc;
-    rc = check_solve_buffers(op, d_g, P, d_lambda, d_x, d_status);
-    if (rc)
-        return rc;
-    if (P == 0)
-        return BPDN_OK;
-    if (!d_iters)
-        return set_error(BPDN_EINVAL, "iters pointer must be non-NULL");
-    if (!d_workspace || workspace_bytes < bpdn_solve_workspace_bytes(h, P, opt))
-        return set_error(BPDN_ESIZE, "solve workspace too small");
-    if (!aligned(d_workspace, 256))
-        return set_error(BPDN_EALIGN, "solve workspace must be 256-byte aligned");
-    if (opt->refit && d_support && !aligned(d_support, 4))
-        return set_error(BPDN_EALIGN, "support must be 4-byte aligned");
-    int dev = op->device;
-    const char *why = rbpg_check(*op, opt->precision, max_smem_optin(dev));
-    if (why[0] != '\0')
-        return set_error(BPDN_ESIZE, "N = %d, L = %d, precision %d: %s", op->N, op->L, opt->precision, why);
-    cudaStream_t s = (cudaStream_t)cuda_stream;
-    unsigned long long *counter = (unsigned long long *)d_workspace;
-    // work counter (8 bytes) and the kernel's error word (4 bytes)
-    rc = check_cuda(cudaMemsetAsync(counter, 0, 16, s), "reset work counter");
-    if (rc)
-        return rc;
-    SolveLaunch a;
-    a.g = (const float2 *)d_g;
-    a.P = P;
-    a.lam = d_lambda;
-    a.lam_pp = lambda_per_pixel ? 1 : 0;
-    a.x = (float2 *)d_x;
-    a.nsupp = d_nsupp;
-    a.status = d_status;
-    a.iters = d_iters;
-    a.nbt = d_nbt;
-    a.counter = counter;
-    a.max_iter = opt->max_iter;
-    a.tol = opt->tol;
-    a.c_alpha = opt->c_alpha;
-    a.alpha0 = (float)(opt->alpha0_scale / (2.0 * op->N));
-    a.max_bt = opt->max_bt;
-    a.precision = opt->precision;
-    a.err = (int *)((char *)d_workspace + 8);
-    rc = check_cuda(launch_rbpg(*op, a, num_sms(dev), s), "iteration kernel");
-    if (rc)
-        return rc;
-    if (opt->refit) {
-        RefitLaunch r;
-        r.g = a.g;
-        r.P = P;
-        r.lam = d_lambda;
-        r.lam_pp = a.lam_pp;
-        r.x_in = a.x;
-        r.x_out = a.x;
-        r.support = d_support;
-        r.nsupp = d_nsupp;
-        r.status = d_status;
-        r.s_max = opt->s_max;
-        r.rounds = opt->refit_rounds;
-        rc = check_cuda(launch_refit(*op, r, s), "refit kernel");
-    }
-    return rc;
+    return bpdn::solve_impl(h, d_g, P, d_lambda, lambda_per_pixel, opt, d_x, d_support, d_nsupp, d_status,
+                            d_iters, d_nbt, d_workspace, workspace_bytes, cuda_stream, true);
 }
 
 int bpdn_refit(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda,

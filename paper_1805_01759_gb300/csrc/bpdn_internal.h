@@ -46,6 +46,12 @@ int check_cuda(cudaError_t e, const char *what);
 
 // ---- launches (each returns a cudaError_t from the launch) ----
 cudaError_t launch_make_operator(const OpHandle &op, const double *d_b, cudaStream_t s);
+
+// bpdn_solve's argument checks, followed by its launches when `launch` is true
+int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, int32_t lambda_per_pixel,
+               const bpdn_options *opt, void *d_x, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
+               int32_t *d_iters, int32_t *d_nbt, void *d_workspace, size_t workspace_bytes, void *cuda_stream,
+               bool launch);
 cudaError_t launch_export(const OpHandle &op, int what, void *dst, cudaStream_t s);
 
 struct SolveLaunch {

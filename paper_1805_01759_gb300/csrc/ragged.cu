@@ -1,0 +1,143 @@
+// bpdn_solve_ragged: many stacks with their own operators in one call.
+//
+// Each stack is an independent bpdn_solve.  The call checks every stack, orders
+// them by estimated cost P N L (largest first) and issues them round-robin on a
+// small pool of library-owned streams that fork from the caller's stream through
+// one event and join back through one event per worker.  The persistent iteration
+// kernel of one stack holds whole SMs, so a stack issued on another stream starts
+// on the SMs the previous stack's last CTAs release; the event fork/join keeps the
+// call capturable into a single CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "bpdn_internal.h"
+
+namespace bpdn {
+namespace {
+
+constexpr int kWorkers = 4;
+constexpr int kMaxDevices = 64;
+constexpr size_t kStackScratch = 256;
+
+struct Pool {
+    bool ready = false;
+    cudaStream_t stream[kWorkers];
+    cudaEvent_t fork;
+    cudaEvent_t join[kWorkers];
+};
+
+std::mutex g_mu;
+Pool g_pool[kMaxDevices];
+
+int pool_for(int dev, Pool **out)
+{
+    if (dev < 0 || dev >= kMaxDevices)
+        return set_error(BPDN_ESTATE, "device %d outside the %d devices the stream pool supports", dev, kMaxDevices);
+    Pool &p = g_pool[dev];
+    if (!p.ready) {
+        int rc = check_cuda(cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming), "create fork event");
+        for (int i = 0; i < kWorkers && !rc; ++i) {
+            rc = check_cuda(cudaStreamCreateWithFlags(&p.stream[i], cudaStreamNonBlocking), "create worker stream");
+            if (!rc)
+                rc = check_cuda(cudaEventCreateWithFlags(&p.join[i], cudaEventDisableTiming), "create join event");
+        }
+        if (rc)
+            return rc;
+        p.ready = true;
+    }
+    *out = &p;
+    return BPDN_OK;
+}
+
+double stack_cost(const bpdn_stack &st)
+{
+    int32_t N = 0, L = 0;
+    double ds = 0.0, lip = 0.0;
+    if (bpdn_op_info(st.op, &N, &L, &ds, &lip) != BPDN_OK)
+        return 0.0;
+    return (double)st.P * (double)N * (double)L;
+}
+
+}  // namespace
+}  // namespace bpdn
+
+using namespace bpdn;
+
+extern "C" {
+
+size_t bpdn_solve_ragged_workspace_bytes(int32_t n_stacks)
+{
+    return n_stacks > 0 ? kStackScratch * (size_t)n_stacks : 0;
+}
+
+int bpdn_solve_ragged(const bpdn_stack *stacks, int32_t n_stacks, const bpdn_options *opt,
+                      void *d_workspace, size_t workspace_bytes, void *cuda_stream)
+{
+    if (n_stacks < 0)
+        return set_error(BPDN_EINVAL, "n_stacks must be >= 0");
+    if (n_stacks == 0)
+        return BPDN_OK;
+    if (!stacks)
+        return set_error(BPDN_EINVAL, "stacks must be non-NULL");
+    if (!d_workspace || workspace_bytes < bpdn_solve_ragged_workspace_bytes(n_stacks))
+        return set_error(BPDN_ESIZE, "ragged workspace too small (%zu bytes for %d stacks)",
+                         bpdn_solve_ragged_workspace_bytes(n_stacks), n_stacks);
+    if (((uintptr_t)d_workspace % 256) != 0)
+        return set_error(BPDN_EALIGN, "ragged workspace must be 256-byte aligned");
+    int dev = -1;
+    int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc)
+        return rc;
+    // every stack is checked before anything is launched
+    for (int i = 0; i < n_stacks; ++i) {
+        const bpdn_stack &st = stacks[i];
+        unsigned char *ws = (unsigned char *)d_workspace + kStackScratch * (size_t)i;
+        rc = solve_impl(st.op, st.d_g, st.P, st.d_lambda, st.lambda_per_pixel, opt, st.d_x, st.d_support,
+                        st.d_nsupp, st.d_status, st.d_iters, st.d_nbt, ws, kStackScratch, nullptr, false);
+        if (rc) {
+            char msg[512];
+            snprintf(msg, sizeof(msg), "%s", bpdn_last_error());
+            return set_error(rc, "stack %d: %s", i, msg);
+        }
+    }
+    std::vector<int> order(n_stacks);
+    std::vector<double> cost(n_stacks);
+    for (int i = 0; i < n_stacks; ++i) {
+        order[i] = i;
+        cost[i] = stack_cost(stacks[i]);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+
+    std::lock_guard<std::mutex> lk(g_mu);
+    Pool *pool = nullptr;
+    rc = pool_for(dev, &pool);
+    if (rc)
+        return rc;
+    cudaStream_t origin = (cudaStream_t)cuda_stream;
+    const int used = n_stacks < kWorkers ? n_stacks : kWorkers;
+    rc = check_cuda(cudaEventRecord(pool->fork, origin), "record fork event");
+    for (int k = 0; k < used && !rc; ++k)
+        rc = check_cuda(cudaStreamWaitEvent(pool->stream[k], pool->fork, 0), "fork worker stream");
+    for (int j = 0; j < n_stacks && !rc; ++j) {
+        const int i = order[j];
+        const bpdn_stack &st = stacks[i];
+        unsigned char *ws = (unsigned char *)d_workspace + kStackScratch * (size_t)i;
+        rc = solve_impl(st.op, st.d_g, st.P, st.d_lambda, st.lambda_per_pixel, opt, st.d_x, st.d_support,
+                        st.d_nsupp, st.d_status, st.d_iters, st.d_nbt, ws, kStackScratch,
+                        (void *)pool->stream[j % used], true);
+    }
+    // join every forked stream back into the caller's stream, also after an error
+    for (int k = 0; k < used; ++k) {
+        const int r1 = check_cuda(cudaEventRecord(pool->join[k], pool->stream[k]), "record join event");
+        const int r2 = r1 ? r1 : check_cuda(cudaStreamWaitEvent(origin, pool->join[k], 0), "join worker stream");
+        if (!rc)
+            rc = r2;
+    }
+    return rc;
+}
+
+}  // extern "C"

@@ -77,3 +77,17 @@ def test_argument_errors_without_gpu(lib):
     assert np.isnan(lib.bpdn_op_lipschitz(None))
     lib.bpdn_destroy_operator(None)  # ignored
     assert lib.bpdn_version().startswith(b"bpdn-gb300")
+
+
+def test_ragged_host_checks():
+    """bpdn_solve_ragged rejects bad arguments on the host, before touching a GPU."""
+    from paper_1805_01759_gb300 import _lib
+    lib = _lib.load()
+    opt = _lib.default_options()
+    assert lib.bpdn_solve_ragged_workspace_bytes(0) == 0
+    assert lib.bpdn_solve_ragged_workspace_bytes(3) == 3 * 256
+    assert lib.bpdn_solve_ragged(None, 0, ctypes.byref(opt), None, 0, None) == _lib.BPDN_OK
+    assert lib.bpdn_solve_ragged(None, -1, ctypes.byref(opt), None, 0, None) == _lib.BPDN_EINVAL
+    assert lib.bpdn_solve_ragged(None, 2, ctypes.byref(opt), None, 0, None) == _lib.BPDN_EINVAL
+    arr = (_lib.Stack * 2)()
+    assert lib.bpdn_solve_ragged(arr, 2, ctypes.byref(opt), None, 0, None) == _lib.BPDN_ESIZE
