@@ -1,0 +1,73 @@
+"""Multi-rank logic of bench.py on CPU: two gloo ranks (one process each).
+
+The weak-scaling run shards the patch by rank (each rank draws its own pixel set of
+the same stack), synchronises with a barrier and reports the maximum step time over
+ranks.  These are exercised here without a GPU.
+"""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank: int, world: int, port: int, out_dir: str) -> None:
+    sys.path.insert(0, ROOT)
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        import bench
+        from paper_1805_01759_gb300 import synth
+
+        r, w, lr = bench.dist_env()
+        assert (r, w, lr) == (rank, world, rank)
+        # the slowest rank's time is the job's time
+        t = bench.reduce_max(10.0 + 3.0 * rank)
+        bench.barrier()
+        # each rank draws a different pixel set of the same stack
+        st = synth.workload_patch(P=64, seed=2, part=bench.shard_part(rank))
+        gsum = torch.tensor([float(np.abs(st.g).sum())], dtype=torch.float64)
+        bsum = torch.tensor([float(st.geom.baselines_m.sum()), st.lam], dtype=torch.float64)
+        gs = [torch.zeros_like(gsum) for _ in range(world)]
+        bs = [torch.zeros_like(bsum) for _ in range(world)]
+        dist.all_gather(gs, gsum)
+        dist.all_gather(bs, bsum)
+        np.save(os.path.join(out_dir, f"r{rank}.npy"),
+                np.array([t] + [float(x) for x in gs] + [float(x) for b in bs for x in b]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_sharding_and_timing(tmp_path):
+    world = 2
+    mp.spawn(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    res = [np.load(tmp_path / f"r{r}.npy") for r in range(world)]
+    for r in res:
+        assert r[0] == 13.0  # max over ranks of 10 + 3 rank
+        g0, g1 = r[1], r[2]
+        assert g0 != g1  # different pixel sets
+        b0, lam0, b1, lam1 = r[3], r[4], r[5], r[6]
+        assert b0 == b1 and lam0 == lam1  # same stack geometry and lambda
+    assert np.array_equal(res[0], res[1])
+
+
+def test_single_process_helpers_are_identities():
+    sys.path.insert(0, ROOT)
+    import bench
+    if dist.is_initialized():
+        pytest.skip("a process group is already initialised")
+    assert bench.reduce_max(4.5) == 4.5
+    bench.barrier()
+    assert bench.shard_part(0) == 0
