@@ -17,7 +17,13 @@
 //      decreasing eps finds the support first.
 //      Precision: the support is found in FP32 (residual <= 1e-4 lambda); the
 //      answer is then finished and checked in FP64 (residual <= 1e-12 lambda),
-//      falling back to an all-FP64 solve when the FP32 support was wrong.
+//      falling back to an all-FP64 solve when the FP32 support was wrong.  The
+//      Newton systems are factored in FP32 in both phases: each step is then an
+//      inexact Newton step (relative error about cond * 6e-8), while the objective,
+//      the residual that decides convergence and the line search stay in the
+//      phase's precision, so the FP64 answer is still checked in FP64.
+//   The helpers stay out of line: inlined into every call site of both precisions
+//   the kernel's code no longer fits the instruction cache.
 //   3. Certificate over the grid: |2 a_l^H (A_W z - g)| <= lambda for l not in W
 //      (FP32 products; grid points within 1e-4 of the bound recomputed in FP64
 //      against 1e-9).  Violators join W, largest first, and step 2 repeats
@@ -82,8 +88,8 @@ __device__ __forceinline__ T warp_max(T v)
 template <typename T>
 struct Solve {
     C2<T> G[KW][KW];
-    T J[2 * KW][2 * KW + 1];  // Newton system, right-hand side in column n2
-    T inv[2 * KW];            // reciprocal pivots
+    float J[2 * KW][2 * KW + 1];  // Newton system in FP32, right-hand side in column n2
+    float inv[2 * KW];            // reciprocal pivots
     C2<T> z[KW], c[KW], zt[KW], dz[KW], gam[KW];
     T q[KW], u0[KW], u1[KW];  // per variable: (smoothed) modulus and unit vector
     int T_[KW];
@@ -108,7 +114,7 @@ constexpr int WARPS = 1;  // pixels (warps) per block
 
 // G_ij = h(l_i - l_j), c_i = a_{l_i}^H g in precision T
 template <typename T>
-__device__ void load_Gc(Solve<T> &S, const PixelSmem &P, const double2 *__restrict__ A64,
+__device__ __noinline__ void load_Gc(Solve<T> &S, const PixelSmem &P, const double2 *__restrict__ A64,
                         const double2 *__restrict__ h, int N, int L, int lane)
 {
     const int m = P.m;
@@ -142,7 +148,7 @@ __device__ __forceinline__ C2<T> gz_row(const Solve<T> &S, int i, int m, const C
 
 // objective over W (|z| smoothed by eps; eps = 0 is exact), without the constant ||g||^2
 template <typename T>
-__device__ T objective(const Solve<T> &S, int m, const C2<T> *z, T lam, T eps, int lane)
+__device__ __noinline__ T objective(const Solve<T> &S, int m, const C2<T> *z, T lam, T eps, int lane)
 {
     T v = T(0);
     if (lane < m) {
@@ -157,7 +163,7 @@ __device__ T objective(const Solve<T> &S, int m, const C2<T> *z, T lam, T eps, i
 // gam = 2 (G z - c); returns the optimality residual
 //   max( max_{z_i != 0} |gam_i + lam u_i| / lam,  max_{z_i = 0} (|gam_i| / lam - 1) )
 template <typename T>
-__device__ T optimality(Solve<T> &S, int m, T lam, int lane)
+__device__ __noinline__ T optimality(Solve<T> &S, int m, T lam, int lane)
 {
     T res = T(0);
     if (lane < m) {
@@ -181,7 +187,7 @@ __device__ T optimality(Solve<T> &S, int m, T lam, int lane)
 // One sweep of exact coordinate minimisations:
 //   z_i <- S_{lam/2}(c_i - sum_{j != i} G_ij z_j) / G_ii
 template <typename T>
-__device__ void cd_sweep(Solve<T> &S, int m, T lam, int lane)
+__device__ __noinline__ void cd_sweep(Solve<T> &S, int m, T lam, int lane)
 {
     for (int i = 0; i < m; ++i) {
         C2<T> t = mk<T>(T(0), T(0));
@@ -207,40 +213,49 @@ __device__ void cd_sweep(Solve<T> &S, int m, T lam, int lane)
 // back substitution with lanes over rows.  Lane i returns x_i.  `ok` is false on
 // a non-positive pivot.
 template <typename T>
-__device__ T solve_spd(Solve<T> &S, int n2, int lane, bool &ok)
+__device__ __noinline__ T solve_spd(Solve<T> &S, int n2, int lane, bool &ok)
 {
     const int rc = (n2 < 32) ? n2 : 0;  // lane that owns the right-hand-side column
     ok = true;
     for (int k = 0; k < n2; ++k) {
         __syncwarp();
-        const T piv = S.J[k][k];
-        if (!(piv > T(0))) {
+        const float piv = S.J[k][k];
+        if (!(piv > 0.f)) {
             ok = false;
             return T(0);
         }
-        const T ip = T(1) / piv;
-        const T pk = (lane > k && lane < n2) ? S.J[k][lane] : T(0);
-        const T pr = (lane == rc) ? S.J[k][n2] : T(0);
+        const float ip = 1.f / piv;
+        const float pk = (lane > k && lane < n2) ? S.J[k][lane] : 0.f;
+        const float pr = (lane == rc) ? S.J[k][n2] : 0.f;
         if (lane == 0)
             S.inv[k] = ip;
-        for (int i = k + 1; i < n2; ++i) {
-            const T f = S.J[i][k] * ip;
-            if (lane > k && lane < n2)
-                S.J[i][lane] -= f * pk;
-            if (lane == rc)
-                S.J[i][n2] -= f * pr;
+        // four rows at a time, every load of a block before its stores
+        const int col = (lane > k && lane < n2) ? lane : ((lane == rc) ? n2 : -1);
+        const float pc = (lane == rc) ? pr : pk;
+        for (int i = k + 1; i < n2; i += 4) {
+            float f[4], v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool in = (i + u < n2);
+                f[u] = in ? S.J[i + u][k] * ip : 0.f;
+                v[u] = (in && col >= 0) ? S.J[i + u][col] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i + u < n2 && col >= 0)
+                    S.J[i + u][col] = v[u] - f[u] * pc;
         }
     }
     __syncwarp();
-    T b = (lane < n2) ? S.J[lane][n2] : T(0);
+    float b = (lane < n2) ? S.J[lane][n2] : 0.f;
     for (int k = n2 - 1; k >= 0; --k) {
-        const T xk = __shfl_sync(0xffffffffu, b, k) * S.inv[k];
+        const float xk = __shfl_sync(0xffffffffu, b, k) * S.inv[k];
         if (lane < k)
             b -= S.J[lane][k] * xk;
         else if (lane == k)
             b = xk;
     }
-    return b;
+    return (T)b;
 }
 
 // Newton direction for the objective restricted to the nonzero coordinates of z
@@ -248,7 +263,7 @@ __device__ T solve_spd(Solve<T> &S, int n2, int lane, bool &ok)
 // (zero off the variables) and returns the directional derivative (negative for
 // a descent direction), or +1 when the system could not be solved.
 template <typename T>
-__device__ T newton_dir(Solve<T> &S, int m, const C2<T> *z, T lam, T eps, int lane)
+__device__ __noinline__ T newton_dir(Solve<T> &S, int m, const C2<T> *z, T lam, T eps, int lane)
 {
     const bool use = (lane < m) && (eps > T(0) || cnz(z[lane]));
     const unsigned bal = __ballot_sync(0xffffffffu, use);
@@ -271,18 +286,23 @@ __device__ T newton_dir(Solve<T> &S, int m, const C2<T> *z, T lam, T eps, int la
         S.u1[lane] = zi.y * iq;
     }
     __syncwarp();
-    for (int rI = 0; rI < n2; ++rI) {
-        const int a = rI >> 1, ra = rI & 1;
-        if (lane < n2) {
-            const int b = lane >> 1, cb = lane & 1;
-            const C2<T> g = S.G[S.T_[a]][S.T_[b]];
-            T v = (ra == 0) ? (cb == 0 ? g.x : -g.y) : (cb == 0 ? g.y : g.x);
-            v *= T(2);
+    // lane 2b + cb fills column 2b + cb, two rows (re, im of variable a) per step
+    if (lane < n2) {
+        const int b = lane >> 1, cb = lane & 1;
+        const int tb = S.T_[b];
+        const T wc = cb ? S.u1[b] : S.u0[b];
+#pragma unroll 4
+        for (int a = 0; a < nt; ++a) {
+            const C2<T> g = S.G[S.T_[a]][tb];
+            T v0 = T(2) * (cb == 0 ? g.x : -g.y);
+            T v1 = T(2) * (cb == 0 ? g.y : g.x);
             if (a == b) {
-                const T wr = ra ? S.u1[a] : S.u0[a], wc = cb ? S.u1[a] : S.u0[a];
-                v += lam / S.q[a] * ((ra == cb ? T(1) : T(0)) - wr * wc);
+                const T sc = lam / S.q[a];
+                v0 += sc * ((cb == 0 ? T(1) : T(0)) - S.u0[a] * wc);
+                v1 += sc * ((cb == 1 ? T(1) : T(0)) - S.u1[a] * wc);
             }
-            S.J[rI][lane] = v;
+            S.J[2 * a][lane] = (float)v0;
+            S.J[2 * a + 1][lane] = (float)v1;
         }
     }
     T gcomp = T(0);
@@ -291,7 +311,7 @@ __device__ T newton_dir(Solve<T> &S, int m, const C2<T> *z, T lam, T eps, int la
         const int ia = S.T_[a];
         const T w = (lane & 1) ? S.u1[a] : S.u0[a];
         gcomp = ((lane & 1) ? S.gam[ia].y : S.gam[ia].x) + lam * w;
-        S.J[lane][n2] = -gcomp;
+        S.J[lane][n2] = (float)(-gcomp);
     }
     bool ok;
     const T d = solve_spd(S, n2, lane, ok);
@@ -324,7 +344,7 @@ __device__ __forceinline__ bool passes_zero(C2<T> zi, C2<T> d, T t)
 
 // coordinate sweeps alternating with Newton steps (see the file header)
 template <typename T>
-__device__ bool fast_path(Solve<T> &S, int m, T lam, int lane, int max_outer, T tol)
+__device__ __noinline__ bool fast_path(Solve<T> &S, int m, T lam, int lane, int max_outer, T tol)
 {
     for (int outer = 0; outer < max_outer; ++outer) {
         cd_sweep(S, m, lam, lane);
@@ -410,7 +430,7 @@ __device__ bool fast_path(Solve<T> &S, int m, T lam, int lane, int max_outer, T 
 // scale of z), at most maxit steps per level; then coordinates below 1e-6 of the
 // scale are set to zero
 template <typename T>
-__device__ void continuation(Solve<T> &S, int m, T lam, int lane, T e0, T e1, int maxit)
+__device__ __noinline__ void continuation(Solve<T> &S, int m, T lam, int lane, T e0, T e1, int maxit)
 {
     T sc = warp_max((lane < m) ? sqrt(cabs2(S.z[lane])) : T(0));
     sc = fmax(sc, T(1e-3));
@@ -443,7 +463,7 @@ __device__ void continuation(Solve<T> &S, int m, T lam, int lane, T e0, T e1, in
 
 // Step 2 on the current W from the start values in P.zkeep: FP32 support search,
 // FP64 finish.  The FP64 answer is left in P.zkeep.  Returns true on convergence.
-__device__ bool restricted_minimiser(PixelSmem &P, const double2 *A64, const double2 *h, int N,
+__device__ __noinline__ bool restricted_minimiser(PixelSmem &P, const double2 *A64, const double2 *h, int N,
                                      int L, double lam, int lane)
 {
     const int m = P.m;
