@@ -239,15 +239,17 @@ def accuracy_sample(st, x, status, n_sample: int, seed: int = 20) -> dict:
     A = oracle.operator(st.geom)
     ref = oracle.minimise_batch(A, st.g[idx], st.lam)
     xs = x[idx].astype(np.complex128)
-    cert = (status[idx] & 64) != 0
+    # pixels where the oracle's own certificate failed have no reference answer
+    resolved = ref["flags"] == 0
+    cert = ((status[idx] & 64) != 0) & resolved
     degen = (ref["margin"] < 1e-6) | ((ref["nS"] > 0) & (ref["min_abs_on"] < 1e-6 * np.abs(ref["x"]).max(1)))
     nr = np.linalg.norm(ref["x"], axis=1)
     err = np.linalg.norm(xs - ref["x"], axis=1) / np.where(nr > 0, nr, 1.0)
     supp_ok = np.all((xs != 0) == (ref["x"] != 0), axis=1) | degen
     ok = cert & (err <= 1e-4) & supp_ok
-    return {"n": int(n_sample), "certified": int(cert.sum()), "ok": int(ok.sum()),
-            "cert_and_wrong": int((cert & ~ok).sum()), "max_err_certified": float(err[cert].max()) if cert.any() else None,
-            "degenerate": int(degen.sum())}
+    return {"n": int(n_sample), "oracle_unresolved": int((~resolved).sum()), "certified": int(cert.sum()),
+            "ok": int(ok.sum()), "cert_and_wrong": int((cert & ~ok).sum()),
+            "max_err_certified": float(err[cert].max()) if cert.any() else None, "degenerate": int(degen.sum())}
 
 
 class PathRunner:

@@ -682,22 +682,38 @@ __global__ void __launch_bounds__(MAXT, 1) k_rbpg(Params prm, int G)
                     if (bal) {
                         // this block's share of A xbar, ascending l; lane n owns rows n, n + 32
                         float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+                        // two nonzeros per trip (two loads in flight), still ascending l
                         unsigned m = bal;
                         while (m) {
-                            const int j = __ffs(m) - 1;
+                            const int j0 = __ffs(m) - 1;
                             m &= m - 1;
-                            const float xr = __shfl_sync(0xffffffffu, bx, j);
-                            const float xi = __shfl_sync(0xffffffffu, by, j);
-                            const int lj = 32 * blk + j;
+                            const bool two = (m != 0);
+                            const int j1 = two ? (__ffs(m) - 1) : j0;
+                            if (two)
+                                m &= m - 1;
+                            const float xr0 = __shfl_sync(0xffffffffu, bx, j0);
+                            const float xi0 = __shfl_sync(0xffffffffu, by, j0);
+                            const float xr1 = __shfl_sync(0xffffffffu, bx, j1);
+                            const float xi1 = __shfl_sync(0xffffffffu, by, j1);
                             if (lane < N) {
-                                const float2 av = Aat(lane, lj);
-                                acc0.x = fmaf(av.x, xr, fmaf(-av.y, xi, acc0.x));
-                                acc0.y = fmaf(av.x, xi, fmaf(av.y, xr, acc0.y));
+                                const float2 a0 = Aat(lane, 32 * blk + j0);
+                                const float2 a1 = Aat(lane, 32 * blk + j1);
+                                acc0.x = fmaf(a0.x, xr0, fmaf(-a0.y, xi0, acc0.x));
+                                acc0.y = fmaf(a0.x, xi0, fmaf(a0.y, xr0, acc0.y));
+                                if (two) {
+                                    acc0.x = fmaf(a1.x, xr1, fmaf(-a1.y, xi1, acc0.x));
+                                    acc0.y = fmaf(a1.x, xi1, fmaf(a1.y, xr1, acc0.y));
+                                }
                             }
                             if (NCH > 1 && lane + 32 < N) {
-                                const float2 av = Aat(lane + 32, lj);
-                                acc1.x = fmaf(av.x, xr, fmaf(-av.y, xi, acc1.x));
-                                acc1.y = fmaf(av.x, xi, fmaf(av.y, xr, acc1.y));
+                                const float2 a0 = Aat(lane + 32, 32 * blk + j0);
+                                acc1.x = fmaf(a0.x, xr0, fmaf(-a0.y, xi0, acc1.x));
+                                acc1.y = fmaf(a0.x, xi0, fmaf(a0.y, xr0, acc1.y));
+                                if (two) {
+                                    const float2 a1 = Aat(lane + 32, 32 * blk + j1);
+                                    acc1.x = fmaf(a1.x, xr1, fmaf(-a1.y, xi1, acc1.x));
+                                    acc1.y = fmaf(a1.x, xi1, fmaf(a1.y, xr1, acc1.y));
+                                }
                             }
                         }
                         if (lane < N)

@@ -24,10 +24,10 @@
 //      phase's precision, so the FP64 answer is still checked in FP64.
 //   The helpers stay out of line: inlined into every call site of both precisions
 //   the kernel's code no longer fits the instruction cache.
-//   3. Certificate over the grid: |2 a_l^H (A_W z - g)| <= lambda for l not in W
-//      (FP32 products; grid points within 1e-4 of the bound recomputed in FP64
-//      against 1e-9).  Violators join W, largest first, and step 2 repeats
-//      (at most `rounds` rounds).
+//   3. Coordinates of W that came out zero leave W.  Certificate over the grid:
+//      |2 a_l^H (A_W z - g)| <= lambda for l not in W (FP32 products; grid points
+//      within 1e-4 of the bound recomputed in FP64 against 1e-9).  Violators join W,
+//      largest first, and step 2 repeats (at most `rounds` rounds).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -622,6 +622,20 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict_
         // 2. exact minimiser over W
         if (!restricted_minimiser(P, A64, h, N, L, lam, lane))
             break;
+        // drop the coordinates the restricted minimiser set to zero: their dual
+        // constraint holds (|2 (G z - c)_i| <= lambda), and the room they free lets the
+        // certificate add violators when x_in had more than s_max nonzeros
+        if (lane == 0) {
+            int k = 0;
+            for (int i = 0; i < P.m; ++i)
+                if (P.zkeep[i].x != 0.0 || P.zkeep[i].y != 0.0) {
+                    P.W[k] = P.W[i];
+                    P.zkeep[k] = P.zkeep[i];
+                    ++k;
+                }
+            P.m = k;
+        }
+        __syncwarp();
         const int m = P.m;
         // residual A_W z - g in FP64 and its FP32 copy
         for (int n = lane; n < N; n += 32) {
