@@ -231,25 +231,70 @@ def alu_flops_per_sweep(path: str, N: int, L: int) -> float:
     return flops
 
 
-def accuracy_sample(st, x, status, n_sample: int, seed: int = 20) -> dict:
-    """Exact minimiser (oracle) on a seeded sample of pixels vs the GPU result."""
-    import oracle
-    rng = np.random.default_rng(seed)
-    idx = np.sort(rng.choice(st.g.shape[0], size=n_sample, replace=False))
-    A = oracle.operator(st.geom)
-    ref = oracle.minimise_batch(A, st.g[idx], st.lam)
-    xs = x[idx].astype(np.complex128)
-    # pixels where the oracle's own certificate failed have no reference answer
-    resolved = ref["flags"] == 0
-    cert = ((status[idx] & 64) != 0) & resolved
-    degen = (ref["margin"] < 1e-6) | ((ref["nS"] > 0) & (ref["min_abs_on"] < 1e-6 * np.abs(ref["x"]).max(1)))
-    nr = np.linalg.norm(ref["x"], axis=1)
-    err = np.linalg.norm(xs - ref["x"], axis=1) / np.where(nr > 0, nr, 1.0)
-    supp_ok = np.all((xs != 0) == (ref["x"] != 0), axis=1) | degen
-    ok = cert & (err <= 1e-4) & supp_ok
-    return {"n": int(n_sample), "oracle_unresolved": int((~resolved).sum()), "certified": int(cert.sum()),
-            "ok": int(ok.sum()), "cert_and_wrong": int((cert & ~ok).sum()),
-            "max_err_certified": float(err[cert].max()) if cert.any() else None, "degenerate": int(degen.sum())}
+class OracleSample:
+    """The exact minimiser (FP64 oracle) on a seeded sample of a stack's pixels."""
+
+    def __init__(self, st, n_sample: int, seed: int = 20):
+        import oracle
+        rng = np.random.default_rng(seed)
+        P = st.g.shape[0]
+        self.idx = np.arange(P) if n_sample >= P else np.sort(rng.choice(P, size=n_sample, replace=False))
+        A = oracle.operator(st.geom)
+        self.ref = oracle.minimise_batch(A, st.g[self.idx], st.lam)
+        ref = self.ref
+        # pixels where the oracle's own certificate failed have no reference answer
+        self.resolved = ref["flags"] == 0
+        self.degen = (ref["margin"] < 1e-6) | ((ref["nS"] > 0) & (ref["min_abs_on"] < 1e-6 * np.abs(ref["x"]).max(1)))
+
+    def errors(self, x) -> tuple[np.ndarray, np.ndarray]:
+        """Relative l2 error and support equality of x[idx] against the minimiser."""
+        xs = x[self.idx].astype(np.complex128)
+        ref = self.ref["x"]
+        nr = np.linalg.norm(ref, axis=1)
+        err = np.linalg.norm(xs - ref, axis=1) / np.where(nr > 0, nr, 1.0)
+        supp = np.all((xs != 0) == (ref != 0), axis=1) | self.degen
+        return err, supp
+
+    def gate(self, x, status) -> dict:
+        """The accuracy gate: certified pixels with error <= 1e-4 and the oracle's support."""
+        err, supp = self.errors(x)
+        cert = ((status[self.idx] & 64) != 0) & self.resolved
+        ok = cert & (err <= 1e-4) & supp
+        return {"n": int(self.idx.size), "oracle_unresolved": int((~self.resolved).sum()),
+                "certified": int(cert.sum()), "ok": int(ok.sum()), "cert_and_wrong": int((cert & ~ok).sum()),
+                "max_err_certified": float(err[cert].max()) if cert.any() else None,
+                "degenerate": int(self.degen.sum())}
+
+    def summary(self, x, tol: float) -> dict:
+        err, supp = self.errors(x)
+        e = err[self.resolved]
+        return {"median": float(np.median(e)), "p99": float(np.quantile(e, 0.99)), "max": float(e.max()),
+                f"frac_le_{tol:g}": float((e <= tol).mean()), "support_equal_frac": float(supp[self.resolved].mean())}
+
+
+def precision_report(api, oracle_patch: "OracleSample", st_patch, op_patch, g_patch, lam_patch,
+                     paths: dict) -> dict:
+    """Error against the FP64 oracle before and after the refit, per path, on the small
+    stack (all 256 pixels) and on the oracle sample of the patch."""
+    from paper_1805_01759_gb300 import synth
+    import torch
+    small = synth.workload_small(P=256, seed=1)
+    o_small = OracleSample(small, 256)
+    op_small = api.Operator.from_geometry(small.geom)
+    g_small = torch.from_numpy(small.g).cuda()
+    out = {}
+    for cname, (o, op, g, lam) in {"small_N25_L200_P256": (o_small, op_small, g_small, small.lam),
+                                   "patch_sample": (oracle_patch, op_patch, g_patch, lam_patch)}.items():
+        rows = {}
+        for name, (prec, tol) in paths.items():
+            it = api.solve(op, g, lam, precision=prec, tol=tol, refit=0)
+            x_it = it.x.cpu().numpy()
+            x_rf, _, _, st_rf = api.refit(op, g, lam, it.x, status=it.status)
+            torch.cuda.synchronize()
+            rows[name] = {"before_refit": o.summary(x_it, 1e-3), "after_refit": o.summary(x_rf.cpu().numpy(), 1e-4),
+                          "certified_frac": float(((st_rf.cpu().numpy() & 64) != 0).mean())}
+        out[cname] = rows
+    return out
 
 
 class PathRunner:
@@ -339,6 +384,8 @@ def run_ours(args) -> None:
     paths = {"fp32": (0, args.tol_fp32), "bf16": (1, args.tol_bf16)}
     if args.precision != "both":
         paths = {args.precision: paths[args.precision]}
+    # the oracle's answers for the accuracy gate, computed on the host before timing
+    oracle_patch = OracleSample(st, args.sample) if rank == 0 else None
     results = {}
     launches = 0
     with ClockSampler(dev.index) as clk:
@@ -361,7 +408,7 @@ def run_ours(args) -> None:
         nbt_np = runner.nbt.cpu().numpy()
         x_np = runner.x.cpu().numpy()
         certified = int(((st_np & 64) != 0).sum())
-        acc = accuracy_sample(st, x_np, st_np, args.sample) if rank == 0 else None
+        acc = oracle_patch.gate(x_np, st_np) if rank == 0 else None
         good = (certified / P) * (acc["ok"] / max(acc["certified"], 1) if acc else 1.0)
         pixel_iters = float(it_np.astype(np.int64).sum())
         sweeps = pixel_iters + float(nbt_np.astype(np.int64).sum())  # a step cut is one more sweep
@@ -407,6 +454,9 @@ def run_ours(args) -> None:
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_leg(args.cpu_sample)
+    prec_report = None
+    if rank == 0 and not args.no_precision_report:
+        prec_report = precision_report(api, oracle_patch, st, op, g_dev, st.lam, paths)
     pixels_total = P * world
     value = pixels_total * good_head / (ms_head / 1e3)
     e2e_value = pixels_total * good_head / (e2e_ms / 1e3)
@@ -449,6 +499,7 @@ def run_ours(args) -> None:
                              "; a step cut is one more sweep) over the iteration kernel's event-timed "
                              "duration" + ("; the BF16 contraction (8 N L per sweep) runs on the tensor "
                                            "cores, see paths.bf16.tensor_tflops" if head == "bf16" else "")},
+        "precision_report": prec_report,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -469,6 +520,8 @@ def main(argv=None) -> None:
     ap.add_argument("--cpu-sample", type=int, default=2048, help="pixels of the CPU baseline leg")
     ap.add_argument("--ref-sample", type=int, default=1024, help="pixels per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision-report", action="store_true",
+                    help="skip the error-before/after-refit report (small stack and patch sample)")
     ap.add_argument("--precision", choices=["fp32", "bf16", "both"], default="both")
     ap.add_argument("--tol-fp32", type=float, default=1e-6)
     ap.add_argument("--tol-bf16", type=float, default=1e-4)
