@@ -69,7 +69,7 @@ typedef struct {
     int32_t refit;        /* 0: none; 1: FP64 restricted solve on the support + certificate     */
     int32_t s_max;        /* largest support the refit handles (<= BPDN_MAX_SMAX, default 16)   */
     int32_t max_bt;       /* step cuts allowed per iteration before BT_LIMIT (default 64)        */
-    int32_t tile_pixels;  /* pixels per CTA (0 = library choice)                                 */
+    int32_t tile_pixels;  /* pixels in flight per SM: 8 or 16 (0 = library choice, 16 when it fits) */
     int32_t refit_rounds; /* working-set rounds of the refit (default 4)                         */
     int32_t reserved[6];
 } bpdn_options;
@@ -178,6 +178,7 @@ typedef struct {
     int32_t *d_status;         /* device int32 [P] out */
     int32_t *d_iters;          /* device int32 [P] out */
     int32_t *d_nbt;            /* device int32 [P] out, or NULL */
+    int32_t tile_pixels;       /* this stack's tile_pixels (0 = the options' value) */
 } bpdn_stack;
 
 /* Workspace of bpdn_solve_ragged: 256 bytes per stack. */

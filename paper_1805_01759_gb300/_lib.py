@@ -75,6 +75,7 @@ class Stack(ctypes.Structure):
         ("d_status", ctypes.c_void_p),
         ("d_iters", ctypes.c_void_p),
         ("d_nbt", ctypes.c_void_p),
+        ("tile_pixels", ctypes.c_int32),
     ]
 
 

@@ -244,17 +244,54 @@ def tune_lambda(op: Operator, g: torch.Tensor, gamma_true: torch.Tensor, lam0: f
     return float(log_lam.exp().item()), history
 
 
+_TILE_CACHE: dict = {}
+
+
+def autotune_tile(op: Operator, g: torch.Tensor, lam, *, candidates=(8, 16), repeats: int = 2,
+                  **options) -> int:
+    """Pick tile_pixels (pixels in flight per SM) for this operator and batch by timing
+    bpdn_solve with each candidate on g itself.  Results are cached by
+    (N, L, precision, P); candidates the kernel cannot run at these sizes are skipped."""
+    P = g.shape[0]
+    prec = int(options.get("precision", 0))
+    key = (op.N, op.L, prec, P)
+    if key in _TILE_CACHE:
+        return _TILE_CACHE[key]
+    best, best_ms = 0, float("inf")
+    for t in candidates:
+        try:
+            solve(op, g, lam, tile_pixels=t, **options)  # warm-up, and checks that it runs
+        except _lib.BPDNError:
+            continue
+        ms = float("inf")
+        for _ in range(repeats):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            solve(op, g, lam, tile_pixels=t, **options)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = min(ms, e0.elapsed_time(e1))
+        if ms < best_ms:
+            best, best_ms = t, ms
+    _TILE_CACHE[key] = best
+    return best
+
+
 class RaggedSolver:
     """Many stacks, each with its own operator and pixel count, through bpdn_solve_ragged.
 
-    items: list of (Operator, g [P_s, N_s] complex64 CUDA tensor, lambda).  Outputs are
+    items: list of (Operator, g [P_s, N_s] complex64 CUDA tensor, lambda).  With
+    autotune=True each stack's tile_pixels is chosen by autotune_tile first.  Outputs are
     allocated once (`results`, one SolveResult per stack).  run() launches on the current
     (or given) stream; capture() records one call into a CUDA graph and replay()
     relaunches it: the graph reads the same g tensors, so new data is copied into them."""
 
-    def __init__(self, items, **options):
+    def __init__(self, items, *, autotune: bool = False, **options):
         lib = _lib.load()
         self.opt = _lib.default_options(**options)
+        self.tiles = [autotune_tile(op, _check_g(op, g), lam, **options) if autotune else 0
+                      for op, g, lam in items]
         self.items = []
         self.results = []
         self._keep = []
@@ -275,7 +312,7 @@ class RaggedSolver:
             )
             arr[i] = _lib.Stack(op.handle.value, g.data_ptr(), P, lam_t.data_ptr(), pp, res.x.data_ptr(),
                                 _ptr(res.support), res.nsupp.data_ptr(), res.status.data_ptr(),
-                                res.iters.data_ptr(), res.nbt.data_ptr())
+                                res.iters.data_ptr(), res.nbt.data_ptr(), self.tiles[i])
             self.items.append((op, g, lam_t))
             self.results.append(res)
         self._arr = arr

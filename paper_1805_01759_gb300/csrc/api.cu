@@ -110,6 +110,8 @@ static int check_options(const bpdn_options *o)
         return set_error(BPDN_EINVAL, "max_bt must be >= 0");
     if (o->refit_rounds < 0 || o->refit_rounds > 64)
         return set_error(BPDN_EINVAL, "refit_rounds must lie in [0, 64]");
+    if (o->tile_pixels != 0 && o->tile_pixels != 8 && o->tile_pixels != 16)
+        return set_error(BPDN_EINVAL, "tile_pixels must be 0 (library choice), 8 or 16");
     return BPDN_OK;
 }
 
@@ -162,7 +164,7 @@ int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     if (opt->refit && d_support && !aligned(d_support, 4))
         return set_error(BPDN_EALIGN, "support must be 4-byte aligned");
     int dev = op->device;
-    const char *why = rbpg_check(*op, opt->precision, max_smem_optin(dev));
+    const char *why = rbpg_check(*op, opt->precision, opt->tile_pixels / 8, max_smem_optin(dev));
     if (why[0] != '\0')
         return set_error(BPDN_ESIZE, "N = %d, L = %d, precision %d: %s", op->N, op->L, opt->precision, why);
     if (!launch)
@@ -190,6 +192,7 @@ int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     a.alpha0 = (float)(opt->alpha0_scale / (2.0 * op->N));
     a.max_bt = opt->max_bt;
     a.precision = opt->precision;
+    a.groups = opt->tile_pixels / 8;
     a.err = (int *)((char *)d_workspace + 8);
     rc = check_cuda(launch_rbpg(*op, a, num_sms(dev), s), "iteration kernel");
     if (rc)

@@ -68,12 +68,13 @@ struct SolveLaunch {
     float alpha0;
     int max_bt;
     int precision;
-    int *err;  // set to 1 if a bounded wait ran out (may be NULL)
+    int groups;  // slot groups of 8 pixels per CTA: 0 = the kernel's choice, 1 or 2
+    int *err;    // set to 1 if a bounded wait ran out (may be NULL)
 };
 // iteration kernel (a.precision 0: FP32 CUDA cores, 1: BF16 tensor cores)
 cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
 // "" when the operator's sizes suit the kernel at this precision, else the reason
-const char *rbpg_check(const OpHandle &op, int precision, int max_smem);
+const char *rbpg_check(const OpHandle &op, int precision, int groups, int max_smem);
 
 struct RefitLaunch {
     const float2 *g;

@@ -6,7 +6,8 @@
 // one event and join back through one event per worker.  The persistent iteration
 // kernel of one stack holds whole SMs, so a stack issued on another stream starts
 // on the SMs the previous stack's last CTAs release; the event fork/join keeps the
-// call capturable into a single CUDA graph.
+// call capturable into a single CUDA graph.  A stack may carry its own tile_pixels
+// (pixels in flight per SM), as an autotuner picks them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -92,11 +93,18 @@ int bpdn_solve_ragged(const bpdn_stack *stacks, int32_t n_stacks, const bpdn_opt
     int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
     if (rc)
         return rc;
+    if (!opt)
+        return set_error(BPDN_EINVAL, "options pointer is NULL");
+    // each stack's options: the call's, with the stack's tile_pixels when it names one
+    std::vector<bpdn_options> sopt(n_stacks, *opt);
+    for (int i = 0; i < n_stacks; ++i)
+        if (stacks[i].tile_pixels)
+            sopt[i].tile_pixels = stacks[i].tile_pixels;
     // every stack is checked before anything is launched
     for (int i = 0; i < n_stacks; ++i) {
         const bpdn_stack &st = stacks[i];
         unsigned char *ws = (unsigned char *)d_workspace + kStackScratch * (size_t)i;
-        rc = solve_impl(st.op, st.d_g, st.P, st.d_lambda, st.lambda_per_pixel, opt, st.d_x, st.d_support,
+        rc = solve_impl(st.op, st.d_g, st.P, st.d_lambda, st.lambda_per_pixel, &sopt[i], st.d_x, st.d_support,
                         st.d_nsupp, st.d_status, st.d_iters, st.d_nbt, ws, kStackScratch, nullptr, false);
         if (rc) {
             char msg[512];
@@ -126,7 +134,7 @@ int bpdn_solve_ragged(const bpdn_stack *stacks, int32_t n_stacks, const bpdn_opt
         const int i = order[j];
         const bpdn_stack &st = stacks[i];
         unsigned char *ws = (unsigned char *)d_workspace + kStackScratch * (size_t)i;
-        rc = solve_impl(st.op, st.d_g, st.P, st.d_lambda, st.lambda_per_pixel, opt, st.d_x, st.d_support,
+        rc = solve_impl(st.op, st.d_g, st.P, st.d_lambda, st.lambda_per_pixel, &sopt[i], st.d_x, st.d_support,
                         st.d_nsupp, st.d_status, st.d_iters, st.d_nbt, ws, kStackScratch,
                         (void *)pool->stream[j % used], true);
     }

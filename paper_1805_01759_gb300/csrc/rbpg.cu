@@ -897,9 +897,10 @@ struct Plan {
     size_t smem;
 };
 
-// Pick groups per CTA and where A lives: two groups before one, A in shared memory
-// before A in global memory.  Returns an empty string on success, else the reason.
-const char *make_plan(const OpHandle &op, bool tc, int max_smem, Plan *pl)
+// Pick groups per CTA and where A lives: two groups before one (or the groups asked
+// for), A in shared memory before A in global memory.  Returns an empty string on
+// success, else the reason.
+const char *make_plan(const OpHandle &op, bool tc, int groups, int max_smem, Plan *pl)
 {
     if (op.Lpad > 32 * kMaxNW)
         return "the iteration kernel handles L <= 1024";
@@ -913,6 +914,8 @@ const char *make_plan(const OpHandle &op, bool tc, int max_smem, Plan *pl)
         if (!sa && tc)
             break;
         for (int g = kMaxGroups; g >= 1; --g) {
+            if (groups && g != groups)
+                continue;
             const int W = warps_for(op.Lpad, g);
             // the BF16 variant is built for at most 832 threads, the FP32 ones for 1024
             if (32 * W > (tc ? 832 : 1024) || tmem_cols_used(T, g, tc) > kTmemCols)
@@ -927,7 +930,8 @@ const char *make_plan(const OpHandle &op, bool tc, int max_smem, Plan *pl)
             return "";
         }
     }
-    return "the iteration kernel's shared memory does not fit (N and L too large)";
+    return groups ? "this tile_pixels does not fit the iteration kernel at these N and L"
+                  : "the iteration kernel's shared memory does not fit (N and L too large)";
 }
 
 template <bool TC, bool SA, int MAXT>
@@ -942,10 +946,10 @@ cudaError_t launch_variant(const Params &prm, const Plan &pl, int grid, size_t s
 
 }  // namespace
 
-const char *rbpg_check(const OpHandle &op, int precision, int max_smem)
+const char *rbpg_check(const OpHandle &op, int precision, int groups, int max_smem)
 {
     Plan pl;
-    return make_plan(op, precision == 1, max_smem, &pl);
+    return make_plan(op, precision == 1, groups, max_smem, &pl);
 }
 
 cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s)
@@ -967,7 +971,7 @@ cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, c
         return e;
     const bool tc = (a.precision == 1);
     Plan pl;
-    if (make_plan(op, tc, max_smem, &pl)[0] != '\0')
+    if (make_plan(op, tc, a.groups, max_smem, &pl)[0] != '\0')
         return cudaErrorInvalidValue;
     // one CTA per SM: each CTA allocates all 512 tensor-memory columns
     size_t smem = pl.smem;

@@ -110,3 +110,37 @@ def test_ragged_rejects_bad_stack_before_launch(api, stacks):
     torch.cuda.synchronize()
     for r in solver.results:
         assert torch.all(r.status == -7)  # nothing ran
+
+
+def test_tile_pixels_do_not_change_results(api, stacks):
+    """8 or 16 pixels in flight per SM: every pixel's arithmetic is the same (sums in a
+    fixed order, the same reduction tree for every slot), so results are bitwise equal."""
+    from paper_1805_01759_gb300 import _lib
+    sts, items = stacks
+    compared = 0
+    for op, g, lam in items:
+        a = api.solve(op, g, lam, tile_pixels=8)
+        try:
+            b = api.solve(op, g, lam, tile_pixels=16)
+        except _lib.BPDNError as e:  # two groups exceed 1024 threads at this L
+            assert e.code == _lib.BPDN_ESIZE
+            continue
+        torch.cuda.synchronize()
+        assert _same(a, b)
+        compared += 1
+    assert compared >= 2
+    op, g, lam = items[0]
+    with pytest.raises(_lib.BPDNError) as ei:
+        api.solve(op, g, lam, tile_pixels=12)
+    assert ei.value.code == _lib.BPDN_EINVAL
+
+
+def test_autotuned_ragged_equals_default(api, stacks):
+    sts, items = stacks
+    tuned = api.RaggedSolver(items, autotune=True)
+    assert all(t in (8, 16) for t in tuned.tiles)
+    out = tuned.run()
+    ref = api.solve_ragged(items)
+    torch.cuda.synchronize()
+    for r, e in zip(out, ref):
+        assert _same(r, e)
