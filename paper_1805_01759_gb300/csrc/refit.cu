@@ -15,7 +15,7 @@
 //      and the step recomputed.  If that does not converge, damped Newton on the
 //      smoothed objective (|z| -> sqrt(|z|^2 + eps^2), strictly convex) for a
 //      decreasing eps finds the support first.
-//      Precision: the support is found in FP32 (residual <= 1e-4 lambda); the
+//      Precision: the support is found in FP32 (residual <= 3e-6 lambda); the
 //      answer is then finished and checked in FP64 (residual <= 1e-12 lambda),
 //      falling back to an all-FP64 solve when the FP32 support was wrong.  The
 //      Newton systems are factored in FP32 in both phases: each step is then an
@@ -40,6 +40,8 @@ namespace {
 
 constexpr int KW = kRefitMax;  // working-set capacity (<= 16, so 2|W| <= 32 lanes)
 constexpr int kFastRounds32 = 15;
+// FP32 phase tolerance, near FP32 resolution: every FP32 step saved here costs ~5x in FP64
+constexpr float kTol32 = 3e-6f;
 constexpr int kFastRounds64 = 8;
 constexpr int kFallbackRounds = 20;
 
@@ -347,7 +349,9 @@ template <typename T>
 __device__ __noinline__ bool fast_path(Solve<T> &S, int m, T lam, int lane, int max_outer, T tol)
 {
     for (int outer = 0; outer < max_outer; ++outer) {
-        cd_sweep(S, m, lam, lane);
+        // the FP64 phase starts from the FP32 answer, whose support is settled: Newton first
+        if (sizeof(T) == 4 || outer > 0)
+            cd_sweep(S, m, lam, lane);
         const T res = optimality(S, m, lam, lane);
         if (res <= tol)
             return true;
@@ -477,9 +481,9 @@ __device__ __noinline__ bool restricted_minimiser(PixelSmem &P, const double2 *A
             S.z[lane] = mk<float>((float)start.x, (float)start.y);
         __syncwarp();
         const float lf = (float)lam;
-        if (!fast_path(S, m, lf, lane, kFastRounds32, 1e-4f)) {
+        if (!fast_path(S, m, lf, lane, kFastRounds32, kTol32)) {
             continuation(S, m, lf, lane, 1e-2f, 1e-6f, 8);
-            fast_path(S, m, lf, lane, kFastRounds32, 1e-4f);
+            fast_path(S, m, lf, lane, kFastRounds32, kTol32);
         }
         if (lane < m)
             P.zkeep[lane] = make_double2((double)S.z[lane].x, (double)S.z[lane].y);
