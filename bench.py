@@ -492,13 +492,23 @@ def run_ours(args) -> None:
         "paths": out_paths,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic, "kernel": kname,
-                     "note": f"peak = FP32 FMA rate, {n_sm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
+                     "note": "the fused iteration (Algorithm 1); see kernels for the refit's share. "
+                             f"peak = FP32 FMA rate, {n_sm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
                              "(unit counts and the max SM clock); achieved = the algorithmic FP32 work of "
                              "Algorithm 1 per pixel sweep (36 L elementwise flops"
                              + ("" if head == "bf16" else " + 8 N L for the contraction") +
                              "; a step cut is one more sweep) over the iteration kernel's event-timed "
                              "duration" + ("; the BF16 contraction (8 N L per sweep) runs on the tensor "
                                            "cores, see paths.bf16.tensor_tflops" if head == "bf16" else "")},
+        "kernels": {
+            "iteration": {"name": kname, "ms": statistics.mean(head_tm["rbpg_ms"]),
+                          "share": statistics.mean(head_tm["rbpg_ms"]) / ms_head,
+                          "bound": "FP32 pipe (roofline above)"},
+            "refit": {"name": "k_refit", "ms": statistics.mean(head_tm["refit_ms"]),
+                      "share": statistics.mean(head_tm["refit_ms"]) / ms_head,
+                      "bound": "latency and instruction fetch (one warp per pixel, FP64 finish); no pipe "
+                               "above ~20 % busy in ncu, so no throughput roofline applies"},
+        },
         "precision_report": prec_report,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

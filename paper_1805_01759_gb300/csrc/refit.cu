@@ -104,13 +104,20 @@ struct PixelSmem {
         Solve<double> s64;
         Solve<float> s32;
     };
-    double2 g[BPDN_MAX_N];   // g in FP64
-    double2 rr[BPDN_MAX_N];  // A_W z - g (FP64)
-    float2 rf[BPDN_MAX_N];   // its FP32 copy
-    double2 zkeep[KW];       // z between the precisions (FP64)
+    double2 *g;   // [N] g in FP64       (these three follow the struct, sized by N)
+    double2 *rr;  // [N] A_W z - g (FP64)
+    float2 *rf;   // [N] its FP32 copy
+    double2 zkeep[KW];  // z between the precisions (FP64)
     int W[KW];
     int m;
 };
+
+// shared memory of one pixel: the struct, then g, rr (FP64) and rf (FP32) of length N
+__host__ __device__ inline size_t pixel_smem_bytes(int N)
+{
+    const size_t b = sizeof(PixelSmem) + (size_t)N * (sizeof(double2) * 2 + sizeof(float2));
+    return (b + 15) & ~(size_t)15;
+}
 
 constexpr int WARPS = 1;  // pixels (warps) per block
 
@@ -533,10 +540,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict_
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    PixelSmem &P = ((PixelSmem *)smem_raw)[warp];
+    unsigned char *pbase = smem_raw + (size_t)warp * pixel_smem_bytes(N);
+    PixelSmem &P = *(PixelSmem *)pbase;
     const long long p = (long long)blockIdx.x * WARPS + warp;
     if (p >= a.P)
         return;
+    if (lane == 0) {
+        P.g = (double2 *)(pbase + sizeof(PixelSmem));
+        P.rr = P.g + N;
+        P.rf = (float2 *)(P.rr + N);
+    }
+    __syncwarp();
     const int smax = a.s_max;
     const float2 *xin = a.x_in + (size_t)p * L;
     const float2 *gp = a.g + (size_t)p * N;
@@ -792,7 +806,7 @@ cudaError_t launch_refit(const OpHandle &op, const RefitLaunch &a, cudaStream_t 
 {
     if (a.P <= 0)
         return cudaSuccess;
-    const size_t smem = WARPS * sizeof(PixelSmem);
+    const size_t smem = WARPS * pixel_smem_bytes(op.N);
     cudaError_t e = cudaFuncSetAttribute(k_refit, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess)
