@@ -138,10 +138,9 @@ static int check_solve_buffers(const OpHandle *op, const void *d_g, int64_t P, c
 }
 
 // Checks every argument of a solve; launches it when `launch` is true.
-int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, int32_t lambda_per_pixel,
+int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, int32_t lambda_per_pixel,
                const bpdn_options *opt, void *d_x, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
-               int32_t *d_iters, int32_t *d_nbt, void *d_workspace, size_t workspace_bytes, void *cuda_stream,
-               bool launch)
+               int32_t *d_iters, int32_t *d_nbt, void *d_workspace, size_t workspace_bytes, SolvePlan *sp)
 {
     OpHandle *op = nullptr;
     int rc = check_op(h, &op);
@@ -153,6 +152,9 @@ int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     rc = check_solve_buffers(op, d_g, P, d_lambda, d_x, d_status);
     if (rc)
         return rc;
+    sp->op = op;
+    sp->refit = false;
+    sp->a.P = 0;
     if (P == 0)
         return BPDN_OK;
     if (!d_iters)
@@ -163,19 +165,10 @@ int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
         return set_error(BPDN_EALIGN, "solve workspace must be 256-byte aligned");
     if (opt->refit && d_support && !aligned(d_support, 4))
         return set_error(BPDN_EALIGN, "support must be 4-byte aligned");
-    int dev = op->device;
-    const char *why = rbpg_check(*op, opt->precision, opt->tile_pixels / 8, max_smem_optin(dev));
+    const char *why = rbpg_check(*op, opt->precision, opt->tile_pixels / 8, max_smem_optin(op->device));
     if (why[0] != '\0')
         return set_error(BPDN_ESIZE, "N = %d, L = %d, precision %d: %s", op->N, op->L, opt->precision, why);
-    if (!launch)
-        return BPDN_OK;
-    cudaStream_t s = (cudaStream_t)cuda_stream;
-    unsigned long long *counter = (unsigned long long *)d_workspace;
-    // work counter (8 bytes) and the kernel's error word (4 bytes)
-    rc = check_cuda(cudaMemsetAsync(counter, 0, 16, s), "reset work counter");
-    if (rc)
-        return rc;
-    SolveLaunch a;
+    SolveLaunch &a = sp->a;
     a.g = (const float2 *)d_g;
     a.P = P;
     a.lam = d_lambda;
@@ -185,7 +178,8 @@ int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     a.status = d_status;
     a.iters = d_iters;
     a.nbt = d_nbt;
-    a.counter = counter;
+    // work counter (8 bytes) and the kernel's error word (4 bytes) at the workspace start
+    a.counter = (unsigned long long *)d_workspace;
     a.max_iter = opt->max_iter;
     a.tol = opt->tol;
     a.c_alpha = opt->c_alpha;
@@ -194,26 +188,43 @@ int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     a.precision = opt->precision;
     a.groups = opt->tile_pixels / 8;
     a.err = (int *)((char *)d_workspace + 8);
-    rc = check_cuda(launch_rbpg(*op, a, num_sms(dev), s), "iteration kernel");
+    sp->refit = opt->refit != 0;
+    RefitLaunch &r = sp->r;
+    r.g = a.g;
+    r.P = P;
+    r.lam = d_lambda;
+    r.lam_pp = a.lam_pp;
+    r.x_in = a.x;
+    r.x_out = a.x;
+    r.support = d_support;
+    r.nsupp = d_nsupp;
+    r.status = d_status;
+    r.s_max = opt->s_max;
+    r.rounds = opt->refit_rounds;
+    return BPDN_OK;
+}
+
+int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, int32_t lambda_per_pixel,
+               const bpdn_options *opt, void *d_x, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
+               int32_t *d_iters, int32_t *d_nbt, void *d_workspace, size_t workspace_bytes, void *cuda_stream,
+               bool launch)
+{
+    SolvePlan sp;
+    int rc = solve_plan(h, d_g, P, d_lambda, lambda_per_pixel, opt, d_x, d_support, d_nsupp, d_status, d_iters,
+                        d_nbt, d_workspace, workspace_bytes, &sp);
+    if (rc || !launch || sp.a.P == 0)
+        return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    rc = check_cuda(cudaMemsetAsync(sp.a.counter, 0, 16, s), "reset work counter");
     if (rc)
         return rc;
-    if (opt->refit) {
-        RefitLaunch r;
-        r.g = a.g;
-        r.P = P;
-        r.lam = d_lambda;
-        r.lam_pp = a.lam_pp;
-        r.x_in = a.x;
-        r.x_out = a.x;
-        r.support = d_support;
-        r.nsupp = d_nsupp;
-        r.status = d_status;
-        r.s_max = opt->s_max;
-        r.rounds = opt->refit_rounds;
-        rc = check_cuda(launch_refit(*op, r, s), "refit kernel");
-    }
-    return rc;
+    rc = check_cuda(launch_rbpg(*sp.op, sp.a, num_sms(sp.op->device), s), "iteration kernel");
+    if (rc || !sp.refit)
+        return rc;
+    return check_cuda(launch_refit(*sp.op, sp.r, s), "refit kernel");
 }
+
+int device_sms(int dev) { return num_sms(dev); }
 }  // namespace bpdn
 
 extern "C" {

@@ -47,6 +47,12 @@ int check_cuda(cudaError_t e, const char *what);
 // ---- launches (each returns a cudaError_t from the launch) ----
 cudaError_t launch_make_operator(const OpHandle &op, const double *d_b, cudaStream_t s);
 
+struct SolvePlan;
+// bpdn_solve's argument checks and launch records (sp->a.P == 0: nothing to launch)
+int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, int32_t lambda_per_pixel,
+               const bpdn_options *opt, void *d_x, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
+               int32_t *d_iters, int32_t *d_nbt, void *d_workspace, size_t workspace_bytes, SolvePlan *sp);
+int device_sms(int dev);
 // bpdn_solve's argument checks, followed by its launches when `launch` is true
 int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, int32_t lambda_per_pixel,
                const bpdn_options *opt, void *d_x, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
@@ -73,6 +79,9 @@ struct SolveLaunch {
 };
 // iteration kernel (a.precision 0: FP32 CUDA cores, 1: BF16 tensor cores)
 cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
+// many stacks in persistent launches, one per kernel variant present (at most 64 stacks each)
+cudaError_t launch_rbpg_batch(const OpHandle *const *ops, const SolveLaunch *as, int n, int num_sms,
+                              cudaStream_t s);
 // "" when the operator's sizes suit the kernel at this precision, else the reason
 const char *rbpg_check(const OpHandle &op, int precision, int groups, int max_smem);
 
@@ -88,6 +97,13 @@ struct RefitLaunch {
     int rounds;
 };
 cudaError_t launch_refit(const OpHandle &op, const RefitLaunch &a, cudaStream_t s);
+
+struct SolvePlan {
+    OpHandle *op;
+    SolveLaunch a;
+    RefitLaunch r;
+    bool refit;
+};
 
 struct BackwardLaunch {
     int64_t P;

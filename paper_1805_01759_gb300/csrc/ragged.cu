@@ -1,13 +1,14 @@
 // bpdn_solve_ragged: many stacks with their own operators in one call.
 //
-// Each stack is an independent bpdn_solve.  The call checks every stack, orders
-// them by estimated cost P N L (largest first) and issues them round-robin on a
-// small pool of library-owned streams that fork from the caller's stream through
-// one event and join back through one event per worker.  The persistent iteration
-// kernel of one stack holds whole SMs, so a stack issued on another stream starts
-// on the SMs the previous stack's last CTAs release; the event fork/join keeps the
-// call capturable into a single CUDA graph.  A stack may carry its own tile_pixels
-// (pixels in flight per SM), as an autotuner picks them.
+// Each stack is an independent bpdn_solve.  The call checks every stack, then runs
+// Algorithm 1 for all of them in one persistent launch of the iteration kernel per
+// kernel variant present (BF16 or FP32; A in shared or in global memory; at most 64
+// stacks each): every CTA walks the stacks, smallest first, and works on each one
+// while it has pixels left.  The refits follow, one launch per stack, spread over a
+// small pool of library-owned streams that fork from and join back into the
+// caller's stream through events, so the call can be captured into one CUDA graph.
+// A stack may carry its own tile_pixels (pixels in flight per SM), as an autotuner
+// picks them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -112,31 +113,51 @@ int bpdn_solve_ragged(const bpdn_stack *stacks, int32_t n_stacks, const bpdn_opt
             return set_error(rc, "stack %d: %s", i, msg);
         }
     }
-    std::vector<int> order(n_stacks);
-    std::vector<double> cost(n_stacks);
+    std::vector<SolvePlan> plans(n_stacks);
     for (int i = 0; i < n_stacks; ++i) {
-        order[i] = i;
-        cost[i] = stack_cost(stacks[i]);
+        const bpdn_stack &st = stacks[i];
+        unsigned char *ws = (unsigned char *)d_workspace + kStackScratch * (size_t)i;
+        rc = solve_plan(st.op, st.d_g, st.P, st.d_lambda, st.lambda_per_pixel, &sopt[i], st.d_x, st.d_support,
+                        st.d_nsupp, st.d_status, st.d_iters, st.d_nbt, ws, kStackScratch, &plans[i]);
+        if (rc)
+            return rc;  // checked above: cannot happen
     }
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-
+    std::vector<const OpHandle *> ops;
+    std::vector<SolveLaunch> as;
+    std::vector<int> refit_order;
+    for (int i = 0; i < n_stacks; ++i) {
+        if (plans[i].a.P == 0)
+            continue;
+        ops.push_back(plans[i].op);
+        as.push_back(plans[i].a);
+        if (plans[i].refit)
+            refit_order.push_back(i);
+    }
+    cudaStream_t origin = (cudaStream_t)cuda_stream;
+    // every stack's work counter and error word in one clear
+    rc = check_cuda(cudaMemsetAsync(d_workspace, 0, kStackScratch * (size_t)n_stacks, origin), "clear work counters");
+    if (rc)
+        return rc;
+    if (!as.empty())
+        rc = check_cuda(launch_rbpg_batch(ops.data(), as.data(), (int)as.size(), device_sms(dev), origin),
+                        "iteration kernel");
+    if (rc || refit_order.empty())
+        return rc;
+    // the refits, largest stacks first, on the worker streams
+    std::stable_sort(refit_order.begin(), refit_order.end(),
+                     [&](int x, int y) { return stack_cost(stacks[x]) > stack_cost(stacks[y]); });
     std::lock_guard<std::mutex> lk(g_mu);
     Pool *pool = nullptr;
     rc = pool_for(dev, &pool);
     if (rc)
         return rc;
-    cudaStream_t origin = (cudaStream_t)cuda_stream;
-    const int used = n_stacks < kWorkers ? n_stacks : kWorkers;
+    const int used = (int)refit_order.size() < kWorkers ? (int)refit_order.size() : kWorkers;
     rc = check_cuda(cudaEventRecord(pool->fork, origin), "record fork event");
     for (int k = 0; k < used && !rc; ++k)
         rc = check_cuda(cudaStreamWaitEvent(pool->stream[k], pool->fork, 0), "fork worker stream");
-    for (int j = 0; j < n_stacks && !rc; ++j) {
-        const int i = order[j];
-        const bpdn_stack &st = stacks[i];
-        unsigned char *ws = (unsigned char *)d_workspace + kStackScratch * (size_t)i;
-        rc = solve_impl(st.op, st.d_g, st.P, st.d_lambda, st.lambda_per_pixel, &sopt[i], st.d_x, st.d_support,
-                        st.d_nsupp, st.d_status, st.d_iters, st.d_nbt, ws, kStackScratch,
-                        (void *)pool->stream[j % used], true);
+    for (size_t j = 0; j < refit_order.size() && !rc; ++j) {
+        const SolvePlan &sp = plans[refit_order[j]];
+        rc = check_cuda(launch_refit(*sp.op, sp.r, pool->stream[j % used]), "refit kernel");
     }
     // join every forked stream back into the caller's stream, also after an error
     for (int k = 0; k < used; ++k) {

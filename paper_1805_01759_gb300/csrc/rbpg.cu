@@ -36,6 +36,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <memory>
+#include <vector>
+
 #include "bpdn_internal.h"
 
 namespace bpdn {
@@ -174,10 +178,20 @@ __host__ __device__ inline int tmem_cols_used(int T, int G, bool tc)
     return (tc ? 32 * T + 16 * T * G : 0) + 32 * T * G;
 }
 
-struct Params {
+// one stack of a launch: its operator, sizes and solve
+struct StackDesc {
     const float *A_re, *A_im;  // global planar tables [N][lda]
     int N, L, Lpad, lda;
+    int groups;  // slot groups of 8 pixels per CTA for this stack
+    int ctas;    // CTAs 0 .. ctas-1 take this stack's pixels
     SolveLaunch a;
+};
+
+constexpr int kMaxStacks = 64;  // stacks per launch (kernel parameters stay below 32 KB)
+
+struct Params {
+    int nstacks;
+    StackDesc st[kMaxStacks];
 };
 
 // barrier of one group (ids 1..kMaxGroups; id 0 is __syncthreads)
@@ -329,11 +343,12 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8])
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-template <bool TC, bool SA, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) k_rbpg(Params prm, int G)
+// Algorithm 1 for one stack, by the whole CTA, until the stack's pixels run out and every
+// slot has drained; tensor memory is allocated by the caller
+template <bool TC, bool SA>
+__device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, unsigned char *smem_raw)
 {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ uint32_t s_tmem;
+    const int G = prm.groups;
     const int N = prm.N, L = prm.L, Lpad = prm.Lpad, lda = prm.lda;
     const int NW = Lpad / 32;  // warps (blocks of 32 grid points) per group
     constexpr int NCH = TC ? 1 : 2;  // rows n = lane + 32 c, c < NCH, per lane (BF16: N <= 32)
@@ -399,15 +414,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_rbpg(Params prm, int G)
             }
         }
     }
-    if (w == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(kTmemCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = s_tmem;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * q4) << 16);
     const int T = (Lpad + 127) / 128;
     const int colD = TC ? 32 * T : 0;
@@ -453,11 +462,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_rbpg(Params prm, int G)
     }
     tc_fence_before();
     __syncthreads();  // A, operator rows of every tile in place before any group's MMA
-    if (!live) {
-        // idle warp: wait for the groups to finish, then leave
-        __syncthreads();
-        return;
-    }
+    if (!live)
+        return;  // idle warp of this stack: the caller's barrier waits for the groups
 
     const float alpha0 = a.alpha0;
     const float tol2 = a.tol * a.tol;
@@ -881,13 +887,49 @@ __global__ void __launch_bounds__(MAXT, 1) k_rbpg(Params prm, int G)
         tc_fence_before();
         group_sync(grp, 32 * NW);
     }
-    // every group has finished and no MMA is in flight: release tensor memory
+    // this group has drained and its last MMA was waited for: retire its mbarrier
+    if constexpr (TC) {
+        if (blk == 0 && lane == 0)
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mbar) : "memory");
+    }
+}
+
+// The persistent kernel: every CTA walks the launch's stacks in order and works on
+// each one it may take (blockIdx.x < ctas) while that stack has pixels left.
+template <bool TC, bool SA, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_rbpg(const __grid_constant__ Params prm)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_go;
+    const int w = threadIdx.x >> 5;
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
     tc_fence_before();
     __syncthreads();
-    if (w == 0) {
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    for (int si = 0; si < prm.nstacks; ++si) {
+        const StackDesc &sd = prm.st[si];
+        if ((int)blockIdx.x >= sd.ctas)
+            continue;
+        if (threadIdx.x == 0)
+            s_go = (*(volatile unsigned long long *)sd.a.counter < (unsigned long long)sd.a.P) ? 1 : 0;
+        __syncthreads();
+        const int go = s_go;
+        __syncthreads();  // everyone has read s_go before it is written again
+        if (!go)
+            continue;  // the other CTAs took every pixel of this stack
+        run_stack<TC, SA>(sd, tmem, smem_raw);
+        tc_fence_before();
+        __syncthreads();  // every group of this stack has drained; no MMA in flight
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
     }
+    if (w == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 // launch shape of one solve
@@ -935,14 +977,16 @@ const char *make_plan(const OpHandle &op, bool tc, int groups, int max_smem, Pla
 }
 
 template <bool TC, bool SA, int MAXT>
-cudaError_t launch_variant(const Params &prm, const Plan &pl, int grid, size_t smem, cudaStream_t s)
+cudaError_t launch_variant(const Params &prm, int threads, int grid, size_t smem, cudaStream_t s)
 {
     cudaError_t e = cudaFuncSetAttribute(k_rbpg<TC, SA, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    k_rbpg<TC, SA, MAXT><<<grid, pl.threads, smem, s>>>(prm, pl.groups);
+    k_rbpg<TC, SA, MAXT><<<grid, threads, smem, s>>>(prm);
     return cudaGetLastError();
 }
+
+static_assert(sizeof(Params) <= 32000, "kernel parameters must stay below 32 KB");
 
 }  // namespace
 
@@ -952,16 +996,8 @@ const char *rbpg_check(const OpHandle &op, int precision, int groups, int max_sm
     return make_plan(op, precision == 1, groups, max_smem, &pl);
 }
 
-cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s)
+cudaError_t launch_rbpg_batch(const OpHandle *const *ops, const SolveLaunch *as, int n, int num_sms, cudaStream_t s)
 {
-    Params prm;
-    prm.A_re = op.A_re;
-    prm.A_im = op.A_im;
-    prm.N = op.N;
-    prm.L = op.L;
-    prm.Lpad = op.Lpad;
-    prm.lda = op.lda;
-    prm.a = a;
     int dev = 0, max_smem = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
@@ -969,26 +1005,76 @@ cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, c
     e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess)
         return e;
-    const bool tc = (a.precision == 1);
-    Plan pl;
-    if (make_plan(op, tc, a.groups, max_smem, &pl)[0] != '\0')
-        return cudaErrorInvalidValue;
-    // one CTA per SM: each CTA allocates all 512 tensor-memory columns
-    size_t smem = pl.smem;
-    if (smem < (size_t)max_smem / 2 + 1024)
-        smem = (size_t)max_smem / 2 + 1024;
-    const long long tiles = (a.P + (long long)pl.groups * TPG - 1) / ((long long)pl.groups * TPG);
-    int grid = (int)((tiles < num_sms) ? tiles : num_sms);
-    if (grid < 1)
-        grid = 1;
-    const bool big = pl.threads > 832;
-    if (tc)
-        return launch_variant<true, true, 832>(prm, pl, grid, smem, s);
-    if (pl.smem_a)
-        return big ? launch_variant<false, true, 1024>(prm, pl, grid, smem, s)
-                   : launch_variant<false, true, 832>(prm, pl, grid, smem, s);
-    return big ? launch_variant<false, false, 1024>(prm, pl, grid, smem, s)
-               : launch_variant<false, false, 832>(prm, pl, grid, smem, s);
+    struct Item {
+        int i;
+        Plan pl;
+    };
+    // kernel variant of a stack: precision, where A lives, launch bound
+    std::vector<Item> byvar[8];
+    for (int i = 0; i < n; ++i) {
+        if (as[i].P <= 0)
+            continue;
+        Item it;
+        it.i = i;
+        const bool tc = (as[i].precision == 1);
+        if (make_plan(*ops[i], tc, as[i].groups, max_smem, &it.pl)[0] != '\0')
+            return cudaErrorInvalidValue;
+        byvar[(tc ? 4 : 0) + (it.pl.smem_a ? 2 : 0) + (it.pl.threads > 832 ? 1 : 0)].push_back(it);
+    }
+    std::unique_ptr<Params> prm(new Params);
+    for (int v = 0; v < 8; ++v) {
+        std::vector<Item> &list = byvar[v];
+        // small stacks first: the large pools at the end absorb the CTAs' uneven progress
+        std::stable_sort(list.begin(), list.end(), [&](const Item &x, const Item &y) { return as[x.i].P < as[y.i].P; });
+        for (size_t c0 = 0; c0 < list.size(); c0 += kMaxStacks) {
+            const size_t c1 = std::min(list.size(), c0 + (size_t)kMaxStacks);
+            prm->nstacks = (int)(c1 - c0);
+            int threads = 32, grid = 1;
+            size_t smem = 0;
+            for (size_t k = c0; k < c1; ++k) {
+                const Item &it = list[k];
+                const OpHandle &op = *ops[it.i];
+                StackDesc &sd = prm->st[k - c0];
+                sd.A_re = op.A_re;
+                sd.A_im = op.A_im;
+                sd.N = op.N;
+                sd.L = op.L;
+                sd.Lpad = op.Lpad;
+                sd.lda = op.lda;
+                sd.groups = it.pl.groups;
+                sd.a = as[it.i];
+                // one stack alone: up to one pixel per slot; a batch: at least four pixels per
+                // slot per CTA, so that the drain at each stack switch stays small
+                const long long per = (n == 1 ? 1LL : 4LL) * TPG * it.pl.groups;
+                const long long want = (as[it.i].P + per - 1) / per;
+                sd.ctas = (int)std::max(1LL, std::min((long long)num_sms, want));
+                threads = std::max(threads, it.pl.threads);
+                grid = std::max(grid, sd.ctas);
+                smem = std::max(smem, it.pl.smem);
+            }
+            // one CTA per SM: each CTA allocates all 512 tensor-memory columns
+            if (smem < (size_t)max_smem / 2 + 1024)
+                smem = (size_t)max_smem / 2 + 1024;
+            const bool tc = (v & 4) != 0, sa = (v & 2) != 0, big = (v & 1) != 0;
+            if (tc)
+                e = launch_variant<true, true, 832>(*prm, threads, grid, smem, s);
+            else if (sa)
+                e = big ? launch_variant<false, true, 1024>(*prm, threads, grid, smem, s)
+                        : launch_variant<false, true, 832>(*prm, threads, grid, smem, s);
+            else
+                e = big ? launch_variant<false, false, 1024>(*prm, threads, grid, smem, s)
+                        : launch_variant<false, false, 832>(*prm, threads, grid, smem, s);
+            if (e != cudaSuccess)
+                return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s)
+{
+    const OpHandle *ops[1] = {&op};
+    return launch_rbpg_batch(ops, &a, 1, num_sms, s);
 }
 
 }  // namespace bpdn
