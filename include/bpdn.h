@@ -188,13 +188,14 @@ size_t bpdn_solve_ragged_workspace_bytes(int32_t n_stacks);
  * Solve many stacks, each with its own operator (N, L, grid) and pixel count, in one
  * call: every stack gets exactly the results bpdn_solve would give it.  Every
  * stack's arguments are checked first; on any error nothing is launched and the
- * message names the stack.  The solves are issued largest first (by P N L) on a
- * few library-owned streams that fork from and join back into cuda_stream through
- * events, so the end of one stack overlaps the start of the next and the whole
- * call can be captured into one CUDA graph.  The streams and events are created by
- * the first call on a device: make that call before any stream capture.  Calls on
- * the same device are serialised on the host; their GPU work may overlap only
- * through cuda_stream's own ordering.  Allocates no device memory.
+ * message names the stack.  Algorithm 1 runs for all stacks in one persistent launch
+ * per kernel variant present (BF16 or FP32, A in shared or global memory; 64 stacks
+ * per launch): every CTA works through the stacks while they have pixels left.  The
+ * refits follow, one launch per stack, on a few library-owned streams that fork from
+ * and join back into cuda_stream through events, so the whole call can be captured
+ * into one CUDA graph.  The streams and events are created by the first call on a
+ * device that needs a refit: make that call before any stream capture.  Calls on the
+ * same device are serialised on the host.  Allocates no device memory.
  * The paper solves one stack at a time; this is the batched form of the same solve.
  */
 int bpdn_solve_ragged(const bpdn_stack *stacks, int32_t n_stacks, const bpdn_options *opt,
