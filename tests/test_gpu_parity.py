@@ -239,3 +239,25 @@ def test_solve_refit_operator_sizes(api, N, L, half_width):
     assert sel.sum() >= 30
     assert np.array_equal(x[sel] != 0, ref["x"][sel] != 0)
     assert _rel(x[sel], ref["x"][sel]).max() <= 1e-4
+
+
+def test_stored_minimiser(api):
+    """The full path against tests/golden/small_minimiser.txt (support and values, 1e-4)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "small_minimiser.txt")
+    st = synth.workload_small(P=8, seed=1)
+    want = np.zeros((8, st.geom.L), np.complex128)
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            if f[1] != "zero":
+                want[int(f[0]), int(f[1])] = float(f[2]) + 1j * float(f[3])
+    op = api.Operator.from_geometry(st.geom)
+    for precision in (0, 1):
+        res = api.solve(op, torch.from_numpy(st.g).cuda(), st.lam, precision=precision)
+        x = res.x.cpu().numpy().astype(np.complex128)
+        assert np.all((res.status.cpu().numpy() & 64) != 0)
+        assert np.array_equal(x != 0, want != 0)
+        err = _rel(x, want)
+        zero = np.linalg.norm(want, axis=1) == 0
+        assert np.all(err[~zero] <= 1e-4) and np.all(x[zero] == 0)

@@ -412,3 +412,33 @@ def test_adjoint_zero_solution():
     assert np.all(x == 0)
     dg, dl, rc = oracle.adjoint(A, lam, x, np.ones(st.geom.L, np.complex128))
     assert rc == 0 and np.all(dg == 0) and dl == 0.0
+
+
+# ------------------------------------------------------------------ stored answers
+
+def _read_golden():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "small_minimiser.txt")
+    lam, rows = None, []
+    for line in open(path):
+        if line.startswith("# lambda"):
+            lam = float(line.split()[2])
+        elif line.strip() and not line.startswith("#"):
+            rows.append(line.split())
+    return lam, rows
+
+
+def test_oracle_reproduces_stored_minimiser():
+    """tests/golden/small_minimiser.txt (written by make_golden.py from this oracle): the
+    oracle must keep producing the same supports and values (to 1e-12 relative)."""
+    lam, rows = _read_golden()
+    st = synth.workload_small(P=8, seed=1)
+    assert lam == st.lam
+    A = oracle.operator(st.geom)
+    r = oracle.minimise_batch(A, st.g, st.lam)
+    want = np.zeros((8, st.geom.L), np.complex128)
+    for row in rows:
+        if row[1] != "zero":
+            want[int(row[0]), int(row[1])] = float(row[2]) + 1j * float(row[3])
+    assert np.array_equal(r["x"] != 0, want != 0)
+    np.testing.assert_allclose(r["x"], want, rtol=0, atol=1e-12 * np.abs(want).max())

@@ -34,7 +34,9 @@ MUTANTS = {
     "adjoint_lambda_sign": ("*dLdlam = -dl;", "*dLdlam = dl;"),
 }
 
-PINS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_")]
+# the stored-answer test compares the oracle with its own earlier output: a regression
+# guard, not a pin, so it does not count as catching a planted mistake
+PINS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_") and "stored" not in n]
 
 
 def _build(tmp_path, name, old, new):
