@@ -16,8 +16,9 @@
 //      smoothed objective (|z| -> sqrt(|z|^2 + eps^2), strictly convex) for a
 //      decreasing eps finds the support first.
 //      Precision: the support is found in FP32 (residual <= 3e-6 lambda); the
-//      answer is then finished and checked in FP64 (residual <= 1e-12 lambda),
-//      falling back to an all-FP64 solve when the FP32 support was wrong.  The
+//      answer is then finished and checked in FP64 (residual <= 1e-12 lambda) by plain
+//      Newton steps, then by the sweep/Newton solve if those stall, falling back to an
+//      all-FP64 solve when the FP32 support was wrong.  The
 //      Newton systems are factored in FP32 in both phases: each step is then an
 //      inexact Newton step (relative error about cond * 6e-8), while the objective,
 //      the residual that decides convergence and the line search stay in the
@@ -472,6 +473,34 @@ __device__ __noinline__ void continuation(Solve<T> &S, int m, T lam, int lane, T
     __syncwarp();
 }
 
+// Newton refinement from a start whose support is settled (the FP32 answer): full
+// Newton steps on the nonzero coordinates while no modulus passes near zero and the
+// residual at least halves.  true when the residual reaches tol; false hands over to
+// fast_path.  Far less code and FP64 work than fast_path's sweeps and line searches.
+template <typename T>
+__device__ __noinline__ bool newton_refine(Solve<T> &S, int m, T lam, int lane, int maxit, T tol)
+{
+    T prev = T(1e300);
+    for (int it = 0; it < maxit; ++it) {
+        const T res = optimality(S, m, lam, lane);
+        if (res <= tol)
+            return true;
+        if (!(res < T(0.5) * prev))
+            return false;
+        prev = res;
+        const T slope = newton_dir(S, m, S.z, lam, T(0), lane);
+        if (slope > T(0))
+            return false;
+        const bool bad = (lane < m) && passes_zero(S.z[lane], S.dz[lane], T(1));
+        if (__any_sync(0xffffffffu, bad))
+            return false;
+        if (lane < m)
+            S.z[lane] = cadd(S.z[lane], S.dz[lane]);
+        __syncwarp();
+    }
+    return optimality(S, m, lam, lane) <= tol;
+}
+
 // Step 2 on the current W from the start values in P.zkeep: FP32 support search,
 // FP64 finish.  The FP64 answer is left in P.zkeep.  Returns true on convergence.
 __device__ __noinline__ bool restricted_minimiser(PixelSmem &P, const double2 *A64, const double2 *h, int N,
@@ -501,7 +530,13 @@ __device__ __noinline__ bool restricted_minimiser(PixelSmem &P, const double2 *A
     if (lane < m)
         S.z[lane] = mk<double>(P.zkeep[lane].x, P.zkeep[lane].y);
     __syncwarp();
-    bool ok = fast_path(S, m, lam, lane, kFastRounds64, 1e-12);
+    bool ok = newton_refine(S, m, lam, lane, 6, 1e-12);
+    if (!ok) {
+        if (lane < m)
+            S.z[lane] = mk<double>(P.zkeep[lane].x, P.zkeep[lane].y);
+        __syncwarp();
+        ok = fast_path(S, m, lam, lane, kFastRounds64, 1e-12);
+    }
     if (!ok) {
         // the FP32 support was wrong: solve in FP64 from the start values
         if (lane < m)
