@@ -346,3 +346,74 @@ class RaggedSolver:
 def solve_ragged(items, *, stream: torch.cuda.Stream | None = None, **options) -> list:
     """Solve every (Operator, g, lambda) stack of `items` in one bpdn_solve_ragged call."""
     return RaggedSolver(items, **options).run(stream)
+
+
+class HostSolver:
+    """Solve pixels that live in (pinned) host memory, with the copies overlapped.
+
+    The batch is cut into `chunks` pieces on two streams with two sets of device buffers:
+    while one piece is solved, the next one's g is copied in and the previous one's x
+    is copied out, so the transfers hide behind the solves.  Results go straight into
+    the host tensors passed to run()."""
+
+    def __init__(self, op: Operator, P: int, *, chunks: int = 8, device=None, **options):
+        self.op = op
+        self.P = P
+        self.chunks = max(1, min(chunks, P)) if P else 1
+        self.C = (P + self.chunks - 1) // self.chunks if P else 0
+        self.options = options
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+        opt = _lib.default_options(**options)
+        C = max(self.C, 1)
+        self.g = [torch.empty((C, op.N), dtype=torch.complex64, device=dev) for _ in range(2)]
+        self.res = [SolveResult(
+            x=torch.empty((C, op.L), dtype=torch.complex64, device=dev),
+            status=torch.zeros(C, dtype=torch.int32, device=dev),
+            iters=torch.empty(C, dtype=torch.int32, device=dev),
+            nbt=torch.empty(C, dtype=torch.int32, device=dev),
+            nsupp=torch.empty(C, dtype=torch.int32, device=dev),
+            support=(torch.empty((C, opt.s_max), dtype=torch.int32, device=dev) if opt.refit else None))
+            for _ in range(2)]
+        self.device = dev
+
+    def run(self, g_host: torch.Tensor, lam, x_host: torch.Tensor, status_host: torch.Tensor) -> None:
+        """g_host complex64 [P, N], x_host complex64 [P, L], status_host int32 [P] (pinned host
+        tensors for overlap); lam a float or a [P] tensor.  Returns when every copy is queued;
+        the caller synchronises the current stream before reading x_host."""
+        if g_host.shape != (self.P, self.op.N) or x_host.shape != (self.P, self.op.L):
+            raise ValueError("host tensors do not match the solver's P, N, L")
+        cur = torch.cuda.current_stream(self.device)
+        lam_pp = isinstance(lam, torch.Tensor) and lam.numel() == self.P
+        lam_d = (lam.to(self.device, dtype=torch.float32, non_blocking=True).reshape(-1) if lam_pp
+                 else _lambda_tensor(lam, self.P, self.device)[0])
+        start = torch.cuda.Event()
+        start.record(cur)
+        for i in range(self.chunks):
+            a, b = i * self.C, min(self.P, (i + 1) * self.C)
+            if a >= b:
+                break
+            n = b - a
+            k = i & 1
+            s = self.streams[k]
+            s.wait_event(start)
+            with torch.cuda.stream(s):
+                g = self.g[k][:n]
+                g.copy_(g_host[a:b], non_blocking=True)
+                r = self.res[k]
+                out = SolveResult(x=r.x[:n], status=r.status[:n], iters=r.iters[:n], nbt=r.nbt[:n],
+                                  nsupp=r.nsupp[:n], support=None if r.support is None else r.support[:n])
+                out.status.zero_()
+                solve(self.op, g, lam_d[a:b] if lam_pp else lam_d, out=out, stream=s, **self.options)
+                x_host[a:b].copy_(out.x, non_blocking=True)
+                status_host[a:b].copy_(out.status, non_blocking=True)
+        for s in self.streams:
+            ev = torch.cuda.Event()
+            ev.record(s)
+            cur.wait_event(ev)
+
+
+def solve_host(op: Operator, g_host: torch.Tensor, lam, x_host: torch.Tensor, status_host: torch.Tensor,
+               *, chunks: int = 8, **options) -> None:
+    """One-shot HostSolver: solve the pixels of g_host into x_host / status_host."""
+    HostSolver(op, g_host.shape[0], chunks=chunks, **options).run(g_host, lam, x_host, status_host)
