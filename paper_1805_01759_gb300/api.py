@@ -128,7 +128,7 @@ def solve(op: Operator, g: torch.Tensor, lam, *, out: SolveResult | None = None,
     if out is None:
         out = SolveResult(
             x=torch.empty((P, op.L), dtype=torch.complex64, device=dev),
-            status=torch.zeros(P, dtype=torch.int32, device=dev),
+            status=torch.empty(P, dtype=torch.int32, device=dev),
             iters=torch.empty(P, dtype=torch.int32, device=dev),
             nbt=torch.empty(P, dtype=torch.int32, device=dev),
             nsupp=torch.empty(P, dtype=torch.int32, device=dev),
@@ -303,7 +303,7 @@ class RaggedSolver:
             lam_t, pp = _lambda_tensor(lam, P, dev)
             res = SolveResult(
                 x=torch.empty((P, op.L), dtype=torch.complex64, device=dev),
-                status=torch.zeros(P, dtype=torch.int32, device=dev),
+                status=torch.empty(P, dtype=torch.int32, device=dev),
                 iters=torch.empty(P, dtype=torch.int32, device=dev),
                 nbt=torch.empty(P, dtype=torch.int32, device=dev),
                 nsupp=torch.empty(P, dtype=torch.int32, device=dev),
@@ -369,7 +369,7 @@ class HostSolver:
         self.g = [torch.empty((C, op.N), dtype=torch.complex64, device=dev) for _ in range(2)]
         self.res = [SolveResult(
             x=torch.empty((C, op.L), dtype=torch.complex64, device=dev),
-            status=torch.zeros(C, dtype=torch.int32, device=dev),
+            status=torch.empty(C, dtype=torch.int32, device=dev),
             iters=torch.empty(C, dtype=torch.int32, device=dev),
             nbt=torch.empty(C, dtype=torch.int32, device=dev),
             nsupp=torch.empty(C, dtype=torch.int32, device=dev),
@@ -403,7 +403,6 @@ class HostSolver:
                 r = self.res[k]
                 out = SolveResult(x=r.x[:n], status=r.status[:n], iters=r.iters[:n], nbt=r.nbt[:n],
                                   nsupp=r.nsupp[:n], support=None if r.support is None else r.support[:n])
-                out.status.zero_()
                 solve(self.op, g, lam_d[a:b] if lam_pp else lam_d, out=out, stream=s, **self.options)
                 x_host[a:b].copy_(out.x, non_blocking=True)
                 status_host[a:b].copy_(out.status, non_blocking=True)
