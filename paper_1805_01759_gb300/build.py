@@ -20,6 +20,10 @@ SOURCES = ["api.cu", "operator.cu", "rbpg.cu", "refit.cu", "backward.cu", "ragge
 HEADERS = ["bpdn_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# The refit's FP32 phase only finds the support that its FP64 phase then finishes and
+# checks, so it takes the approximate FP32 divide and square root (these flags change
+# no FP64 operation).
+FILE_FLAGS = {"refit.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
 
 
 def _nvcc() -> str:
@@ -48,7 +52,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + header_deps):
-            jobs.append([nvcc, *ARCH, *FLAGS, "-I", os.path.join(ROOT, "include"), "-c", s, "-o", o])
+            jobs.append([nvcc, *ARCH, *FLAGS, *FILE_FLAGS.get(src, []), "-I", os.path.join(ROOT, "include"),
+                         "-c", s, "-o", o])
 
     def run(cmd):
         if verbose:

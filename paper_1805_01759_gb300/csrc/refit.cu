@@ -24,7 +24,10 @@
 //      the residual that decides convergence and the line search stay in the
 //      phase's precision, so the FP64 answer is still checked in FP64.
 //   The helpers stay out of line: inlined into every call site of both precisions
-//   the kernel's code no longer fits the instruction cache.
+//   the kernel's code no longer fits the instruction cache.  This file is compiled
+//   with approximate FP32 division and square root (and FP32 denormals flushed):
+//   that touches only the FP32 support search and the FP32 screen of the
+//   certificate, whose answers the FP64 phase and the FP64 recheck decide.
 //   3. Coordinates of W that came out zero leave W.  Certificate over the grid:
 //      |2 a_l^H (A_W z - g)| <= lambda for l not in W (FP32 products; grid points
 //      within 1e-4 of the bound recomputed in FP64 against 1e-9).  Violators join W,
@@ -109,6 +112,7 @@ struct PixelSmem {
     double2 *rr;  // [N] A_W z - g (FP64)
     float2 *rf;   // [N] its FP32 copy
     double2 zkeep[KW];  // z between the precisions (FP64)
+    double2 c64[KW];    // c = A_W^H g (FP64) of the current W
     int W[KW];
     int m;
 };
@@ -123,17 +127,10 @@ __host__ __device__ inline size_t pixel_smem_bytes(int N)
 constexpr int WARPS = 1;  // pixels (warps) per block
 
 // G_ij = h(l_i - l_j), c_i = a_{l_i}^H g in precision T
-template <typename T>
-__device__ __noinline__ void load_Gc(Solve<T> &S, const PixelSmem &P, const double2 *__restrict__ A64,
-                        const double2 *__restrict__ h, int N, int L, int lane)
+// c_i = a_{l_i}^H g in FP64 for the current W (lane i), into P.c64
+__device__ __noinline__ void load_c(PixelSmem &P, const double2 *__restrict__ A64, int N, int L, int lane)
 {
-    const int m = P.m;
-    for (int e = lane; e < m * m; e += 32) {
-        const int i = e / m, j = e - (e / m) * m;
-        const double2 v = h[P.W[i] - P.W[j] + L - 1];
-        S.G[i][j] = mk<T>((T)v.x, (T)v.y);
-    }
-    if (lane < m) {
+    if (lane < P.m) {
         const int l = P.W[lane];
         double ax = 0.0, ay = 0.0;
         for (int n = 0; n < N; ++n) {
@@ -141,8 +138,23 @@ __device__ __noinline__ void load_Gc(Solve<T> &S, const PixelSmem &P, const doub
             ax += av.x * gv.x + av.y * gv.y;
             ay += av.x * gv.y - av.y * gv.x;
         }
-        S.c[lane] = mk<T>((T)ax, (T)ay);
+        P.c64[lane] = make_double2(ax, ay);
     }
+    __syncwarp();
+}
+
+template <typename T>
+__device__ __noinline__ void load_Gc(Solve<T> &S, const PixelSmem &P, const double2 *__restrict__ h, int L,
+                                     int lane)
+{
+    const int m = P.m;
+    for (int e = lane; e < m * m; e += 32) {
+        const int i = e / m, j = e - (e / m) * m;
+        const double2 v = h[P.W[i] - P.W[j] + L - 1];
+        S.G[i][j] = mk<T>((T)v.x, (T)v.y);
+    }
+    if (lane < m)
+        S.c[lane] = mk<T>((T)P.c64[lane].x, (T)P.c64[lane].y);
     __syncwarp();
 }
 
@@ -381,6 +393,10 @@ __device__ __noinline__ bool fast_path(Solve<T> &S, int m, T lam, int lane, int 
             continue;
         const bool blk = (lane < m) && passes_zero(S.z[lane], S.dz[lane], T(1));
         if (__any_sync(0xffffffffu, blk)) {
+            // the direction from z, kept for the line search if the step with the
+            // blocked coordinates set to zero does not pay
+            const C2<T> dz0 = (lane < m) ? S.dz[lane] : mk<T>(T(0), T(0));
+            const T slope0 = slope;
             const C2<T> zk = (lane < m) ? S.z[lane] : mk<T>(T(0), T(0));
             if (lane < m)
                 S.zt[lane] = blk ? mk<T>(T(0), T(0)) : zk;
@@ -404,9 +420,10 @@ __device__ __noinline__ bool fast_path(Solve<T> &S, int m, T lam, int lane, int 
                     continue;
                 }
             }
-            slope = newton_dir(S, m, S.z, lam, T(0), lane);
-            if (slope > T(0))
-                continue;
+            if (lane < m)
+                S.dz[lane] = dz0;
+            __syncwarp();
+            slope = slope0;
         }
         T t = T(1);
         for (int hh = 0; hh < 60; ++hh) {
@@ -522,15 +539,18 @@ __device__ __noinline__ bool restricted_minimiser(PixelSmem &P, const double2 *A
     if (m == 0)
         return true;
     double2 start = (lane < m) ? P.zkeep[lane] : make_double2(0.0, 0.0);
+    load_c(P, A64, N, L, lane);
     {
         Solve<float> &S = P.s32;
-        load_Gc(S, P, A64, h, N, L, lane);
+        load_Gc(S, P, h, L, lane);
         if (lane < m)
             S.z[lane] = mk<float>((float)start.x, (float)start.y);
         __syncwarp();
         const float lf = (float)lam;
         if (!fast_path(S, m, lf, lane, kFastRounds32, kTol32)) {
-            continuation(S, m, lf, lane, 1e-2f, 1e-6f, 8);
+            // four damped steps per smoothing level: the FP32 phase only has to land in
+            // the support's basin, and the FP64 phase finishes
+            continuation(S, m, lf, lane, 1e-2f, 1e-6f, 4);
             fast_path(S, m, lf, lane, kFastRounds32, kTol32);
         }
         if (lane < m)
@@ -538,7 +558,7 @@ __device__ __noinline__ bool restricted_minimiser(PixelSmem &P, const double2 *A
         __syncwarp();
     }
     Solve<double> &S = P.s64;
-    load_Gc(S, P, A64, h, N, L, lane);
+    load_Gc(S, P, h, L, lane);
     if (lane < m)
         S.z[lane] = mk<double>(P.zkeep[lane].x, P.zkeep[lane].y);
     __syncwarp();
