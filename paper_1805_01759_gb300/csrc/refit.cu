@@ -97,7 +97,7 @@ struct Solve {
     float J[2 * KW][2 * KW + 1];  // Newton system in FP32, right-hand side in column n2
     float inv[2 * KW];            // reciprocal pivots
     C2<T> z[KW], c[KW], zt[KW], dz[KW], gam[KW];
-    T q[KW], u0[KW], u1[KW];  // per variable: (smoothed) modulus and unit vector
+    T q[KW], u0[KW], u1[KW];  // per variable: lambda / (smoothed) modulus and unit vector
     int T_[KW];
 };
 
@@ -195,7 +195,8 @@ __device__ __noinline__ T optimality(Solve<T> &S, int m, T lam, int lane)
         const C2<T> zi = S.z[lane];
         const T a = sqrt(cabs2(zi));
         if (a > T(0)) {
-            const T ex = gm.x + lam * zi.x / a, ey = gm.y + lam * zi.y / a;
+            const T la = lam / a;
+            const T ex = fma(la, zi.x, gm.x), ey = fma(la, zi.y, gm.y);
             res = sqrt(ex * ex + ey * ey) / lam;
         } else {
             res = sqrt(cabs2(gm)) / lam - T(1);
@@ -285,14 +286,15 @@ __device__ __noinline__ T solve_spd(Solve<T> &S, int n2, int lane, bool &ok)
 // (zero off the variables) and returns the directional derivative (negative for
 // a descent direction), or +1 when the system could not be solved.
 template <typename T>
-__device__ __noinline__ T newton_dir(Solve<T> &S, int m, const C2<T> *z, T lam, T eps, int lane)
+__device__ __noinline__ T newton_dir(Solve<T> &S, int m, const C2<T> *z, T lam, T eps, int lane,
+                                     bool have_gam = false)
 {
     const bool use = (lane < m) && (eps > T(0) || cnz(z[lane]));
     const unsigned bal = __ballot_sync(0xffffffffu, use);
     const int nt = __popc(bal), n2 = 2 * nt;
     if (use)
         S.T_[__popc(bal & ((1u << lane) - 1u))] = lane;
-    if (lane < m) {
+    if (lane < m && !have_gam) {
         const C2<T> gz = gz_row(S, lane, m, z);
         S.gam[lane] = mk<T>(T(2) * (gz.x - S.c[lane].x), T(2) * (gz.y - S.c[lane].y));
     }
@@ -303,7 +305,7 @@ __device__ __noinline__ T newton_dir(Solve<T> &S, int m, const C2<T> *z, T lam, 
         const C2<T> zi = z[S.T_[lane]];
         const T q = sqrt(cabs2(zi) + eps * eps);
         const T iq = T(1) / q;
-        S.q[lane] = q;
+        S.q[lane] = lam * iq;
         S.u0[lane] = zi.x * iq;
         S.u1[lane] = zi.y * iq;
     }
@@ -319,7 +321,7 @@ __device__ __noinline__ T newton_dir(Solve<T> &S, int m, const C2<T> *z, T lam, 
             T v0 = T(2) * (cb == 0 ? g.x : -g.y);
             T v1 = T(2) * (cb == 0 ? g.y : g.x);
             if (a == b) {
-                const T sc = lam / S.q[a];
+                const T sc = S.q[a];
                 v0 += sc * ((cb == 0 ? T(1) : T(0)) - S.u0[a] * wc);
                 v1 += sc * ((cb == 1 ? T(1) : T(0)) - S.u1[a] * wc);
             }
@@ -370,10 +372,14 @@ __device__ __forceinline__ bool passes_zero(C2<T> zi, C2<T> d, T t)
     const T dd = cabs2(d);
     if (!(dd > T(0)) || !cnz(zi))
         return false;
-    T s = -(zi.x * d.x + zi.y * d.y) / dd;
-    s = fmin(fmax(s, T(0)), t);
-    const C2<T> p = mk<T>(zi.x + s * d.x, zi.y + s * d.y);
-    return cabs2(p) < T(0.01) * cabs2(zi);
+    // the closest point to zero along the line is at s* = zd / dd
+    const T zz = cabs2(zi), zd = -(zi.x * d.x + zi.y * d.y);
+    if (!(zd > T(0)))
+        return false;  // |z_i + s dz_i| grows for s > 0
+    if (zd <= t * dd)  // s* in (0, t]: the minimum modulus^2 is zz - zd^2 / dd
+        return T(0.99) * zz * dd < zd * zd;
+    const C2<T> p = mk<T>(zi.x + t * d.x, zi.y + t * d.y);
+    return cabs2(p) < T(0.01) * zz;
 }
 
 // coordinate sweeps alternating with Newton steps (see the file header)
@@ -388,7 +394,7 @@ __device__ __noinline__ bool fast_path(Solve<T> &S, int m, T lam, int lane, int 
         if (res <= tol)
             return true;
         const T F0 = objective(S, m, S.z, lam, T(0), lane);
-        T slope = newton_dir(S, m, S.z, lam, T(0), lane);
+        T slope = newton_dir(S, m, S.z, lam, T(0), lane, true);  // optimality() left gam for z
         if (slope > T(0))
             continue;
         const bool blk = (lane < m) && passes_zero(S.z[lane], S.dz[lane], T(1));
@@ -517,7 +523,7 @@ __device__ __noinline__ bool newton_refine(Solve<T> &S, int m, T lam, int lane, 
         if (!(res < T(0.5) * prev))
             return false;
         prev = res;
-        const T slope = newton_dir(S, m, S.z, lam, T(0), lane);
+        const T slope = newton_dir(S, m, S.z, lam, T(0), lane, true);  // gam from optimality()
         if (slope > T(0))
             return false;
         const bool bad = (lane < m) && passes_zero(S.z[lane], S.dz[lane], T(1));
