@@ -387,9 +387,12 @@ template <typename T>
 __device__ __noinline__ bool fast_path(Solve<T> &S, int m, T lam, int lane, int max_outer, T tol)
 {
     for (int outer = 0; outer < max_outer; ++outer) {
-        // the FP64 phase starts from the FP32 answer, whose support is settled: Newton first
+        // the FP64 phase starts from the FP32 answer, whose support is settled: Newton first.
+        // The FP32 phase opens with three sweeps: they zero most of the small spurious
+        // coordinates of the iterate, which would otherwise block the Newton steps.
         if (sizeof(T) == 4 || outer > 0)
-            cd_sweep(S, m, lam, lane);
+            for (int e = (sizeof(T) == 4 && outer == 0) ? 3 : 1; e > 0; --e)
+                cd_sweep(S, m, lam, lane);
         const T res = optimality(S, m, lam, lane);
         if (res <= tol)
             return true;
@@ -744,11 +747,14 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict_
         const float near = (float)lam * (1.0f - 1e-4f);
         double worst = 0.0;
         int worst_l = -1;
+        uint32_t inW = 0;  // bit j: l = lane + 32 j is in W (L <= 1024)
+        for (int i = 0; i < m; ++i) {
+            const int w = P.W[i];
+            if ((w & 31) == lane)
+                inW |= 1u << (w >> 5);
+        }
         for (int l = lane; l < L; l += 32) {
-            bool inW = false;
-            for (int i = 0; i < m; ++i)
-                inW |= (P.W[i] == l);
-            if (inW)
+            if ((inW >> (l >> 5)) & 1u)
                 continue;
             float ux = 0.f, uy = 0.f;
             for (int n = 0; n < N; ++n) {
