@@ -14,6 +14,9 @@ Functions and what they follow:
   minimise(_batch)        the exact minimiser of Eq. 6 (coordinate descent + Newton + certificate)
   newton_polish           Newton on the smooth optimality system of Eq. 6 on a given support
   kkt, objective          optimality certificate and F of Eq. 6
+  select (module)         SL1MMER steps (2)-(3) of Sec. III-A: scatterer candidates from the
+                          minimiser's runs, BIC model order, least-squares elevations and
+                          amplitudes, and the detection rule of the detection-rate experiment
 """
 from __future__ import annotations
 

@@ -41,6 +41,9 @@ __all__ = [
     "workload_diff",
     "workload_ragged",
     "dft_geometry",
+    "elevation_resolution",
+    "DetectionSet",
+    "workload_detection",
 ]
 
 
@@ -211,3 +214,55 @@ def dft_geometry(N: int, ds: float = 1.0, wavelength_m: float = 0.031,
     xi = np.arange(N, dtype=np.float64) / (N * ds)
     b = xi * wavelength_m * range_m / 2.0
     return StackGeometry(b, wavelength_m, range_m, 0.0, (N - 1) * ds, N)
+
+
+def elevation_resolution(geom: StackGeometry) -> float:
+    """Inherent elevation resolution 1 / (xi_max - xi_min) = wavelength*range/(2*Delta_b).
+
+    Eq. 16 prints wavelength*range/Delta_b; the paper's own figures (a 269.5 m aperture
+    giving 40.5 m at X band) and the two-way phase xi = 2b/(wavelength*range) of Eq. 5
+    give half of that, which is what the detection experiment measures kappa against."""
+    b = geom.baselines_m
+    return geom.wavelength_m * geom.range_m / (2.0 * float(b.max() - b.min()))
+
+
+@dataclasses.dataclass
+class DetectionSet:
+    """Two-scatterer pixels of the detection-rate experiment (Sec. IV-A, last figure)."""
+
+    geom: StackGeometry
+    g: np.ndarray        # complex64 [P, N]
+    lam: np.ndarray      # float32 [P], per pixel (it follows the pixel's noise level)
+    kappa: np.ndarray    # float64 [P] normalised separation (Eq. 17, against elevation_resolution)
+    snr_db: np.ndarray   # float64 [P] per scatterer
+    s_true: np.ndarray   # float64 [P, 2] ascending
+    seed: int = 0
+
+
+def workload_detection(kappas=tuple(np.round(np.arange(0.1, 1.51, 0.1), 2)), snrs_db=(2.0, 7.0),
+                       n_per: int = 5000, seed: int = 6, N: int = 29, L: int = 201,
+                       aperture_m: float = 269.5, half_height_m: float = 100.0) -> DetectionSet:
+    """The detection-rate Monte Carlo: N = 29 acquisitions over a 269.5 m aperture (the
+    paper's Las Vegas stack), two unit scatterers with equal phase (Delta phi = 0, the
+    worst case) at c -/+ kappa*rho_s/2 with c ~ U[-0.5, 0.5] m (off the 1 m grid), per
+    scatterer SNR in snrs_db, n_per realisations per (kappa, SNR).  Grid: L points on
+    [-half_height, half_height].  lambda = 2*sigma*sqrt(N ln L) with the pixel's own
+    noise sigma (the level of the other workloads, taken at the simulated SNR)."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(0.0, 1.0, N)
+    b = (u - u.min()) / (u.max() - u.min()) * aperture_m - aperture_m / 2.0
+    geom = StackGeometry(np.asarray(b, np.float64), 0.031, 7.0e5, -half_height_m, half_height_m, L)
+    rho = elevation_resolution(geom)
+    kap = np.repeat(np.tile(np.asarray(kappas, np.float64), len(snrs_db)), n_per)
+    snr = np.repeat(np.asarray(snrs_db, np.float64), len(kappas) * n_per)
+    P = kap.size
+    c = rng.uniform(-0.5, 0.5, P)
+    s_true = np.stack([c - 0.5 * kap * rho, c + 0.5 * kap * rho], axis=1)
+    ph = rng.uniform(0.0, 2.0 * np.pi, P)
+    sigma2 = 10.0 ** (-snr / 10.0)
+    noise = (rng.standard_normal((P, N)) + 1j * rng.standard_normal((P, N))) * np.sqrt(sigma2 / 2.0)[:, None]
+    a = np.exp(1j * ph)[:, None]
+    g = noise + a * (_phasors(geom, s_true[:, 0]) + _phasors(geom, s_true[:, 1]))
+    lam = (2.0 * np.sqrt(sigma2) * math.sqrt(N * math.log(L))).astype(np.float32)
+    return DetectionSet(geom, np.ascontiguousarray(g.astype(np.complex64)), lam, kap, snr, s_true, seed)
+
