@@ -578,6 +578,104 @@ def run_ragged(args) -> None:
                       "pixels": P_total, "precision": args.precision, "runs": out}), flush=True)
 
 
+def _detected(khat, s_hat, s_true):
+    """Detection rule of the detection-rate experiment: K_hat = 2 and each sorted estimate
+    within half the true separation of its sorted true elevation (vectorised)."""
+    st = np.sort(s_true, axis=1)
+    se = np.sort(np.where(np.isnan(s_hat[:, :2]), np.inf, s_hat[:, :2]), axis=1)
+    half = 0.5 * (st[:, 1] - st[:, 0])
+    return (khat == 2) & np.all(np.abs(se - st) < half[:, None], axis=1)
+
+
+def run_detection(args) -> None:
+    """The detection-rate Monte Carlo (N = 29, two equal-phase scatterers, SNR 2 and 7 dB,
+    kappa 0.1..1.5, args.det_per realisations each) through the whole SL1MMER chain on the
+    GPU: bpdn_solve (BF16 + FP64 refit) and bpdn_select.  Prints one JSON line with the
+    chain's pixels/s, the kernel split, P_D per (SNR, kappa), and the oracle chain timed on
+    a bounded sample of the same pixels with its model orders compared."""
+    import torch
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_1805_01759_gb300 import api, synth
+    d = synth.workload_detection(n_per=args.det_per)
+    P = d.g.shape[0]
+    op = api.Operator.from_geometry(d.geom)
+    g = torch.from_numpy(d.g).cuda()
+    lam = torch.from_numpy(d.lam).cuda()
+    kw = dict(precision=1, tol=args.tol_bf16)
+
+    def step():
+        res = api.solve(op, g, lam, **kw)
+        return res, api.select(op, g, res)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_chain, t_sel = [], []
+    for _ in range(args.steps):
+        ev[0].record()
+        res = api.solve(op, g, lam, **kw)
+        ev[1].record()
+        sel = api.select(op, g, res)
+        ev[2].record()
+        torch.cuda.synchronize()
+        t_chain.append(ev[0].elapsed_time(ev[2]))
+        t_sel.append(ev[1].elapsed_time(ev[2]))
+    ms = statistics.mean(t_chain)
+    kh = sel.khat.cpu().numpy()
+    sh = sel.s_hat.cpu().numpy()
+    cert = (res.status.cpu().numpy() & 64) != 0
+    det = _detected(kh, sh, d.s_true)
+    pd = {}
+    for snr in sorted(set(d.snr_db.tolist())):
+        row = {}
+        for k in sorted(set(d.kappa.tolist())):
+            m = (d.snr_db == snr) & (d.kappa == k)
+            row[f"{k:.1f}"] = round(float(det[m].mean()), 4)
+        pd[f"{snr:g} dB"] = row
+    line = {
+        "metric": "SL1MMER chain pixels/s (BF16 solve + FP64 refit + model selection)",
+        "value": P / (ms / 1e3), "unit": "pixels/s", "higher_is_better": True, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "pixels": P, "data": "synthetic",
+        "workload": f"detection-rate Monte Carlo: N=29 over 269.5 m, L=201 on [-100,100] m, two unit "
+                    f"scatterers with equal phase at c -/+ kappa*rho/2, SNR 2 and 7 dB, kappa 0.1..1.5, "
+                    f"{args.det_per} realisations each, seed 6",
+        "kernels_ms": {"solve_and_refit": ms - statistics.mean(t_sel), "select": statistics.mean(t_sel)},
+        "certified_frac": float(cert.mean()),
+        "khat_hist": np.bincount(kh + 1, minlength=6).tolist(),
+        "detection_rate": pd,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = _detection_cpu_leg(d, kh, sh, cert, args.cpu_det_sample)
+    print(json.dumps(line), flush=True)
+
+
+def _detection_cpu_leg(d, kh, sh, cert, n):
+    """The oracle chain (FP64 minimiser + model selection) on a seeded sample of the
+    detection pixels: its rate, and its model orders against the GPU's."""
+    import oracle
+    from oracle import select as osel
+    rng = np.random.default_rng(61)
+    idx = np.sort(rng.choice(d.g.shape[0], size=min(n, d.g.shape[0]), replace=False))
+    A = oracle.operator(d.geom)
+    xi = oracle.xi(d.geom.baselines_m, d.geom.wavelength_m, d.geom.range_m)
+    s = oracle.grid(d.geom.s_min_m, d.geom.s_max_m, d.geom.L)
+    t0 = time.perf_counter()
+    ref = oracle.minimise_batch(A, d.g[idx], d.lam[idx].astype(np.float64))
+    okh, osh, _ = osel.select_batch(d.g[idx], ref["x"], xi, s)
+    t = time.perf_counter() - t0
+    both = cert[idx] & (ref["flags"] == 0)
+    agree = int(np.sum(okh[both] == kh[idx][both]))
+    elev = np.abs(np.nan_to_num(osh[both] - sh[idx][both], nan=0.0)).max() if both.any() else 0.0
+    return {"value": len(idx) / t, "unit": "pixels/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{len(idx)} seeded pixels of the same set: FP64 coordinate-descent minimiser + "
+                      f"model selection, {t:.1f} s",
+            "khat_agree": agree, "khat_compared": int(both.sum()), "max_elevation_diff_m": float(elev)}
+
+
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -597,8 +695,11 @@ def main(argv=None) -> None:
                     help="stopping tolerance of the BF16 path: BF16 operands carry 2^-9 relative error, "
                          "so smaller steps are not resolved")
     ap.add_argument("--e2e-chunks", type=int, default=8, help="chunks of the end-to-end leg")
-    ap.add_argument("--workload", choices=["patch", "ragged"], default="patch",
-                    help="patch: the headline line; ragged: the 64-stack ragged batch (separate line)")
+    ap.add_argument("--workload", choices=["patch", "ragged", "detection"], default="patch",
+                    help="patch: the headline line; ragged: the 64-stack ragged batch; detection: the "
+                         "detection-rate Monte Carlo through solve + model selection (separate lines)")
+    ap.add_argument("--det-per", type=int, default=5000, help="realisations per (SNR, kappa)")
+    ap.add_argument("--cpu-det-sample", type=int, default=256, help="oracle pixels of the detection leg")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -606,6 +707,8 @@ def main(argv=None) -> None:
         run_reference(args)
     elif args.workload == "ragged":
         run_ragged(args)
+    elif args.workload == "detection":
+        run_detection(args)
     else:
         run_ours(args)
 

@@ -59,6 +59,7 @@ enum bpdn_status {
 #define BPDN_MAX_N 64
 #define BPDN_MAX_L 1024
 #define BPDN_MAX_SMAX 16
+#define BPDN_MAX_KSEL 4  /* scatterers per pixel bpdn_select considers */
 
 typedef struct {
     int32_t max_iter;     /* N_K of Algorithm 1 (default 500)                                  */
@@ -245,6 +246,41 @@ int bpdn_backward(bpdn_op_t op, int64_t P, const float *d_lambda, int32_t lambda
                   const int32_t *d_status, int32_t s_max,
                   const void *d_dL_dx, void *d_dL_dg, float *d_dL_dlambda, void *d_workspace,
                   size_t workspace_bytes, void *cuda_stream);
+
+/*
+ * SL1MMER model selection and parameter estimation (Sec. III-A, steps (2) and (3))
+ * on the output of a solve with refit: the number of scatterers in each pixel, their
+ * elevations and amplitudes.  The paper defines these steps only by reference; the
+ * library's reading:
+ *   candidates   maximal runs of adjacent grid points of supp(x); elevation = the
+ *                modulus-weighted centroid of the run, energy = sum |x_l|^2; ranked by
+ *                energy (ties: lower grid index first), the first kmax kept
+ *   model order  K_hat = the first minimiser over K = 0..K_c of
+ *                C(K) = 2 N ln RSS_K + K * penalty, where RSS_K is the residual of the
+ *                least-squares fit of g by the steering vectors (Eq. 5) of the first K
+ *                candidates at their off-grid elevations (a BIC; penalty <= 0 selects
+ *                3 ln(2N))
+ *   estimates    the K_hat elevations, ascending, and the amplitudes of that fit
+ * All arithmetic in FP64, one warp per pixel.
+ *
+ * d_g         device c64 [P, N]  the pixels' measurements (as given to bpdn_solve)
+ * d_x         device c64 [P, L]  the solution (bpdn_solve / bpdn_refit output)
+ * d_support   device int32 [P, s_max]  its ascending support (-1 padded), as written by
+ *             bpdn_solve / bpdn_refit with the same s_max
+ * d_nsupp     device int32 [P]  number of nonzeros (entries beyond s_max are ignored,
+ *             as are support entries outside [0, L) or where x is 0)
+ * d_status    device int32 [P] (may be NULL): pixels with BPDN_PX_NONFINITE or
+ *             BPDN_PX_SUPPORT_OVERFLOW get K_hat = -1
+ * s_max       1..BPDN_MAX_SMAX;  kmax  1..BPDN_MAX_KSEL
+ * d_khat      device int32 [P] out: K_hat (or -1)
+ * d_s_hat     device float64 [P, kmax] out: elevations in metres, ascending; NaN past K_hat
+ * d_gamma_hat device c128 [P, kmax] out: amplitudes matching d_s_hat; 0 past K_hat
+ * Asynchronous on cuda_stream; allocates nothing.  Returns BPDN_EINVAL (NULL pointer,
+ * bad s_max / kmax, P < 0) or BPDN_EALIGN before launching anything.
+ */
+int bpdn_select(bpdn_op_t op, const void *d_g, int64_t P, const void *d_x, const int32_t *d_support,
+                const int32_t *d_nsupp, const int32_t *d_status, int32_t s_max, int32_t kmax,
+                double penalty, int32_t *d_khat, double *d_s_hat, void *d_gamma_hat, void *cuda_stream);
 
 /*
  * bpdn_solve without a workspace, for callers that cannot allocate device memory

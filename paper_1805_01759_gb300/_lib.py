@@ -25,13 +25,14 @@ PX_CERTIFIED = 64
 MAX_N = 64
 MAX_L = 1024
 MAX_SMAX = 16
+MAX_KSEL = 4
 
 EXPORTED = [
     "bpdn_default_options", "bpdn_op_workspace_bytes", "bpdn_make_operator",
     "bpdn_destroy_operator", "bpdn_op_info", "bpdn_op_lipschitz", "bpdn_op_export",
     "bpdn_solve_workspace_bytes", "bpdn_solve", "bpdn_refit", "bpdn_last_error", "bpdn_version",
     "bpdn_solve_noalloc", "bpdn_backward_workspace_bytes", "bpdn_backward",
-    "bpdn_solve_ragged_workspace_bytes", "bpdn_solve_ragged",
+    "bpdn_solve_ragged_workspace_bytes", "bpdn_solve_ragged", "bpdn_select",
 ]
 
 
@@ -131,6 +132,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.bpdn_solve_ragged_workspace_bytes.restype = sz
     lib.bpdn_solve_ragged.argtypes = [ctypes.POINTER(Stack), i32, optp, vp, sz, vp]
     lib.bpdn_solve_ragged.restype = ctypes.c_int
+    lib.bpdn_select.argtypes = [op_t, vp, i64, vp, vp, vp, vp, i32, i32, dbl, vp, vp, vp, vp]
+    lib.bpdn_select.restype = ctypes.c_int
     lib.bpdn_last_error.argtypes = []
     lib.bpdn_last_error.restype = ctypes.c_char_p
     lib.bpdn_version.argtypes = []

@@ -12,6 +12,7 @@ from __future__ import annotations
 import ctypes
 import math
 import dataclasses
+from typing import NamedTuple
 
 import numpy as np
 import torch
@@ -195,6 +196,36 @@ def backward(op: Operator, x: torch.Tensor, support: torch.Tensor, nsupp: torch.
                                  dLdlam.data_ptr(), ws.data_ptr() if ws_bytes else None, ws_bytes,
                                  _stream(stream)))
     return dLdg, dLdlam
+
+
+class Selection(NamedTuple):
+    """Output of select(): khat [P] int32 (-1: not selected), s_hat [P, kmax] float64
+    (NaN past khat), gamma_hat [P, kmax] complex128 (0 past khat)."""
+    khat: torch.Tensor
+    s_hat: torch.Tensor
+    gamma_hat: torch.Tensor
+
+
+def select(op: Operator, g: torch.Tensor, res: "SolveResult", *, kmax: int = _lib.MAX_KSEL,
+           penalty: float = 0.0, stream: torch.cuda.Stream | None = None) -> Selection:
+    """SL1MMER model selection and parameter estimation (bpdn_select) on a solve's result
+    (which must come from a solve with the refit, so that its support is written)."""
+    lib = _lib.load()
+    g = _check_g(op, g)
+    P = g.shape[0]
+    if res.support is None:
+        raise ValueError("select needs the support of a solve with refit")
+    if res.x.shape != (P, op.L) or res.support.shape[0] != P:
+        raise ValueError("the solve result does not match g")
+    dev = g.device
+    out = Selection(torch.empty(P, dtype=torch.int32, device=dev),
+                    torch.empty((P, kmax), dtype=torch.float64, device=dev),
+                    torch.empty((P, kmax), dtype=torch.complex128, device=dev))
+    _lib.check(lib.bpdn_select(op.handle, g.data_ptr(), P, res.x.data_ptr(), res.support.data_ptr(),
+                               res.nsupp.data_ptr(), _ptr(res.status), res.support.shape[1], kmax,
+                               float(penalty), out.khat.data_ptr(), out.s_hat.data_ptr(),
+                               out.gamma_hat.data_ptr(), _stream(stream)))
+    return out
 
 
 class BPDNFunction(torch.autograd.Function):

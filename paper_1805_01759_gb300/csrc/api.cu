@@ -502,4 +502,44 @@ int bpdn_backward(bpdn_op_t h, int64_t P, const float *d_lambda, int32_t lambda_
     return check_cuda(launch_backward(*op, a, s), "backward kernel");
 }
 
+int bpdn_select(bpdn_op_t h, const void *d_g, int64_t P, const void *d_x, const int32_t *d_support,
+                const int32_t *d_nsupp, const int32_t *d_status, int32_t s_max, int32_t kmax,
+                double penalty, int32_t *d_khat, double *d_s_hat, void *d_gamma_hat, void *cuda_stream)
+{
+    OpHandle *op = nullptr;
+    int rc = check_op(h, &op);
+    if (rc)
+        return rc;
+    if (P < 0)
+        return set_error(BPDN_EINVAL, "P must be >= 0");
+    if (s_max < 1 || s_max > BPDN_MAX_SMAX)
+        return set_error(BPDN_EINVAL, "s_max must lie in 1..%d", BPDN_MAX_SMAX);
+    if (kmax < 1 || kmax > BPDN_MAX_KSEL)
+        return set_error(BPDN_EINVAL, "kmax must lie in 1..%d", BPDN_MAX_KSEL);
+    if (!(penalty == penalty))
+        return set_error(BPDN_EINVAL, "penalty must not be NaN");
+    if (P == 0)
+        return BPDN_OK;
+    if (!d_g || !d_x || !d_support || !d_nsupp || !d_khat || !d_s_hat || !d_gamma_hat)
+        return set_error(BPDN_EINVAL, "g, x, support, nsupp, khat, s_hat and gamma_hat must be non-NULL");
+    if (!aligned(d_g, 8) || !aligned(d_x, 8) || !aligned(d_s_hat, 8) || !aligned(d_gamma_hat, 16))
+        return set_error(BPDN_EALIGN, "g and x must be 8-byte aligned, s_hat 8-byte, gamma_hat 16-byte");
+    if (!aligned(d_support, 4) || !aligned(d_nsupp, 4) || !aligned(d_khat, 4) || (d_status && !aligned(d_status, 4)))
+        return set_error(BPDN_EALIGN, "int32 arrays must be 4-byte aligned");
+    SelectLaunch a;
+    a.P = P;
+    a.g = (const float2 *)d_g;
+    a.x = (const float2 *)d_x;
+    a.support = d_support;
+    a.nsupp = d_nsupp;
+    a.status = d_status;
+    a.s_max = s_max;
+    a.kmax = kmax;
+    a.penalty = penalty;
+    a.khat = d_khat;
+    a.s_hat = d_s_hat;
+    a.gamma_hat = (double2 *)d_gamma_hat;
+    return check_cuda(launch_select(*op, a, (cudaStream_t)cuda_stream), "select kernel");
+}
+
 }  // extern "C"

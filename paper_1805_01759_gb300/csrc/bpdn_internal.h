@@ -120,4 +120,17 @@ struct BackwardLaunch {
 };
 cudaError_t launch_backward(const OpHandle &op, const BackwardLaunch &a, cudaStream_t s);
 
+struct SelectLaunch {
+    int64_t P;
+    const float2 *g, *x;
+    const int32_t *support, *nsupp;
+    const int32_t *status;  // may be NULL
+    int s_max, kmax;
+    double penalty;         // <= 0: 3 ln(2N)
+    int32_t *khat;
+    double *s_hat;
+    double2 *gamma_hat;
+};
+cudaError_t launch_select(const OpHandle &op, const SelectLaunch &a, cudaStream_t s);
+
 }  // namespace bpdn

@@ -91,3 +91,13 @@ def test_ragged_host_checks():
     assert lib.bpdn_solve_ragged(None, 2, ctypes.byref(opt), None, 0, None) == _lib.BPDN_EINVAL
     arr = (_lib.Stack * 2)()
     assert lib.bpdn_solve_ragged(arr, 2, ctypes.byref(opt), None, 0, None) == _lib.BPDN_ESIZE
+
+
+def test_select_host_checks():
+    """bpdn_select rejects a missing operator on the host, before touching a GPU."""
+    from paper_1805_01759_gb300 import _lib
+    lib = _lib.load()
+    assert lib.bpdn_select(None, None, 0, None, None, None, None, 16, 4, 0.0, None, None, None, None) == \
+        _lib.BPDN_EINVAL
+    assert _lib.MAX_KSEL == 4
+
