@@ -11,6 +11,8 @@ tensor-core contraction, each followed by the FP64 refit -- and the BF16 path is
 the headline value; pixels count only when certified and the oracle sample agrees.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --workload ragged       # the 64-stack ragged batch (its own line)
+    python bench.py --workload detection    # detection-rate Monte Carlo, solve + model selection
 
 Prints one JSON line (rank 0).  Under torchrun each rank solves its own 2^20 pixels
 of the same stack (weak scaling, no collective on the data path; a barrier and a
