@@ -82,3 +82,127 @@ def test_full_patch(patch, precision, tol):
         assert err <= 1e-4, (p, err)
         checked += 1
     assert checked >= 40, checked
+
+
+def test_full_ragged_batch():
+    """The 64-stack ragged batch as bench.py runs it (one RaggedSolver per option set,
+    captured and replayed as a CUDA graph): every output's properties, and two seeded
+    pixels of every stack against the oracle."""
+    from paper_1805_01759_gb300 import api, _lib
+    _lib.load()
+    sts = synth.workload_ragged(n_stacks=64, seed=3)
+    items = [(api.Operator.from_geometry(st.geom), torch.from_numpy(st.g).cuda(), st.lam) for st in sts]
+
+    def opts(op):
+        ok = 2 * op.N <= 64 and op.L <= 512
+        return dict(precision=1 if ok else 0, tol=1e-3 if ok else 1e-6)
+
+    results = {}
+    for key in sorted({tuple(sorted(opts(op).items())) for op, _, _ in items}):
+        sub = [i for i, it in enumerate(items) if tuple(sorted(opts(it[0]).items())) == key]
+        sv = api.RaggedSolver([items[i] for i in sub], **dict(key))
+        sv.capture()
+        sv.replay()
+        torch.cuda.synchronize()
+        for i, r in zip(sub, sv.results):
+            results[i] = r
+    rng = np.random.default_rng(33)
+    checked = total = cert_n = 0
+    for i, st in enumerate(sts):
+        r = results[i]
+        P_i = st.g.shape[0]
+        total += P_i
+        assert bool(torch.isfinite(torch.view_as_real(r.x)).all())
+        assert int((r.status & ~DEFINED_BITS).abs().sum()) == 0
+        nnz = (r.x != 0).sum(dim=1).to(torch.int32)
+        assert bool(torch.equal((r.status & 32) != 0, nnz == 0))
+        cert = (r.status & 64) != 0
+        cert_n += int(cert.sum())
+        assert bool(torch.equal(r.nsupp[cert], nnz[cert]))
+        idx = np.sort(rng.choice(P_i, size=2, replace=False))
+        A = oracle.operator(st.geom)
+        ref = oracle.minimise_batch(A, st.g[idx], st.lam)
+        xs = r.x[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.complex128)
+        ss = r.status.cpu().numpy()[idx]
+        for j in range(2):
+            xr = ref["x"][j]
+            if not (ss[j] & 64) or ref["flags"][j] != 0 or ref["margin"][j] <= 1e-6:
+                continue
+            if ref["min_abs_on"][j] <= 1e-6 * max(np.abs(xr).max(), 1e-300):
+                continue
+            assert np.array_equal(xs[j] != 0, xr != 0), (i, idx[j])
+            nr = np.linalg.norm(xr)
+            err = np.linalg.norm(xs[j] - xr) / nr if nr > 0 else np.linalg.norm(xs[j])
+            assert err <= 1e-4, (i, idx[j], err)
+            checked += 1
+    assert cert_n >= 0.97 * total, (cert_n, total)
+    assert checked >= 90, checked
+
+
+def test_full_differentiation_workload():
+    """The differentiation workload at full size (N = 25, L = 400, 2^18 pixels, FP32 forward
+    with the refit): per-pixel dL/dlambda and a directional derivative in g of
+    L_p = sum_l |x_l - gamma_l|^2 on 64 pixels against FP64 central differences of the
+    oracle's exact minimiser, then 50 steps of gradient descent on log lambda over all
+    pixels from 1.5 times the default weight (the error must fall below its starting value).
+
+    The implicit gradient describes the error's smooth part on fixed supports.  Below the
+    default weight, supports change as lambda moves and those jumps dominate the batch
+    error: from 0.5 times the default weight the descent raised the error (0.6604 ->
+    0.6702 over 50 steps), so the tuning starts where supports are small and strict."""
+    from paper_1805_01759_gb300 import api, _lib
+    _lib.load()
+    st = synth.workload_diff(P=1 << 18, seed=5)
+    op = api.Operator.from_geometry(st.geom)
+    P_d = st.g.shape[0]
+    g = torch.from_numpy(st.g).cuda().requires_grad_(True)
+    lam = torch.full((P_d,), st.lam, dtype=torch.float32, device="cuda", requires_grad=True)
+    gt = torch.from_numpy(st.gamma_true).cuda()
+    x, status = api.BPDNFunction.apply(g, lam, op, None)
+    loss = (x - gt).abs().pow(2).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    assert float(((status & 64) != 0).float().mean()) >= 0.97
+
+    rng = np.random.default_rng(77)
+    idx = np.sort(rng.choice(P_d, size=64, replace=False))
+    A = oracle.operator(st.geom)
+    G = st.g[idx].astype(np.complex128)
+    gam = st.gamma_true[idx].astype(np.complex128)
+    delta = rng.standard_normal(G.shape) + 1j * rng.standard_normal(G.shape)
+    delta /= np.linalg.norm(delta, axis=1, keepdims=True)
+    lam0 = float(st.lam)
+    hl = 1e-6 * lam0
+    hg = 1e-6 * np.linalg.norm(G, axis=1).mean()
+
+    def L(X):
+        return np.sum(np.abs(X - gam) ** 2, axis=1)
+
+    base = oracle.minimise_batch(A, G, lam0)
+    lp = L(oracle.minimise_batch(A, G, lam0 + hl)["x"])
+    lm = L(oracle.minimise_batch(A, G, lam0 - hl)["x"])
+    gp = L(oracle.minimise_batch(A, G + hg * delta, lam0)["x"])
+    gm = L(oracle.minimise_batch(A, G - hg * delta, lam0)["x"])
+    fd_l = (lp - lm) / (2 * hl)
+    fd_g = (gp - gm) / (2 * hg)
+    dl = lam.grad.cpu().numpy()[idx].astype(np.float64)
+    dg = g.grad.cpu().numpy()[idx].astype(np.complex128)
+    dg_dir = np.sum(dg.real * delta.real + dg.imag * delta.imag, axis=1)
+    st_s = status.cpu().numpy()[idx]
+    xs = x.detach().cpu().numpy()[idx]
+    checked = 0
+    for j in range(64):
+        if not (st_s[j] & 64) or base["flags"][j] != 0 or base["margin"][j] < 1e-3:
+            continue
+        if not np.array_equal(xs[j] != 0, base["x"][j] != 0):
+            continue
+        scale_l = max(abs(fd_l[j]), 1e-3 * abs(L(base["x"][j:j + 1])[0]) / lam0, 1e-12)
+        scale_g = max(abs(fd_g[j]), 1e-12)
+        assert abs(dl[j] - fd_l[j]) <= 2e-3 * scale_l, (j, dl[j], fd_l[j])
+        assert abs(dg_dir[j] - fd_g[j]) <= 2e-3 * scale_g + 1e-6 * np.linalg.norm(dg[j]), (j, dg_dir[j], fd_g[j])
+        checked += 1
+    assert checked >= 48, checked
+
+    lam_end, hist = api.tune_lambda(op, g.detach(), gt, 1.5 * lam0, steps=50, lr=0.1)
+    errs = [h[1] for h in hist]
+    assert min(errs[1:]) < errs[0] and errs[-1] < errs[0], (hist[:3], hist[-3:])
