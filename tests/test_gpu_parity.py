@@ -218,18 +218,22 @@ def test_bf16_rejects_unsupported_sizes(api):
     assert ei.value.code == -3
 
 
-@pytest.mark.parametrize("N,L,half_width", [(60, 600, 250.0), (40, 300, 120.0), (12, 1000, 300.0)])
-def test_solve_refit_operator_sizes(api, N, L, half_width):
-    """FP32 path beyond the sizes of the benchmark stack: N > 32 (two rows per lane),
-    L > 512, and an operator too large for shared memory (N=60, L=600: A is read from
-    global memory).  Same bar as the small workload against the exact minimiser."""
+@pytest.mark.parametrize("N,L,half_width,precision", [(60, 600, 250.0, 0), (40, 300, 120.0, 0), (12, 1000, 300.0, 0),
+                                                       (64, 1024, 300.0, 0), (32, 512, 200.0, 1)])
+def test_solve_refit_operator_sizes(api, N, L, half_width, precision):
+    """Beyond the sizes of the benchmark stack: N > 32 (two rows per lane), L > 512, an
+    operator too large for shared memory (N=60, L=600: A is read from global memory), and
+    the library's maximum sizes (FP32: N = 64, L = 1024, one 1024-thread group per CTA;
+    BF16: 2N = 64 contraction terms, L = 512).  Same bar as the small workload against the
+    exact minimiser."""
     rng = np.random.default_rng(1000 + N + L)
     geom = synth.make_geometry(rng, N, L, 250.0, half_width)
     st = synth.make_stack(geom, 48, rng, lam=synth.default_lambda(N, L), snr_db_range=(5.0, 20.0))
     A = oracle.operator(st.geom)
     ref = oracle.minimise_batch(A, st.g, st.lam)
     op = api.Operator.from_geometry(st.geom)
-    res = api.solve(op, torch.from_numpy(st.g).cuda(), st.lam)
+    res = api.solve(op, torch.from_numpy(st.g).cuda(), st.lam, precision=precision,
+                    tol=1e-3 if precision else 1e-6)
     x = res.x.cpu().numpy().astype(np.complex128)
     status = res.status.cpu().numpy()
     cert = (status & 64) != 0
