@@ -40,7 +40,7 @@ struct SelSmem {
     int l[BPDN_MAX_SMAX];
     double cen[BPDN_MAX_SMAX], en[BPDN_MAX_SMAX];
     int first[BPDN_MAX_SMAX], rank[BPDN_MAX_SMAX];
-    int nv, nc, kc, khat;
+    int kc;                     // candidates kept (<= kmax)
 };
 
 __device__ __forceinline__ double warp_sum_d(double v)
@@ -187,8 +187,6 @@ __global__ void __launch_bounds__(WARPS * 32) k_select(const double *__restrict_
             }
             S.rank[j + 1] = c;
         }
-        S.nv = nv;
-        S.nc = nc;
         S.kc = min(nc, kmax);
     }
     __syncwarp();
