@@ -11,6 +11,9 @@ Functions and what they follow:
   lipschitz               the step constant of Eq. 14's remark, read as 2*lambda_max(A^H A)
   soft                    Eq. 10 read for complex values (complex soft threshold)
   rbpg / rbpg_batch       Algorithm 1 with Eqs. 11-15 (the readings are listed in the C file)
+  rbpg_block(_batch)      Algorithm 1 with randomized blocks of one pixel's grid (Eqs. 13-14);
+  block_probabilities     Eq. 14's P_j from the block Lipschitz constants;
+  splitmix64              the counter-based generator of the block draws
   minimise(_batch)        the exact minimiser of Eq. 6 (coordinate descent + Newton + certificate)
   newton_polish           Newton on the smooth optimality system of Eq. 6 on a given support
   kkt, objective          optimality certificate and F of Eq. 6
@@ -95,6 +98,13 @@ def _configure(lib):
     lib.orc_adjoint.restype = c_int
     lib.orc_adjoint_batch.argtypes = [dp, c_int, c_int, dp, c_i64, dp, dp, dp, dp, ip]
     lib.orc_num_threads.restype = c_int
+    u64, u64p = ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)
+    lib.orc_splitmix64.argtypes = [u64, c_int, u64p]
+    lib.orc_rbpg_block.argtypes = [dp, c_int, c_int, dp, c_double, c_double, c_double, c_double,
+                                   c_int, c_int, c_int, dp, u64, c_i64, dp, ip, ip]
+    lib.orc_rbpg_block.restype = c_int
+    lib.orc_rbpg_block_batch.argtypes = [dp, c_int, c_int, dp, c_i64, dp, c_double, c_double,
+                                         c_double, c_int, c_int, c_int, dp, u64, dp, ip, ip]
     return lib
 
 
@@ -221,6 +231,71 @@ def rbpg_batch(A, G, lam, *, alpha0: float | None = None, c_alpha: float = 0.5,
     status = np.zeros(P, np.int32)
     _load().orc_rbpg_batch(_dp(A), N, L, _dp(G), P, _dp(lam_v), a0, float(c_alpha), float(tol),
                            int(max_iter), int(max_bt), _dp(x), _ip(iters), _ip(status))
+    return {"x": x, "iters": iters, "status": status}
+
+
+# ------------------------------------------------- randomized blocks (Eqs. 13-14)
+
+def splitmix64(state: int, n: int) -> np.ndarray:
+    """n outputs of SplitMix64 from the given state (the generator the block draws use)."""
+    out = np.zeros(n, np.uint64)
+    _load().orc_splitmix64(ctypes.c_uint64(state & 0xFFFFFFFFFFFFFFFF), int(n),
+                           out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    return out
+
+
+def block_bounds(L: int, J: int):
+    """[lo_j, hi_j) of the J contiguous blocks of an L-point grid."""
+    lo = np.array([(j * L) // J for j in range(J)])
+    hi = np.array([((j + 1) * L) // J for j in range(J)])
+    return lo, hi
+
+
+def block_probabilities(A, J: int):
+    """Eq. 14: P_j = L_j / sum L_j with L_j = 2 lambda_max(A_j^H A_j), the Lipschitz constant of
+    the block gradient (lambda_max taken from the N x N matrix A_j A_j^H).  Returns (P, cum)
+    with the last cumulative entry exactly 1."""
+    A = _c128(A)
+    lo, hi = block_bounds(A.shape[1], J)
+    Lj = np.array([2.0 * np.linalg.eigvalsh(A[:, a:b] @ A[:, a:b].conj().T)[-1] for a, b in zip(lo, hi)])
+    P = Lj / Lj.sum()
+    cum = np.cumsum(P)
+    cum[-1] = 1.0
+    return P, cum
+
+
+def rbpg_block(A, g, lam: float, J: int, seed: int, pixel: int = 0, *, alpha0: float | None = None,
+               c_alpha: float = 0.5, tol: float = 1e-6, max_iter: int = 500, max_bt: int = 64):
+    """Algorithm 1 with J randomized blocks of the grid (orc_rbpg_block).  Returns
+    (x, block iterations, status, drawn blocks)."""
+    A, g = _c128(A), _c128(g)
+    N, L = A.shape
+    _, cum = block_probabilities(A, J)
+    a0 = default_alpha0(A) if alpha0 is None else float(alpha0)
+    x = np.zeros(L, np.complex128)
+    it = np.zeros(1, np.int32)
+    trace = np.full(max_iter * J, -1, np.int32)
+    st = _load().orc_rbpg_block(_dp(A), N, L, _dp(g), float(lam), a0, float(c_alpha), float(tol),
+                                int(max_iter), int(max_bt), int(J), _dp(np.ascontiguousarray(cum)),
+                                ctypes.c_uint64(seed), int(pixel), _dp(x), _ip(it), _ip(trace))
+    return x, int(it[0]), int(st), trace[:int(it[0])]
+
+
+def rbpg_block_batch(A, G, lam, J: int, seed: int, *, alpha0: float | None = None, c_alpha: float = 0.5,
+                     tol: float = 1e-6, max_iter: int = 500, max_bt: int = 64):
+    """rbpg_block for every row of G; row p draws from the stream of pixel p."""
+    A, G = _c128(A), _c128(G)
+    N, L = A.shape
+    P = G.shape[0]
+    _, cum = block_probabilities(A, J)
+    lam_v = np.ascontiguousarray(np.broadcast_to(np.asarray(lam, np.float64), (P,)))
+    a0 = default_alpha0(A) if alpha0 is None else float(alpha0)
+    x = np.empty((P, L), np.complex128)
+    iters = np.zeros(P, np.int32)
+    status = np.zeros(P, np.int32)
+    _load().orc_rbpg_block_batch(_dp(A), N, L, _dp(G), P, _dp(lam_v), a0, float(c_alpha), float(tol),
+                                 int(max_iter), int(max_bt), int(J), _dp(np.ascontiguousarray(cum)),
+                                 ctypes.c_uint64(seed), _dp(x), _ip(iters), _ip(status))
     return {"x": x, "iters": iters, "status": status}
 
 

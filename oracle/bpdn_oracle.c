@@ -20,6 +20,9 @@
  *   orc_grid / orc_operator / orc_gram_toeplitz / orc_aah   : the operator (Eq. 5)
  *   orc_soft                                                 : complex soft threshold (Eq. 10)
  *   orc_rbpg                                                 : Algorithm 1 (RBPG with backtracking)
+ *   orc_rbpg_block                                           : Algorithm 1 with randomized blocks of
+ *                                                              one pixel's grid (Eqs. 13-14), drawn
+ *                                                              by SplitMix64 (orc_splitmix64)
  *   orc_cd                                                   : cyclic coordinate descent (exact minimiser)
  *   orc_newton_polish                                        : Newton on the smooth optimality
  *                                                              system restricted to a support
@@ -329,6 +332,162 @@ done:
         *iters_out = k;
     free(x); free(xp); free(y); free(grad); free(v); free(xb);
     free(Ay); free(r); free(Axb); free(tmp);
+    return status;
+}
+
+/* ------------------------------------------- randomized blocks (Eqs. 13-14) */
+
+/*
+ * SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+ * generators", 2014): the state advances by the golden-ratio increment and each
+ * output is the state passed through the generator's mixing function.  n outputs
+ * from the given state.
+ */
+static uint64_t orc_sm64_next(uint64_t *state)
+{
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+void orc_splitmix64(uint64_t state, int n, uint64_t *out)
+{
+    for (int i = 0; i < n; ++i)
+        out[i] = orc_sm64_next(&state);
+}
+
+/* Block i_k of Eq. 14 for one uniform draw: the first j with u < cum[j]. */
+static int orc_draw_block(uint64_t *state, int J, const double *cum)
+{
+    double u = (double)(orc_sm64_next(state) >> 11) * 0x1.0p-53;
+    for (int j = 0; j < J - 1; ++j)
+        if (u < cum[j])
+            return j;
+    return J - 1;
+}
+
+/*
+ * Algorithm 1 with the elevation grid of one pixel split into J contiguous blocks
+ * (block j = [floor(jL/J), floor((j+1)L/J))), the reading of Eqs. 13-14 in which the
+ * blocks are coordinates of one pixel.  Per iteration k:
+ *   i = block drawn with P_i = L_i / sum_j L_j (cum = cumulative P, last entry 1),
+ *       from SplitMix64 started at state seed + pixel * 2^40;
+ *   y = x, and on block i  y_i = x_i + beta_k (x_i - x_i^{k-1}),  beta_k = (k-2)/(k+1)
+ *       (x^{k-1} is the previous iterate, as Algorithm 1 writes it);
+ *   xbar = y, and on block i  xbar_i = S_{alpha_i lambda}(y_i - alpha_i grad_i f(y)),
+ *       grad_i f(y) = 2 A_i^H (A y - g), with Eq. 15 on block i:
+ *       ||A (xbar - y)||^2 <= ||xbar - y||^2 / (2 alpha_i), else alpha_i *= c_alpha;
+ *       each block carries its own alpha_i (Eq. 13's alpha_{i_k}), all starting at alpha0;
+ *   accept xbar when F(xbar) <= F(x^k) (x^{k+1} = xbar), else x^{k+1} = x^k;
+ *   a step is small when ||xbar - x^k|| <= tol ||xbar||; stop once every block has taken a
+ *       small step since the last step that was not small (each block's proximal-gradient
+ *       step is then small: a block that stays zero takes a zero step, so counting small
+ *       steps without regard to the block would stop on the empty blocks of a sparse
+ *       iterate), or after max_iter * J iterations (NOT_CONVERGED).
+ * trace (may be NULL, max_iter*J entries) receives the drawn blocks.
+ */
+int orc_rbpg_block(const cplx *A, int N, int L, const cplx *g, double lam, double alpha0,
+                   double c_alpha, double tol, int max_iter, int max_bt, int J, const double *cum,
+                   uint64_t seed, int64_t pixel, cplx *x_out, int *iters_out, int *trace)
+{
+    int status = 0;
+    size_t Lz = (size_t)L, Nz = (size_t)N;
+    cplx *x = (cplx *)calloc(Lz, sizeof(cplx));
+    cplx *xp = (cplx *)calloc(Lz, sizeof(cplx));
+    cplx *y = (cplx *)calloc(Lz, sizeof(cplx));
+    cplx *grad = (cplx *)calloc(Lz, sizeof(cplx));
+    cplx *xb = (cplx *)calloc(Lz, sizeof(cplx));
+    cplx *Ay = (cplx *)calloc(Nz, sizeof(cplx));
+    cplx *r = (cplx *)calloc(Nz, sizeof(cplx));
+    cplx *Axb = (cplx *)calloc(Nz, sizeof(cplx));
+    cplx *tmp = (cplx *)calloc(Nz, sizeof(cplx));
+    double *alpha = (double *)malloc(sizeof(double) * (size_t)J);
+    uint64_t state = seed + ((uint64_t)pixel << 40);
+    int kmax = max_iter * J, k = 0, stopped = 0;
+    unsigned done_mask = 0, all_mask = (J >= 32) ? 0xFFFFFFFFu : ((1u << J) - 1u);
+
+    if (!all_finite(g, N)) {
+        status = ORC_NONFINITE;
+        goto done;
+    }
+    for (int j = 0; j < J; ++j)
+        alpha[j] = alpha0;
+    double Fx = norm2sq(g, N); /* F(0) */
+    for (k = 1; k <= kmax; ++k) {
+        const int i = orc_draw_block(&state, J, cum);
+        const int lo = (int)(((int64_t)i * L) / J), hi = (int)(((int64_t)(i + 1) * L) / J);
+        if (trace)
+            trace[k - 1] = i;
+        double beta = (double)(k - 2) / (double)(k + 1);
+        for (int l = 0; l < L; ++l)
+            y[l] = (l >= lo && l < hi) ? x[l] + beta * (x[l] - xp[l]) : x[l];
+        matvec(A, N, L, y, Ay);
+        for (int n = 0; n < N; ++n)
+            r[n] = Ay[n] - g[n];
+        matvec_h(A, N, L, r, grad);
+        int nbt = 0;
+        for (;;) {
+            double tau = alpha[i] * lam;
+            for (int l = 0; l < L; ++l)
+                xb[l] = (l >= lo && l < hi) ? orc_soft(y[l] - alpha[i] * 2.0 * grad[l], tau) : y[l];
+            matvec(A, N, L, xb, Axb);
+            for (int n = 0; n < N; ++n)
+                tmp[n] = Axb[n] - Ay[n];
+            double lhs = norm2sq(tmp, N), dd = 0.0;
+            for (int l = 0; l < L; ++l) {
+                cplx d = xb[l] - y[l];
+                dd += creal(d) * creal(d) + cimag(d) * cimag(d);
+            }
+            if (lhs <= dd / (2.0 * alpha[i]))
+                break;
+            if (nbt >= max_bt) {
+                status |= ORC_BT_LIMIT;
+                break;
+            }
+            alpha[i] *= c_alpha;
+            ++nbt;
+        }
+        for (int n = 0; n < N; ++n)
+            tmp[n] = Axb[n] - g[n];
+        double Fb = norm2sq(tmp, N) + lam * l1(xb, L);
+        int accepted = (Fb <= Fx);
+        double dnorm = 0.0, xnorm = 0.0;
+        for (int l = 0; l < L; ++l) {
+            cplx xk = x[l];
+            cplx d = xb[l] - xk;
+            dnorm += creal(d) * creal(d) + cimag(d) * cimag(d);
+            xnorm += creal(xb[l]) * creal(xb[l]) + cimag(xb[l]) * cimag(xb[l]);
+            xp[l] = xk;
+            if (accepted)
+                x[l] = xb[l];
+        }
+        if (accepted)
+            Fx = Fb;
+        done_mask = (sqrt(dnorm) <= tol * fmax(sqrt(xnorm), 1e-30)) ? (done_mask | (1u << i)) : 0u;
+        if (done_mask == all_mask) {
+            stopped = 1;
+            break;
+        }
+    }
+    if (!stopped) {
+        status |= ORC_NOT_CONVERGED;
+        k = kmax;
+    }
+    {
+        int nz = 0;
+        for (int l = 0; l < L; ++l)
+            nz |= (x[l] != 0.0);
+        if (!nz)
+            status |= ORC_ZERO_SOLUTION;
+    }
+done:
+    for (int l = 0; l < L; ++l)
+        x_out[l] = x[l];
+    if (iters_out)
+        *iters_out = k;
+    free(x); free(xp); free(y); free(grad); free(xb);
+    free(Ay); free(r); free(Axb); free(tmp); free(alpha);
     return status;
 }
 
@@ -757,6 +916,16 @@ void orc_rbpg_batch(const cplx *A, int N, int L, const cplx *g, int64_t P, const
     for (int64_t p = 0; p < P; ++p)
         status[p] = orc_rbpg(A, N, L, g + (size_t)p * N, lam[p], alpha0, c_alpha, tol, max_iter,
                              max_bt, x + (size_t)p * L, iters + p, NULL, NULL, NULL, NULL, NULL);
+}
+
+void orc_rbpg_block_batch(const cplx *A, int N, int L, const cplx *g, int64_t P, const double *lam,
+                          double alpha0, double c_alpha, double tol, int max_iter, int max_bt, int J,
+                          const double *cum, uint64_t seed, cplx *x, int *iters, int *status)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t p = 0; p < P; ++p)
+        status[p] = orc_rbpg_block(A, N, L, g + (size_t)p * N, lam[p], alpha0, c_alpha, tol, max_iter,
+                                   max_bt, J, cum, seed, p, x + (size_t)p * L, iters + p, NULL);
 }
 
 void orc_min_batch(const cplx *A, int N, int L, const cplx *g, int64_t P, const double *lam,

@@ -414,6 +414,96 @@ def test_adjoint_zero_solution():
     assert rc == 0 and np.all(dg == 0) and dl == 0.0
 
 
+# ------------------------------------------------- randomized blocks (Eqs. 13-14)
+
+def test_splitmix64_published_outputs():
+    """The block draws' generator against its published first outputs (tests/golden)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "splitmix64_seed0.txt")
+    want = [int(l, 16) for l in open(path) if l.strip() and not l.startswith("#")]
+    assert [int(v) for v in oracle.splitmix64(0, len(want))] == want
+
+
+def test_blocks_one_block_is_algorithm_1():
+    """With J = 1 the block reading is Algorithm 1: identical iterates and counts."""
+    st = synth.workload_small(P=16, seed=1)
+    A = oracle.operator(st.geom)
+    r1 = oracle.rbpg_batch(A, st.g, st.lam, tol=1e-6)
+    rb = oracle.rbpg_block_batch(A, st.g, st.lam, 1, 5, tol=1e-6)
+    assert np.array_equal(r1["x"], rb["x"]) and np.array_equal(r1["iters"], rb["iters"])
+    assert np.array_equal(r1["status"], rb["status"])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_blocks_dft_closed_form(seed):
+    """Orthogonal columns (DFT geometry): every block has L_j = 2N, so the draw is uniform,
+    and one block step with alpha = 1/(2N) lands on that block's part of the closed form
+    x* = S_{lambda/2}(A^H g)/N, so the iterate equals x* once every block was drawn.  Eq. 15
+    holds with equality there (||A d||^2 = N ||d||^2), so rounding can halve alpha on a
+    block, which then converges geometrically: compared at 1e-10."""
+    N = 16
+    A = oracle.operator(synth.dft_geometry(N))
+    Pj, cum = oracle.block_probabilities(A, 4)
+    np.testing.assert_allclose(Pj, 0.25, rtol=0, atol=1e-12)
+    rng = np.random.default_rng(seed)
+    g = rng.normal(size=N) + 1j * rng.normal(size=N)
+    lam = float(rng.uniform(0.5, 2.0)) * float(np.abs(A.conj().T @ g).max()) / 2
+    xs = oracle.soft(A.conj().T @ g, lam / 2) / N
+    x, it, st, trace = oracle.rbpg_block(A, g, lam, 4, 100 + seed, 0, tol=1e-15, max_iter=400)
+    assert set(trace.tolist()) == {0, 1, 2, 3}
+    assert np.abs(x - xs).max() <= 1e-10 * max(1.0, np.abs(xs).max())
+
+
+def test_blocks_draw_frequencies():
+    """Eq. 14: the drawn blocks follow P_j = L_j / sum L_j (chi-square over 12,800 draws of
+    64 pixels' streams).  On a uniform grid equal blocks have equal constants (shifting a
+    block is a unitary diagonal similarity of A_j A_j^H), so the grid here has L = 13 points
+    in blocks of 3, 3, 3 and 4, whose constants differ."""
+    rng = np.random.default_rng(8)
+    geom = synth.make_geometry(rng, 12, 13, 250.0, 100.0)
+    A = oracle.operator(geom)
+    Pj, _ = oracle.block_probabilities(A, 4)
+    assert Pj.max() / Pj.min() > 1.05
+    g = np.zeros(12, np.complex128)
+    counts = np.zeros(4)
+    for p in range(64):
+        _, it, _, trace = oracle.rbpg_block(A, g + 1.0, 1e6, 4, 21, p, tol=-1.0, max_iter=50)
+        counts += np.bincount(trace, minlength=4)
+    n = counts.sum()
+    assert n == 64 * 50 * 4
+    chi2 = float(np.sum((counts - n * Pj) ** 2 / (n * Pj)))
+    assert chi2 < 16.3, (chi2, counts / n, Pj)  # 3 degrees of freedom, p = 0.001
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_blocks_converge_to_minimiser(seed):
+    """Tiny problems (N = 4, L = 8; J = 2, and J = 3, which does not divide L): the block
+    iteration reaches the exact minimiser of Eq. 6 (coordinate-descent oracle) to 1e-6."""
+    rng = np.random.default_rng(seed)
+    geom = synth.make_geometry(rng, 4, 8, 250.0, 100.0)
+    A = oracle.operator(geom)
+    g = rng.normal(size=4) + 1j * rng.normal(size=4)
+    lam = 0.5 * float(np.abs(A.conj().T @ g).max())
+    ref = oracle.minimise(A, g, lam)
+    for J in (2, 3):
+        x, it, st, _ = oracle.rbpg_block(A, g, lam, J, 9, seed, tol=1e-12, max_iter=30000)
+        assert np.linalg.norm(x - ref["x"]) <= 1e-6 * max(np.linalg.norm(ref["x"]), 1e-30), J
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_blocks_phase_invariance(seed):
+    """g -> e^{j phi} g rotates every iterate (the draws do not depend on g); 200 block
+    iterations without the stopping test."""
+    st = synth.workload_small(P=4, seed=1)
+    A = oracle.operator(st.geom)
+    phi = 0.3 + seed
+    g = st.g[seed % 4].astype(np.complex128)
+    a = oracle.rbpg_block(A, g, st.lam, 4, 3, 7, tol=-1.0, max_iter=50)
+    b = oracle.rbpg_block(A, np.exp(1j * phi) * g, st.lam, 4, 3, 7, tol=-1.0, max_iter=50)
+    assert a[1] == b[1] == 200 and np.array_equal(a[3], b[3])
+    np.testing.assert_allclose(b[0], np.exp(1j * phi) * a[0], rtol=0, atol=1e-9 * max(np.abs(a[0]).max(), 1e-30))
+
+
 # ------------------------------------------------------------------ stored answers
 
 def _read_golden():

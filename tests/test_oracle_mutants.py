@@ -32,6 +32,13 @@ MUTANTS = {
                                 "Gij += A[(size_t)n * L + S[i]] * conj(A[(size_t)n * L + S[j]]);"),
     "adjoint_dg_factor": ("dLdg[n] = 2.0 * acc;", "dLdg[n] = acc;"),
     "adjoint_lambda_sign": ("*dLdlam = -dl;", "*dLdlam = dl;"),
+    "splitmix_shift": ("z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;", "z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ULL;"),
+    "block_extrapolate_everywhere": ("y[l] = (l >= lo && l < hi) ? x[l] + beta * (x[l] - xp[l]) : x[l];",
+                                     "y[l] = x[l] + beta * (x[l] - xp[l]);"),
+    "block_stop_first_small": ("? (done_mask | (1u << i)) : 0u;", "? all_mask : 0u;"),
+    "block_alpha_wrong_block": ("alpha[i] *= c_alpha;", "alpha[0] *= c_alpha;"),
+    "block_bounds_gap": ("const int lo = (int)(((int64_t)i * L) / J)", "const int lo = (int)(((int64_t)i * L + J - 1) / J)"),
+    "block_draw_uniform": ("if (u < cum[j])", "if (u < (double)(j + 1) / J)"),
 }
 
 # the stored-answer test compares the oracle with its own earlier output: a regression
