@@ -20,8 +20,10 @@ MUTANTS = {
     "soft_half": ("return v * (1.0 - tau / a);", "return v * (1.0 - 0.5 * tau / a);"),
     "grad_factor": ("grad[l] *= 2.0;", "grad[l] *= 1.0;"),
     "adjoint_no_conj": ("acc += conj(A[(size_t)n * L + l]) * r[n];", "acc += A[(size_t)n * L + l] * r[n];"),
-    "momentum_index": ("double beta = (double)(k - 2) / (double)(k + 1);", "double beta = (double)(k - 1) / (double)(k + 2);"),
-    "accept_reversed": ("int accepted = (Fb <= Fx);", "int accepted = (Fb >= Fx);"),
+    "momentum_index": ("k <= max_iter; ++k) {\n        double beta = (double)(k - 2) / (double)(k + 1);",
+                       "k <= max_iter; ++k) {\n        double beta = (double)(k - 1) / (double)(k + 2);"),
+    "accept_reversed": ("margin = fmin(margin, am);\n\n        int accepted = (Fb <= Fx);",
+                        "margin = fmin(margin, am);\n\n        int accepted = (Fb >= Fx);"),
     "linesearch_factor": ("double rhs = dd / (2.0 * alpha);", "double rhs = dd / alpha;"),
     "cd_threshold": ("cplx nw = orc_soft(vv, 0.5 * lam) / Gll;", "cplx nw = orc_soft(vv, lam) / Gll;"),
     "newton_residual_sign": ("phi[i] = 2.0 * acc + lam * z[i] / cabs(z[i]);", "phi[i] = 2.0 * acc - lam * z[i] / cabs(z[i]);"),
@@ -39,6 +41,9 @@ MUTANTS = {
     "block_alpha_wrong_block": ("alpha[i] *= c_alpha;", "alpha[0] *= c_alpha;"),
     "block_bounds_gap": ("const int lo = (int)(((int64_t)i * L) / J)", "const int lo = (int)(((int64_t)i * L + J - 1) / J)"),
     "block_draw_uniform": ("if (u < cum[j])", "if (u < (double)(j + 1) / J)"),
+    "block_momentum_index": ("trace[k - 1] = i;\n        double beta = (double)(k - 2) / (double)(k + 1);",
+                             "trace[k - 1] = i;\n        double beta = (double)(k - 1) / (double)(k + 2);"),
+    "block_accept_reversed": ("l1(xb, L);\n        int accepted = (Fb <= Fx);", "l1(xb, L);\n        int accepted = (Fb >= Fx);"),
 }
 
 # the stored-answer test compares the oracle with its own earlier output: a regression
