@@ -72,7 +72,12 @@ typedef struct {
     int32_t max_bt;       /* step cuts allowed per iteration before BT_LIMIT (default 64)        */
     int32_t tile_pixels;  /* pixels in flight per SM: 8 or 16 (0 = library choice, 16 when it fits) */
     int32_t refit_rounds; /* working-set rounds of the refit (default 4)                         */
-    int32_t reserved[6];
+    int32_t blocks;       /* 0 or 1: Algorithm 1 on each pixel's whole grid (default); 2..8:     */
+                          /* the grid split into that many contiguous blocks, one drawn per    */
+                          /* iteration with probability L_j / sum L_j (Eqs. 13-14); FP32 only */
+    uint32_t seed;        /* stream of the block draws: pixel p uses SplitMix64 from state     */
+                          /* seed + p * 2^40 (default 0)                                       */
+    int32_t reserved[4];
 } bpdn_options;
 
 /* Fill *opt with the defaults above. */

@@ -49,7 +49,9 @@ class Options(ctypes.Structure):
         ("max_bt", ctypes.c_int32),
         ("tile_pixels", ctypes.c_int32),
         ("refit_rounds", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("blocks", ctypes.c_int32),
+        ("seed", ctypes.c_uint32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 

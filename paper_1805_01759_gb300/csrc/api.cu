@@ -112,6 +112,12 @@ static int check_options(const bpdn_options *o)
         return set_error(BPDN_EINVAL, "refit_rounds must lie in [0, 64]");
     if (o->tile_pixels != 0 && o->tile_pixels != 8 && o->tile_pixels != 16)
         return set_error(BPDN_EINVAL, "tile_pixels must be 0 (library choice), 8 or 16");
+    if (o->blocks < 0 || o->blocks > 8)
+        return set_error(BPDN_EINVAL, "blocks must lie in [0, 8]");
+    if (o->blocks >= 2 && o->precision != 0)
+        return set_error(BPDN_EINVAL, "randomized blocks (blocks >= 2) run in FP32 only (precision 0)");
+    if (o->blocks >= 2 && o->max_iter > (1 << 27))
+        return set_error(BPDN_EINVAL, "max_iter must be <= 2^27 with randomized blocks");
     return BPDN_OK;
 }
 
@@ -165,7 +171,9 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
         return set_error(BPDN_EALIGN, "solve workspace must be 256-byte aligned");
     if (opt->refit && d_support && !aligned(d_support, 4))
         return set_error(BPDN_EALIGN, "support must be 4-byte aligned");
-    const char *why = rbpg_check(*op, opt->precision, opt->tile_pixels / 8, max_smem_optin(op->device));
+    const char *why = (opt->blocks >= 2) ? rbpg_block_check(*op, opt->blocks, max_smem_optin(op->device))
+                                         : rbpg_check(*op, opt->precision, opt->tile_pixels / 8,
+                                                      max_smem_optin(op->device));
     if (why[0] != '\0')
         return set_error(BPDN_ESIZE, "N = %d, L = %d, precision %d: %s", op->N, op->L, opt->precision, why);
     SolveLaunch &a = sp->a;
@@ -188,6 +196,12 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     a.precision = opt->precision;
     a.groups = opt->tile_pixels / 8;
     a.err = (int *)((char *)d_workspace + 8);
+    // randomized blocks: draw table at bytes 16.., A_j A_j^H after the first 256 bytes
+    a.blocks = opt->blocks >= 2 ? opt->blocks : 0;
+    a.seed = opt->seed;
+    a.blip = (double *)((char *)d_workspace + 16);
+    a.cum = (double *)((char *)d_workspace + 16 + 8 * 8);
+    a.bscratch = a.blocks ? (double2 *)((char *)d_workspace + 256) : nullptr;
     sp->refit = opt->refit != 0;
     RefitLaunch &r = sp->r;
     r.g = a.g;
@@ -218,7 +232,15 @@ int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     rc = check_cuda(cudaMemsetAsync(sp.a.counter, 0, 16, s), "reset work counter");
     if (rc)
         return rc;
-    rc = check_cuda(launch_rbpg(*sp.op, sp.a, num_sms(sp.op->device), s), "iteration kernel");
+    if (sp.a.blocks) {
+        rc = check_cuda(launch_block_probs(*sp.op, sp.a.blocks, sp.a.bscratch, sp.a.blip, sp.a.cum, s),
+                        "block draw table");
+        if (rc)
+            return rc;
+        rc = check_cuda(launch_rbpg_block(*sp.op, sp.a, s), "block iteration kernel");
+    } else {
+        rc = check_cuda(launch_rbpg(*sp.op, sp.a, num_sms(sp.op->device), s), "iteration kernel");
+    }
     if (rc || !sp.refit)
         return rc;
     return check_cuda(launch_refit(*sp.op, sp.r, s), "refit kernel");
@@ -397,8 +419,9 @@ size_t bpdn_solve_workspace_bytes(bpdn_op_t h, int64_t P, const bpdn_options *op
 {
     (void)h;
     (void)P;
-    (void)opt;
-    return 256;  // a 64-bit work counter and an error word, padded
+    // a 64-bit work counter, an error word and the block draw table, padded; with
+    // randomized blocks, A_j A_j^H of every block after that
+    return 256 + block_scratch_bytes(opt ? opt->blocks : 0);
 }
 
 

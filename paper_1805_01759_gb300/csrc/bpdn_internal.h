@@ -76,6 +76,12 @@ struct SolveLaunch {
     int precision;
     int groups;  // slot groups of 8 pixels per CTA: 0 = the kernel's choice, 1 or 2
     int *err;    // set to 1 if a bounded wait ran out (may be NULL)
+    // randomized blocks of the grid (blocks >= 2; Eqs. 13-14)
+    int blocks;
+    unsigned seed;
+    double2 *bscratch;  // [blocks][N][N]: A_j A_j^H
+    double *blip;       // [blocks]: lambda_max(A_j A_j^H)
+    double *cum;        // [blocks]: cumulative draw probabilities, last = 1
 };
 // iteration kernel (a.precision 0: FP32 CUDA cores, 1: BF16 tensor cores)
 cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
@@ -84,6 +90,13 @@ cudaError_t launch_rbpg_batch(const OpHandle *const *ops, const SolveLaunch *as,
                               cudaStream_t s);
 // "" when the operator's sizes suit the kernel at this precision, else the reason
 const char *rbpg_check(const OpHandle &op, int precision, int groups, int max_smem);
+// Algorithm 1 with randomized blocks (a.blocks >= 2), FP32, one warp per pixel
+cudaError_t launch_rbpg_block(const OpHandle &op, const SolveLaunch &a, cudaStream_t s);
+const char *rbpg_block_check(const OpHandle &op, int blocks, int max_smem);
+// Eq. 14's draw table: lambda_max(A_j A_j^H) per block and cumulative probabilities
+cudaError_t launch_block_probs(const OpHandle &op, int J, double2 *M, double *lmax, double *cum, cudaStream_t s);
+// scratch bytes of a solve with `blocks` (0 when blocks < 2)
+size_t block_scratch_bytes(int blocks);
 
 struct RefitLaunch {
     const float2 *g;

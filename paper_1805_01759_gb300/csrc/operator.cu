@@ -145,6 +145,39 @@ __global__ void k_lambda_max(const double2 *M, int N, double *out)
     }
 }
 
+// (A_j A_j^H)_{nm} over the grid columns [lo, hi) of one block
+__global__ void k_aah_cols(const double2 *A64, int N, int L, int lo, int hi, double2 *M)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N)
+        return;
+    int n = idx / N, m = idx % N;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = lo; l < hi; ++l) {
+        double2 a = A64[(size_t)n * L + l], b = A64[(size_t)m * L + l];
+        acc.x += a.x * b.x + a.y * b.y;
+        acc.y += a.y * b.x - a.x * b.y;
+    }
+    M[idx] = acc;
+}
+
+// cumulative draw probabilities P_j = lmax_j / sum lmax (Eq. 14; the factor 2 of
+// L_j = 2 lambda_max cancels), the last entry exactly 1
+__global__ void k_block_cum(const double *lmax, int J, double *cum)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0)
+        return;
+    double tot = 0.0;
+    for (int j = 0; j < J; ++j)
+        tot += lmax[j];
+    double run = 0.0;
+    for (int j = 0; j < J; ++j) {
+        run += lmax[j];
+        cum[j] = (tot > 0.0) ? run / tot : (double)(j + 1) / J;
+    }
+    cum[J - 1] = 1.0;
+}
+
 __global__ void k_export_c64(const double2 *src, size_t n, float2 *dst)
 {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -169,6 +202,30 @@ cudaError_t launch_make_operator(const OpHandle &op, const double *d_b, cudaStre
     if (e != cudaSuccess)
         return e;
     k_lambda_max<<<1, 1024, smem, s>>>(op.aah, N, op.scal);
+    return cudaGetLastError();
+}
+
+size_t block_scratch_bytes(int blocks)
+{
+    if (blocks < 2)
+        return 0;
+    return (size_t)round_up(blocks * BPDN_MAX_N * BPDN_MAX_N * (int)sizeof(double2), 256);
+}
+
+cudaError_t launch_block_probs(const OpHandle &op, int J, double2 *M, double *lmax, double *cum, cudaStream_t s)
+{
+    const int N = op.N, L = op.L;
+    size_t smem = 2 * (size_t)N * N * sizeof(double2);
+    cudaError_t e = cudaFuncSetAttribute(k_lambda_max, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    for (int j = 0; j < J; ++j) {
+        const int lo = (int)(((long long)j * L) / J), hi = (int)(((long long)(j + 1) * L) / J);
+        double2 *Mj = M + (size_t)j * N * N;
+        k_aah_cols<<<(N * N + 127) / 128, 128, 0, s>>>(op.A64, N, L, lo, hi, Mj);
+        k_lambda_max<<<1, 1024, smem, s>>>(Mj, N, lmax + j);
+    }
+    k_block_cum<<<1, 32, 0, s>>>(lmax, J, cum);
     return cudaGetLastError();
 }
 

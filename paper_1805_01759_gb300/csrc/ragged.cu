@@ -96,6 +96,8 @@ int bpdn_solve_ragged(const bpdn_stack *stacks, int32_t n_stacks, const bpdn_opt
         return rc;
     if (!opt)
         return set_error(BPDN_EINVAL, "options pointer is NULL");
+    if (opt->blocks >= 2)
+        return set_error(BPDN_EINVAL, "randomized blocks (blocks >= 2) are not available in bpdn_solve_ragged");
     // each stack's options: the call's, with the stack's tile_pixels when it names one
     std::vector<bpdn_options> sopt(n_stacks, *opt);
     for (int i = 0; i < n_stacks; ++i)
