@@ -13,6 +13,7 @@ the headline value; pixels count only when certified and the oracle sample agree
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --workload ragged       # the 64-stack ragged batch (its own line)
     python bench.py --workload detection    # detection-rate Monte Carlo, solve + model selection
+    python bench.py --workload blocks       # randomized-block reading of Eqs. 13-14 vs the default
 
 Prints one JSON line (rank 0).  Under torchrun each rank solves its own 2^20 pixels
 of the same stack (weak scaling, no collective on the data path; a barrier and a
@@ -678,6 +679,67 @@ def _detection_cpu_leg(d, kh, sh, cert, n):
             "khat_agree": agree, "khat_compared": int(both.sum()), "max_elevation_diff_m": float(elev)}
 
 
+def run_blocks(args) -> None:
+    """The randomized-block reading of Eqs. 13-14 (options.blocks = J) against the default
+    reading (a block is a whole pixel) on the same pixels of the patch: both FP32 with the
+    FP64 refit, certified pixels/s, iterations, and a seeded oracle sample of each."""
+    import torch
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_1805_01759_gb300 import api, synth
+    st = synth.workload_patch(P=args.block_pixels, seed=2)
+    op = api.Operator.from_geometry(st.geom)
+    g = torch.from_numpy(st.g).cuda()
+    P = st.g.shape[0]
+    out = {}
+    for name, kw in (("default_reading", dict(tol=args.tol_fp32)),
+                     (f"blocks_{args.blocks}", dict(tol=args.tol_fp32, blocks=args.blocks, seed=1))):
+        for _ in range(args.warmup):
+            api.solve(op, g, st.lam, **kw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            res = api.solve(op, g, st.lam, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        cert = (res.status & 64) != 0
+        it = res.iters.double()
+        out[name] = {"ms_per_step": ms, "certified_frac": float(cert.float().mean()),
+                     "certified_pixels_per_s": float(cert.sum()) / (ms / 1e3),
+                     "mean_iterations": float(it.mean()),
+                     "frac_max_iter": float(((res.status & 1) != 0).float().mean())}
+        if not args.no_cpu_baseline:
+            out[name]["oracle_sample"] = _block_sample(st, res, 64)
+    print(json.dumps({"metric": "certified pixels/s, randomized-block reading vs default reading (FP32 + refit)",
+                      "value": out[f"blocks_{args.blocks}"]["certified_pixels_per_s"], "unit": "pixels/s",
+                      "workload": f"patch N=25, L=400, {P} pixels, seed 2; blocks={args.blocks} (iterations "
+                                  f"counted in block steps, max 500*blocks)", "runs": out}), flush=True)
+
+
+def _block_sample(st, res, n):
+    """Certified pixels of a seeded sample against the exact minimiser (oracle)."""
+    import oracle
+    rng = np.random.default_rng(62)
+    idx = np.sort(rng.choice(st.g.shape[0], size=n, replace=False))
+    A = oracle.operator(st.geom)
+    ref = oracle.minimise_batch(A, st.g[idx], st.lam)
+    import torch
+    x = res.x[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.complex128)
+    cert = (res.status.cpu().numpy()[idx] & 64) != 0
+    ok = 0
+    for j in range(n):
+        if not cert[j] or ref["flags"][j] != 0:
+            continue
+        nr = np.linalg.norm(ref["x"][j])
+        err = np.linalg.norm(x[j] - ref["x"][j]) / nr if nr > 0 else np.linalg.norm(x[j])
+        ok += int(err <= 1e-4 and np.array_equal(x[j] != 0, ref["x"][j] != 0))
+    return {"n": n, "certified": int(cert.sum()), "certified_and_ok": ok}
+
+
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -697,10 +759,12 @@ def main(argv=None) -> None:
                     help="stopping tolerance of the BF16 path: BF16 operands carry 2^-9 relative error, "
                          "so smaller steps are not resolved")
     ap.add_argument("--e2e-chunks", type=int, default=8, help="chunks of the end-to-end leg")
-    ap.add_argument("--workload", choices=["patch", "ragged", "detection"], default="patch",
+    ap.add_argument("--workload", choices=["patch", "ragged", "detection", "blocks"], default="patch",
                     help="patch: the headline line; ragged: the 64-stack ragged batch; detection: the "
                          "detection-rate Monte Carlo through solve + model selection (separate lines)")
     ap.add_argument("--det-per", type=int, default=5000, help="realisations per (SNR, kappa)")
+    ap.add_argument("--blocks", type=int, default=4, help="blocks of the randomized-block reading")
+    ap.add_argument("--block-pixels", type=int, default=1 << 16, help="pixels of the block comparison")
     ap.add_argument("--cpu-det-sample", type=int, default=256, help="oracle pixels of the detection leg")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
@@ -711,6 +775,8 @@ def main(argv=None) -> None:
         run_ragged(args)
     elif args.workload == "detection":
         run_detection(args)
+    elif args.workload == "blocks":
+        run_blocks(args)
     else:
         run_ours(args)
 
