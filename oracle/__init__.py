@@ -7,6 +7,7 @@ import this package.  It shares no code with the CUDA implementation in
 
 Functions and what they follow:
   grid, xi, operator      Eq. 5 and the definitions after Eq. 2
+  operator_md             Eq. 4's multi-component operator (elevation x motion grids)
   gram_toeplitz, aah      A^H A and A A^H of the Eq. 5 operator
   lipschitz               the step constant of Eq. 14's remark, read as 2*lambda_max(A^H A)
   soft                    Eq. 10 read for complex values (complex soft threshold)
@@ -150,6 +151,20 @@ def operator(geom) -> np.ndarray:
     _load().orc_operator(_dp(b), b.size, float(geom.wavelength_m), float(geom.range_m),
                          float(geom.s_min_m), float(geom.s_max_m), int(geom.L), _dp(A))
     return A
+
+
+def operator_md(geom) -> np.ndarray:
+    """The multi-component operator of Eq. 4 (elevation x motion grids, elevation index
+    fastest): A_nl = exp(-j 2 pi (xi_n s_{l_s} + sum_m eta_{m,n} p_{m,l_m})), in numpy FP64."""
+    N = geom.baselines_m.size
+    x = xi(geom.baselines_m, geom.wavelength_m, geom.range_m)
+    cols = [np.outer(x, grid(geom.s_min_m, geom.s_max_m, geom.L))]  # [N, L_s]
+    phase = cols[0]
+    for m in range(np.asarray(geom.eta).shape[0]):
+        pm = np.linspace(geom.p_min[m], geom.p_max[m], int(geom.L_p[m])) if geom.L_p[m] > 1 else np.array([geom.p_min[m]])
+        part = np.outer(np.asarray(geom.eta, np.float64)[m], pm)  # [N, L_m]
+        phase = (phase[:, None, :] + part[:, :, None]).reshape(N, -1)
+    return np.exp(-2j * np.pi * phase)
 
 
 def gram_toeplitz(geom) -> np.ndarray:

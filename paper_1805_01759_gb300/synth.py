@@ -44,6 +44,9 @@ __all__ = [
     "elevation_resolution",
     "DetectionSet",
     "workload_detection",
+    "MotionGeometry",
+    "make_stack_md",
+    "workload_motion",
 ]
 
 
@@ -265,4 +268,75 @@ def workload_detection(kappas=tuple(np.round(np.arange(0.1, 1.51, 0.1), 2)), snr
     g = noise + a * (_phasors(geom, s_true[:, 0]) + _phasors(geom, s_true[:, 1]))
     lam = (2.0 * np.sqrt(sigma2) * math.sqrt(N * math.log(L))).astype(np.float32)
     return DetectionSet(geom, np.ascontiguousarray(g.astype(np.complex64)), lam, kap, snr, s_true, seed)
+
+
+@dataclasses.dataclass
+class MotionGeometry(StackGeometry):
+    """A stack observed over time (Eqs. 2-4): besides the elevation grid, M motion
+    coefficients p_m on grids of L_p[m] points, with temporal frequencies eta[m, n]
+    (for linear motion p = velocity and eta = 2 t_n / wavelength).  L counts elevation
+    points; the whole grid has L * prod(L_p) points, elevation index fastest."""
+
+    eta: np.ndarray | None = None    # float64 [M, N]
+    p_min: np.ndarray | None = None  # float64 [M]
+    p_max: np.ndarray | None = None  # float64 [M]
+    L_p: np.ndarray | None = None    # int [M]
+
+    @property
+    def L_total(self) -> int:
+        return int(self.L * np.prod(self.L_p))
+
+    def motion(self):
+        return (self.eta, self.p_min, self.p_max, self.L_p)
+
+
+def make_stack_md(geom: MotionGeometry, P: int, rng: np.random.Generator, *, lam: float,
+                  snr_db_range=(5.0, 20.0), k_probs=(0.3, 0.5, 0.2)) -> Stack:
+    """P pixels of K in {0,1,2} unit scatterers, each at an elevation uniform over the grid's
+    extent and motion coefficients uniform over the inner 80 % of each motion grid:
+    g_n = sum_k gamma_k exp(-j 2 pi (xi_n s_k + sum_m eta[m, n] p_{m,k})) + noise (Eq. 4)."""
+    N, M = geom.N, geom.eta.shape[0]
+    xi = 2.0 * geom.baselines_m / (geom.wavelength_m * geom.range_m)
+    K = rng.choice(3, size=P, p=np.asarray(k_probs))
+    snr = rng.uniform(snr_db_range[0], snr_db_range[1], P)
+    g = np.zeros((P, N), np.complex128)
+    gamma = np.zeros((P, geom.L_total), np.complex64)
+    ds = (geom.s_max_m - geom.s_min_m) / (geom.L - 1) if geom.L > 1 else 1.0
+    for k in range(2):
+        on = K > k
+        s = rng.uniform(geom.s_min_m, geom.s_max_m, P)
+        ph = np.exp(1j * rng.uniform(0.0, 2.0 * np.pi, P))
+        phase = np.outer(s, xi)
+        idx = np.clip(np.rint((s - geom.s_min_m) / ds), 0, geom.L - 1).astype(np.int64)
+        stride = geom.L
+        for m in range(M):
+            span = geom.p_max[m] - geom.p_min[m]
+            pm = rng.uniform(geom.p_min[m] + 0.1 * span, geom.p_max[m] - 0.1 * span, P)
+            phase += np.outer(pm, geom.eta[m])
+            dp = span / (geom.L_p[m] - 1) if geom.L_p[m] > 1 else 1.0
+            im = np.clip(np.rint((pm - geom.p_min[m]) / dp), 0, geom.L_p[m] - 1).astype(np.int64)
+            idx = idx + stride * im
+            stride *= int(geom.L_p[m])
+        g[on] += ph[on, None] * np.exp(-2j * np.pi * phase[on])
+        rows = np.flatnonzero(on)
+        gamma[rows, idx[on]] += ph[on].astype(np.complex64)
+    sigma2 = 10.0 ** (-snr / 10.0)
+    g += (rng.standard_normal((P, N)) + 1j * rng.standard_normal((P, N))) * np.sqrt(sigma2 / 2.0)[:, None]
+    return Stack(geom, np.ascontiguousarray(g.astype(np.complex64)), float(np.float32(lam)), gamma,
+                 K.astype(np.int8), snr.astype(np.float32), None, 0)
+
+
+def workload_motion(P: int = 1 << 18, seed: int = 7, L_s: int = 32, L_v: int = 16) -> Stack:
+    """Differential tomography with linear deformation: N = 25 acquisitions, baselines
+    U[-250, 250] m, times U[0, 4] years (eta = 2 t_n / wavelength per m/yr of velocity),
+    elevation grid L_s on [-100, 100] m, velocity grid L_v on [-0.02, 0.02] m/yr, SNR
+    U[5, 20] dB; lambda by the rule of the other workloads with the whole grid's size."""
+    rng = np.random.default_rng(seed)
+    N = 25
+    b = rng.uniform(-250.0, 250.0, N)
+    t = rng.uniform(0.0, 4.0, N)
+    geom = MotionGeometry(np.asarray(b, np.float64), 0.031, 7.0e5, -100.0, 100.0, L_s,
+                          eta=(2.0 * t / 0.031)[None, :], p_min=np.array([-0.02]), p_max=np.array([0.02]),
+                          L_p=np.array([L_v]))
+    return make_stack_md(geom, P, rng, lam=default_lambda(N, geom.L_total))
 

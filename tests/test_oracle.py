@@ -414,6 +414,32 @@ def test_adjoint_zero_solution():
     assert rc == 0 and np.all(dg == 0) and dl == 0.0
 
 
+# ------------------------------------------------ multi-component operator (Eq. 4)
+
+def test_operator_md_without_motion_is_the_elevation_operator():
+    """One motion point at p = 0: Eq. 4 reduces to Eq. 5 (the C oracle's operator)."""
+    rng = np.random.default_rng(4)
+    geom = synth.MotionGeometry(rng.uniform(-250, 250, 20), 0.031, 7e5, -50.0, 50.0, 40,
+                                eta=rng.uniform(0, 300, (1, 20)), p_min=np.zeros(1), p_max=np.zeros(1),
+                                L_p=np.array([1]))
+    np.testing.assert_allclose(oracle.operator_md(geom), oracle.operator(geom), rtol=0, atol=1e-13)
+
+
+def test_operator_md_folds_onto_a_longer_elevation_grid():
+    """With eta = c * xi the phase xi s + eta p = xi (s + c p): on an elevation grid of 8
+    points spaced 1 m and a motion grid spaced 8/c, column (l_s, l_v) is the elevation
+    column at s_{l_s} + 8 l_v, so the whole operator equals the elevation-only operator
+    (C oracle) on a 24-point grid, column for column."""
+    rng = np.random.default_rng(5)
+    b = rng.uniform(-250, 250, 16)
+    x = oracle.xi(b, 0.031, 7e5)
+    c = 3.5
+    geom = synth.MotionGeometry(b, 0.031, 7e5, 0.0, 7.0, 8, eta=(c * x)[None, :], p_min=np.zeros(1),
+                                p_max=np.array([16.0 / c]), L_p=np.array([3]))
+    long = synth.StackGeometry(b, 0.031, 7e5, 0.0, 23.0, 24)
+    np.testing.assert_allclose(oracle.operator_md(geom), oracle.operator(long), rtol=0, atol=1e-12)
+
+
 # ------------------------------------------------- randomized blocks (Eqs. 13-14)
 
 def test_splitmix64_published_outputs():
