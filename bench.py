@@ -14,6 +14,7 @@ the headline value; pixels count only when certified and the oracle sample agree
     python bench.py --workload ragged       # the 64-stack ragged batch (its own line)
     python bench.py --workload detection    # detection-rate Monte Carlo, solve + model selection
     python bench.py --workload blocks       # randomized-block reading of Eqs. 13-14 vs the default
+    python bench.py --workload motion       # elevation x velocity grids (Eq. 4)
 
 Prints one JSON line (rank 0).  Under torchrun each rank solves its own 2^20 pixels
 of the same stack (weak scaling, no collective on the data path; a barrier and a
@@ -740,6 +741,65 @@ def _block_sample(st, res, n):
     return {"n": n, "certified": int(cert.sum()), "certified_and_ok": ok}
 
 
+def run_motion(args) -> None:
+    """Differential tomography (Eq. 4): a stack observed over four years with linear
+    deformation, on an elevation x velocity grid (32 x 16 = 512 points, BF16 + refit, and
+    64 x 16 = 1024 points, FP32 + refit).  Certified pixels/s per path, and a seeded oracle
+    sample of each (exact minimiser on the same multi-component operator)."""
+    import torch
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_1805_01759_gb300 import api, synth
+    out = {}
+    for name, L_s, kw in (("bf16_32x16", 32, dict(precision=1, tol=args.tol_bf16)),
+                          ("fp32_64x16", 64, dict(precision=0, tol=args.tol_fp32))):
+        st = synth.workload_motion(P=args.motion_pixels, seed=7, L_s=L_s, L_v=16)
+        op = api.Operator.from_geometry(st.geom)
+        g = torch.from_numpy(st.g).cuda()
+        for _ in range(args.warmup):
+            api.solve(op, g, st.lam, **kw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            res = api.solve(op, g, st.lam, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        cert = (res.status & 64) != 0
+        out[name] = {"L": op.L, "ms_per_step": ms, "certified_frac": float(cert.float().mean()),
+                     "certified_pixels_per_s": float(cert.sum()) / (ms / 1e3),
+                     "mean_iterations": float(res.iters.double().mean())}
+        if not args.no_cpu_baseline:
+            out[name]["oracle_sample"] = _motion_sample(st, res, 32)
+    print(json.dumps({"metric": "certified pixels/s, multi-component operator (elevation x velocity)",
+                      "value": out["bf16_32x16"]["certified_pixels_per_s"], "unit": "pixels/s",
+                      "workload": f"N=25, times U[0,4] yr, linear velocity grid 16 points on [-0.02,0.02] m/yr, "
+                                  f"elevation on [-100,100] m, {args.motion_pixels} pixels, seed 7",
+                      "runs": out}), flush=True)
+
+
+def _motion_sample(st, res, n):
+    import oracle
+    import torch
+    rng = np.random.default_rng(63)
+    idx = np.sort(rng.choice(st.g.shape[0], size=n, replace=False))
+    A = oracle.operator_md(st.geom)
+    ref = oracle.minimise_batch(A, st.g[idx], st.lam)
+    x = res.x[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.complex128)
+    cert = (res.status.cpu().numpy()[idx] & 64) != 0
+    ok = 0
+    for j in range(n):
+        if not cert[j] or ref["flags"][j] != 0:
+            continue
+        nr = np.linalg.norm(ref["x"][j])
+        err = np.linalg.norm(x[j] - ref["x"][j]) / nr if nr > 0 else np.linalg.norm(x[j])
+        ok += int(err <= 1e-4 and np.array_equal(x[j] != 0, ref["x"][j] != 0))
+    return {"n": n, "certified": int(cert.sum()), "certified_and_ok": ok}
+
+
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -759,12 +819,13 @@ def main(argv=None) -> None:
                     help="stopping tolerance of the BF16 path: BF16 operands carry 2^-9 relative error, "
                          "so smaller steps are not resolved")
     ap.add_argument("--e2e-chunks", type=int, default=8, help="chunks of the end-to-end leg")
-    ap.add_argument("--workload", choices=["patch", "ragged", "detection", "blocks"], default="patch",
+    ap.add_argument("--workload", choices=["patch", "ragged", "detection", "blocks", "motion"], default="patch",
                     help="patch: the headline line; ragged: the 64-stack ragged batch; detection: the "
                          "detection-rate Monte Carlo through solve + model selection (separate lines)")
     ap.add_argument("--det-per", type=int, default=5000, help="realisations per (SNR, kappa)")
     ap.add_argument("--blocks", type=int, default=4, help="blocks of the randomized-block reading")
     ap.add_argument("--block-pixels", type=int, default=1 << 16, help="pixels of the block comparison")
+    ap.add_argument("--motion-pixels", type=int, default=1 << 18, help="pixels of the motion workload")
     ap.add_argument("--cpu-det-sample", type=int, default=256, help="oracle pixels of the detection leg")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
@@ -777,6 +838,8 @@ def main(argv=None) -> None:
         run_detection(args)
     elif args.workload == "blocks":
         run_blocks(args)
+    elif args.workload == "motion":
+        run_motion(args)
     else:
         run_ours(args)
 

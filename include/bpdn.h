@@ -60,6 +60,7 @@ enum bpdn_status {
 #define BPDN_MAX_L 1024
 #define BPDN_MAX_SMAX 16
 #define BPDN_MAX_KSEL 4  /* scatterers per pixel bpdn_select considers */
+#define BPDN_MAX_MOTION 2 /* motion dimensions of bpdn_make_operator_md */
 
 typedef struct {
     int32_t max_iter;     /* N_K of Algorithm 1 (default 500)                                  */
@@ -109,6 +110,27 @@ size_t bpdn_op_workspace_bytes(int32_t N, int32_t L);
 int bpdn_make_operator(const double *baselines_m, int32_t N, double wavelength_m, double range_m,
                        double s_min_m, double s_max_m, int32_t L, void *d_workspace,
                        size_t workspace_bytes, void *cuda_stream, bpdn_op_t *out);
+
+/*
+ * The multi-component operator of Eq. 4 (differential tomography): the grid is the
+ * product of the elevation grid (L_s points on [s_min, s_max]) and M <= BPDN_MAX_MOTION
+ * motion-coefficient grids (L_p[m] points on [p_min[m], p_max[m]]), flattened with the
+ * elevation index fastest, l = l_s + L_s (l_1 + L_p[0] l_2), and
+ *     A_nl = exp(-j 2 pi (xi_n s_{l_s} + sum_m eta_{m,n} p_{m,l_m})),
+ * where eta_{m,n} is the temporal frequency of motion base function m at acquisition n
+ * (for linear motion 2 t_n / wavelength).  Everything else is as bpdn_make_operator,
+ * with L = L_s * prod L_p[m] <= BPDN_MAX_L.  A^H A is not Toeplitz in one index here, so
+ * the refit and the adjoint form its entries from the FP64 operator; bpdn_select (an
+ * elevation-only reading) refuses such operators, and so does the export of h.
+ *
+ * eta      host, M x N values (row m holds eta_{m,n}), finite
+ * p_min, p_max, L_p   host, M values each: p_min <= p_max, L_p >= 1 (L_p = 1 needs p_min == p_max)
+ * Returns BPDN_EINVAL / BPDN_ESIZE / BPDN_EALIGN as bpdn_make_operator, before any launch.
+ */
+int bpdn_make_operator_md(const double *baselines_m, int32_t N, double wavelength_m, double range_m,
+                          double s_min_m, double s_max_m, int32_t L_s, int32_t M, const double *eta,
+                          const double *p_min, const double *p_max, const int32_t *L_p, void *d_workspace,
+                          size_t workspace_bytes, void *cuda_stream, bpdn_op_t *out);
 
 /* Free the host handle (the caller's workspace is not touched). NULL is ignored. */
 void bpdn_destroy_operator(bpdn_op_t op);

@@ -26,13 +26,14 @@ MAX_N = 64
 MAX_L = 1024
 MAX_SMAX = 16
 MAX_KSEL = 4
+MAX_MOTION = 2
 
 EXPORTED = [
     "bpdn_default_options", "bpdn_op_workspace_bytes", "bpdn_make_operator",
     "bpdn_destroy_operator", "bpdn_op_info", "bpdn_op_lipschitz", "bpdn_op_export",
     "bpdn_solve_workspace_bytes", "bpdn_solve", "bpdn_refit", "bpdn_last_error", "bpdn_version",
     "bpdn_solve_noalloc", "bpdn_backward_workspace_bytes", "bpdn_backward",
-    "bpdn_solve_ragged_workspace_bytes", "bpdn_solve_ragged", "bpdn_select",
+    "bpdn_solve_ragged_workspace_bytes", "bpdn_solve_ragged", "bpdn_select", "bpdn_make_operator_md",
 ]
 
 
@@ -110,6 +111,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.bpdn_make_operator.argtypes = [dblp, i32, dbl, dbl, dbl, dbl, i32, vp, sz, vp,
                                        ctypes.POINTER(op_t)]
     lib.bpdn_make_operator.restype = ctypes.c_int
+    lib.bpdn_make_operator_md.argtypes = [dblp, i32, dbl, dbl, dbl, dbl, i32, i32, dblp, dblp, dblp,
+                                          ctypes.POINTER(i32), vp, sz, vp, ctypes.POINTER(op_t)]
+    lib.bpdn_make_operator_md.restype = ctypes.c_int
     lib.bpdn_destroy_operator.argtypes = [op_t]
     lib.bpdn_destroy_operator.restype = None
     lib.bpdn_op_info.argtypes = [op_t, i32p, i32p, dblp, dblp]

@@ -33,22 +33,39 @@ class Operator:
     """The steering operator of one stack (Eq. 5), resident on the current GPU."""
 
     def __init__(self, baselines_m, wavelength_m: float, range_m: float, s_min_m: float,
-                 s_max_m: float, L: int, *, device: torch.device | str | None = None,
+                 s_max_m: float, L: int, *, motion=None, device: torch.device | str | None = None,
                  stream: torch.cuda.Stream | None = None):
+        """motion: None (elevation only, Eq. 5) or (eta [M, N], p_min [M], p_max [M], L_p [M]) for
+        the multi-component grid of Eq. 4 (bpdn_make_operator_md); L is then the number of
+        elevation points and self.L the size of the whole grid."""
         lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         b = np.ascontiguousarray(baselines_m, dtype=np.float64)
-        self.N, self.L = int(b.size), int(L)
+        self.N, self.Ls = int(b.size), int(L)
+        self.L = self.Ls
+        if motion is not None:
+            eta = np.ascontiguousarray(motion[0], dtype=np.float64).reshape(-1, self.N)
+            pmin = np.ascontiguousarray(motion[1], dtype=np.float64).reshape(-1)
+            pmax = np.ascontiguousarray(motion[2], dtype=np.float64).reshape(-1)
+            Lp = np.ascontiguousarray(motion[3], dtype=np.int32).reshape(-1)
+            self.L = self.Ls * int(np.prod(Lp))
         nbytes = lib.bpdn_op_workspace_bytes(self.N, self.L)
         if nbytes == 0:
             raise _lib.BPDNError(-3, f"N = {self.N}, L = {self.L} outside the supported range")
+        dp = ctypes.POINTER(ctypes.c_double)
         with torch.cuda.device(self.device):
             self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
             h = ctypes.c_void_p()
-            _lib.check(lib.bpdn_make_operator(
-                b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.N, float(wavelength_m),
-                float(range_m), float(s_min_m), float(s_max_m), self.L, self.workspace.data_ptr(),
-                nbytes, _stream(stream), ctypes.byref(h)))
+            if motion is None:
+                _lib.check(lib.bpdn_make_operator(
+                    b.ctypes.data_as(dp), self.N, float(wavelength_m), float(range_m), float(s_min_m),
+                    float(s_max_m), self.L, self.workspace.data_ptr(), nbytes, _stream(stream), ctypes.byref(h)))
+            else:
+                _lib.check(lib.bpdn_make_operator_md(
+                    b.ctypes.data_as(dp), self.N, float(wavelength_m), float(range_m), float(s_min_m),
+                    float(s_max_m), self.Ls, int(eta.shape[0]), eta.ctypes.data_as(dp), pmin.ctypes.data_as(dp),
+                    pmax.ctypes.data_as(dp), Lp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                    self.workspace.data_ptr(), nbytes, _stream(stream), ctypes.byref(h)))
         self._h = h
         self.baselines_m = b
         self.wavelength_m, self.range_m = float(wavelength_m), float(range_m)
@@ -60,8 +77,9 @@ class Operator:
 
     @classmethod
     def from_geometry(cls, geom, **kw) -> "Operator":
+        motion = getattr(geom, "motion", None)
         return cls(geom.baselines_m, geom.wavelength_m, geom.range_m, geom.s_min_m, geom.s_max_m,
-                   geom.L, **kw)
+                   geom.L, motion=motion() if callable(motion) else motion, **kw)
 
     @property
     def handle(self) -> ctypes.c_void_p:

@@ -279,9 +279,12 @@ size_t bpdn_op_workspace_bytes(int32_t N, int32_t L)
     return op_layout(N, L).total;
 }
 
-int bpdn_make_operator(const double *baselines_m, int32_t N, double wavelength_m, double range_m,
-                       double s_min_m, double s_max_m, int32_t L, void *d_workspace,
-                       size_t workspace_bytes, void *cuda_stream, bpdn_op_t *out)
+}  // extern "C"
+
+namespace bpdn {
+static int make_operator_impl(const double *baselines_m, int32_t N, double wavelength_m, double range_m,
+                              double s_min_m, double s_max_m, int32_t L, int32_t Ls, const MdGrid *md,
+                              void *d_workspace, size_t workspace_bytes, void *cuda_stream, bpdn_op_t *out)
 {
     if (!out)
         return set_error(BPDN_EINVAL, "out is NULL");
@@ -299,8 +302,8 @@ int bpdn_make_operator(const double *baselines_m, int32_t N, double wavelength_m
         return set_error(BPDN_EINVAL, "wavelength and range must be finite and > 0");
     if (!isfinite(s_min_m) || !isfinite(s_max_m) || s_max_m < s_min_m)
         return set_error(BPDN_EINVAL, "elevation extent must be finite with s_min <= s_max");
-    if (L > 1 && !(s_max_m > s_min_m))
-        return set_error(BPDN_EINVAL, "L > 1 needs s_max > s_min");
+    if (Ls > 1 && !(s_max_m > s_min_m))
+        return set_error(BPDN_EINVAL, "more than one elevation point needs s_max > s_min");
     const OpLayout lay = op_layout(N, L);
     if (workspace_bytes < lay.total)
         return set_error(BPDN_ESIZE, "operator workspace %zu bytes < %zu needed", workspace_bytes,
@@ -325,7 +328,9 @@ int bpdn_make_operator(const double *baselines_m, int32_t N, double wavelength_m
     op->range = range_m;
     op->s_min = s_min_m;
     op->s_max = s_max_m;
-    op->ds = (L > 1) ? (s_max_m - s_min_m) / (double)(L - 1) : 0.0;
+    op->ds = (Ls > 1) ? (s_max_m - s_min_m) / (double)(Ls - 1) : 0.0;
+    op->md = md ? 1 : 0;
+    op->Ls = Ls;
     char *base = (char *)d_workspace;
     op->A_re = (float *)(base + lay.A_re);
     op->A_im = (float *)(base + lay.A_im);
@@ -342,7 +347,8 @@ int bpdn_make_operator(const double *baselines_m, int32_t N, double wavelength_m
     rc = check_cuda(cudaMemcpyAsync(d_b, baselines_m, sizeof(double) * N, cudaMemcpyHostToDevice, s),
                     "copy baselines");
     if (!rc)
-        rc = check_cuda(launch_make_operator(*op, d_b, s), "operator kernels");
+        rc = check_cuda(md ? launch_make_operator_md(*op, d_b, *md, s) : launch_make_operator(*op, d_b, s),
+                        "operator kernels");
     double lmax = 0.0;
     if (!rc)
         rc = check_cuda(cudaMemcpyAsync(&lmax, op->scal, sizeof(double), cudaMemcpyDeviceToHost, s),
@@ -357,6 +363,61 @@ int bpdn_make_operator(const double *baselines_m, int32_t N, double wavelength_m
     op->lipschitz = 2.0 * lmax;
     *out = reinterpret_cast<bpdn_op_t>(op);
     return BPDN_OK;
+}
+
+}  // namespace bpdn
+
+extern "C" {
+
+int bpdn_make_operator(const double *baselines_m, int32_t N, double wavelength_m, double range_m,
+                       double s_min_m, double s_max_m, int32_t L, void *d_workspace,
+                       size_t workspace_bytes, void *cuda_stream, bpdn_op_t *out)
+{
+    return make_operator_impl(baselines_m, N, wavelength_m, range_m, s_min_m, s_max_m, L, L, nullptr,
+                              d_workspace, workspace_bytes, cuda_stream, out);
+}
+
+int bpdn_make_operator_md(const double *baselines_m, int32_t N, double wavelength_m, double range_m,
+                          double s_min_m, double s_max_m, int32_t L_s, int32_t M, const double *eta,
+                          const double *p_min, const double *p_max, const int32_t *L_p, void *d_workspace,
+                          size_t workspace_bytes, void *cuda_stream, bpdn_op_t *out)
+{
+    if (!out)
+        return set_error(BPDN_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (M < 1 || M > BPDN_MAX_MOTION)
+        return set_error(BPDN_EINVAL, "M must lie in 1..%d", BPDN_MAX_MOTION);
+    if (!eta || !p_min || !p_max || !L_p)
+        return set_error(BPDN_EINVAL, "eta, p_min, p_max and L_p must be non-NULL");
+    if (N < 1 || N > BPDN_MAX_N)
+        return set_error(BPDN_ESIZE, "N = %d outside [1, %d]", N, BPDN_MAX_N);
+    if (L_s < 1 || L_s > BPDN_MAX_L)
+        return set_error(BPDN_ESIZE, "L_s = %d outside [1, %d]", L_s, BPDN_MAX_L);
+    MdGrid md;
+    memset(&md, 0, sizeof(md));
+    md.M = M;
+    long long L = L_s;
+    for (int m = 0; m < M; ++m) {
+        if (L_p[m] < 1 || L_p[m] > BPDN_MAX_L)
+            return set_error(BPDN_ESIZE, "L_p[%d] = %d outside [1, %d]", m, L_p[m], BPDN_MAX_L);
+        if (!isfinite(p_min[m]) || !isfinite(p_max[m]) || p_max[m] < p_min[m])
+            return set_error(BPDN_EINVAL, "motion grid %d must be finite with p_min <= p_max", m);
+        if (L_p[m] > 1 && !(p_max[m] > p_min[m]))
+            return set_error(BPDN_EINVAL, "motion grid %d: more than one point needs p_max > p_min", m);
+        for (int n = 0; n < N; ++n) {
+            if (!isfinite(eta[(size_t)m * N + n]))
+                return set_error(BPDN_EINVAL, "eta[%d][%d] is not finite", m, n);
+            md.eta[m][n] = eta[(size_t)m * N + n];
+        }
+        md.Lp[m] = L_p[m];
+        md.pmin[m] = p_min[m];
+        md.pmax[m] = p_max[m];
+        L *= L_p[m];
+        if (L > BPDN_MAX_L)
+            return set_error(BPDN_ESIZE, "grid of %lld points exceeds %d", L, BPDN_MAX_L);
+    }
+    return make_operator_impl(baselines_m, N, wavelength_m, range_m, s_min_m, s_max_m, (int32_t)L, L_s, &md,
+                              d_workspace, workspace_bytes, cuda_stream, out);
 }
 
 void bpdn_destroy_operator(bpdn_op_t h)
@@ -404,7 +465,11 @@ int bpdn_op_export(bpdn_op_t h, int32_t what, void *d_dst, size_t dst_bytes, voi
     switch (what) {
     case 0: need = 8 * (size_t)op->N * op->L; break;
     case 1: need = 16 * (size_t)op->N * op->L; break;
-    case 2: need = 16 * (size_t)(2 * op->L - 1); break;
+    case 2:
+        if (op->md)
+            return set_error(BPDN_EINVAL, "a multi-component operator has no Toeplitz generator");
+        need = 16 * (size_t)(2 * op->L - 1);
+        break;
     case 3: need = 16 * (size_t)op->N * op->N; break;
     default: return set_error(BPDN_EINVAL, "unknown table %d", what);
     }
@@ -539,6 +604,8 @@ int bpdn_select(bpdn_op_t h, const void *d_g, int64_t P, const void *d_x, const 
         return set_error(BPDN_EINVAL, "s_max must lie in 1..%d", BPDN_MAX_SMAX);
     if (kmax < 1 || kmax > BPDN_MAX_KSEL)
         return set_error(BPDN_EINVAL, "kmax must lie in 1..%d", BPDN_MAX_KSEL);
+    if (op->md)
+        return set_error(BPDN_EINVAL, "model selection reads an elevation-only grid; this operator has motion dimensions");
     if (!(penalty == penalty))
         return set_error(BPDN_EINVAL, "penalty must not be NaN");
     if (P == 0)

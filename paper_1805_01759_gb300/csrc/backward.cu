@@ -124,7 +124,19 @@ __global__ void __launch_bounds__(kWarps * 32) k_backward(BackwardLaunch a, cons
         for (int r = 0; r < n2; ++r) {
             if (lane < n2) {
                 const int ia = r >> 1, ra = r & 1, ib = lane >> 1, cb = lane & 1;
-                const double2 gv = h[S.W[ia] - S.W[ib] + L - 1];  // (A^H A)_{W_a W_b}
+                // (A^H A)_{W_a W_b}: the Toeplitz generator, or the FP64 operator on a
+                // multi-component grid
+                double2 gv;
+                if (h) {
+                    gv = h[S.W[ia] - S.W[ib] + L - 1];
+                } else {
+                    gv = make_double2(0.0, 0.0);
+                    for (int n = 0; n < N; ++n) {
+                        const double2 ca = A64[(size_t)n * L + S.W[ia]], cb2 = A64[(size_t)n * L + S.W[ib]];
+                        gv.x += ca.x * cb2.x + ca.y * cb2.y;
+                        gv.y += ca.x * cb2.y - ca.y * cb2.x;
+                    }
+                }
                 double val = (ra == 0) ? (cb == 0 ? gv.x : -gv.y) : (cb == 0 ? gv.y : gv.x);
                 val *= 2.0;
                 if (ia == ib) {
@@ -200,7 +212,7 @@ __global__ void __launch_bounds__(kSumThreads) k_sum_fixed(const double *__restr
 cudaError_t launch_backward(const OpHandle &op, const BackwardLaunch &a, cudaStream_t s)
 {
     const long long blocks = (a.P + kWarps - 1) / kWarps;
-    k_backward<<<(unsigned)blocks, kWarps * 32, 0, s>>>(a, op.A64, op.h, op.N, op.L);
+    k_backward<<<(unsigned)blocks, kWarps * 32, 0, s>>>(a, op.A64, op.md ? nullptr : op.h, op.N, op.L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || a.lam_pp)
         return e;

@@ -30,6 +30,19 @@ struct OpHandle {
     double *xi;          // [N]
     double *scal;        // [8] device scalars (lambda_max, ...)
     size_t ws_bytes;
+    // multi-component grid (Eq. 4): elevation x motion coefficients; A^H A is then not
+    // Toeplitz, h is unused and kernels build Gram entries from A64
+    int md;
+    int Ls;  // elevation points (= L when md == 0)
+};
+
+// The motion part of a multi-component grid: grid index l = l_s + Ls (l_1 + Lp[0] l_2),
+// A_nl = exp(-j 2 pi (xi_n s_{l_s} + eta[0][n] p_{0,l_1} + eta[1][n] p_{1,l_2})).
+struct MdGrid {
+    int M;  // motion dimensions, 1 or BPDN_MAX_MOTION
+    int Lp[BPDN_MAX_MOTION];
+    double pmin[BPDN_MAX_MOTION], pmax[BPDN_MAX_MOTION];
+    double eta[BPDN_MAX_MOTION][BPDN_MAX_N];
 };
 
 // Workspace layout of an operator (offsets in bytes, 256-aligned sections).
@@ -46,6 +59,7 @@ int check_cuda(cudaError_t e, const char *what);
 
 // ---- launches (each returns a cudaError_t from the launch) ----
 cudaError_t launch_make_operator(const OpHandle &op, const double *d_b, cudaStream_t s);
+cudaError_t launch_make_operator_md(const OpHandle &op, const double *d_b, const MdGrid &md, cudaStream_t s);
 
 struct SolvePlan;
 // bpdn_solve's argument checks and launch records (sp->a.P == 0: nothing to launch)

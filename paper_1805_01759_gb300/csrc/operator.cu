@@ -145,6 +145,34 @@ __global__ void k_lambda_max(const double2 *M, int N, double *out)
     }
 }
 
+// Eq. 4 on a multi-component grid (elevation fastest, then the motion coefficients):
+// A_nl = exp(-j 2 pi (xi_n s + sum_m eta_{m,n} p_m)), FP64 table plus the planar FP32 tables.
+__global__ void k_operator_md(const double *xi, int N, int L, int Ls, int lda, double s_min, double s_max,
+                              MdGrid md, double2 *A64, float *A_re, float *A_im)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * lda)
+        return;
+    int n = idx / lda, l = idx % lda;
+    if (l >= L) {
+        A_re[idx] = 0.f;
+        A_im[idx] = 0.f;
+        return;
+    }
+    const int ls = l % Ls;
+    int rest = l / Ls;
+    double t = xi[n] * grid_point(s_min, s_max, Ls, ls);
+    for (int m = 0; m < md.M; ++m) {
+        const int lm = rest % md.Lp[m];
+        rest /= md.Lp[m];
+        t += md.eta[m][n] * grid_point(md.pmin[m], md.pmax[m], md.Lp[m], lm);
+    }
+    double2 a = cis2pi(-t);
+    A64[(size_t)n * L + l] = a;
+    A_re[idx] = (float)a.x;
+    A_im[idx] = (float)a.y;
+}
+
 // (A_j A_j^H)_{nm} over the grid columns [lo, hi) of one block
 __global__ void k_aah_cols(const double2 *A64, int N, int L, int lo, int hi, double2 *M)
 {
@@ -199,6 +227,25 @@ cudaError_t launch_make_operator(const OpHandle &op, const double *d_b, cudaStre
     size_t smem = 2 * (size_t)N * N * sizeof(double2);
     cudaError_t e = cudaFuncSetAttribute(k_lambda_max, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    k_lambda_max<<<1, 1024, smem, s>>>(op.aah, N, op.scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_make_operator_md(const OpHandle &op, const double *d_b, const MdGrid &md, cudaStream_t s)
+{
+    const int N = op.N, L = op.L;
+    k_xi<<<(N + 63) / 64, 64, 0, s>>>(d_b, N, op.wavelength, op.range, op.xi);
+    int tot = N * op.lda;
+    k_operator_md<<<(tot + 255) / 256, 256, 0, s>>>(op.xi, N, L, op.Ls, op.lda, op.s_min, op.s_max, md, op.A64,
+                                                    op.A_re, op.A_im);
+    cudaError_t e = cudaMemsetAsync(op.h, 0, (2 * (size_t)L - 1) * sizeof(double2), s);
+    if (e != cudaSuccess)
+        return e;
+    k_aah<<<(N * N + 127) / 128, 128, 0, s>>>(op.A64, N, L, op.aah);
+    size_t smem = 2 * (size_t)N * N * sizeof(double2);
+    e = cudaFuncSetAttribute(k_lambda_max, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
     k_lambda_max<<<1, 1024, smem, s>>>(op.aah, N, op.scal);

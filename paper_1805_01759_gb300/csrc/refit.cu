@@ -143,14 +143,26 @@ __device__ __noinline__ void load_c(PixelSmem &P, const double2 *__restrict__ A6
     __syncwarp();
 }
 
+// G_ij = h(l_i - l_j) from the Toeplitz generator, or (no generator: a multi-component
+// grid) sum_n conj(A_{n l_i}) A_{n l_j} from the FP64 operator
 template <typename T>
-__device__ __noinline__ void load_Gc(Solve<T> &S, const PixelSmem &P, const double2 *__restrict__ h, int L,
-                                     int lane)
+__device__ __noinline__ void load_Gc(Solve<T> &S, const PixelSmem &P, const double2 *__restrict__ A64,
+                                     const double2 *__restrict__ h, int N, int L, int lane)
 {
     const int m = P.m;
     for (int e = lane; e < m * m; e += 32) {
         const int i = e / m, j = e - (e / m) * m;
-        const double2 v = h[P.W[i] - P.W[j] + L - 1];
+        double2 v;
+        if (h) {
+            v = h[P.W[i] - P.W[j] + L - 1];
+        } else {
+            v = make_double2(0.0, 0.0);
+            for (int n = 0; n < N; ++n) {
+                const double2 a = A64[(size_t)n * L + P.W[i]], b = A64[(size_t)n * L + P.W[j]];
+                v.x += a.x * b.x + a.y * b.y;
+                v.y += a.x * b.y - a.y * b.x;
+            }
+        }
         S.G[i][j] = mk<T>((T)v.x, (T)v.y);
     }
     if (lane < m)
@@ -551,7 +563,7 @@ __device__ __noinline__ bool restricted_minimiser(PixelSmem &P, const double2 *A
     load_c(P, A64, N, L, lane);
     {
         Solve<float> &S = P.s32;
-        load_Gc(S, P, h, L, lane);
+        load_Gc(S, P, A64, h, N, L, lane);
         if (lane < m)
             S.z[lane] = mk<float>((float)start.x, (float)start.y);
         __syncwarp();
@@ -567,7 +579,7 @@ __device__ __noinline__ bool restricted_minimiser(PixelSmem &P, const double2 *A
         __syncwarp();
     }
     Solve<double> &S = P.s64;
-    load_Gc(S, P, h, L, lane);
+    load_Gc(S, P, A64, h, N, L, lane);
     if (lane < m)
         S.z[lane] = mk<double>(P.zkeep[lane].x, P.zkeep[lane].y);
     __syncwarp();
@@ -891,7 +903,7 @@ cudaError_t launch_refit(const OpHandle &op, const RefitLaunch &a, cudaStream_t 
     if (e != cudaSuccess)
         return e;
     const long long blocks = (a.P + WARPS - 1) / WARPS;
-    k_refit<<<(unsigned)blocks, WARPS * 32, smem, s>>>(op.A64, op.h, op.A_re, op.A_im, op.N, op.L,
+    k_refit<<<(unsigned)blocks, WARPS * 32, smem, s>>>(op.A64, op.md ? nullptr : op.h, op.A_re, op.A_im, op.N, op.L,
                                                        op.lda, a);
     return cudaGetLastError();
 }
