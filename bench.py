@@ -319,6 +319,8 @@ class PathRunner:
         self.support = torch.empty((P, self.opt_refit.s_max), dtype=torch.int32, device=dev)
         self.ws_bytes = lib.bpdn_solve_workspace_bytes(op.handle, P, ctypes.byref(self.opt_solve))
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.rws_bytes = lib.bpdn_refit_workspace_bytes(op.handle, P)
+        self.rws = torch.empty(max(self.rws_bytes, 1), dtype=torch.uint8, device=dev)
         self.stream = stream
         self.precision, self.tol = precision, tol
 
@@ -334,7 +336,8 @@ class PathRunner:
         ev_mid.record(self.stream)
         _lib.check(lib.bpdn_refit(self.op.handle, self.g_dev.data_ptr(), self.P, self.lam_t.data_ptr(), 0,
                                   ctypes.byref(self.opt_refit), self.x.data_ptr(), self.x.data_ptr(),
-                                  self.support.data_ptr(), self.nsupp.data_ptr(), self.status.data_ptr(), s))
+                                  self.support.data_ptr(), self.nsupp.data_ptr(), self.status.data_ptr(),
+                                  self.rws.data_ptr(), self.rws_bytes, s))
         return ev_mid
 
     def timed(self, steps: int, warmup: int, dev):

@@ -150,8 +150,12 @@ int bpdn_op_export(bpdn_op_t op, int32_t what, void *d_dst, size_t dst_bytes, vo
 
 /* ------------------------------------------------------------------- solve */
 
-/* Bytes of device workspace bpdn_solve needs for P pixels (a work counter and
- * per-launch scratch; independent of the data).  256-byte aligned buffer. */
+/* Bytes of device workspace for bpdn_solve on P pixels (256-byte aligned buffer;
+ * independent of the data): a work counter, an error word and the block draw table
+ * (256 bytes), A_j A_j^H per block when opt->blocks >= 2, and, with the refit, 200 bytes
+ * per pixel of scratch for the two-launch refit (the FP32 support search of every pixel,
+ * then the FP64 finish).  A workspace smaller than this, down to the first two parts,
+ * is accepted too: the refit then runs in a single launch, with the same results. */
 size_t bpdn_solve_workspace_bytes(bpdn_op_t op, int64_t P, const bpdn_options *opt);
 
 /*
@@ -184,12 +188,19 @@ int bpdn_solve(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda,
  * (at most opt->refit_rounds rounds).  Certified pixels get BPDN_PX_CERTIFIED
  * and x = the minimiser; the others keep x_in and get KKT_FAIL or
  * SUPPORT_OVERFLOW.  Status bits already in d_status are kept (OR-ed).
- * d_x_in and d_x_out may alias.  Other arguments as in bpdn_solve.
+ * d_x_in and d_x_out may alias.  d_workspace (may be NULL) with
+ * workspace_bytes >= bpdn_refit_workspace_bytes(op, P), 256-byte aligned, lets the refit
+ * run as two launches (the FP32 support search of every pixel, then the FP64 finish);
+ * without it the refit runs in one launch, with the same results.  Other arguments as in
+ * bpdn_solve.
  */
 int bpdn_refit(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda,
                int32_t lambda_per_pixel, const bpdn_options *opt, const void *d_x_in,
                void *d_x_out, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
-               void *cuda_stream);
+               void *d_workspace, size_t workspace_bytes, void *cuda_stream);
+
+/* Bytes of scratch that let bpdn_refit run as two launches for P pixels (200 per pixel). */
+size_t bpdn_refit_workspace_bytes(bpdn_op_t op, int64_t P);
 
 /* ------------------------------------------------------------ ragged batch */
 

@@ -31,7 +31,8 @@ MAX_MOTION = 2
 EXPORTED = [
     "bpdn_default_options", "bpdn_op_workspace_bytes", "bpdn_make_operator",
     "bpdn_destroy_operator", "bpdn_op_info", "bpdn_op_lipschitz", "bpdn_op_export",
-    "bpdn_solve_workspace_bytes", "bpdn_solve", "bpdn_refit", "bpdn_last_error", "bpdn_version",
+    "bpdn_solve_workspace_bytes", "bpdn_solve", "bpdn_refit", "bpdn_refit_workspace_bytes",
+    "bpdn_last_error", "bpdn_version",
     "bpdn_solve_noalloc", "bpdn_backward_workspace_bytes", "bpdn_backward",
     "bpdn_solve_ragged_workspace_bytes", "bpdn_solve_ragged", "bpdn_select", "bpdn_make_operator_md",
 ]
@@ -126,7 +127,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.bpdn_solve_workspace_bytes.restype = sz
     lib.bpdn_solve.argtypes = [op_t, vp, i64, vp, i32, optp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.bpdn_solve.restype = ctypes.c_int
-    lib.bpdn_refit.argtypes = [op_t, vp, i64, vp, i32, optp, vp, vp, vp, vp, vp, vp]
+    lib.bpdn_refit.argtypes = [op_t, vp, i64, vp, i32, optp, vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.bpdn_refit_workspace_bytes.argtypes = [op_t, i64]
+    lib.bpdn_refit_workspace_bytes.restype = sz
     lib.bpdn_refit.restype = ctypes.c_int
     lib.bpdn_solve_noalloc.argtypes = [op_t, vp, i64, vp, i32, optp, vp, vp, vp, vp, vp, vp, vp]
     lib.bpdn_solve_noalloc.restype = ctypes.c_int

@@ -176,9 +176,11 @@ def refit(op: Operator, g: torch.Tensor, lam, x_in: torch.Tensor, *, status: tor
     support = torch.empty((P, opt.s_max), dtype=torch.int32, device=g.device)
     nsupp = torch.empty(P, dtype=torch.int32, device=g.device)
     st = torch.zeros(P, dtype=torch.int32, device=g.device) if status is None else status.clone()
+    ws_bytes = lib.bpdn_refit_workspace_bytes(op.handle, P)
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=g.device)
     _lib.check(lib.bpdn_refit(op.handle, g.data_ptr(), P, lam_t.data_ptr(), pp, ctypes.byref(opt),
                               x_in.data_ptr(), x.data_ptr(), support.data_ptr(), nsupp.data_ptr(),
-                              st.data_ptr(), _stream(stream)))
+                              st.data_ptr(), ws.data_ptr() if ws_bytes else None, ws_bytes, _stream(stream)))
     return x, support, nsupp, st
 
 

@@ -126,6 +126,13 @@ static int check_options(const bpdn_options *o)
 using namespace bpdn;
 
 namespace bpdn {
+size_t solve_min_workspace_bytes(const bpdn_options *opt)
+{
+    // a 64-bit work counter, an error word and the block draw table, padded; with
+    // randomized blocks, A_j A_j^H of every block after that
+    return 256 + block_scratch_bytes(opt ? opt->blocks : 0);
+}
+
 static int check_solve_buffers(const OpHandle *op, const void *d_g, int64_t P, const float *d_lambda,
                                const void *d_x, const int32_t *d_status)
 {
@@ -165,7 +172,7 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
         return BPDN_OK;
     if (!d_iters)
         return set_error(BPDN_EINVAL, "iters pointer must be non-NULL");
-    if (!d_workspace || workspace_bytes < bpdn_solve_workspace_bytes(h, P, opt))
+    if (!d_workspace || workspace_bytes < solve_min_workspace_bytes(opt))
         return set_error(BPDN_ESIZE, "solve workspace too small");
     if (!aligned(d_workspace, 256))
         return set_error(BPDN_EALIGN, "solve workspace must be 256-byte aligned");
@@ -215,6 +222,9 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     r.status = d_status;
     r.s_max = opt->s_max;
     r.rounds = opt->refit_rounds;
+    // the two-launch refit when the workspace holds its scratch, else one launch
+    const size_t base = solve_min_workspace_bytes(opt);
+    r.split = (workspace_bytes >= base + refit_scratch_bytes(P)) ? (unsigned char *)d_workspace + base : nullptr;
     return BPDN_OK;
 }
 
@@ -483,10 +493,9 @@ int bpdn_op_export(bpdn_op_t h, int32_t what, void *d_dst, size_t dst_bytes, voi
 size_t bpdn_solve_workspace_bytes(bpdn_op_t h, int64_t P, const bpdn_options *opt)
 {
     (void)h;
-    (void)P;
-    // a 64-bit work counter, an error word and the block draw table, padded; with
-    // randomized blocks, A_j A_j^H of every block after that
-    return 256 + block_scratch_bytes(opt ? opt->blocks : 0);
+    // the least workspace, then the scratch of the two-launch refit (a smaller workspace,
+    // down to the least one, runs the refit in a single launch)
+    return solve_min_workspace_bytes(opt) + ((opt && opt->refit) ? refit_scratch_bytes(P) : 0);
 }
 
 
@@ -499,10 +508,16 @@ int bpdn_solve(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda,
                             d_iters, d_nbt, d_workspace, workspace_bytes, cuda_stream, true);
 }
 
+size_t bpdn_refit_workspace_bytes(bpdn_op_t h, int64_t P)
+{
+    (void)h;
+    return refit_scratch_bytes(P);
+}
+
 int bpdn_refit(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda,
                int32_t lambda_per_pixel, const bpdn_options *opt, const void *d_x_in,
                void *d_x_out, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
-               void *cuda_stream)
+               void *d_workspace, size_t workspace_bytes, void *cuda_stream)
 {
     OpHandle *op = nullptr;
     int rc = check_op(h, &op);
@@ -530,6 +545,10 @@ int bpdn_refit(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda,
     r.status = d_status;
     r.s_max = opt->s_max;
     r.rounds = opt->refit_rounds;
+    // the two-launch refit when the caller's workspace holds its scratch
+    r.split = (d_workspace && aligned(d_workspace, 256) && workspace_bytes >= refit_scratch_bytes(P))
+                  ? (unsigned char *)d_workspace
+                  : nullptr;
     return check_cuda(launch_refit(*op, r, (cudaStream_t)cuda_stream), "refit kernel");
 }
 

@@ -63,7 +63,8 @@ extern "C" int bpdn_solve_noalloc(bpdn_op_t op, const void *d_g, int64_t P, cons
                                   int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
                                   int32_t *d_iters, int32_t *d_nbt, void *cuda_stream)
 {
-    const size_t need = bpdn_solve_workspace_bytes(op, P, opt);
+    (void)P;
+    const size_t need = solve_min_workspace_bytes(opt);
     if (need > kNoAllocScratchBytes)
         return set_error(BPDN_ESIZE,
                          "this solve needs %zu bytes of scratch; the static scratch holds %zu",

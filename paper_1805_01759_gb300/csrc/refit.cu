@@ -553,14 +553,11 @@ __device__ __noinline__ bool newton_refine(Solve<T> &S, int m, T lam, int lane, 
 
 // Step 2 on the current W from the start values in P.zkeep: FP32 support search,
 // FP64 finish.  The FP64 answer is left in P.zkeep.  Returns true on convergence.
-__device__ __noinline__ bool restricted_minimiser(PixelSmem &P, const double2 *A64, const double2 *h, int N,
-                                     int L, double lam, int lane)
+__device__ __noinline__ void fp32_phase(PixelSmem &P, const double2 *A64, const double2 *h, int N, int L,
+                                        double lam, int lane)
 {
     const int m = P.m;
-    if (m == 0)
-        return true;
-    double2 start = (lane < m) ? P.zkeep[lane] : make_double2(0.0, 0.0);
-    load_c(P, A64, N, L, lane);
+    const double2 start = (lane < m) ? P.zkeep[lane] : make_double2(0.0, 0.0);
     {
         Solve<float> &S = P.s32;
         load_Gc(S, P, A64, h, N, L, lane);
@@ -578,6 +575,12 @@ __device__ __noinline__ bool restricted_minimiser(PixelSmem &P, const double2 *A
             P.zkeep[lane] = make_double2((double)S.z[lane].x, (double)S.z[lane].y);
         __syncwarp();
     }
+}
+
+__device__ __noinline__ bool fp64_phase(PixelSmem &P, const double2 *A64, const double2 *h, int N, int L,
+                                        double lam, int lane, double2 start)
+{
+    const int m = P.m;
     Solve<double> &S = P.s64;
     load_Gc(S, P, A64, h, N, L, lane);
     if (lane < m)
@@ -604,6 +607,18 @@ __device__ __noinline__ bool restricted_minimiser(PixelSmem &P, const double2 *A
     return ok;
 }
 
+__device__ __noinline__ bool restricted_minimiser(PixelSmem &P, const double2 *A64, const double2 *h, int N,
+                                     int L, double lam, int lane)
+{
+    const int m = P.m;
+    if (m == 0)
+        return true;
+    const double2 start = (lane < m) ? P.zkeep[lane] : make_double2(0.0, 0.0);
+    load_c(P, A64, N, L, lane);
+    fp32_phase(P, A64, h, N, L, lam, lane);
+    return fp64_phase(P, A64, h, N, L, lam, lane, start);
+}
+
 __device__ void sort_W(PixelSmem &P)
 {
     for (int i = 1; i < P.m; ++i) {
@@ -620,7 +635,20 @@ __device__ void sort_W(PixelSmem &P)
     }
 }
 
-__global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict__ A64,
+// Between the two launches of the split refit, per pixel: the working set, its FP32
+// answer of round 0 and the support count of x_in.
+struct SplitScratch {
+    int *m;      // [P]
+    int *meta;   // [P]: nnz | truncated << 30
+    int *W;      // [P][16]
+    float2 *z;   // [P][16]
+};
+
+// PH 0: the whole refit in one launch.  PH 1: working set and the FP32 support search of
+// round 0, into the scratch.  PH 2: from the scratch, the FP64 finish of round 0, the
+// certificate and any further rounds (both precisions), and the outputs.
+template <int PH>
+__global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const double2 *__restrict__ A64,
                                                       const double2 *__restrict__ h,
                                                       const float *__restrict__ A_re,
                                                       const float *__restrict__ A_im, int N,
@@ -644,14 +672,28 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict_
     const float2 *gp = a.g + (size_t)p * N;
     const double lam = (double)(a.lam_pp ? a.lam[p] : a.lam[0]);
 
-    // 1. working set W
     int nnz = 0;
+    bool truncated = false;
+    if constexpr (PH == 2) {
+        const int mm = sc.m[p];
+        const int meta = sc.meta[p];
+        nnz = meta & ((1 << 30) - 1);
+        truncated = (meta >> 30) & 1;
+        if (lane < mm) {
+            P.W[lane] = sc.W[(size_t)p * 16 + lane];
+            const float2 zz = sc.z[(size_t)p * 16 + lane];
+            P.zkeep[lane] = make_double2((double)zz.x, (double)zz.y);
+        }
+        if (lane == 0)
+            P.m = mm;
+    } else {
+    // 1. working set W
     for (int l0 = 0; l0 < L; l0 += 32) {
         const int l = l0 + lane;
         const float2 v = (l < L) ? xin[l] : make_float2(0.f, 0.f);
         nnz += __popc(__ballot_sync(0xffffffffu, v.x != 0.f || v.y != 0.f));
     }
-    const bool truncated = nnz > smax;
+    truncated = nnz > smax;
     if (!truncated) {
         int m = 0;
         for (int l0 = 0; l0 < L; l0 += 32) {
@@ -711,22 +753,55 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict_
             }
         }
     }
+    }  // working set
     const int status = a.status[p];
     for (int n = lane; n < N; n += 32) {
         const float2 gg = gp[n];
         P.g[n] = make_double2((double)gg.x, (double)gg.y);
     }
     __syncwarp();
-    if (lane < P.m) {
-        const float2 v = xin[P.W[lane]];
-        P.zkeep[lane] = make_double2((double)v.x, (double)v.y);
+    if constexpr (PH != 2) {
+        if (lane < P.m) {
+            const float2 v = xin[P.W[lane]];
+            P.zkeep[lane] = make_double2((double)v.x, (double)v.y);
+        }
+        __syncwarp();
     }
-    __syncwarp();
+    if constexpr (PH == 1) {
+        // FP32 support search of round 0, stored for the second launch
+        const int mm = P.m;
+        if (mm > 0) {
+            load_c(P, A64, N, L, lane);
+            fp32_phase(P, A64, h, N, L, lam, lane);
+        }
+        if (lane < mm) {
+            sc.W[(size_t)p * 16 + lane] = P.W[lane];
+            sc.z[(size_t)p * 16 + lane] = make_float2((float)P.zkeep[lane].x, (float)P.zkeep[lane].y);
+        }
+        if (lane == 0) {
+            sc.m[p] = mm;
+            sc.meta[p] = nnz | (truncated ? (1 << 30) : 0);
+        }
+        return;
+    }
 
     bool certified = false, noroom = false;
     for (int round = 0; round <= a.rounds; ++round) {
         // 2. exact minimiser over W
-        if (!restricted_minimiser(P, A64, h, N, L, lam, lane))
+        bool okr;
+        if (PH == 2 && round == 0) {
+            // the FP32 phase ran in the first launch: finish in FP64 from its answer
+            const int mm = P.m;
+            okr = true;
+            if (mm > 0) {
+                const float2 v = (lane < mm) ? xin[P.W[lane]] : make_float2(0.f, 0.f);
+                load_c(P, A64, N, L, lane);
+                okr = fp64_phase(P, A64, h, N, L, lam, lane, make_double2((double)v.x, (double)v.y));
+            }
+        } else {
+            okr = restricted_minimiser(P, A64, h, N, L, lam, lane);
+        }
+        if (!okr)
             break;
         // drop the coordinates the restricted minimiser set to zero: their dual
         // constraint holds (|2 (G z - c)_i| <= lambda), and the room they free lets the
@@ -893,18 +968,48 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit(const double2 *__restrict_
 
 }  // namespace
 
+size_t refit_scratch_bytes(int64_t P)
+{
+    if (P <= 0)
+        return 0;
+    return (size_t)((8 * P + 64 * P + 128 * P + 4 * 256 + 255) / 256 * 256);
+}
+
 cudaError_t launch_refit(const OpHandle &op, const RefitLaunch &a, cudaStream_t s)
 {
     if (a.P <= 0)
         return cudaSuccess;
     const size_t smem = WARPS * pixel_smem_bytes(op.N);
-    cudaError_t e = cudaFuncSetAttribute(k_refit, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const long long blocks = (a.P + WARPS - 1) / WARPS;
+    const double2 *h = op.md ? nullptr : op.h;
+    if (a.split) {
+        // two launches: the FP32 support search of every pixel, then the FP64 finish and
+        // certificate; each runs a smaller body of code than the single launch
+        SplitScratch sc;
+        unsigned char *b = a.split;
+        auto take = [&](size_t bytes) {
+            unsigned char *r = b;
+            b += (bytes + 255) / 256 * 256;
+            return r;
+        };
+        sc.m = (int *)take(4 * (size_t)a.P);
+        sc.meta = (int *)take(4 * (size_t)a.P);
+        sc.W = (int *)take(64 * (size_t)a.P);
+        sc.z = (float2 *)take(128 * (size_t)a.P);
+        cudaError_t e = cudaFuncSetAttribute(k_refit_t<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_refit_t<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        k_refit_t<1><<<(unsigned)blocks, WARPS * 32, smem, s>>>(sc, op.A64, h, op.A_re, op.A_im, op.N, op.L, op.lda, a);
+        k_refit_t<2><<<(unsigned)blocks, WARPS * 32, smem, s>>>(sc, op.A64, h, op.A_re, op.A_im, op.N, op.L, op.lda, a);
+        return cudaGetLastError();
+    }
+    SplitScratch none = {nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e = cudaFuncSetAttribute(k_refit_t<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    const long long blocks = (a.P + WARPS - 1) / WARPS;
-    k_refit<<<(unsigned)blocks, WARPS * 32, smem, s>>>(op.A64, op.md ? nullptr : op.h, op.A_re, op.A_im, op.N, op.L,
-                                                       op.lda, a);
+    k_refit_t<0><<<(unsigned)blocks, WARPS * 32, smem, s>>>(none, op.A64, h, op.A_re, op.A_im, op.N, op.L, op.lda, a);
     return cudaGetLastError();
 }
 

@@ -265,3 +265,31 @@ def test_stored_minimiser(api):
         err = _rel(x, want)
         zero = np.linalg.norm(want, axis=1) == 0
         assert np.all(err[~zero] <= 1e-4) and np.all(x[zero] == 0)
+
+
+def test_two_launch_refit_equals_single_launch(api):
+    """With the full workspace the refit runs as two launches (FP32 support search, then the
+    FP64 finish); with the least workspace as one.  Both give bitwise the same results."""
+    import ctypes
+    from paper_1805_01759_gb300 import _lib
+    lib = _lib.load()
+    st = synth.workload_patch(P=4096, seed=2)
+    op = api.Operator.from_geometry(st.geom)
+    g = torch.from_numpy(st.g).cuda()
+    for precision, tol in ((0, 1e-6), (1, 1e-3)):
+        full = api.solve(op, g, st.lam, precision=precision, tol=tol)
+        opt = _lib.default_options(precision=precision, tol=tol)
+        P = g.shape[0]
+        assert lib.bpdn_solve_workspace_bytes(op.handle, P, ctypes.byref(opt)) >= 256 + 200 * P
+        ws = torch.empty(256, dtype=torch.uint8, device="cuda")
+        lam = torch.tensor([st.lam], dtype=torch.float32, device="cuda")
+        x = torch.empty_like(full.x)
+        ints = [torch.empty(P, dtype=torch.int32, device="cuda") for _ in range(4)]
+        sup = torch.empty_like(full.support)
+        _lib.check(lib.bpdn_solve(op.handle, g.data_ptr(), P, lam.data_ptr(), 0, ctypes.byref(opt), x.data_ptr(),
+                                  sup.data_ptr(), ints[0].data_ptr(), ints[1].data_ptr(), ints[2].data_ptr(),
+                                  ints[3].data_ptr(), ws.data_ptr(), 256, None))
+        torch.cuda.synchronize()
+        assert torch.equal(x, full.x) and torch.equal(ints[1], full.status)
+        assert torch.equal(sup, full.support) and torch.equal(ints[0], full.nsupp)
+
