@@ -513,11 +513,12 @@ def run_ours(args) -> None:
             "iteration": {"name": kname, "ms": statistics.mean(head_tm["rbpg_ms"]),
                           "share": statistics.mean(head_tm["rbpg_ms"]) / ms_head,
                           "bound": "FP32 pipe (roofline above)"},
-            "refit": {"name": "k_refit_t<1> + k_refit_t<2>", "ms": statistics.mean(head_tm["refit_ms"]),
+            "refit": {"name": "k_refit_t<1> + k_refit_t<2> + k_refit_t<3>",
+                      "ms": statistics.mean(head_tm["refit_ms"]),
                       "share": statistics.mean(head_tm["refit_ms"]) / ms_head,
                       "bound": "latency (one warp per pixel): the FP32 support search issues at ~55 %, "
-                               "the FP64 finish and certificate is bound by FP64 work and instruction "
-                               "fetch (FP64 pipe ~35 %); no throughput roofline applies"},
+                               "the FP64 finish keeps the FP64 pipe ~60 % busy, the further rounds are "
+                               "few but long; no throughput roofline applies"},
         },
         "precision_report": prec_report,
         "cpu_baseline": cpu,

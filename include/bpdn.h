@@ -152,9 +152,9 @@ int bpdn_op_export(bpdn_op_t op, int32_t what, void *d_dst, size_t dst_bytes, vo
 
 /* Bytes of device workspace for bpdn_solve on P pixels (256-byte aligned buffer;
  * independent of the data): a work counter, an error word and the block draw table
- * (256 bytes), A_j A_j^H per block when opt->blocks >= 2, and, with the refit, 200 bytes
- * per pixel of scratch for the two-launch refit (the FP32 support search of every pixel,
- * then the FP64 finish).  A workspace smaller than this, down to the first two parts,
+ * (256 bytes), A_j A_j^H per block when opt->blocks >= 2, and, with the refit, 460 bytes
+ * per pixel of scratch for the refit in three launches (the FP32 support search of every
+ * pixel, the FP64 finish and certificate, further rounds for the pixels that need them).  A workspace smaller than this, down to the first two parts,
  * is accepted too: the refit then runs in a single launch, with the same results. */
 size_t bpdn_solve_workspace_bytes(bpdn_op_t op, int64_t P, const bpdn_options *opt);
 
@@ -190,7 +190,8 @@ int bpdn_solve(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda,
  * SUPPORT_OVERFLOW.  Status bits already in d_status are kept (OR-ed).
  * d_x_in and d_x_out may alias.  d_workspace (may be NULL) with
  * workspace_bytes >= bpdn_refit_workspace_bytes(op, P), 256-byte aligned, lets the refit
- * run as two launches (the FP32 support search of every pixel, then the FP64 finish);
+ * run as three launches (the FP32 support search of every pixel, the FP64 finish and
+ * certificate, then further rounds for the pixels that need them);
  * without it the refit runs in one launch, with the same results.  Other arguments as in
  * bpdn_solve.
  */
@@ -199,7 +200,7 @@ int bpdn_refit(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda,
                void *d_x_out, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
                void *d_workspace, size_t workspace_bytes, void *cuda_stream);
 
-/* Bytes of scratch that let bpdn_refit run as two launches for P pixels (200 per pixel). */
+/* Bytes of scratch that let bpdn_refit run as three launches for P pixels (460 per pixel). */
 size_t bpdn_refit_workspace_bytes(bpdn_op_t op, int64_t P);
 
 /* ------------------------------------------------------------ ragged batch */

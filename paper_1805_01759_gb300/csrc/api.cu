@@ -222,7 +222,7 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     r.status = d_status;
     r.s_max = opt->s_max;
     r.rounds = opt->refit_rounds;
-    // the two-launch refit when the workspace holds its scratch, else one launch
+    // the split refit (three launches) when the workspace holds its scratch, else one launch
     const size_t base = solve_min_workspace_bytes(opt);
     r.split = (workspace_bytes >= base + refit_scratch_bytes(P)) ? (unsigned char *)d_workspace + base : nullptr;
     return BPDN_OK;
@@ -493,7 +493,7 @@ int bpdn_op_export(bpdn_op_t h, int32_t what, void *d_dst, size_t dst_bytes, voi
 size_t bpdn_solve_workspace_bytes(bpdn_op_t h, int64_t P, const bpdn_options *opt)
 {
     (void)h;
-    // the least workspace, then the scratch of the two-launch refit (a smaller workspace,
+    // the least workspace, then the scratch of the split refit (a smaller workspace,
     // down to the least one, runs the refit in a single launch)
     return solve_min_workspace_bytes(opt) + ((opt && opt->refit) ? refit_scratch_bytes(P) : 0);
 }
@@ -545,7 +545,7 @@ int bpdn_refit(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda,
     r.status = d_status;
     r.s_max = opt->s_max;
     r.rounds = opt->refit_rounds;
-    // the two-launch refit when the caller's workspace holds its scratch
+    // the split refit when the caller's workspace holds its scratch
     r.split = (d_workspace && aligned(d_workspace, 256) && workspace_bytes >= refit_scratch_bytes(P))
                   ? (unsigned char *)d_workspace
                   : nullptr;

@@ -122,14 +122,14 @@ struct RefitLaunch {
     int32_t *support, *nsupp, *status;
     int s_max;
     int rounds;
-    // scratch of the two-launch refit (refit_scratch_bytes(P)), or NULL: one launch
+    // scratch of the split refit (refit_scratch_bytes(P)), or NULL: one launch
     unsigned char *split;
 };
 cudaError_t launch_refit(const OpHandle &op, const RefitLaunch &a, cudaStream_t s);
-// bytes of scratch the two-launch refit needs for P pixels (256-byte multiple)
+// bytes of scratch the split refit needs for P pixels (256-byte multiple)
 size_t refit_scratch_bytes(int64_t P);
 // the least solve workspace (work counter, error word, block draw table and matrices);
-// bpdn_solve_workspace_bytes adds the two-launch refit's scratch to it
+// bpdn_solve_workspace_bytes adds the split refit's scratch to it
 size_t solve_min_workspace_bytes(const bpdn_options *opt);
 
 struct SolvePlan {

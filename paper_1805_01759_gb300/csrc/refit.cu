@@ -635,18 +635,24 @@ __device__ void sort_W(PixelSmem &P)
     }
 }
 
-// Between the two launches of the split refit, per pixel: the working set, its FP32
-// answer of round 0 and the support count of x_in.
+// Between the launches of the split refit, per pixel: the working set, its FP32 answer of
+// round 0 and the support count of x_in (launch 1 -> 2); whether the pixel needs further
+// rounds, with its working set and FP64 state (launch 2 -> 3).
 struct SplitScratch {
-    int *m;      // [P]
-    int *meta;   // [P]: nnz | truncated << 30
-    int *W;      // [P][16]
-    float2 *z;   // [P][16]
+    int *m;       // [P]
+    int *meta;    // [P]: nnz | truncated << 30
+    int *W;       // [P][16]
+    float2 *z;    // [P][16]
+    int *pend;    // [P]: 1 when launch 3 continues the pixel
+    double2 *zs;  // [P][16]
 };
 
 // PH 0: the whole refit in one launch.  PH 1: working set and the FP32 support search of
-// round 0, into the scratch.  PH 2: from the scratch, the FP64 finish of round 0, the
-// certificate and any further rounds (both precisions), and the outputs.
+// round 0, into the scratch.  PH 2: from the scratch, the FP64 finish and the certificate
+// of round 0; a pixel the certificate sends to another round is handed on, the others get
+// their outputs.  PH 3: the further rounds (both precisions) of the handed-on pixels only.
+// Splitting keeps each launch's executed code small: one fused launch stalled on
+// instruction fetch while the warps of an SM ran different phases.
 template <int PH>
 __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const double2 *__restrict__ A64,
                                                       const double2 *__restrict__ h,
@@ -674,15 +680,23 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
 
     int nnz = 0;
     bool truncated = false;
-    if constexpr (PH == 2) {
+    if constexpr (PH == 3) {
+        if (!sc.pend[p])
+            return;
+    }
+    if constexpr (PH >= 2) {
         const int mm = sc.m[p];
         const int meta = sc.meta[p];
         nnz = meta & ((1 << 30) - 1);
         truncated = (meta >> 30) & 1;
         if (lane < mm) {
             P.W[lane] = sc.W[(size_t)p * 16 + lane];
-            const float2 zz = sc.z[(size_t)p * 16 + lane];
-            P.zkeep[lane] = make_double2((double)zz.x, (double)zz.y);
+            if constexpr (PH == 2) {
+                const float2 zz = sc.z[(size_t)p * 16 + lane];
+                P.zkeep[lane] = make_double2((double)zz.x, (double)zz.y);
+            } else {
+                P.zkeep[lane] = sc.zs[(size_t)p * 16 + lane];
+            }
         }
         if (lane == 0)
             P.m = mm;
@@ -760,7 +774,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
         P.g[n] = make_double2((double)gg.x, (double)gg.y);
     }
     __syncwarp();
-    if constexpr (PH != 2) {
+    if constexpr (PH < 2) {
         if (lane < P.m) {
             const float2 v = xin[P.W[lane]];
             P.zkeep[lane] = make_double2((double)v.x, (double)v.y);
@@ -785,8 +799,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
         return;
     }
 
-    bool certified = false, noroom = false;
-    for (int round = 0; round <= a.rounds; ++round) {
+    bool certified = false, noroom = false, more = false;
+    const int round_first = (PH == 3) ? 1 : 0, round_last = (PH == 2) ? 0 : a.rounds;
+    for (int round = round_first; round <= round_last; ++round) {
+        more = false;
         // 2. exact minimiser over W
         bool okr;
         if (PH == 2 && round == 0) {
@@ -908,6 +924,24 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
         __syncwarp();
         if (noroom)
             break;
+        more = true;  // violators joined W: another round follows, if the limit allows one
+    }
+    if constexpr (PH == 2) {
+        // hand the pixel on to the third launch when it needs a further round
+        const int hand = (more && a.rounds >= 1) ? 1 : 0;
+        if (hand) {
+            const int mm = P.m;
+            if (lane < mm) {
+                sc.W[(size_t)p * 16 + lane] = P.W[lane];
+                sc.zs[(size_t)p * 16 + lane] = P.zkeep[lane];
+            }
+            if (lane == 0)
+                sc.m[p] = mm;
+        }
+        if (lane == 0)
+            sc.pend[p] = hand;
+        if (hand)
+            return;
     }
 
     float2 *xo = a.x_out + (size_t)p * L;
@@ -972,7 +1006,7 @@ size_t refit_scratch_bytes(int64_t P)
 {
     if (P <= 0)
         return 0;
-    return (size_t)((8 * P + 64 * P + 128 * P + 4 * 256 + 255) / 256 * 256);
+    return (size_t)((12 * P + 64 * P + 128 * P + 256 * P + 6 * 256 + 255) / 256 * 256);
 }
 
 cudaError_t launch_refit(const OpHandle &op, const RefitLaunch &a, cudaStream_t s)
@@ -983,8 +1017,8 @@ cudaError_t launch_refit(const OpHandle &op, const RefitLaunch &a, cudaStream_t 
     const long long blocks = (a.P + WARPS - 1) / WARPS;
     const double2 *h = op.md ? nullptr : op.h;
     if (a.split) {
-        // two launches: the FP32 support search of every pixel, then the FP64 finish and
-        // certificate; each runs a smaller body of code than the single launch
+        // three launches: the FP32 support search of every pixel, the FP64 finish and
+        // certificate, then further rounds for the pixels that need them
         SplitScratch sc;
         unsigned char *b = a.split;
         auto take = [&](size_t bytes) {
@@ -996,16 +1030,21 @@ cudaError_t launch_refit(const OpHandle &op, const RefitLaunch &a, cudaStream_t 
         sc.meta = (int *)take(4 * (size_t)a.P);
         sc.W = (int *)take(64 * (size_t)a.P);
         sc.z = (float2 *)take(128 * (size_t)a.P);
+        sc.pend = (int *)take(4 * (size_t)a.P);
+        sc.zs = (double2 *)take(256 * (size_t)a.P);
         cudaError_t e = cudaFuncSetAttribute(k_refit_t<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_refit_t<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_refit_t<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
         k_refit_t<1><<<(unsigned)blocks, WARPS * 32, smem, s>>>(sc, op.A64, h, op.A_re, op.A_im, op.N, op.L, op.lda, a);
         k_refit_t<2><<<(unsigned)blocks, WARPS * 32, smem, s>>>(sc, op.A64, h, op.A_re, op.A_im, op.N, op.L, op.lda, a);
+        k_refit_t<3><<<(unsigned)blocks, WARPS * 32, smem, s>>>(sc, op.A64, h, op.A_re, op.A_im, op.N, op.L, op.lda, a);
         return cudaGetLastError();
     }
-    SplitScratch none = {nullptr, nullptr, nullptr, nullptr};
+    SplitScratch none = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaError_t e = cudaFuncSetAttribute(k_refit_t<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;

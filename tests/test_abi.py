@@ -74,7 +74,7 @@ def test_argument_errors_without_gpu(lib):
                           None, 0, None) == -1
     assert lib.bpdn_refit(None, None, 1, None, 0, ctypes.byref(opt), None, None, None, None, None, None, 0,
                           None) == -1
-    assert lib.bpdn_refit_workspace_bytes(None, 1 << 20) >= 200 * (1 << 20)
+    assert lib.bpdn_refit_workspace_bytes(None, 1 << 20) >= 460 * (1 << 20)
     assert lib.bpdn_op_info(None, None, None, None, None) == -1
     assert np.isnan(lib.bpdn_op_lipschitz(None))
     lib.bpdn_destroy_operator(None)  # ignored
