@@ -277,19 +277,47 @@ class BPDNFunction(torch.autograd.Function):
         return dLdg, dLdlam.reshape(ctx.lam_shape), None, None
 
 
+def global_error_and_grad(num: float, den: float, dnum: float, group=None):
+    """Sum (error numerator, its normaliser, d numerator / d log lambda) over the ranks of the
+    default (or given) process group, when one is initialised, and return the batch's
+    relative squared error and its derivative in log lambda.  This is the one collective of
+    lambda tuning with pixels sharded over GPUs: two sums and a derivative, reduced in FP64."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend(group) == "nccl" \
+            else torch.device("cpu")
+        v = torch.tensor([num, den, dnum], dtype=torch.float64, device=dev)
+        dist.all_reduce(v, op=dist.ReduceOp.SUM, group=group)
+        num, den, dnum = (float(t) for t in v.cpu())
+    den = max(den, 1e-30)
+    return num / den, dnum / den
+
+
 def tune_lambda(op: Operator, g: torch.Tensor, gamma_true: torch.Tensor, lam0: float, *,
-                steps: int = 50, lr: float = 0.1, options: dict | None = None):
+                steps: int = 50, lr: float = 0.1, options: dict | None = None, group=None):
     """Learn one lambda by gradient descent on log lambda, minimising the relative squared
     error sum |x(lambda) - gamma_true|^2 / sum |gamma_true|^2 over pixels and grid points.
+    Under torch.distributed (pixels sharded over ranks) the sums run over every rank's
+    pixels (global_error_and_grad), so all ranks take the same steps.
     Returns (lambda, [(lambda, error) per step])."""
+    import torch.distributed as dist
+    sharded = dist.is_available() and dist.is_initialized()
     log_lam = torch.tensor([math.log(lam0)], dtype=torch.float32, device=g.device, requires_grad=True)
     history = []
     for _ in range(steps):
         lam = log_lam.exp()
         x, _ = BPDNFunction.apply(g, lam, op, options)
-        mse = (x - gamma_true).abs().pow(2).sum() / gamma_true.abs().pow(2).sum().clamp_min(1e-30)
-        (grad,) = torch.autograd.grad(mse, log_lam)
-        history.append((float(lam.item()), float(mse.item())))
+        if sharded:
+            num = (x - gamma_true).abs().pow(2).sum()
+            (dnum,) = torch.autograd.grad(num, log_lam)
+            den = gamma_true.abs().pow(2).sum()
+            mse_v, grad_v = global_error_and_grad(float(num.item()), float(den.item()), float(dnum.item()), group)
+            grad = torch.tensor([grad_v], dtype=torch.float32, device=g.device)
+        else:
+            mse = (x - gamma_true).abs().pow(2).sum() / gamma_true.abs().pow(2).sum().clamp_min(1e-30)
+            (grad,) = torch.autograd.grad(mse, log_lam)
+            mse_v = float(mse.item())
+        history.append((float(lam.item()), mse_v))
         with torch.no_grad():
             log_lam -= lr * grad
     return float(log_lam.exp().item()), history

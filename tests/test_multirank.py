@@ -71,3 +71,36 @@ def test_single_process_helpers_are_identities():
     assert bench.reduce_max(4.5) == 4.5
     bench.barrier()
     assert bench.shard_part(0) == 0
+
+
+def _tune_rank(rank: int, world: int, port: int, out_dir: str) -> None:
+    sys.path.insert(0, ROOT)
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        from paper_1805_01759_gb300 import api
+        # rank r holds a shard with error numerator n_r, normaliser d_r and derivative q_r
+        n, d, q = [3.0, 5.0][rank], [10.0, 30.0][rank], [-0.2, 0.6][rank]
+        err, grad = api.global_error_and_grad(n, d, q)
+        np.save(os.path.join(out_dir, f"t{rank}.npy"), np.array([err, grad]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_lambda_tuning_reduction(tmp_path):
+    """The collective of lambda tuning with sharded pixels: every rank gets the error and
+    derivative of the whole batch, (n_0 + n_1) / (d_0 + d_1) and (q_0 + q_1) / (d_0 + d_1)."""
+    world = 2
+    mp.spawn(_tune_rank, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    for r in range(world):
+        err, grad = np.load(tmp_path / f"t{r}.npy")
+        assert abs(err - 8.0 / 40.0) < 1e-15 and abs(grad - 0.4 / 40.0) < 1e-15
+
+
+def test_lambda_tuning_reduction_without_process_group():
+    sys.path.insert(0, ROOT)
+    from paper_1805_01759_gb300 import api
+    if dist.is_initialized():
+        pytest.skip("a process group is already initialised")
+    err, grad = api.global_error_and_grad(3.0, 12.0, -0.6)
+    assert err == 0.25 and abs(grad + 0.05) < 1e-16
+
