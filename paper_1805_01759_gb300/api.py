@@ -422,6 +422,21 @@ class RaggedSolver:
         return self.results
 
 
+def deal_stacks(costs, world: int) -> list:
+    """Deal stacks to `world` ranks by estimated cost (e.g. P * N * L per stack): largest first,
+    each to the rank with the least cost so far (ties: the lower rank).  Deterministic, so every
+    rank computes the same dealing without communicating.  Returns the rank of each stack."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    load = [0.0] * world
+    rank_of = [0] * len(costs)
+    for i in sorted(range(len(costs)), key=lambda i: (-float(costs[i]), i)):
+        r = min(range(world), key=lambda k: (load[k], k))
+        rank_of[i] = r
+        load[r] += float(costs[i])
+    return rank_of
+
+
 def solve_ragged(items, *, stream: torch.cuda.Stream | None = None, **options) -> list:
     """Solve every (Operator, g, lambda) stack of `items` in one bpdn_solve_ragged call."""
     return RaggedSolver(items, **options).run(stream)

@@ -104,3 +104,21 @@ def test_lambda_tuning_reduction_without_process_group():
     err, grad = api.global_error_and_grad(3.0, 12.0, -0.6)
     assert err == 0.25 and abs(grad + 0.05) < 1e-16
 
+
+def test_deal_stacks_by_cost():
+    """Stacks go to ranks by estimated cost, largest first, each to the least-loaded rank:
+    every stack exactly once, the dealing deterministic, and the heaviest rank's load within
+    the largest single cost of the average (the greedy bound)."""
+    sys.path.insert(0, ROOT)
+    from paper_1805_01759_gb300 import api, synth
+    sts = synth.workload_ragged(n_stacks=64, seed=3, scale_pixels=0.01)
+    costs = [st.g.shape[0] * st.geom.N * st.geom.L for st in sts]
+    for world in (1, 2, 3, 8):
+        owner = api.deal_stacks(costs, world)
+        assert owner == api.deal_stacks(costs, world) and len(owner) == len(costs)
+        assert set(owner) <= set(range(world))
+        loads = [sum(c for c, r in zip(costs, owner) if r == k) for k in range(world)]
+        assert max(loads) <= sum(costs) / world + max(costs)
+    assert api.deal_stacks(costs, 1) == [0] * len(costs)
+    assert api.deal_stacks([5, 1, 4, 2], 2) == [0, 0, 1, 1]  # 5 | 4, then 2 -> rank 1, 1 -> rank 0
+
