@@ -221,8 +221,15 @@ typedef struct {
     int32_t tile_pixels;       /* this stack's tile_pixels (0 = the options' value) */
 } bpdn_stack;
 
-/* Workspace of bpdn_solve_ragged: 256 bytes per stack. */
+/* Least workspace of bpdn_solve_ragged: 256 bytes per stack (the refits then run as single
+ * launches). */
 size_t bpdn_solve_ragged_workspace_bytes(int32_t n_stacks);
+
+/* Workspace with which bpdn_solve_ragged runs each stack's refit in three launches (as
+ * bpdn_solve does): 256 bytes per stack, then, when opt->refit, 460 bytes per pixel of every
+ * stack.  Same results either way.  0 if stacks is NULL with n_stacks > 0. */
+size_t bpdn_solve_ragged_workspace_bytes_for(const bpdn_stack *stacks, int32_t n_stacks,
+                                             const bpdn_options *opt);
 
 /*
  * Solve many stacks, each with its own operator (N, L, grid) and pixel count, in one

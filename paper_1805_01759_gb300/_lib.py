@@ -34,7 +34,8 @@ EXPORTED = [
     "bpdn_solve_workspace_bytes", "bpdn_solve", "bpdn_refit", "bpdn_refit_workspace_bytes",
     "bpdn_last_error", "bpdn_version",
     "bpdn_solve_noalloc", "bpdn_backward_workspace_bytes", "bpdn_backward",
-    "bpdn_solve_ragged_workspace_bytes", "bpdn_solve_ragged", "bpdn_select", "bpdn_make_operator_md",
+    "bpdn_solve_ragged_workspace_bytes", "bpdn_solve_ragged_workspace_bytes_for", "bpdn_solve_ragged",
+    "bpdn_select", "bpdn_make_operator_md",
 ]
 
 
@@ -139,6 +140,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.bpdn_backward.restype = ctypes.c_int
     lib.bpdn_solve_ragged_workspace_bytes.argtypes = [i32]
     lib.bpdn_solve_ragged_workspace_bytes.restype = sz
+    lib.bpdn_solve_ragged_workspace_bytes_for.argtypes = [ctypes.POINTER(Stack), i32, optp]
+    lib.bpdn_solve_ragged_workspace_bytes_for.restype = sz
     lib.bpdn_solve_ragged.argtypes = [ctypes.POINTER(Stack), i32, optp, vp, sz, vp]
     lib.bpdn_solve_ragged.restype = ctypes.c_int
     lib.bpdn_select.argtypes = [op_t, vp, i64, vp, vp, vp, vp, i32, i32, dbl, vp, vp, vp, vp]

@@ -395,7 +395,8 @@ class RaggedSolver:
             self.items.append((op, g, lam_t))
             self.results.append(res)
         self._arr = arr
-        self.ws_bytes = lib.bpdn_solve_ragged_workspace_bytes(len(items))
+        # room for every stack's refit to run in three launches
+        self.ws_bytes = lib.bpdn_solve_ragged_workspace_bytes_for(arr, len(items), ctypes.byref(self.opt))
         dev = self.items[0][1].device if self.items else torch.device("cuda")
         self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
         self.graph = None

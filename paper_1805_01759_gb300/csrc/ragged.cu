@@ -71,6 +71,19 @@ using namespace bpdn;
 
 extern "C" {
 
+size_t bpdn_solve_ragged_workspace_bytes_for(const bpdn_stack *stacks, int32_t n_stacks, const bpdn_options *opt)
+{
+    if (n_stacks <= 0)
+        return 0;
+    if (!stacks)
+        return 0;
+    size_t b = kStackScratch * (size_t)n_stacks;
+    if (opt && opt->refit)
+        for (int i = 0; i < n_stacks; ++i)
+            b += refit_scratch_bytes(stacks[i].P);
+    return b;
+}
+
 size_t bpdn_solve_ragged_workspace_bytes(int32_t n_stacks)
 {
     return n_stacks > 0 ? kStackScratch * (size_t)n_stacks : 0;
@@ -123,6 +136,16 @@ int bpdn_solve_ragged(const bpdn_stack *stacks, int32_t n_stacks, const bpdn_opt
                         st.d_nsupp, st.d_status, st.d_iters, st.d_nbt, ws, kStackScratch, &plans[i]);
         if (rc)
             return rc;  // checked above: cannot happen
+    }
+    // with room for it, each stack's refit runs in three launches: its scratch follows the
+    // per-stack headers, in stack order
+    if (opt->refit && workspace_bytes >= bpdn_solve_ragged_workspace_bytes_for(stacks, n_stacks, opt)) {
+        unsigned char *b = (unsigned char *)d_workspace + kStackScratch * (size_t)n_stacks;
+        for (int i = 0; i < n_stacks; ++i) {
+            if (plans[i].refit)
+                plans[i].r.split = b;
+            b += refit_scratch_bytes(stacks[i].P);
+        }
     }
     std::vector<const OpHandle *> ops;
     std::vector<SolveLaunch> as;

@@ -88,6 +88,13 @@ def test_ragged_host_checks():
     opt = _lib.default_options()
     assert lib.bpdn_solve_ragged_workspace_bytes(0) == 0
     assert lib.bpdn_solve_ragged_workspace_bytes(3) == 3 * 256
+    arr3 = (_lib.Stack * 3)()
+    for i, P in enumerate((10, 0, 1000)):
+        arr3[i].P = P
+    full = lib.bpdn_solve_ragged_workspace_bytes_for(arr3, 3, ctypes.byref(opt))
+    assert full >= 3 * 256 + 460 * 1010
+    opt0 = _lib.default_options(refit=0)
+    assert lib.bpdn_solve_ragged_workspace_bytes_for(arr3, 3, ctypes.byref(opt0)) == 3 * 256
     assert lib.bpdn_solve_ragged(None, 0, ctypes.byref(opt), None, 0, None) == _lib.BPDN_OK
     assert lib.bpdn_solve_ragged(None, -1, ctypes.byref(opt), None, 0, None) == _lib.BPDN_EINVAL
     assert lib.bpdn_solve_ragged(None, 2, ctypes.byref(opt), None, 0, None) == _lib.BPDN_EINVAL
