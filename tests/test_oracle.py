@@ -440,6 +440,37 @@ def test_operator_md_folds_onto_a_longer_elevation_grid():
     np.testing.assert_allclose(oracle.operator_md(geom), oracle.operator(long), rtol=0, atol=1e-12)
 
 
+OPERATOR_MD_MUTANTS = {
+    "motion_sign": ("phase = (phase[:, None, :] + part[:, :, None])", "phase = (phase[:, None, :] - part[:, :, None])"),
+    "elevation_slowest": ("phase = (phase[:, None, :] + part[:, :, None]).reshape(N, -1)",
+                          "phase = (phase[:, :, None] + part[:, None, :]).reshape(N, -1)"),
+    "grid_open_end": ("np.linspace(geom.p_min[m], geom.p_max[m], int(geom.L_p[m]))",
+                      "np.linspace(geom.p_min[m], geom.p_max[m], int(geom.L_p[m]), endpoint=False)"),
+    "phase_sign": ("return np.exp(-2j * np.pi * phase)", "return np.exp(2j * np.pi * phase)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(OPERATOR_MD_MUTANTS))
+def test_operator_md_mutant_caught(name, monkeypatch):
+    """Planted mistakes in oracle.operator_md each fail one of its two pins."""
+    import inspect
+    import textwrap
+    old, new = OPERATOR_MD_MUTANTS[name]
+    src = textwrap.dedent(inspect.getsource(oracle.operator_md))
+    assert src.count(old) == 1, name
+    ns = dict(oracle.__dict__)
+    exec(compile(src.replace(old, new), f"<{name}>", "exec"), ns)
+    monkeypatch.setattr(oracle, "operator_md", ns["operator_md"])
+    caught = False
+    for pin in (test_operator_md_without_motion_is_the_elevation_operator,
+                test_operator_md_folds_onto_a_longer_elevation_grid):
+        try:
+            pin()
+        except AssertionError:
+            caught = True
+    assert caught, f"no pin catches the planted mistake {name}"
+
+
 # ------------------------------------------------- randomized blocks (Eqs. 13-14)
 
 def test_splitmix64_published_outputs():
