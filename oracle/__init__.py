@@ -80,7 +80,7 @@ def _configure(lib):
     lib.orc_objective.argtypes = [dp, c_int, c_int, dp, c_double, dp]
     lib.orc_objective.restype = c_double
     lib.orc_rbpg.argtypes = [dp, c_int, c_int, dp, c_double, c_double, c_double, c_double,
-                             c_int, c_int, dp, ip, dp, ip, ip, dp, dp]
+                             c_int, c_int, dp, ip, dp, ip, ip, dp, dp, dp]
     lib.orc_rbpg.restype = c_int
     lib.orc_cd.argtypes = [dp, c_int, c_int, dp, c_double, c_double, c_long, dp, lp]
     lib.orc_cd.restype = c_int
@@ -220,16 +220,16 @@ def rbpg(A, g, lam: float, *, alpha0: float | None = None, c_alpha: float = 0.5,
     x = np.empty(L, np.complex128)
     it = np.zeros(1, np.int32)
     T = max(int(max_iter), 1)
-    ta, tacc, tn, tF, tm = (np.zeros(T), np.zeros(T, np.int32), np.zeros(T, np.int32),
-                            np.zeros(T), np.zeros(T))
+    ta, tacc, tn, tF, tm, ts = (np.zeros(T), np.zeros(T, np.int32), np.zeros(T, np.int32),
+                                np.zeros(T), np.zeros(T), np.zeros(T))
     st = _load().orc_rbpg(_dp(A), N, L, _dp(g), float(lam), a0, float(c_alpha), float(tol),
                           int(max_iter), int(max_bt), _dp(x), _ip(it), _dp(ta), _ip(tacc),
-                          _ip(tn), _dp(tF), _dp(tm))
+                          _ip(tn), _dp(tF), _dp(tm), _dp(ts))
     out = {"x": x, "iters": int(it[0]), "status": int(st)}
     if trace:
         k = int(it[0])
         out.update(alpha=ta[:k].copy(), accepted=tacc[:k].astype(bool), n_bt=tn[:k].copy(),
-                   F=tF[:k].copy(), margin=tm[:k].copy())
+                   F=tF[:k].copy(), margin=tm[:k].copy(), step=ts[:k].copy())
     return out
 
 

@@ -203,14 +203,15 @@ static int all_finite(const cplx *v, int n)
  *     max_iter iterations (status NOT_CONVERGED).  x = xbar = 0 at k = 1 stops at once.
  *
  * trace arrays (length >= max_iter, may be NULL): alpha after backtracking,
- * accept flag, number of step reductions, F(xbar) and the smallest relative
+ * accept flag, number of step reductions, F(xbar), the smallest relative
  * margin of any discrete decision taken in the iteration (prox thresholds,
- * line-search test, accept test).
+ * line-search test, accept test) and the relative candidate step
+ * ||xbar - x^k|| / max(||xbar||, 1e-30) that the stopping test compares with tol.
  */
 int orc_rbpg(const cplx *A, int N, int L, const cplx *g, double lam, double alpha0,
              double c_alpha, double tol, int max_iter, int max_bt, cplx *x_out,
              int *iters_out, double *tr_alpha, int *tr_acc, int *tr_nbt, double *tr_F,
-             double *tr_margin)
+             double *tr_margin, double *tr_step)
 {
     int status = 0;
     size_t Lz = (size_t)L, Nz = (size_t)N;
@@ -309,6 +310,8 @@ int orc_rbpg(const cplx *A, int N, int L, const cplx *g, double lam, double alph
             tr_F[k - 1] = Fb;
         if (tr_margin)
             tr_margin[k - 1] = margin;
+        if (tr_step)
+            tr_step[k - 1] = sqrt(dnorm) / fmax(sqrt(xnorm), 1e-30);
         if (sqrt(dnorm) <= tol * fmax(sqrt(xnorm), 1e-30)) {
             stopped = 1;
             break;
@@ -778,11 +781,156 @@ void orc_kkt(const cplx *A, int N, int L, const cplx *g, double lam, const cplx 
 }
 
 /*
+ * Coordinate descent on Eq. 6 restricted to the index set S (x_l = 0 for l not in S):
+ * the same one-coordinate minimisations as orc_cd, over the m columns of A_S only,
+ * starting from z.  Stops when max |dz_i| <= tol * max(1, max |z_i|).  Returns 0 on
+ * convergence, 1 if max_sweeps was reached.
+ */
+static int cd_restricted(const cplx *A, int N, int L, const cplx *g, double lam, int m, const int *S,
+                         cplx *z, double tol, long max_sweeps)
+{
+    size_t mz = (size_t)m;
+    cplx *G = (cplx *)malloc(sizeof(cplx) * mz * mz);
+    cplx *q = (cplx *)malloc(sizeof(cplx) * mz);
+    for (int i = 0; i < m; ++i) {
+        cplx c = 0.0;
+        for (int n = 0; n < N; ++n)
+            c += conj(A[(size_t)n * L + S[i]]) * g[n];
+        q[i] = c;
+        for (int j = 0; j < m; ++j) {
+            cplx acc = 0.0;
+            for (int n = 0; n < N; ++n)
+                acc += conj(A[(size_t)n * L + S[i]]) * A[(size_t)n * L + S[j]];
+            G[(size_t)i * m + j] = acc;
+        }
+    }
+    /* q = c - G z */
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j)
+            q[i] -= G[(size_t)i * m + j] * z[j];
+    int rc = 1;
+    for (long sw = 0; sw < max_sweeps; ++sw) {
+        double maxd = 0.0, maxz = 0.0;
+        for (int i = 0; i < m; ++i) {
+            double Gii = creal(G[(size_t)i * m + i]);
+            cplx old = z[i];
+            cplx nw = orc_soft(q[i] + Gii * old, 0.5 * lam) / Gii;
+            cplx dlt = nw - old;
+            if (dlt != 0.0) {
+                for (int j = 0; j < m; ++j)
+                    q[j] -= G[(size_t)j * m + i] * dlt;
+                z[i] = nw;
+                if (cabs(dlt) > maxd)
+                    maxd = cabs(dlt);
+            }
+            if (cabs(z[i]) > maxz)
+                maxz = cabs(z[i]);
+        }
+        if (maxd <= tol * fmax(1.0, maxz)) {
+            rc = 0;
+            break;
+        }
+    }
+    free(G);
+    free(q);
+    return rc;
+}
+
+/*
+ * Working-set repair of a minimiser whose certificate failed: S = supp(x) plus the
+ * grid points whose dual constraint |2 a_l^H (A x - g)| <= lambda is violated (the
+ * eight largest violations per round); the restricted problem on S is solved by
+ * coordinate descent and polished by Newton on its nonzeros; repeated until the
+ * certificate holds or the rounds run out.  x is replaced by the last restricted
+ * solution.  Returns 0 when the certificate holds.
+ */
+static int repair_working_set(const cplx *A, int N, int L, const cplx *g, double lam, cplx *x, int rounds)
+{
+    int *S = (int *)malloc(sizeof(int) * (size_t)L);
+    int *inS = (int *)malloc(sizeof(int) * (size_t)L);
+    cplx *z = (cplx *)malloc(sizeof(cplx) * (size_t)L);
+    cplx *r = (cplx *)malloc(sizeof(cplx) * (size_t)N);
+    cplx *u = (cplx *)malloc(sizeof(cplx) * (size_t)L);
+    int ok = 1;
+    for (int round = 0; round < rounds; ++round) {
+        double on, off, mn;
+        int nS;
+        orc_kkt(A, N, L, g, lam, x, &on, &off, &mn, &nS);
+        if (on <= 1e-9 && off <= 1.0 + 1e-9) {
+            ok = 0;
+            break;
+        }
+        /* S = supp(x) and the largest violators off it */
+        int m = 0;
+        for (int l = 0; l < L; ++l) {
+            inS[l] = (x[l] != 0.0);
+            if (inS[l])
+                S[m++] = l;
+        }
+        matvec(A, N, L, x, r);
+        for (int n = 0; n < N; ++n)
+            r[n] -= g[n];
+        matvec_h(A, N, L, r, u);
+        for (int add = 0; add < 8; ++add) {
+            int best = -1;
+            double bv = lam * (1.0 + 1e-12);
+            for (int l = 0; l < L; ++l)
+                if (!inS[l] && 2.0 * cabs(u[l]) > bv) {
+                    bv = 2.0 * cabs(u[l]);
+                    best = l;
+                }
+            if (best < 0)
+                break;
+            inS[best] = 1;
+            S[m++] = best;
+        }
+        /* ascending order of S */
+        for (int i = 1; i < m; ++i) {
+            int v = S[i], j = i - 1;
+            while (j >= 0 && S[j] > v) {
+                S[j + 1] = S[j];
+                --j;
+            }
+            S[j + 1] = v;
+        }
+        for (int i = 0; i < m; ++i)
+            z[i] = x[S[i]];
+        cd_restricted(A, N, L, g, lam, m, S, z, 1e-13, 200000);
+        /* Newton on the nonzero coordinates of the restricted solution */
+        int k = 0;
+        for (int i = 0; i < m; ++i)
+            if (z[i] != 0.0) {
+                S[k] = S[i];
+                z[k] = z[i];
+                ++k;
+            }
+        double res;
+        if (k > 0)
+            orc_newton_polish(A, N, L, g, lam, k, S, z, 50, 1e-13, &res);
+        for (int l = 0; l < L; ++l)
+            x[l] = 0.0;
+        for (int i = 0; i < k; ++i)
+            x[S[i]] = z[i];
+    }
+    if (ok) {
+        double on, off, mn;
+        int nS;
+        orc_kkt(A, N, L, g, lam, x, &on, &off, &mn, &nS);
+        ok = !(on <= 1e-9 && off <= 1.0 + 1e-9);
+    }
+    free(S); free(inS); free(z); free(r); free(u);
+    return ok;
+}
+
+/*
  * Exact minimiser of Eq. 6 for one pixel: coordinate descent, then Newton on
  * the support CD found (when CD stops, its support is the minimiser's unless
- * a component sits at a tie), then the certificate.
- * flags: bit0 CD hit max_sweeps, bit1 Newton did not converge (CD result kept),
- *        bit2 certificate failed (on_res > 1e-9 or off_max > 1 + 1e-9), bit3 non-finite input.
+ * a component sits at a tie), then the certificate.  When the certificate fails
+ * (CD stopped early at a wrong support), the working-set repair above continues
+ * from that point.
+ * flags (0 whenever the final certificate holds): bit0 CD hit max_sweeps, bit1 Newton
+ * did not converge (CD result kept), bit2 certificate failed (on_res > 1e-9 or
+ * off_max > 1 + 1e-9) even after the repair, bit3 non-finite input.
  */
 int orc_min(const cplx *A, int N, int L, const cplx *g, double lam, double cd_tol,
             long max_sweeps, cplx *x, double *on_res, double *off_max, double *min_abs_on,
@@ -820,8 +968,16 @@ int orc_min(const cplx *A, int N, int L, const cplx *g, double lam, double cd_to
     }
     free(S);
     orc_kkt(A, N, L, g, lam, x, on_res, off_max, min_abs_on, nS);
-    if (*on_res > 1e-9 || *off_max > 1.0 + 1e-9)
+    if (*on_res > 1e-9 || *off_max > 1.0 + 1e-9) {
+        if (repair_working_set(A, N, L, g, lam, x, 50) == 0) {
+            orc_kkt(A, N, L, g, lam, x, on_res, off_max, min_abs_on, nS);
+            return 0;
+        }
+        orc_kkt(A, N, L, g, lam, x, on_res, off_max, min_abs_on, nS);
         flags |= 4;
+    } else if (flags) {
+        flags = 0;  /* certified: how CD and Newton got there does not matter */
+    }
     return flags;
 }
 
@@ -915,7 +1071,7 @@ void orc_rbpg_batch(const cplx *A, int N, int L, const cplx *g, int64_t P, const
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t p = 0; p < P; ++p)
         status[p] = orc_rbpg(A, N, L, g + (size_t)p * N, lam[p], alpha0, c_alpha, tol, max_iter,
-                             max_bt, x + (size_t)p * L, iters + p, NULL, NULL, NULL, NULL, NULL);
+                             max_bt, x + (size_t)p * L, iters + p, NULL, NULL, NULL, NULL, NULL, NULL);
 }
 
 void orc_rbpg_block_batch(const cplx *A, int N, int L, const cplx *g, int64_t P, const double *lam,

@@ -237,6 +237,60 @@ def test_bruteforce_tiny(seed):
     assert oracle.objective(A, g, lam, ra["x"]) >= Fb - 1e-9
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_repair_from_an_unconverged_descent(seed):
+    """Coordinate descent stopped after one sweep leaves a wrong support; the exact
+    minimiser must still come out (through the working-set repair), equal to the
+    brute-force enumeration of supports, with a clean certificate."""
+    rng = np.random.default_rng(300 + seed)
+    N = int(rng.integers(3, 5))
+    L = 8
+    b = rng.uniform(-250, 250, N)
+    geom = _geom(b, -30.0, 30.0, L)  # 8.6 m bins: strongly coherent neighbouring columns
+    A = oracle.operator(geom)
+    g = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    lam = rng.uniform(0.3, 0.6) * np.max(np.abs(2 * A.conj().T @ g))
+    xb, Fb = bruteforce_min(A, g, lam)
+    assert np.isfinite(Fb)
+    x1, sweeps, rc = oracle.cd(A, g, lam, max_sweeps=1)
+    on, off, _, _ = oracle.kkt(A, g, lam, x1)
+    assert rc == 1 and (on > 1e-6 or off > 1 + 1e-6)  # one sweep is not the minimiser
+    r = oracle.minimise(A, g, lam, max_sweeps=1)
+    assert r["flags"] == 0 and r["sweeps"] == 1
+    np.testing.assert_allclose(r["x"], xb, atol=1e-9 * max(1.0, np.abs(xb).max()))
+    assert np.array_equal(r["x"] != 0, xb != 0)
+
+
+def test_repair_on_workload_pixels():
+    """On the small workload, three descent sweeps plus the repair give the same
+    minimiser as descent run to convergence."""
+    st = synth.workload_small(P=16, seed=3)
+    A = oracle.operator(st.geom)
+    full = oracle.minimise_batch(A, st.g, st.lam)
+    short = oracle.minimise_batch(A, st.g, st.lam, max_sweeps=3)
+    assert np.all(full["flags"] == 0) and np.all(short["flags"] == 0)
+    np.testing.assert_allclose(short["x"], full["x"], atol=1e-9 * np.abs(full["x"]).max())
+
+
+def test_stopping_trace_matches_the_stop():
+    """Algorithm 1 stops at the first iteration whose relative candidate step
+    ||xbar - x^k|| / ||xbar|| is at most tol; from x^0 = 0 the first step is exactly 1."""
+    st = synth.workload_small(P=24, seed=4)
+    A = oracle.operator(st.geom)
+    for tol in (1e-2, 1e-4):
+        for p in range(st.g.shape[0]):
+            r = oracle.rbpg(A, st.g[p], st.lam, tol=tol, max_iter=300, trace=True)
+            step = r["step"]
+            if np.all(r["x"] == 0):
+                continue
+            assert step[0] == 1.0
+            small = np.nonzero(step <= tol)[0]
+            if r["status"] & oracle.STATUS_NOT_CONVERGED:
+                assert small.size == 0 and r["iters"] == 300
+            else:
+                assert small.size >= 1 and r["iters"] == small[0] + 1
+
+
 def test_certificate_on_workload():
     """Eq. 6 optimality at every oracle output of the small workload: on the support
     2 a_l^H (A x - g) = -lambda x_l/|x_l|, off it |2 a_l^H (A x - g)| <= lambda."""

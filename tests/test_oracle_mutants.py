@@ -26,6 +26,9 @@ MUTANTS = {
                         "margin = fmin(margin, am);\n\n        int accepted = (Fb >= Fx);"),
     "linesearch_factor": ("double rhs = dd / (2.0 * alpha);", "double rhs = dd / alpha;"),
     "cd_threshold": ("cplx nw = orc_soft(vv, 0.5 * lam) / Gll;", "cplx nw = orc_soft(vv, lam) / Gll;"),
+    "repair_cd_threshold": ("cplx nw = orc_soft(q[i] + Gii * old, 0.5 * lam) / Gii;",
+                            "cplx nw = orc_soft(q[i] + Gii * old, lam) / Gii;"),
+    "repair_stale_residual": ("q[j] -= G[(size_t)j * m + i] * dlt;", "q[j] -= G[(size_t)i * m + j] * dlt;"),
     "newton_residual_sign": ("phi[i] = 2.0 * acc + lam * z[i] / cabs(z[i]);", "phi[i] = 2.0 * acc - lam * z[i] / cabs(z[i]);"),
     "kkt_factor": ("cplx zl = 2.0 * z[l];", "cplx zl = z[l];"),
     "adjoint_curvature_sign": ("Jm[(size_t)(2 * i) * n2 + 2 * i] += curv * (1.0 - u0 * u0);",
