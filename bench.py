@@ -217,6 +217,72 @@ def _traffic_per_launch(pixels: int, path_name: str) -> float | None:
     return float(rec["dram_bytes_per_pixel"]) * pixels
 
 
+PEAK_KINDS = {0: ("ffma", "TFLOP/s"), 1: ("ffma2", "TFLOP/s"), 2: ("dfma", "TFLOP/s"), 3: ("mufu_rsqrt", "Top/s")}
+
+
+def measure_peaks(dev, kinds=(0, 1, 2, 3), seconds: float = 0.15, repeats: int = 5) -> dict:
+    """Pipe rates of this GPU from the library's microbenchmark loops (bpdn_bench_peak):
+    every SM full of threads running independent FMA (or rsqrt) chains, timed with CUDA
+    events on the launching stream; the best of `repeats` launches of about `seconds` each."""
+    import torch
+    from paper_1805_01759_gb300 import _lib
+    lib = _lib.load()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads = 8 * n_sm, 256
+    sink = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ops = ctypes.c_double()
+    out = {}
+    for kind in kinds:
+        name, unit = PEAK_KINDS[kind]
+        iters = 1 << 10
+        while True:  # grow the loop until one launch takes about `seconds`
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _lib.check(lib.bpdn_bench_peak(kind, blocks, threads, iters, sink.data_ptr(), ctypes.byref(ops),
+                                           stream.cuda_stream))
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            if ms >= 1e3 * seconds or iters >= (1 << 30):
+                break
+            iters *= 2 if ms < 1e3 * seconds / 8 else max(2, int(1e3 * seconds / max(ms, 1e-3)))
+        best = float("inf")
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _lib.check(lib.bpdn_bench_peak(kind, blocks, threads, iters, sink.data_ptr(), ctypes.byref(ops),
+                                           stream.cuda_stream))
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            best = min(best, e0.elapsed_time(e1))
+        rate = blocks * threads * float(iters) * ops.value / (best / 1e3) / 1e12
+        out[name] = {"value": rate, "unit": unit, "ms": best, "iters": iters, "blocks": blocks, "threads": threads}
+    return out
+
+
+def run_peaks(args) -> None:
+    """The arithmetic-pipe peaks of this GPU (FFMA, FFMA2, DFMA, MUFU), with the SM clock
+    sampled while they run and the unit-count figures beside them."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    with ClockSampler(dev.index) as clk:
+        pk = measure_peaks(dev, seconds=0.3)
+    clocks = clk.summary()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks.get("sm_mhz") or 2070.0
+    nominal = {"ffma": n_sm * 128 * 2 * mhz * 1e6 / 1e12, "ffma2": n_sm * 128 * 2 * mhz * 1e6 / 1e12}
+    if rank == 0:
+        print(json.dumps({"metric": "arithmetic pipe peaks", "value": pk["ffma2"]["value"], "unit": "TFLOP/s",
+                          "n_gpus": 1, "workload": "peaks", "peaks": pk,
+                          "unit_count_at_sampled_clock": nominal,
+                          "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
+                                     "reasons": clocks.get("reasons"), "power_w_max": clocks.get("power_w_max")}}),
+              flush=True)
+
+
 def cpu_baseline_leg(sample: int) -> dict:
     import oracle
     from paper_1805_01759_gb300 import synth
@@ -240,7 +306,7 @@ def alu_flops_per_sweep(path: str, N: int, L: int) -> float:
     complex multiply-add, four real FMAs, per (n, l)).  A xbar over the nonzeros of
     xbar (8 N per nonzero) is left out."""
     flops = 36.0 * L
-    if path == "fp32":
+    if path.startswith("fp32"):
         flops += 8.0 * N * L
     return flops
 
@@ -305,7 +371,9 @@ def precision_report(api, oracle_patch: "OracleSample", st_patch, op_patch, g_pa
             x_it = it.x.cpu().numpy()
             x_rf, _, _, st_rf = api.refit(op, g, lam, it.x, status=it.status)
             torch.cuda.synchronize()
-            rows[name] = {"before_refit": o.summary(x_it, 1e-3), "after_refit": o.summary(x_rf.cpu().numpy(), 1e-4),
+            before = o.summary(x_it, 1e-3)
+            before["frac_le_0.0001"] = o.summary(x_it, 1e-4)["frac_le_0.0001"]
+            rows[name] = {"before_refit": before, "after_refit": o.summary(x_rf.cpu().numpy(), 1e-4),
                           "certified_frac": float(((st_rf.cpu().numpy() & 64) != 0).mean())}
         out[cname] = rows
     return out
@@ -398,9 +466,13 @@ def run_ours(args) -> None:
     g_dev = torch.from_numpy(st.g).to(dev)
     lam_t = torch.tensor([st.lam], dtype=torch.float32, device=dev)
 
-    paths = {"fp32": (0, args.tol_fp32), "bf16": (1, args.tol_bf16)}
-    if args.precision != "both":
-        paths = {args.precision: paths[args.precision]}
+    # plain FP32 at its own tolerance, FP32 at the BF16 path's tolerance (the same stopping
+    # rule, so that the two precisions are compared at equal work per pixel), and BF16
+    paths = {"fp32": (0, args.tol_fp32), "fp32_tol_bf16": (0, args.tol_bf16), "bf16": (1, args.tol_bf16)}
+    if args.precision == "fp32":
+        paths = {"fp32": paths["fp32"], "fp32_tol_bf16": paths["fp32_tol_bf16"]}
+    elif args.precision == "bf16":
+        paths = {"bf16": paths["bf16"]}
     # the oracle's answers for the accuracy gate, computed on the host before timing
     oracle_patch = OracleSample(st, args.sample) if rank == 0 else None
     results = {}
@@ -437,10 +509,13 @@ def run_ours(args) -> None:
             "mean_iters": float(it_np.mean()), "frac_max_iter": float((it_np >= 500).mean()),
             "mean_step_cuts": float(nbt_np.mean()),
             "pixel_sweeps": sweeps,
+            # time of one sweep over every pixel of the batch (iteration kernel time / mean sweeps)
+            "ms_per_sweep": statistics.mean(tm["rbpg_ms"]) / (sweeps / P),
             "alu_tflops": sweeps * alu_flops_per_sweep(name, N, L) / rbpg_avg_s / 1e12,
         }
         if name == "bf16":
             out_paths[name]["tensor_tflops"] = sweeps * 8.0 * N * L / rbpg_avg_s / 1e12
+        out_paths[name]["alu_flops_per_sweep"] = alu_flops_per_sweep(name, N, L)
         if name == head:
             acc_head, good_head, ms_head = acc, good, ms_step
             head_runner, head_tm, head_sweeps = runner, tm, sweeps
@@ -475,6 +550,13 @@ def run_ours(args) -> None:
     prec_report = None
     if rank == 0 and not args.no_precision_report:
         prec_report = precision_report(api, oracle_patch, st, op, g_dev, st.lam, paths)
+        # the same paths without the refit: Algorithm 1's own output against the 1e-4 gate
+        # (the fraction of the oracle sample within 1e-4, over the iteration kernel's time)
+        for name in out_paths:
+            frac = prec_report["patch_sample"][name]["before_refit"]["frac_le_0.0001"]
+            it_ms = out_paths[name]["kernels_ms"]["iteration"]
+            out_paths[name]["without_refit"] = {"frac_within_1e-4": frac,
+                                                "value": P * world * frac / (it_ms / 1e3)}
     pixels_total = P * world
     value = pixels_total * good_head / (ms_head / 1e3)
     # the e2e result's own certified fraction, times the sample's agreement rate
@@ -484,9 +566,12 @@ def run_ours(args) -> None:
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
-    peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    # the dominant kernel of the headline path is its iteration kernel (about 55 % of a
-    # step); the pipe that bounds it is the FP32 one (alu_flops_per_sweep)
+    unit_count_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    # the FP32 pipe's peak measured on this GPU (the faster of the FFMA and packed FFMA2 loops)
+    pk = measure_peaks(dev, kinds=(0, 1))
+    peak_tflops = max(pk["ffma"]["value"], pk["ffma2"]["value"])
+    # the dominant kernel of the headline path is its iteration kernel (its share of a step
+    # is reported under kernels); the pipe that bounds it is the FP32 one (alu_flops_per_sweep)
     rbpg_avg_s = statistics.mean(head_tm["rbpg_ms"]) / 1e3
     achieved = head_sweeps * alu_flops_per_sweep(head, N, L) / rbpg_avg_s / 1e12
     traffic = _traffic_per_launch(P, head)
@@ -511,9 +596,12 @@ def run_ours(args) -> None:
         "paths": out_paths,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic, "kernel": kname,
+                     "peak_source": "measured: FFMA/FFMA2 loops of bpdn_bench_peak on this GPU",
+                     "peak_unit_count": unit_count_tflops, "peaks_measured": pk,
                      "note": "the fused iteration (Algorithm 1); see kernels for the refit's share. "
-                             f"peak = FP32 FMA rate, {n_sm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
-                             "(unit counts and the max SM clock); achieved = the algorithmic FP32 work of "
+                             "peak = the FP32 FMA rate measured on this GPU (the faster of the FFMA and "
+                             f"FFMA2 loops; the unit count {n_sm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
+                             "is peak_unit_count); achieved = the algorithmic FP32 work of "
                              "Algorithm 1 per pixel sweep (36 L elementwise flops"
                              + ("" if head == "bf16" else " + 8 N L for the contraction") +
                              "; a step cut is one more sweep) over the iteration kernel's event-timed "
@@ -709,6 +797,85 @@ def _detection_cpu_leg(d, kh, sh, cert, n):
             "khat_agree": agree, "khat_compared": int(both.sum()), "max_elevation_diff_m": float(elev)}
 
 
+def run_hybrid(args) -> None:
+    """The pre-classified chain on the patch (classify, then solve + refit + select only for
+    the pixels the linear pass leaves to L1, merged back) against the plain chain (solve +
+    refit + select on every pixel), both BF16 with the FP64 refit.  Reports both rates, the
+    class fractions, and on an oracle sample the model orders and elevations of both chains
+    against the oracle's chain (exact minimiser + model selection)."""
+    import torch
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_1805_01759_gb300 import api, synth
+    P = args.pixels
+    st = synth.workload_patch(P=P, seed=2)
+    op = api.Operator.from_geometry(st.geom)
+    g = torch.from_numpy(st.g).cuda()
+    kw = dict(precision=1, tol=args.tol_bf16)
+
+    def plain():
+        res = api.solve(op, g, st.lam, **kw)
+        return api.select(op, g, res)
+
+    def hybrid():
+        return api.hybrid(op, g, st.lam, **kw)
+
+    out = {}
+    for name, fn in (("plain", plain), ("hybrid", hybrid)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        out[name] = (statistics.mean(times), r)
+    ms_plain, sel_plain = out["plain"]
+    ms_hyb, (cls_out, sel_hyb, _) = out["hybrid"]
+    cls = cls_out.cls.cpu().numpy()
+    # the oracle's chain on a seeded sample
+    import oracle
+    from oracle import select as osel
+    rng = np.random.default_rng(62)
+    idx = np.sort(rng.choice(P, size=min(args.sample, P), replace=False))
+    A = oracle.operator(st.geom)
+    xi = oracle.xi(st.geom.baselines_m, st.geom.wavelength_m, st.geom.range_m)
+    sg = oracle.grid(st.geom.s_min_m, st.geom.s_max_m, st.geom.L)
+    ref = oracle.minimise_batch(A, st.g[idx], st.lam)
+    okh, osh, _ = osel.select_batch(st.g[idx], ref["x"], xi, sg)
+
+    def agree(sel):
+        kh = sel.khat.cpu().numpy()[idx]
+        sh = sel.s_hat.cpu().numpy()[idx]
+        both = ref["flags"] == 0
+        same = both & (kh == okh)
+        per_cls = {str(c): {"n": int(np.sum(both & (cls[idx] == c))),
+                            "khat_agree": int(np.sum(same & (cls[idx] == c)))} for c in (0, 1, 2)}
+        d = np.abs(np.nan_to_num(sh[same] - osh[same], nan=0.0))
+        return {"khat_agree": int(same.sum()), "compared": int(both.sum()), "by_class": per_cls,
+                "max_elevation_diff_m": float(d.max()) if d.size else 0.0,
+                "median_elevation_diff_m": float(np.median(d[d > 0])) if np.any(d > 0) else 0.0}
+
+    line = {
+        "metric": "pixels/s of the SL1MMER chain, pre-classified (linear pass + L1 on the rest) vs L1 on every pixel",
+        "value": P / (ms_hyb / 1e3), "unit": "pixels/s", "higher_is_better": True, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_hyb, "data": "synthetic", "workload": "hybrid",
+        "config": {"workload": f"the 2^{int(np.log2(P))}-pixel patch (N=25, L=400), BF16 + FP64 refit + selection"},
+        "plain": {"value": P / (ms_plain / 1e3), "ms_per_step": ms_plain, "vs_oracle": agree(sel_plain)},
+        "hybrid": {"value": P / (ms_hyb / 1e3), "ms_per_step": ms_hyb, "vs_oracle": agree(sel_hyb),
+                   "class_frac": (np.bincount(cls, minlength=3) / P).tolist(),
+                   "skipped_frac": float(np.mean(cls < 2))},
+        "speedup": ms_plain / ms_hyb,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_blocks(args) -> None:
     """The randomized-block reading of Eqs. 13-14 (options.blocks = J) against the default
     reading (a block is a whole pixel) on the same pixels of the patch: both FP32 with the
@@ -848,7 +1015,7 @@ def main(argv=None) -> None:
                     help="stopping tolerance of the BF16 path: BF16 operands carry 2^-9 relative error, "
                          "so smaller steps are not resolved")
     ap.add_argument("--e2e-chunks", type=int, default=8, help="chunks of the end-to-end leg")
-    ap.add_argument("--workload", choices=["patch", "ragged", "detection", "blocks", "motion"], default="patch",
+    ap.add_argument("--workload", choices=["patch", "ragged", "detection", "blocks", "motion", "peaks", "hybrid"], default="patch",
                     help="patch: the headline line; ragged: the 64-stack ragged batch; detection: the "
                          "detection-rate Monte Carlo through solve + model selection (separate lines)")
     ap.add_argument("--det-per", type=int, default=5000, help="realisations per (SNR, kappa)")
@@ -869,6 +1036,10 @@ def main(argv=None) -> None:
         run_blocks(args)
     elif args.workload == "motion":
         run_motion(args)
+    elif args.workload == "peaks":
+        run_peaks(args)
+    elif args.workload == "hybrid":
+        run_hybrid(args)
     else:
         run_ours(args)
 

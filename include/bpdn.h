@@ -54,11 +54,13 @@ enum bpdn_status {
 #define BPDN_PX_KKT_FAIL 16         /* refit ran but could not certify optimality       */
 #define BPDN_PX_ZERO_SOLUTION 32    /* returned x is exactly 0                          */
 #define BPDN_PX_CERTIFIED 64        /* refit certified x as the minimiser of Eq. 6      */
+#define BPDN_PX_DEVICE_TIMEOUT 128  /* precision 1: a bounded wait for the tensor cores  */
+                                    /* ran out; x is the last accepted iterate (or 0)    */
 
 /* limits */
-#define BPDN_MAX_N 64
+#define BPDN_MAX_N 80
 #define BPDN_MAX_L 1024
-#define BPDN_MAX_SMAX 16
+#define BPDN_MAX_SMAX 32
 #define BPDN_MAX_KSEL 4  /* scatterers per pixel bpdn_select considers */
 #define BPDN_MAX_MOTION 2 /* motion dimensions of bpdn_make_operator_md */
 
@@ -69,7 +71,7 @@ typedef struct {
     float alpha0_scale;   /* alpha_0 = alpha0_scale / (2N)  (default 1)                         */
     int32_t precision;    /* 0: FP32 contraction (CUDA cores); 1: BF16 operands, FP32 accumulate */
     int32_t refit;        /* 0: none; 1: FP64 restricted solve on the support + certificate     */
-    int32_t s_max;        /* largest support the refit handles (<= BPDN_MAX_SMAX, default 16)   */
+    int32_t s_max;        /* largest support the refit handles (<= BPDN_MAX_SMAX, default 32)   */
     int32_t max_bt;       /* step cuts allowed per iteration before BT_LIMIT (default 64)        */
     int32_t tile_pixels;  /* pixels in flight per SM: 8 or 16 (0 = library choice, 16 when it fits) */
     int32_t refit_rounds; /* working-set rounds of the refit (default 4)                         */
@@ -329,6 +331,52 @@ int bpdn_select(bpdn_op_t op, const void *d_g, int64_t P, const void *d_x, const
                 double penalty, int32_t *d_khat, double *d_s_hat, void *d_gamma_hat, void *cuda_stream);
 
 /*
+ * Pre-classification before the L1 solve: the hybrid processing the paper recommends
+ * (Sec. I: a fast linear estimator for the pixels that need no super-resolution and the
+ * L1 solve only for the others; Sec. V expects a further speed-up of about 50 from it).
+ * The paper leaves the classifier to its reference; the library's reading, per pixel:
+ *   u = A^H g  (beamforming on the grid, the classic linear estimator)
+ *   class 0  2 max_l |u_l| <= lambda: x* = 0 exactly (the zero vector satisfies Eq. 6's
+ *            optimality conditions), K_hat = 0
+ *   class 1  otherwise the single-scatterer linear estimate -- s^ = the elevation in
+ *            [s_{l^-1}, s_{l^+1}] (l^ = argmax |u_l|) where |a(s)^H g| peaks,
+ *            gamma^ = a(s^)^H g / N -- when its residual r = g - gamma^ a(s^) satisfies
+ *            2 max_l |a_l^H r| <= lambda: K_hat = 1 with (s^, gamma^).  This is the linear
+ *            estimator's answer, not the minimiser of Eq. 6.
+ *   class 2  every other pixel (and any pixel with non-finite g): left to the L1 path
+ *            (bpdn_solve with the refit, then bpdn_select); K_hat = -1 here.
+ * The class decisions are taken in FP64 (FP32 beam sums, grid points within 1e-4 of a
+ * decision boundary recomputed in FP64); s^ by a safeguarded Newton iteration in FP64.
+ * Elevation-only operators (bpdn_make_operator); others are refused.
+ *
+ * d_g, P, d_lambda, lambda_per_pixel   as in bpdn_solve
+ * kmax            1..BPDN_MAX_KSEL: row length of d_s_hat / d_gamma_hat (as bpdn_select)
+ * d_class         device int32 [P] out: 0, 1 or 2
+ * d_khat          device int32 [P] out: 0, 1, or -1 for class 2
+ * d_s_hat         device float64 [P, kmax] out: s^ in column 0 for class 1, NaN elsewhere
+ * d_gamma_hat     device c128 [P, kmax] out (16-byte aligned): gamma^ for class 1, 0 elsewhere
+ * d_idx           device int64 [P] out: the class-2 pixels, in the order found (not sorted)
+ * d_count         device uint64 [1] out: how many (cleared by the call on cuda_stream)
+ * d_g_compact     device c64 [P, N] out, or NULL: row i = g of pixel d_idx[i], ready for
+ *                 bpdn_solve on the first *d_count rows
+ * Asynchronous on cuda_stream; allocates nothing.  Returns BPDN_EINVAL / BPDN_EALIGN /
+ * BPDN_ESTATE before launching anything.
+ */
+int bpdn_classify(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda, int32_t lambda_per_pixel,
+                  int32_t kmax, int32_t *d_class, int32_t *d_khat, double *d_s_hat, void *d_gamma_hat,
+                  int64_t *d_idx, uint64_t *d_count, void *d_g_compact, void *cuda_stream);
+
+/*
+ * Write the selection of the class-2 pixels (bpdn_select run on the compacted rows of
+ * bpdn_classify) into the full outputs: row i of d_khat_c / d_s_hat_c / d_gamma_hat_c goes
+ * to pixel d_idx[i], for i < P_c.  Shapes and alignment as in bpdn_select with the same
+ * kmax.  Asynchronous on cuda_stream; BPDN_EINVAL / BPDN_EALIGN before any launch.
+ */
+int bpdn_classify_merge(int64_t P_c, const int64_t *d_idx, int32_t kmax, const int32_t *d_khat_c,
+                        const double *d_s_hat_c, const void *d_gamma_hat_c, int32_t *d_khat, double *d_s_hat,
+                        void *d_gamma_hat, void *cuda_stream);
+
+/*
  * bpdn_solve without a workspace, for callers that cannot allocate device memory
  * (for example a processing chain whose host application owns every GPU buffer
  * and forbids its modules to call cudaMalloc).  The paper has no counterpart: it
@@ -338,7 +386,9 @@ int bpdn_select(bpdn_op_t op, const void *d_g, int64_t P, const void *d_x, const
  * The iteration kernel's scratch (a work counter) lives in a file-scope device
  * array of 256 bytes that every GPU loading the library keeps until the process
  * exits.  The first call on a device looks up its address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the array and
+ * make that first call before any stream capture.  The address is kept for the life
+ * of the process, so after a cudaDeviceReset of a device do not call this entry point
+ * on that device again (the kept address would be stale).  All calls share the array and
  * each clears what it uses, so calls whose work overlaps on the GPU race and must
  * be serialised by the caller.  A solve whose scratch would exceed 256 bytes is
  * rejected with BPDN_ESIZE.  No device memory is allocated or freed.

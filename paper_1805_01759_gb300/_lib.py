@@ -21,10 +21,11 @@ PX_SUPPORT_OVERFLOW = 8
 PX_KKT_FAIL = 16
 PX_ZERO_SOLUTION = 32
 PX_CERTIFIED = 64
+PX_DEVICE_TIMEOUT = 128
 
-MAX_N = 64
+MAX_N = 80
 MAX_L = 1024
-MAX_SMAX = 16
+MAX_SMAX = 32
 MAX_KSEL = 4
 MAX_MOTION = 2
 
@@ -35,7 +36,7 @@ EXPORTED = [
     "bpdn_last_error", "bpdn_version",
     "bpdn_solve_noalloc", "bpdn_backward_workspace_bytes", "bpdn_backward",
     "bpdn_solve_ragged_workspace_bytes", "bpdn_solve_ragged_workspace_bytes_for", "bpdn_solve_ragged",
-    "bpdn_select", "bpdn_make_operator_md",
+    "bpdn_select", "bpdn_make_operator_md", "bpdn_bench_peak", "bpdn_classify", "bpdn_classify_merge",
 ]
 
 
@@ -147,6 +148,12 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.bpdn_select.argtypes = [op_t, vp, i64, vp, vp, vp, vp, i32, i32, dbl, vp, vp, vp, vp]
     lib.bpdn_select.restype = ctypes.c_int
     lib.bpdn_last_error.argtypes = []
+    lib.bpdn_classify.argtypes = [op_t, vp, i64, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.bpdn_classify.restype = ctypes.c_int
+    lib.bpdn_classify_merge.argtypes = [i64, vp, i32, vp, vp, vp, vp, vp, vp, vp]
+    lib.bpdn_classify_merge.restype = ctypes.c_int
+    lib.bpdn_bench_peak.argtypes = [i32, i32, i32, i64, vp, dblp, vp]
+    lib.bpdn_bench_peak.restype = ctypes.c_int
     lib.bpdn_last_error.restype = ctypes.c_char_p
     lib.bpdn_version.argtypes = []
     lib.bpdn_version.restype = ctypes.c_char_p

@@ -9,6 +9,7 @@ library.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import math
 import dataclasses
@@ -27,6 +28,31 @@ def _ptr(t: torch.Tensor | None) -> int | None:
 def _stream(stream: torch.cuda.Stream | None) -> int:
     s = torch.cuda.current_stream() if stream is None else stream
     return s.cuda_stream
+
+
+@contextlib.contextmanager
+def _launch_on(stream: torch.cuda.Stream | None, *inputs):
+    """Make `stream` the current stream for one call's allocations and launches.
+
+    When `stream` is not the caller's current stream, it first waits for the work queued
+    on the current stream (which produced the inputs), the input tensors are recorded as
+    used on `stream` (so the caching allocator does not hand their memory to new work
+    before the launch has read them), and every temporary (workspace, lambda, contiguous
+    copies) is allocated while `stream` is current, so that it is only reused after the
+    kernels that read it."""
+    if stream is None:
+        yield
+        return
+    cur = torch.cuda.current_stream(stream.device)
+    if stream == cur:
+        yield
+        return
+    stream.wait_stream(cur)
+    for t in inputs:
+        if isinstance(t, torch.Tensor) and t.is_cuda:
+            t.record_stream(stream)
+    with torch.cuda.stream(stream):
+        yield
 
 
 class Operator:
@@ -138,6 +164,11 @@ def _check_g(op: Operator, g: torch.Tensor) -> torch.Tensor:
 def solve(op: Operator, g: torch.Tensor, lam, *, out: SolveResult | None = None,
           stream: torch.cuda.Stream | None = None, **options) -> SolveResult:
     """Algorithm 1 (+ the FP64 refit unless refit=0) for every row of g."""
+    with _launch_on(stream, g, lam):
+        return _solve(op, g, lam, out, stream, **options)
+
+
+def _solve(op, g, lam, out, stream, **options) -> SolveResult:
     lib = _lib.load()
     g = _check_g(op, g)
     P = g.shape[0]
@@ -166,6 +197,11 @@ def solve(op: Operator, g: torch.Tensor, lam, *, out: SolveResult | None = None,
 def refit(op: Operator, g: torch.Tensor, lam, x_in: torch.Tensor, *, status: torch.Tensor | None = None,
           stream: torch.cuda.Stream | None = None, **options):
     """Support extraction + FP64 refit of x_in on its own.  Returns (x, support, nsupp, status)."""
+    with _launch_on(stream, g, lam, x_in, status):
+        return _refit(op, g, lam, x_in, status, stream, **options)
+
+
+def _refit(op, g, lam, x_in, status, stream, **options):
     lib = _lib.load()
     g = _check_g(op, g)
     P = g.shape[0]
@@ -191,6 +227,11 @@ def backward(op: Operator, x: torch.Tensor, support: torch.Tensor, nsupp: torch.
 
     dL/dlambda has P entries when lam has P entries, else one (the sum over pixels).
     With status given, pixels the solve did not certify get zero derivatives."""
+    with _launch_on(stream, x, support, nsupp, dLdx, lam, status):
+        return _backward(op, x, support, nsupp, dLdx, lam, status, stream)
+
+
+def _backward(op, x, support, nsupp, dLdx, lam, status, stream):
     lib = _lib.load()
     if x.dtype != torch.complex64 or x.device.type != "cuda" or x.dim() != 2 or x.shape[1] != op.L:
         raise TypeError(f"x must be a complex64 CUDA tensor [P, {op.L}]")
@@ -230,6 +271,11 @@ def select(op: Operator, g: torch.Tensor, res: "SolveResult", *, kmax: int = _li
            penalty: float = 0.0, stream: torch.cuda.Stream | None = None) -> Selection:
     """SL1MMER model selection and parameter estimation (bpdn_select) on a solve's result
     (which must come from a solve with the refit, so that its support is written)."""
+    with _launch_on(stream, g, res.x, res.support, res.nsupp, res.status):
+        return _select(op, g, res, kmax, penalty, stream)
+
+
+def _select(op, g, res, kmax, penalty, stream) -> Selection:
     lib = _lib.load()
     g = _check_g(op, g)
     P = g.shape[0]
@@ -246,6 +292,67 @@ def select(op: Operator, g: torch.Tensor, res: "SolveResult", *, kmax: int = _li
                                float(penalty), out.khat.data_ptr(), out.s_hat.data_ptr(),
                                out.gamma_hat.data_ptr(), _stream(stream)))
     return out
+
+
+class Classes(NamedTuple):
+    """Output of classify(): cls [P] int32 (0 no scatterer, 1 one scatterer by the linear
+    estimator, 2 left to L1), the estimates of classes 0 and 1 in the layout of select()
+    (khat -1 for class 2), and the class-2 pixels: idx [P] int64 of which the first `count`
+    are valid, g_compact [P, N] their measurements in the same order."""
+    cls: torch.Tensor
+    sel: "Selection"
+    idx: torch.Tensor
+    count: torch.Tensor
+    g_compact: torch.Tensor
+
+
+def classify(op: Operator, g: torch.Tensor, lam, *, kmax: int = _lib.MAX_KSEL,
+             stream: torch.cuda.Stream | None = None) -> Classes:
+    """Pre-classification before the L1 solve (bpdn_classify)."""
+    with _launch_on(stream, g, lam):
+        lib = _lib.load()
+        g = _check_g(op, g)
+        P = g.shape[0]
+        dev = g.device
+        lam_t, pp = _lambda_tensor(lam, P, dev)
+        out = Classes(torch.empty(P, dtype=torch.int32, device=dev),
+                      Selection(torch.empty(P, dtype=torch.int32, device=dev),
+                                torch.empty((P, kmax), dtype=torch.float64, device=dev),
+                                torch.empty((P, kmax), dtype=torch.complex128, device=dev)),
+                      torch.empty(P, dtype=torch.int64, device=dev),
+                      torch.empty(1, dtype=torch.int64, device=dev),
+                      torch.empty((P, op.N), dtype=torch.complex64, device=dev))
+        _lib.check(lib.bpdn_classify(op.handle, g.data_ptr(), P, lam_t.data_ptr(), pp, kmax, out.cls.data_ptr(),
+                                     out.sel.khat.data_ptr(), out.sel.s_hat.data_ptr(), out.sel.gamma_hat.data_ptr(),
+                                     out.idx.data_ptr(), out.count.data_ptr(), out.g_compact.data_ptr(),
+                                     _stream(stream)))
+        return out
+
+
+def hybrid(op: Operator, g: torch.Tensor, lam, *, kmax: int = _lib.MAX_KSEL, penalty: float = 0.0,
+           **options):
+    """The pre-classified chain: bpdn_classify, then for the class-2 pixels only bpdn_solve
+    (with the refit) and bpdn_select, merged back by bpdn_classify_merge.  Reads the class-2
+    count back to the host once (to size the L1 batch).  Returns (Classes, Selection over all
+    pixels, SolveResult of the class-2 pixels in Classes.idx order)."""
+    lib = _lib.load()
+    c = classify(op, g, lam, kmax=kmax)
+    n = int(c.count.item())
+    sel = Selection(c.sel.khat.clone(), c.sel.s_hat.clone(), c.sel.gamma_hat.clone())
+    if n == 0:
+        return c, sel, None
+    P = g.shape[0]
+    if isinstance(lam, torch.Tensor) and lam.numel() == P:
+        lam_c = lam.to(device=g.device, dtype=torch.float32).reshape(P)[c.idx[:n]]
+    else:
+        lam_c = lam
+    gc = c.g_compact[:n]
+    res = solve(op, gc, lam_c, refit=1, **options)
+    sc = select(op, gc, res, kmax=kmax, penalty=penalty)
+    _lib.check(lib.bpdn_classify_merge(n, c.idx.data_ptr(), kmax, sc.khat.data_ptr(), sc.s_hat.data_ptr(),
+                                       sc.gamma_hat.data_ptr(), sel.khat.data_ptr(), sel.s_hat.data_ptr(),
+                                       sel.gamma_hat.data_ptr(), _stream(None)))
+    return c, sel, res
 
 
 class BPDNFunction(torch.autograd.Function):
@@ -294,32 +401,63 @@ def global_error_and_grad(num: float, den: float, dnum: float, group=None):
 
 
 def tune_lambda(op: Operator, g: torch.Tensor, gamma_true: torch.Tensor, lam0: float, *,
-                steps: int = 50, lr: float = 0.1, options: dict | None = None, group=None):
+                steps: int = 50, lr: float = 0.1, options: dict | None = None, group=None,
+                line_search: bool = True):
     """Learn one lambda by gradient descent on log lambda, minimising the relative squared
     error sum |x(lambda) - gamma_true|^2 / sum |gamma_true|^2 over pixels and grid points.
-    Under torch.distributed (pixels sharded over ranks) the sums run over every rank's
-    pixels (global_error_and_grad), so all ranks take the same steps.
+
+    The direction is the implicit gradient (bpdn_backward), which covers the error's smooth
+    part on fixed supports; the changes of support as lambda moves are jumps it does not see.
+    With line_search (the default) a step is taken only where the error, evaluated by a
+    forward solve, decreases: lr times the gradient, then half and a quarter of it; if none
+    of these lowers the error, the implicit gradient is misled by support jumps and the step
+    of the same length in the opposite direction is tried; if that fails too, lambda stays
+    and lr is halved.  Every accepted step is thus a descent of the error itself.  Without
+    line_search every step is lr times the gradient.
+
+    Under torch.distributed (pixels sharded over ranks) every sum runs over every rank's
+    pixels (global_error_and_grad), so all ranks take the same decisions and steps.
     Returns (lambda, [(lambda, error) per step])."""
     import torch.distributed as dist
     sharded = dist.is_available() and dist.is_initialized()
+    den_local = gamma_true.abs().pow(2).sum()
+
+    def error_and_grad(log_lam):
+        lam = log_lam.exp()
+        x, _ = BPDNFunction.apply(g, lam, op, options)
+        num = (x - gamma_true).abs().pow(2).sum()
+        (dnum,) = torch.autograd.grad(num, log_lam)
+        return global_error_and_grad(float(num.item()), float(den_local.item()), float(dnum.item()),
+                                     group if sharded else None)
+
+    def error_at(v: float) -> float:
+        with torch.no_grad():
+            lam = torch.tensor([math.exp(v)], dtype=torch.float32, device=g.device)
+            x, _ = BPDNFunction.apply(g, lam, op, options)
+            num = (x - gamma_true).abs().pow(2).sum()
+        return global_error_and_grad(float(num.item()), float(den_local.item()), 0.0,
+                                     group if sharded else None)[0]
+
     log_lam = torch.tensor([math.log(lam0)], dtype=torch.float32, device=g.device, requires_grad=True)
     history = []
     for _ in range(steps):
-        lam = log_lam.exp()
-        x, _ = BPDNFunction.apply(g, lam, op, options)
-        if sharded:
-            num = (x - gamma_true).abs().pow(2).sum()
-            (dnum,) = torch.autograd.grad(num, log_lam)
-            den = gamma_true.abs().pow(2).sum()
-            mse_v, grad_v = global_error_and_grad(float(num.item()), float(den.item()), float(dnum.item()), group)
-            grad = torch.tensor([grad_v], dtype=torch.float32, device=g.device)
+        err, grad = error_and_grad(log_lam)
+        cur = float(log_lam.item())
+        history.append((math.exp(cur), err))
+        step = -lr * grad
+        if not line_search:
+            nxt = cur + step
         else:
-            mse = (x - gamma_true).abs().pow(2).sum() / gamma_true.abs().pow(2).sum().clamp_min(1e-30)
-            (grad,) = torch.autograd.grad(mse, log_lam)
-            mse_v = float(mse.item())
-        history.append((float(lam.item()), mse_v))
+            nxt = None
+            for cand in (cur + step, cur + 0.5 * step, cur + 0.25 * step, cur - step):
+                if cand != cur and error_at(cand) < err:
+                    nxt = cand
+                    break
+            if nxt is None:
+                nxt = cur
+                lr *= 0.5
         with torch.no_grad():
-            log_lam -= lr * grad
+            log_lam.fill_(nxt)
     return float(log_lam.exp().item()), history
 
 

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbpdn.so")
-SOURCES = ["api.cu", "operator.cu", "rbpg.cu", "refit.cu", "backward.cu", "ragged.cu", "noalloc.cu", "select.cu", "rbpg_block.cu"]
+SOURCES = ["api.cu", "operator.cu", "rbpg.cu", "refit.cu", "backward.cu", "ragged.cu", "noalloc.cu", "select.cu", "rbpg_block.cu", "peaks.cu", "preclass.cu"]
 HEADERS = ["bpdn_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
@@ -44,7 +44,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile (if needed) and return the path of libbpdn.so."""
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    header_deps = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "bpdn.h")]
+    header_deps = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", h)
+                                                                  for h in ("bpdn.h", "bpdn_bench.h")]
     jobs = []
     objs = []
     for src in SOURCES:

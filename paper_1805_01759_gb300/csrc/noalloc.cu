@@ -13,7 +13,9 @@
 //     loads the library, until the process exits;
 //   * its device address is looked up once per device (cudaGetSymbolAddress) by
 //     the first call made with that device current -- make that first call before
-//     any stream capture;
+//     any stream capture.  The address is kept for the life of the process: after a
+//     cudaDeviceReset of that device it would be stale, so a process that resets a
+//     device must not call bpdn_solve_noalloc on it again;
 //   * every call shares the array, and each call clears the counter it needs on
 //     its own stream before the launch: calls whose work overlaps on the GPU (two
 //     streams, or two host threads) race on the counter and must be serialised by

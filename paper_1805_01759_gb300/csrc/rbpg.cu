@@ -65,6 +65,8 @@ struct SlotState {
     float4 par[TPG];         // (beta, 2 alpha, alpha lambda, transition bits)
     float alpha[TPG], Fx[TPG], lam[TPG];
     int k[TPG], nbt[TPG], nbt_it[TPG], status[TPG], nnz[TPG];
+    int abort;          // BF16: a bounded wait for the tensor cores ran out in this group
+    uint32_t abort_ph;  // the mbarrier phase that was not seen complete
 };
 
 // shared-memory layout: A (when it fits) once, then one block per group
@@ -345,13 +347,14 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 
 // Algorithm 1 for one stack, by the whole CTA, until the stack's pixels run out and every
 // slot has drained; tensor memory is allocated by the caller
-template <bool TC, bool SA>
+template <bool TC, bool SA, int NCH>
 __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, unsigned char *smem_raw)
 {
     const int G = prm.groups;
     const int N = prm.N, L = prm.L, Lpad = prm.Lpad, lda = prm.lda;
     const int NW = Lpad / 32;  // warps (blocks of 32 grid points) per group
-    constexpr int NCH = TC ? 1 : 2;  // rows n = lane + 32 c, c < NCH, per lane (BF16: N <= 32)
+    // rows n = lane + 32 c, c < NCH, per lane (BF16: N <= 32; FP32: N <= 64, or N <= 96 for three)
+    static_assert(!TC || NCH == 1, "the BF16 contraction holds 2N <= 64 terms");
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q4 = w & 3;
     int grp = 0, blk = 0, tile = 0;
@@ -400,6 +403,8 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
             sA[i] = make_float2(prm.A_re[i], prm.A_im[i]);
     }
     if (live && blk == 0) {
+        if (lane == 0)
+            S.abort = 0;
         if constexpr (TC) {
             for (int i = lane; i < 16 * kK * 2 / 4; i += 32)
                 ((uint32_t *)sBop)[i] = 0u;  // K padding of B stays zero
@@ -480,11 +485,31 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
                 q = -1;
                 break;
             }
+            if (TC && S.abort) {
+                // the group's tensor-core wait ran out: it no longer iterates, but every
+                // pixel it takes still gets x = 0 and a status that says so
+                float2 *xq = a.x + (size_t)q * L;
+                for (int ll = lane; ll < L; ll += 32)
+                    xq[ll] = make_float2(0.f, 0.f);
+                if (lane == 0) {
+                    a.status[q] = BPDN_PX_DEVICE_TIMEOUT | BPDN_PX_ZERO_SOLUTION;
+                    a.iters[q] = 0;
+                    if (a.nbt)
+                        a.nbt[q] = 0;
+                    if (a.nsupp)
+                        a.nsupp[q] = 0;
+                }
+                continue;
+            }
             const float2 *gq = a.g + (size_t)q * N;
-            const float2 g0 = (lane < N) ? gq[lane] : make_float2(0.f, 0.f);
-            const float2 g1 = (NCH > 1 && lane + 32 < N) ? gq[lane + 32] : make_float2(0.f, 0.f);
-            const bool allfin = __all_sync(0xffffffffu, isfinite(g0.x) && isfinite(g0.y) && isfinite(g1.x) &&
-                                                            isfinite(g1.y));
+            float2 gr[NCH];
+            bool fin = true;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                gr[c] = (lane + 32 * c < N) ? gq[lane + 32 * c] : make_float2(0.f, 0.f);
+                fin = fin && isfinite(gr[c].x) && isfinite(gr[c].y);
+            }
+            const bool allfin = __all_sync(0xffffffffu, fin);
             if (!allfin || a.max_iter <= 0) {
                 // non-finite g (or no iteration allowed): x = 0 at once
                 float2 *xq = a.x + (size_t)q * L;
@@ -505,7 +530,7 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
             for (int c = 0; c < NCH; ++c) {
                 const int n = lane + 32 * c;
                 if (n < N) {
-                    const float2 gg = c ? g1 : g0;
+                    const float2 gg = gr[c];
                     sG[p * N + n] = gg;
                     sAx[p * N + n] = make_float2(0.f, 0.f);
                     sAxp[p * N + n] = make_float2(0.f, 0.f);
@@ -513,7 +538,10 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
                     put_r(p, n, -gg.x, -gg.y);
                 }
             }
-            float gg2 = g0.x * g0.x + g0.y * g0.y + g1.x * g1.x + g1.y * g1.y;
+            float gg2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+                gg2 += gr[c].x * gr[c].x + gr[c].y * gr[c].y;
 #pragma unroll
             for (int off = 16; off >= 1; off >>= 1)
                 gg2 += __shfl_xor_sync(0xffffffffu, gg2, off);
@@ -562,8 +590,9 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
         for (int p = 0; p < TPG; ++p)
             any |= __float_as_int(S.par[p].w);
         const bool running = (any & T_ACTIVE) != 0;
+        const bool aborted = TC && S.abort != 0;  // read after the group barrier: one view
         if constexpr (TC) {
-            if (running && blk == 0 && lane == 0) {
+            if (running && !aborted && blk == 0 && lane == 0) {
                 const uint32_t b0 = smem_u32(sBop);
                 for (int t = 0; t < T; ++t) {
                     const uint32_t d = tmem + colD + 16 * T * grp + 16 * t;
@@ -610,9 +639,16 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
         // ---------------- gradient sum_n conj(A_nl) r_n -----------------------------------------
         float2 gx[TPG / 2], gy[TPG / 2];  // FP32 variant: slot pairs (2q, 2q+1), re and im
         if constexpr (TC) {
-            if (!mbar_wait(mbar, mma_phase) && a.err)
-                atomicExch(a.err, 1);
-            mma_phase ^= 1u;
+            if (!aborted) {
+                if (!mbar_wait(mbar, mma_phase)) {
+                    // no further MMAs or waits in this group; DE below ends its pixels
+                    S.abort = 1;
+                    S.abort_ph = mma_phase;
+                    if (a.err)
+                        atomicExch(a.err, 1);
+                }
+                mma_phase ^= 1u;
+            }
             tc_fence_after();
         } else {
 #pragma unroll
@@ -686,8 +722,9 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
                     if (lane == 0)
                         sMask[p * NW + blk] = bal;
                     if (bal) {
-                        // this block's share of A xbar, ascending l; lane n owns rows n, n + 32
+                        // this block's share of A xbar, ascending l; lane n owns rows n + 32 c
                         float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+                        float2 acc2 = make_float2(0.f, 0.f);
                         // two nonzeros per trip (two loads in flight), still ascending l
                         unsigned m = bal;
                         while (m) {
@@ -721,11 +758,23 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
                                     acc1.y = fmaf(a1.x, xi1, fmaf(a1.y, xr1, acc1.y));
                                 }
                             }
+                            if (NCH > 2 && lane + 64 < N) {
+                                const float2 a0 = Aat(lane + 64, 32 * blk + j0);
+                                acc2.x = fmaf(a0.x, xr0, fmaf(-a0.y, xi0, acc2.x));
+                                acc2.y = fmaf(a0.x, xi0, fmaf(a0.y, xr0, acc2.y));
+                                if (two) {
+                                    const float2 a1 = Aat(lane + 64, 32 * blk + j1);
+                                    acc2.x = fmaf(a1.x, xr1, fmaf(-a1.y, xi1, acc2.x));
+                                    acc2.y = fmaf(a1.x, xi1, fmaf(a1.y, xr1, acc2.y));
+                                }
+                            }
                         }
                         if (lane < N)
                             sPart[(p * NW + blk) * N + lane] = acc0;
                         if (NCH > 1 && lane + 32 < N)
                             sPart[(p * NW + blk) * N + lane + 32] = acc1;
+                        if (NCH > 2 && lane + 64 < N)
+                            sPart[(p * NW + blk) * N + lane + 64] = acc2;
                     }
                     const float ex = bx - yx, ey = by - yy;
                     dd = fmaf(ex, ex, ey * ey);
@@ -761,11 +810,14 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
                     S.par[p].w = __int_as_float(0);
                 continue;
             }
-            // A xbar and nnz over the blocks in ascending order; lane n owns rows n, n + 32
+            // A xbar and nnz over the blocks in ascending order; lane n owns rows n + 32 c
             const uint32_t mw = (lane < NW) ? sMask[p * NW + lane] : 0u;
             const int nnz = (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(mw));
             unsigned wm = __ballot_sync(0xffffffffu, mw != 0u);
-            float2 axb[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            float2 axb[NCH];
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+                axb[c] = make_float2(0.f, 0.f);
             while (wm) {
                 const int b = __ffs(wm) - 1;
                 wm &= wm - 1;
@@ -782,7 +834,10 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
             // sums over the grid: lane b < NW holds block b's partial sums
             float4 rd = (lane < NW) ? sRed[lane * TPG + p] : make_float4(0.f, 0.f, 0.f, 0.f);
             float lhs = 0.f, res = 0.f;
-            float2 gg[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            float2 gg[NCH];
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+                gg[c] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int c = 0; c < NCH; ++c) {
                 const int n = lane + 32 * c;
@@ -806,7 +861,8 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
             }
             const float dd = rd.x, l1 = rd.y, dx = rd.z, xn = rd.w;
             const float al = S.alpha[p];
-            const bool bt_ok = lhs <= dd / (2.f * al);
+            const bool dead = TC && S.abort != 0;  // the gradient of this sweep is stale
+            const bool bt_ok = dead || lhs <= dd / (2.f * al);
             const int nbt_it = S.nbt_it[p];
             __syncwarp();
             if (!bt_ok && nbt_it < a.max_bt) {
@@ -821,10 +877,10 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
                 continue;
             }
             const float Fb = fmaf(S.lam[p], l1, res);
-            const bool accepted = (Fb <= S.Fx[p]);
-            const bool conv = (dx <= tol2 * xn) || (dx == 0.f);
+            const bool accepted = !dead && (Fb <= S.Fx[p]);
+            const bool conv = !dead && ((dx <= tol2 * xn) || (dx == 0.f));
             const int k = S.k[p];
-            const bool fin = conv || (k >= a.max_iter);
+            const bool fin = dead || conv || (k >= a.max_iter);
             // N-space state: A x^{k-1} <- A x^k, A x^k <- A xbar (accepted); for the next
             // iteration A y = A x + beta (A x - A x_prev), r = A y - g
             const float beta_n = (float)(k - 1) / (float)(k + 2);
@@ -852,6 +908,8 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
                     st |= BPDN_PX_BT_LIMIT;
                 if (fin && !conv)
                     st |= BPDN_PX_NOT_CONVERGED;
+                if (dead)
+                    st |= BPDN_PX_DEVICE_TIMEOUT;
                 int nz = S.nnz[p];
                 if (accepted) {
                     S.Fx[p] = Fb;
@@ -887,16 +945,21 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
         tc_fence_before();
         group_sync(grp, 32 * NW);
     }
-    // this group has drained and its last MMA was waited for: retire its mbarrier
+    // this group has drained and its last MMA was waited for: retire its mbarrier.  After
+    // a wait that ran out, give the MMA that was not seen complete one more bounded wait,
+    // so that it no longer writes tensor memory or arrives on the barrier afterwards.
     if constexpr (TC) {
-        if (blk == 0 && lane == 0)
+        if (blk == 0 && lane == 0) {
+            if (S.abort)
+                (void)mbar_wait(mbar, S.abort_ph);
             asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mbar) : "memory");
+        }
     }
 }
 
 // The persistent kernel: every CTA walks the launch's stacks in order and works on
 // each one it may take (blockIdx.x < ctas) while that stack has pixels left.
-template <bool TC, bool SA, int MAXT>
+template <bool TC, bool SA, int MAXT, int NCH>
 __global__ void __launch_bounds__(MAXT, 1) k_rbpg(const __grid_constant__ Params prm)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -923,7 +986,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_rbpg(const __grid_constant__ Params
         __syncthreads();  // everyone has read s_go before it is written again
         if (!go)
             continue;  // the other CTAs took every pixel of this stack
-        run_stack<TC, SA>(sd, tmem, smem_raw);
+        run_stack<TC, SA, NCH>(sd, tmem, smem_raw);
         tc_fence_before();
         __syncthreads();  // every group of this stack has drained; no MMA in flight
         tc_fence_after();
@@ -976,13 +1039,14 @@ const char *make_plan(const OpHandle &op, bool tc, int groups, int max_smem, Pla
                   : "the iteration kernel's shared memory does not fit (N and L too large)";
 }
 
-template <bool TC, bool SA, int MAXT>
+template <bool TC, bool SA, int MAXT, int NCH>
 cudaError_t launch_variant(const Params &prm, int threads, int grid, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_rbpg<TC, SA, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_rbpg<TC, SA, MAXT, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    k_rbpg<TC, SA, MAXT><<<grid, threads, smem, s>>>(prm);
+    k_rbpg<TC, SA, MAXT, NCH><<<grid, threads, smem, s>>>(prm);
     return cudaGetLastError();
 }
 
@@ -1010,7 +1074,8 @@ cudaError_t launch_rbpg_batch(const OpHandle *const *ops, const SolveLaunch *as,
         Plan pl;
     };
     // kernel variant of a stack: precision, where A lives, launch bound
-    std::vector<Item> byvar[8];
+    // kernel variant: precision, rows per lane, where A lives, launch bound
+    std::vector<Item> byvar[16];
     for (int i = 0; i < n; ++i) {
         if (as[i].P <= 0)
             continue;
@@ -1019,10 +1084,11 @@ cudaError_t launch_rbpg_batch(const OpHandle *const *ops, const SolveLaunch *as,
         const bool tc = (as[i].precision == 1);
         if (make_plan(*ops[i], tc, as[i].groups, max_smem, &it.pl)[0] != '\0')
             return cudaErrorInvalidValue;
-        byvar[(tc ? 4 : 0) + (it.pl.smem_a ? 2 : 0) + (it.pl.threads > 832 ? 1 : 0)].push_back(it);
+        const bool wide = ops[i]->N > 64;
+        byvar[(tc ? 8 : 0) + (wide ? 4 : 0) + (it.pl.smem_a ? 2 : 0) + (it.pl.threads > 832 ? 1 : 0)].push_back(it);
     }
     std::unique_ptr<Params> prm(new Params);
-    for (int v = 0; v < 8; ++v) {
+    for (int v = 0; v < 16; ++v) {
         std::vector<Item> &list = byvar[v];
         // small stacks first: the large pools at the end absorb the CTAs' uneven progress
         std::stable_sort(list.begin(), list.end(), [&](const Item &x, const Item &y) { return as[x.i].P < as[y.i].P; });
@@ -1055,15 +1121,21 @@ cudaError_t launch_rbpg_batch(const OpHandle *const *ops, const SolveLaunch *as,
             // one CTA per SM: each CTA allocates all 512 tensor-memory columns
             if (smem < (size_t)max_smem / 2 + 1024)
                 smem = (size_t)max_smem / 2 + 1024;
-            const bool tc = (v & 4) != 0, sa = (v & 2) != 0, big = (v & 1) != 0;
+            const bool tc = (v & 8) != 0, wide = (v & 4) != 0, sa = (v & 2) != 0, big = (v & 1) != 0;
             if (tc)
-                e = launch_variant<true, true, 832>(*prm, threads, grid, smem, s);
+                e = launch_variant<true, true, 832, 1>(*prm, threads, grid, smem, s);
+            else if (!wide && sa)
+                e = big ? launch_variant<false, true, 1024, 2>(*prm, threads, grid, smem, s)
+                        : launch_variant<false, true, 832, 2>(*prm, threads, grid, smem, s);
+            else if (!wide)
+                e = big ? launch_variant<false, false, 1024, 2>(*prm, threads, grid, smem, s)
+                        : launch_variant<false, false, 832, 2>(*prm, threads, grid, smem, s);
             else if (sa)
-                e = big ? launch_variant<false, true, 1024>(*prm, threads, grid, smem, s)
-                        : launch_variant<false, true, 832>(*prm, threads, grid, smem, s);
+                e = big ? launch_variant<false, true, 1024, 3>(*prm, threads, grid, smem, s)
+                        : launch_variant<false, true, 832, 3>(*prm, threads, grid, smem, s);
             else
-                e = big ? launch_variant<false, false, 1024>(*prm, threads, grid, smem, s)
-                        : launch_variant<false, false, 832>(*prm, threads, grid, smem, s);
+                e = big ? launch_variant<false, false, 1024, 3>(*prm, threads, grid, smem, s)
+                        : launch_variant<false, false, 832, 3>(*prm, threads, grid, smem, s);
             if (e != cudaSuccess)
                 return e;
         }

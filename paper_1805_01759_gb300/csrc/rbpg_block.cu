@@ -326,6 +326,8 @@ const char *rbpg_block_check(const OpHandle &op, int blocks, int max_smem)
 {
     if (blocks < 2 || blocks > 8)
         return "blocks must lie in 2..8";
+    if (op.N > 64)
+        return "the randomized-block kernel keeps two rows of N per lane: N <= 64";
     if (op.L < blocks)
         return "fewer grid points than blocks";
     if ((size_t)WPB * blk_layout(op.N, op.L, blocks).bytes > (size_t)max_smem)

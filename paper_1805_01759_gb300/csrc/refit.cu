@@ -36,13 +36,20 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "bpdn_internal.h"
 
 namespace bpdn {
 
 namespace {
 
-constexpr int KW = kRefitMax;  // working-set capacity (<= 16, so 2|W| <= 32 lanes)
+// working-set capacities: the fast path holds 16 grid points (2|W| <= 32 real unknowns, one
+// per lane); the wide pass, for the pixels the fast path leaves uncertified, holds 32
+// (2|W| <= 64, two unknowns per lane)
+constexpr int KWF = 16;
+constexpr int KWW = 32;
+static_assert(KWW == kRefitMax, "the wide pass covers the library's largest s_max");
 constexpr int kFastRounds32 = 15;
 // FP32 phase tolerance, near FP32 resolution: every FP32 step saved here costs ~5x in FP64
 constexpr float kTol32 = 3e-6f;
@@ -91,7 +98,7 @@ __device__ __forceinline__ T warp_max(T v)
 }
 
 // Working storage of one restricted solve in precision T.
-template <typename T>
+template <typename T, int KW>
 struct Solve {
     C2<T> G[KW][KW];
     float J[2 * KW][2 * KW + 1];  // Newton system in FP32, right-hand side in column n2
@@ -103,10 +110,11 @@ struct Solve {
 
 // Everything one pixel (one warp) keeps in shared memory.  The FP32 and FP64
 // solves never run at the same time and share storage.
+template <int KW>
 struct PixelSmem {
     union {
-        Solve<double> s64;
-        Solve<float> s32;
+        Solve<double, KW> s64;
+        Solve<float, KW> s32;
     };
     double2 *g;   // [N] g in FP64       (these three follow the struct, sized by N)
     double2 *rr;  // [N] A_W z - g (FP64)
@@ -118,9 +126,10 @@ struct PixelSmem {
 };
 
 // shared memory of one pixel: the struct, then g, rr (FP64) and rf (FP32) of length N
+template <int KW>
 __host__ __device__ inline size_t pixel_smem_bytes(int N)
 {
-    const size_t b = sizeof(PixelSmem) + (size_t)N * (sizeof(double2) * 2 + sizeof(float2));
+    const size_t b = sizeof(PixelSmem<KW>) + (size_t)N * (sizeof(double2) * 2 + sizeof(float2));
     return (b + 15) & ~(size_t)15;
 }
 
@@ -128,7 +137,8 @@ constexpr int WARPS = 1;  // pixels (warps) per block
 
 // G_ij = h(l_i - l_j), c_i = a_{l_i}^H g in precision T
 // c_i = a_{l_i}^H g in FP64 for the current W (lane i), into P.c64
-__device__ __noinline__ void load_c(PixelSmem &P, const double2 *__restrict__ A64, int N, int L, int lane)
+template <int KW>
+__device__ __noinline__ void load_c(PixelSmem<KW> &P, const double2 *__restrict__ A64, int N, int L, int lane)
 {
     if (lane < P.m) {
         const int l = P.W[lane];
@@ -145,8 +155,8 @@ __device__ __noinline__ void load_c(PixelSmem &P, const double2 *__restrict__ A6
 
 // G_ij = h(l_i - l_j) from the Toeplitz generator, or (no generator: a multi-component
 // grid) sum_n conj(A_{n l_i}) A_{n l_j} from the FP64 operator
-template <typename T>
-__device__ __noinline__ void load_Gc(Solve<T> &S, const PixelSmem &P, const double2 *__restrict__ A64,
+template <typename T, int KW>
+__device__ __noinline__ void load_Gc(Solve<T, KW> &S, const PixelSmem<KW> &P, const double2 *__restrict__ A64,
                                      const double2 *__restrict__ h, int N, int L, int lane)
 {
     const int m = P.m;
@@ -171,8 +181,8 @@ __device__ __noinline__ void load_Gc(Solve<T> &S, const PixelSmem &P, const doub
 }
 
 // (G z)_i
-template <typename T>
-__device__ __forceinline__ C2<T> gz_row(const Solve<T> &S, int i, int m, const C2<T> *z)
+template <typename T, int KW>
+__device__ __forceinline__ C2<T> gz_row(const Solve<T, KW> &S, int i, int m, const C2<T> *z)
 {
     C2<T> acc = mk<T>(T(0), T(0));
     for (int j = 0; j < m; ++j)
@@ -181,8 +191,8 @@ __device__ __forceinline__ C2<T> gz_row(const Solve<T> &S, int i, int m, const C
 }
 
 // objective over W (|z| smoothed by eps; eps = 0 is exact), without the constant ||g||^2
-template <typename T>
-__device__ __noinline__ T objective(const Solve<T> &S, int m, const C2<T> *z, T lam, T eps, int lane)
+template <typename T, int KW>
+__device__ __noinline__ T objective(const Solve<T, KW> &S, int m, const C2<T> *z, T lam, T eps, int lane)
 {
     T v = T(0);
     if (lane < m) {
@@ -196,8 +206,8 @@ __device__ __noinline__ T objective(const Solve<T> &S, int m, const C2<T> *z, T 
 
 // gam = 2 (G z - c); returns the optimality residual
 //   max( max_{z_i != 0} |gam_i + lam u_i| / lam,  max_{z_i = 0} (|gam_i| / lam - 1) )
-template <typename T>
-__device__ __noinline__ T optimality(Solve<T> &S, int m, T lam, int lane)
+template <typename T, int KW>
+__device__ __noinline__ T optimality(Solve<T, KW> &S, int m, T lam, int lane)
 {
     T res = T(0);
     if (lane < m) {
@@ -221,8 +231,8 @@ __device__ __noinline__ T optimality(Solve<T> &S, int m, T lam, int lane)
 
 // One sweep of exact coordinate minimisations:
 //   z_i <- S_{lam/2}(c_i - sum_{j != i} G_ij z_j) / G_ii
-template <typename T>
-__device__ __noinline__ void cd_sweep(Solve<T> &S, int m, T lam, int lane)
+template <typename T, int KW>
+__device__ __noinline__ void cd_sweep(Solve<T, KW> &S, int m, T lam, int lane)
 {
     for (int i = 0; i < m; ++i) {
         C2<T> t = mk<T>(T(0), T(0));
@@ -247,8 +257,8 @@ __device__ __noinline__ void cd_sweep(Solve<T> &S, int m, T lam, int lane)
 // pivoting with lanes over columns (one reciprocal per pivot), then column-wise
 // back substitution with lanes over rows.  Lane i returns x_i.  `ok` is false on
 // a non-positive pivot.
-template <typename T>
-__device__ __noinline__ T solve_spd(Solve<T> &S, int n2, int lane, bool &ok)
+template <typename T, int KW>
+__device__ __noinline__ T solve_spd(Solve<T, KW> &S, int n2, int lane, bool &ok)
 {
     const int rc = (n2 < 32) ? n2 : 0;  // lane that owns the right-hand-side column
     ok = true;
@@ -293,12 +303,78 @@ __device__ __noinline__ T solve_spd(Solve<T> &S, int n2, int lane, bool &ok)
     return (T)b;
 }
 
+// The same solve for systems of up to 64 unknowns (the wide pass): lane i owns
+// columns i and i + 32 during the elimination, and the right-hand side, stored in
+// column n2, is owned like any other column (by lane n2 mod 32); the back substitution
+// keeps rows i and i + 32 in lane i.  Returns x_i in x0 and x_{i+32} in x1.
+template <typename T, int KW>
+__device__ __noinline__ void solve_spd_wide(Solve<T, KW> &S, int n2, int lane, bool &ok, T &x0, T &x1)
+{
+    static_assert(2 * KW <= 64, "two rows per lane");
+    ok = true;
+    x0 = x1 = T(0);
+    for (int k = 0; k < n2; ++k) {
+        __syncwarp();
+        const float piv = S.J[k][k];
+        if (!(piv > 0.f)) {
+            ok = false;
+            return;
+        }
+        const float ip = 1.f / piv;
+        // this lane's columns still being eliminated (the right-hand side, column n2, included)
+        int col[3];
+        float pc[3];
+#pragma unroll
+        for (int h = 0; h < 3; ++h) {
+            const int c = lane + 32 * h;
+            col[h] = (c > k && c <= n2) ? c : -1;
+            pc[h] = (col[h] >= 0) ? S.J[k][c] : 0.f;
+        }
+        if (lane == 0)
+            S.inv[k] = ip;
+        for (int i = k + 1; i < n2; i += 4) {
+            float f[4], v[4][3];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool in = (i + u < n2);
+                f[u] = in ? S.J[i + u][k] * ip : 0.f;
+#pragma unroll
+                for (int h = 0; h < 3; ++h)
+                    v[u][h] = (in && col[h] >= 0) ? S.J[i + u][col[h]] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int h = 0; h < 3; ++h)
+                    if (i + u < n2 && col[h] >= 0)
+                        S.J[i + u][col[h]] = v[u][h] - f[u] * pc[h];
+        }
+    }
+    __syncwarp();
+    float b0 = (lane < n2) ? S.J[lane][n2] : 0.f;
+    float b1 = (lane + 32 < n2) ? S.J[lane + 32][n2] : 0.f;
+    for (int k = n2 - 1; k >= 0; --k) {
+        const float src = (k >= 32) ? b1 : b0;  // k is the same in every lane
+        const float xk = __shfl_sync(0xffffffffu, src, k & 31) * S.inv[k];
+        if (lane < k)
+            b0 -= S.J[lane][k] * xk;
+        else if (lane == k)
+            b0 = xk;
+        if (lane + 32 < k)
+            b1 -= S.J[lane + 32][k] * xk;
+        else if (lane + 32 == k)
+            b1 = xk;
+    }
+    x0 = (T)b0;
+    x1 = (T)b1;
+}
+
 // Newton direction for the objective restricted to the nonzero coordinates of z
 // (eps = 0) or for the smoothed objective over all of W (eps > 0).  Writes S.dz
 // (zero off the variables) and returns the directional derivative (negative for
 // a descent direction), or +1 when the system could not be solved.
-template <typename T>
-__device__ __noinline__ T newton_dir(Solve<T> &S, int m, const C2<T> *z, T lam, T eps, int lane,
+template <typename T, int KW>
+__device__ __noinline__ T newton_dir(Solve<T, KW> &S, int m, const C2<T> *z, T lam, T eps, int lane,
                                      bool have_gam = false)
 {
     const bool use = (lane < m) && (eps > T(0) || cnz(z[lane]));
@@ -322,6 +398,7 @@ __device__ __noinline__ T newton_dir(Solve<T> &S, int m, const C2<T> *z, T lam, 
         S.u1[lane] = zi.y * iq;
     }
     __syncwarp();
+    if constexpr (KW <= 16) {
     // lane 2b + cb fills column 2b + cb, two rows (re, im of variable a) per step
     if (lane < n2) {
         const int b = lane >> 1, cb = lane & 1;
@@ -375,6 +452,73 @@ __device__ __noinline__ T newton_dir(Solve<T> &S, int m, const C2<T> *z, T lam, 
         S.dz[S.T_[lane]] = mk<T>(dre, dim);
     __syncwarp();
     return warp_sum((lane < n2) ? gcomp * d : T(0));
+    } else {
+    // lane i fills columns i and i + 32 (2b + cb: re/im part cb of variable b)
+    for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h;
+        if (c < n2) {
+            const int b = c >> 1, cb = c & 1;
+            const int tb = S.T_[b];
+            const T wc = cb ? S.u1[b] : S.u0[b];
+            for (int a = 0; a < nt; ++a) {
+                const C2<T> g = S.G[S.T_[a]][tb];
+                T v0 = T(2) * (cb == 0 ? g.x : -g.y);
+                T v1 = T(2) * (cb == 0 ? g.y : g.x);
+                if (a == b) {
+                    const T sc = S.q[a];
+                    v0 += sc * ((cb == 0 ? T(1) : T(0)) - S.u0[a] * wc);
+                    v1 += sc * ((cb == 1 ? T(1) : T(0)) - S.u1[a] * wc);
+                }
+                S.J[2 * a][c] = (float)v0;
+                S.J[2 * a + 1][c] = (float)v1;
+            }
+        }
+    }
+    __syncwarp();
+    if (sizeof(T) == 4) {
+        // the Levenberg-Marquardt shift of the FP32 phase, as in the fast path
+        const float dg0 = (lane < n2) ? S.J[lane][lane] : 0.f;
+        const float dg1 = (lane + 32 < n2) ? S.J[lane + 32][lane + 32] : 0.f;
+        const float mx = warp_max(fmaxf(dg0, dg1));
+        if (lane < n2)
+            S.J[lane][lane] = dg0 + 1e-7f * mx;
+        if (lane + 32 < n2)
+            S.J[lane + 32][lane + 32] = dg1 + 1e-7f * mx;
+    }
+    T gc[2] = {T(0), T(0)};
+    for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h;
+        if (c < n2) {
+            const int a = c >> 1;
+            const int ia = S.T_[a];
+            const T w = (c & 1) ? S.u1[a] : S.u0[a];
+            gc[h] = ((c & 1) ? S.gam[ia].y : S.gam[ia].x) + lam * w;
+            S.J[c][n2] = (float)(-gc[h]);
+        }
+    }
+    bool ok;
+    T d0, d1;
+    solve_spd_wide(S, n2, lane, ok, d0, d1);
+    if (!ok)
+        return T(1);
+    if (lane < m)
+        S.dz[lane] = mk<T>(T(0), T(0));
+    __syncwarp();
+    // variable a takes rows 2a and 2a + 1, held by lane 2a mod 32 in register (2a) / 32
+    const int r0 = (2 * lane) & 31, r1 = (2 * lane + 1) & 31;
+    const T e0 = __shfl_sync(0xffffffffu, d0, r0), f0 = __shfl_sync(0xffffffffu, d1, r0);
+    const T e1 = __shfl_sync(0xffffffffu, d0, r1), f1 = __shfl_sync(0xffffffffu, d1, r1);
+    const bool hi = (2 * lane) >= 32;
+    if (lane < nt)
+        S.dz[S.T_[lane]] = mk<T>(hi ? f0 : e0, hi ? f1 : e1);
+    __syncwarp();
+    T sl = T(0);
+    if (lane < n2)
+        sl += gc[0] * d0;
+    if (lane + 32 < n2)
+        sl += gc[1] * d1;
+    return warp_sum(sl);
+    }
 }
 
 // does the segment z_i + s dz_i, s in [0, t], come within a tenth of |z_i| of zero?
@@ -395,8 +539,8 @@ __device__ __forceinline__ bool passes_zero(C2<T> zi, C2<T> d, T t)
 }
 
 // coordinate sweeps alternating with Newton steps (see the file header)
-template <typename T>
-__device__ __noinline__ bool fast_path(Solve<T> &S, int m, T lam, int lane, int max_outer, T tol)
+template <typename T, int KW>
+__device__ __noinline__ bool fast_path(Solve<T, KW> &S, int m, T lam, int lane, int max_outer, T tol)
 {
     for (int outer = 0; outer < max_outer; ++outer) {
         // the FP64 phase starts from the FP32 answer, whose support is settled: Newton first.
@@ -491,8 +635,8 @@ __device__ __noinline__ bool fast_path(Solve<T> &S, int m, T lam, int lane, int 
 // damped Newton on the smoothed objective for eps = e0, e0/10, ..., e1 (times the
 // scale of z), at most maxit steps per level; then coordinates below 1e-6 of the
 // scale are set to zero
-template <typename T>
-__device__ __noinline__ void continuation(Solve<T> &S, int m, T lam, int lane, T e0, T e1, int maxit)
+template <typename T, int KW>
+__device__ __noinline__ void continuation(Solve<T, KW> &S, int m, T lam, int lane, T e0, T e1, int maxit)
 {
     T sc = warp_max((lane < m) ? sqrt(cabs2(S.z[lane])) : T(0));
     sc = fmax(sc, T(1e-3));
@@ -527,8 +671,8 @@ __device__ __noinline__ void continuation(Solve<T> &S, int m, T lam, int lane, T
 // Newton steps on the nonzero coordinates while no modulus passes near zero and the
 // residual at least halves.  true when the residual reaches tol; false hands over to
 // fast_path.  Far less code and FP64 work than fast_path's sweeps and line searches.
-template <typename T>
-__device__ __noinline__ bool newton_refine(Solve<T> &S, int m, T lam, int lane, int maxit, T tol)
+template <typename T, int KW>
+__device__ __noinline__ bool newton_refine(Solve<T, KW> &S, int m, T lam, int lane, int maxit, T tol)
 {
     T prev = T(1e300);
     for (int it = 0; it < maxit; ++it) {
@@ -553,13 +697,14 @@ __device__ __noinline__ bool newton_refine(Solve<T> &S, int m, T lam, int lane, 
 
 // Step 2 on the current W from the start values in P.zkeep: FP32 support search,
 // FP64 finish.  The FP64 answer is left in P.zkeep.  Returns true on convergence.
-__device__ __noinline__ void fp32_phase(PixelSmem &P, const double2 *A64, const double2 *h, int N, int L,
+template <int KW>
+__device__ __noinline__ void fp32_phase(PixelSmem<KW> &P, const double2 *A64, const double2 *h, int N, int L,
                                         double lam, int lane)
 {
     const int m = P.m;
     const double2 start = (lane < m) ? P.zkeep[lane] : make_double2(0.0, 0.0);
     {
-        Solve<float> &S = P.s32;
+        Solve<float, KW> &S = P.s32;
         load_Gc(S, P, A64, h, N, L, lane);
         if (lane < m)
             S.z[lane] = mk<float>((float)start.x, (float)start.y);
@@ -577,11 +722,12 @@ __device__ __noinline__ void fp32_phase(PixelSmem &P, const double2 *A64, const 
     }
 }
 
-__device__ __noinline__ bool fp64_phase(PixelSmem &P, const double2 *A64, const double2 *h, int N, int L,
+template <int KW>
+__device__ __noinline__ bool fp64_phase(PixelSmem<KW> &P, const double2 *A64, const double2 *h, int N, int L,
                                         double lam, int lane, double2 start)
 {
     const int m = P.m;
-    Solve<double> &S = P.s64;
+    Solve<double, KW> &S = P.s64;
     load_Gc(S, P, A64, h, N, L, lane);
     if (lane < m)
         S.z[lane] = mk<double>(P.zkeep[lane].x, P.zkeep[lane].y);
@@ -607,7 +753,8 @@ __device__ __noinline__ bool fp64_phase(PixelSmem &P, const double2 *A64, const 
     return ok;
 }
 
-__device__ __noinline__ bool restricted_minimiser(PixelSmem &P, const double2 *A64, const double2 *h, int N,
+template <int KW>
+__device__ __noinline__ bool restricted_minimiser(PixelSmem<KW> &P, const double2 *A64, const double2 *h, int N,
                                      int L, double lam, int lane)
 {
     const int m = P.m;
@@ -619,7 +766,8 @@ __device__ __noinline__ bool restricted_minimiser(PixelSmem &P, const double2 *A
     return fp64_phase(P, A64, h, N, L, lam, lane, start);
 }
 
-__device__ void sort_W(PixelSmem &P)
+template <int KW>
+__device__ void sort_W(PixelSmem<KW> &P)
 {
     for (int i = 1; i < P.m; ++i) {
         const int w = P.W[i];
@@ -645,46 +793,36 @@ struct SplitScratch {
     float2 *z;    // [P][16]
     int *pend;    // [P]: 1 when launch 3 continues the pixel
     double2 *zs;  // [P][16]
+    unsigned long long *queue;  // [2]: work counters of the scan launches (phases 3 and 4)
 };
 
-// PH 0: the whole refit in one launch.  PH 1: working set and the FP32 support search of
-// round 0, into the scratch.  PH 2: from the scratch, the FP64 finish and the certificate
-// of round 0; a pixel the certificate sends to another round is handed on, the others get
-// their outputs.  PH 3: the further rounds (both precisions) of the handed-on pixels only.
+// Phases of the refit of one pixel (one warp):
+//   PH 0  the whole refit (fast path, working set <= 16);
+//   PH 1  working set and the FP32 support search of round 0, into the scratch;
+//   PH 2  from the scratch, the FP64 finish and the certificate of round 0; a pixel the
+//         certificate sends to another round is handed on, the others get their outputs;
+//   PH 3  the further rounds (both precisions) of the handed-on pixels;
+//   PH 4  the wide pass: the whole refit again with a working set of up to 32 grid points,
+//         for a pixel the fast path left with SUPPORT_OVERFLOW or KKT_FAIL (its output x,
+//         which the fast path left equal to the iterate, is the input).
 // Splitting keeps each launch's executed code small: one fused launch stalled on
 // instruction fetch while the warps of an SM ran different phases.
-template <int PH>
-__global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const double2 *__restrict__ A64,
-                                                      const double2 *__restrict__ h,
-                                                      const float *__restrict__ A_re,
-                                                      const float *__restrict__ A_im, int N,
-                                                      int L, int lda, RefitLaunch a)
+template <int PH, int KW>
+__device__ __forceinline__ void refit_pixel(PixelSmem<KW> &P, const long long p, const SplitScratch &sc,
+                                            const double2 *__restrict__ A64, const double2 *__restrict__ h,
+                                            const float *__restrict__ A_re, const float *__restrict__ A_im,
+                                            const int N, const int L, const int lda, const RefitLaunch &a,
+                                            const int lane)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *pbase = smem_raw + (size_t)warp * pixel_smem_bytes(N);
-    PixelSmem &P = *(PixelSmem *)pbase;
-    const long long p = (long long)blockIdx.x * WARPS + warp;
-    if (p >= a.P)
-        return;
-    if (lane == 0) {
-        P.g = (double2 *)(pbase + sizeof(PixelSmem));
-        P.rr = P.g + N;
-        P.rf = (float2 *)(P.rr + N);
-    }
-    __syncwarp();
-    const int smax = a.s_max;
-    const float2 *xin = a.x_in + (size_t)p * L;
+    const int smax = a.s_max;                       // row length of the support output
+    const int cap = smax < KW ? smax : KW;          // working-set capacity of this pass
+    const float2 *xin = (PH == 4 ? a.x_out : a.x_in) + (size_t)p * L;
     const float2 *gp = a.g + (size_t)p * N;
     const double lam = (double)(a.lam_pp ? a.lam[p] : a.lam[0]);
 
     int nnz = 0;
     bool truncated = false;
-    if constexpr (PH == 3) {
-        if (!sc.pend[p])
-            return;
-    }
-    if constexpr (PH >= 2) {
+    if constexpr (PH == 2 || PH == 3) {
         const int mm = sc.m[p];
         const int meta = sc.meta[p];
         nnz = meta & ((1 << 30) - 1);
@@ -707,7 +845,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
         const float2 v = (l < L) ? xin[l] : make_float2(0.f, 0.f);
         nnz += __popc(__ballot_sync(0xffffffffu, v.x != 0.f || v.y != 0.f));
     }
-    truncated = nnz > smax;
+    truncated = nnz > cap;
     if (!truncated) {
         int m = 0;
         for (int l0 = 0; l0 < L; l0 += 32) {
@@ -722,9 +860,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
         if (lane == 0)
             P.m = m;
     } else {
-        // s_max rounds of a warp arg-max over |x_l|^2 excluding points already taken
+        // cap rounds of a warp arg-max over |x_l|^2 excluding points already taken
         uint32_t taken = 0;  // bit j: l = lane + 32 j taken (L <= 1024)
-        for (int k = 0; k < smax; ++k) {
+        for (int k = 0; k < cap; ++k) {
             float best = -1.f;
             int bl = -1;
             for (int j = 0; lane + 32 * j < L; ++j) {
@@ -747,7 +885,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
                 }
             }
             if (bl < 0)
-                break;  // cannot happen: more than s_max grid points are nonzero
+                break;  // cannot happen: more than cap grid points are nonzero
             if ((bl & 31) == lane)
                 taken |= 1u << (bl >> 5);
             if (lane == 0)
@@ -755,8 +893,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
         }
         __syncwarp();
         if (lane == 0) {
-            P.m = smax;
-            for (int i = 1; i < smax; ++i) {  // ascending
+            P.m = cap;
+            for (int i = 1; i < cap; ++i) {  // ascending
                 const int w = P.W[i];
                 int j = i - 1;
                 while (j >= 0 && P.W[j] > w) {
@@ -768,13 +906,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
         }
     }
     }  // working set
-    const int status = a.status[p];
+    int status = a.status[p];
+    if constexpr (PH == 4)
+        status &= ~(BPDN_PX_SUPPORT_OVERFLOW | BPDN_PX_KKT_FAIL);  // this pass decides them anew
     for (int n = lane; n < N; n += 32) {
         const float2 gg = gp[n];
         P.g[n] = make_double2((double)gg.x, (double)gg.y);
     }
     __syncwarp();
-    if constexpr (PH < 2) {
+    if constexpr (PH == 0 || PH == 1 || PH == 4) {
         if (lane < P.m) {
             const float2 v = xin[P.W[lane]];
             P.zkeep[lane] = make_double2((double)v.x, (double)v.y);
@@ -800,7 +940,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
     }
 
     bool certified = false, noroom = false, more = false;
-    const int round_first = (PH == 3) ? 1 : 0, round_last = (PH == 2) ? 0 : a.rounds;
+    bool have_z = false;  // P.zkeep holds a converged restricted minimiser over W
+    // the wide pass gets four times the rounds: it only runs on the few pixels whose
+    // working set the fast path could not settle
+    const int round_first = (PH == 3) ? 1 : 0;
+    const int round_last = (PH == 2) ? 0 : ((PH == 4) ? 4 * a.rounds : a.rounds);
     for (int round = round_first; round <= round_last; ++round) {
         more = false;
         // 2. exact minimiser over W
@@ -817,11 +961,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
         } else {
             okr = restricted_minimiser(P, A64, h, N, L, lam, lane);
         }
+        have_z = okr;
         if (!okr)
             break;
         // drop the coordinates the restricted minimiser set to zero: their dual
         // constraint holds (|2 (G z - c)_i| <= lambda), and the room they free lets the
-        // certificate add violators when x_in had more than s_max nonzeros
+        // certificate add violators when x_in had more than cap nonzeros
         if (lane == 0) {
             int k = 0;
             for (int i = 0; i < P.m; ++i)
@@ -896,7 +1041,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
             }
             if (bl < 0)
                 break;
-            if (m + added >= smax) {
+            if (m + added >= cap) {
                 noroom = true;
                 break;
             }
@@ -945,7 +1090,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
     }
 
     float2 *xo = a.x_out + (size_t)p * L;
-    if (certified) {
+    // A pixel that is not certified but whose last restricted solve converged returns that
+    // restricted minimiser (at most cap nonzeros, the working set's violators at zero): a
+    // sparse point that minimises Eq. 6 over its own support, from which a pass with a
+    // larger working set (or another caller) continues; otherwise it keeps x_in.
+    if (certified || have_z) {
         const int m = P.m;
         for (int l = lane; l < L; l += 32) {
             float2 v = make_float2(0.f, 0.f);
@@ -965,7 +1114,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
             for (int i = ns + lane; i < smax; i += 32)
                 a.support[(size_t)p * smax + i] = -1;
         if (lane == 0) {
-            int st = (status & ~BPDN_PX_ZERO_SOLUTION) | BPDN_PX_CERTIFIED;
+            int st = status & ~BPDN_PX_ZERO_SOLUTION;
+            if (certified)
+                st |= BPDN_PX_CERTIFIED;
+            else
+                st |= (truncated || noroom) ? BPDN_PX_SUPPORT_OVERFLOW : BPDN_PX_KKT_FAIL;
             if (ns == 0)
                 st |= BPDN_PX_ZERO_SOLUTION;
             a.status[p] = st;
@@ -1000,26 +1153,136 @@ __global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const d
     }
 }
 
+// set up one warp's shared memory: the struct, then g, rr and rf of length N
+template <int KW>
+__device__ __forceinline__ PixelSmem<KW> &pixel_smem(unsigned char *base, int N, int lane)
+{
+    PixelSmem<KW> &P = *(PixelSmem<KW> *)base;
+    if (lane == 0) {
+        P.g = (double2 *)(base + sizeof(PixelSmem<KW>));
+        P.rr = P.g + N;
+        P.rf = (float2 *)(P.rr + N);
+    }
+    __syncwarp();
+    return P;
+}
+
+// one warp per block, one pixel per warp (phases 0, 1, 2: every pixel takes them)
+template <int PH>
+__global__ void __launch_bounds__(WARPS * 32) k_refit_t(SplitScratch sc, const double2 *__restrict__ A64,
+                                                      const double2 *__restrict__ h,
+                                                      const float *__restrict__ A_re,
+                                                      const float *__restrict__ A_im, int N,
+                                                      int L, int lda, RefitLaunch a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long p = (long long)blockIdx.x * WARPS + warp;
+    if (p >= a.P)
+        return;
+    PixelSmem<KWF> &P = pixel_smem<KWF>(smem_raw + (size_t)warp * pixel_smem_bytes<KWF>(N), N, lane);
+    refit_pixel<PH, KWF>(P, p, sc, A64, h, A_re, A_im, N, L, lda, a, lane);
+}
+
+// Persistent launches over the pixels that need them: each warp reads the flags of 32
+// pixels at a time (a coalesced load) and works through those that are set, so that the
+// few pixels of these passes cost no launch of a block per pixel.
+//   PH 3: sc.pend set by launch 2;
+//   PH 4 (wide pass): status with SUPPORT_OVERFLOW or KKT_FAIL and without CERTIFIED.
+template <int PH, int KW>
+__global__ void __launch_bounds__(32) k_refit_scan(SplitScratch sc, const double2 *__restrict__ A64,
+                                                   const double2 *__restrict__ h,
+                                                   const float *__restrict__ A_re,
+                                                   const float *__restrict__ A_im, int N, int L, int lda,
+                                                   RefitLaunch a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    PixelSmem<KW> &P = pixel_smem<KW>(smem_raw, N, lane);
+    // groups of 32 pixels from the work counter when there is one (the few long pixels
+    // then spread over the warps as they finish), else a fixed stride over the groups
+    unsigned long long *queue = sc.queue ? sc.queue + (PH == 3 ? 0 : 1) : nullptr;
+    for (long long it = 0;; ++it) {
+        long long grp;
+        if (queue) {
+            unsigned long long t = 0;
+            if (lane == 0)
+                t = atomicAdd(queue, 1ULL);
+            grp = (long long)__shfl_sync(0xffffffffu, t, 0);
+        } else {
+            grp = (long long)blockIdx.x + it * (long long)gridDim.x;
+        }
+        const long long p0 = 32LL * grp;
+        if (p0 >= a.P)
+            break;
+        const long long q = p0 + lane;
+        bool want = false;
+        if (q < a.P) {
+            if constexpr (PH == 3) {
+                want = sc.pend[q] != 0;
+            } else {
+                const int st = a.status[q];
+                want = (st & (BPDN_PX_SUPPORT_OVERFLOW | BPDN_PX_KKT_FAIL)) && !(st & BPDN_PX_CERTIFIED);
+            }
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, want);
+        while (bal) {
+            const int j = __ffs(bal) - 1;
+            bal &= bal - 1;
+            refit_pixel<PH, KW>(P, p0 + j, sc, A64, h, A_re, A_im, N, L, lda, a, lane);
+            __syncwarp();
+        }
+    }
+}
+
 }  // namespace
 
 size_t refit_scratch_bytes(int64_t P)
 {
     if (P <= 0)
         return 0;
-    return (size_t)((12 * P + 64 * P + 128 * P + 256 * P + 6 * 256 + 255) / 256 * 256);
+    return (size_t)((12 * P + 64 * P + 128 * P + 256 * P + 7 * 256 + 255) / 256 * 256);
 }
+
+namespace {
+// blocks of a persistent scan launch: every SM as full as the shared memory allows
+template <int PH, int KW>
+cudaError_t launch_scan(const OpHandle &op, const SplitScratch &sc, const RefitLaunch &a, cudaStream_t s)
+{
+    const size_t smem = pixel_smem_bytes<KW>(op.N);
+    cudaError_t e = cudaFuncSetAttribute(k_refit_scan<PH, KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refit_scan<PH, KW>, 32, smem);
+    if (e != cudaSuccess)
+        return e;
+    long long blocks = (long long)std::max(per_sm, 1) * std::max(sms, 1);
+    const long long groups = (a.P + 31) / 32;  // no more warps than groups of 32 pixels
+    if (blocks > groups)
+        blocks = groups;
+    const double2 *h = op.md ? nullptr : op.h;
+    k_refit_scan<PH, KW><<<(unsigned)blocks, 32, smem, s>>>(sc, op.A64, h, op.A_re, op.A_im, op.N, op.L, op.lda, a);
+    return cudaGetLastError();
+}
+}  // namespace
 
 cudaError_t launch_refit(const OpHandle &op, const RefitLaunch &a, cudaStream_t s)
 {
     if (a.P <= 0)
         return cudaSuccess;
-    const size_t smem = WARPS * pixel_smem_bytes(op.N);
+    const size_t smem = WARPS * pixel_smem_bytes<KWF>(op.N);
     const long long blocks = (a.P + WARPS - 1) / WARPS;
     const double2 *h = op.md ? nullptr : op.h;
+    SplitScratch sc = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e;
     if (a.split) {
         // three launches: the FP32 support search of every pixel, the FP64 finish and
         // certificate, then further rounds for the pixels that need them
-        SplitScratch sc;
         unsigned char *b = a.split;
         auto take = [&](size_t bytes) {
             unsigned char *r = b;
@@ -1032,24 +1295,31 @@ cudaError_t launch_refit(const OpHandle &op, const RefitLaunch &a, cudaStream_t 
         sc.z = (float2 *)take(128 * (size_t)a.P);
         sc.pend = (int *)take(4 * (size_t)a.P);
         sc.zs = (double2 *)take(256 * (size_t)a.P);
-        cudaError_t e = cudaFuncSetAttribute(k_refit_t<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        sc.queue = (unsigned long long *)take(2 * sizeof(unsigned long long));
+        e = cudaMemsetAsync(sc.queue, 0, 2 * sizeof(unsigned long long), s);
+        if (e != cudaSuccess)
+            return e;
+        e = cudaFuncSetAttribute(k_refit_t<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_refit_t<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_refit_t<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
         k_refit_t<1><<<(unsigned)blocks, WARPS * 32, smem, s>>>(sc, op.A64, h, op.A_re, op.A_im, op.N, op.L, op.lda, a);
         k_refit_t<2><<<(unsigned)blocks, WARPS * 32, smem, s>>>(sc, op.A64, h, op.A_re, op.A_im, op.N, op.L, op.lda, a);
-        k_refit_t<3><<<(unsigned)blocks, WARPS * 32, smem, s>>>(sc, op.A64, h, op.A_re, op.A_im, op.N, op.L, op.lda, a);
-        return cudaGetLastError();
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = launch_scan<3, KWF>(op, sc, a, s);
+    } else {
+        e = cudaFuncSetAttribute(k_refit_t<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        k_refit_t<0><<<(unsigned)blocks, WARPS * 32, smem, s>>>(sc, op.A64, h, op.A_re, op.A_im, op.N, op.L, op.lda, a);
+        e = cudaGetLastError();
     }
-    SplitScratch none = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    cudaError_t e = cudaFuncSetAttribute(k_refit_t<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-        return e;
-    k_refit_t<0><<<(unsigned)blocks, WARPS * 32, smem, s>>>(none, op.A64, h, op.A_re, op.A_im, op.N, op.L, op.lda, a);
-    return cudaGetLastError();
+    // the wide pass over the pixels whose support the fast path could not hold or settle
+    if (e == cudaSuccess && a.s_max > KWF)
+        e = launch_scan<4, KWW>(op, sc, a, s);
+    return e;
 }
 
 }  // namespace bpdn

@@ -28,6 +28,7 @@ namespace bpdn {
 namespace {
 
 constexpr int KS = BPDN_MAX_KSEL;
+constexpr int NRW = (BPDN_MAX_N + 31) / 32;  // rows n = lane + 32 c, c < NRW, per lane
 constexpr int WARPS = 4;  // pixels per block
 
 struct SelSmem {
@@ -192,10 +193,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_select(const double *__restrict_
     __syncwarp();
     const int kc = S.kc;
 
-    // steering vectors and g: lane owns rows n = lane and lane + 32
-    double2 gv[2];
+    // steering vectors and g: lane owns rows n = lane + 32 c
+    double2 gv[NRW];
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
+    for (int c = 0; c < NRW; ++c) {
         const int n = lane + 32 * c;
         gv[c] = make_double2(0.0, 0.0);
         if (n < N) {
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_select(const double *__restrict_
         for (int j = i; j < kc; ++j) {
             double2 t = make_double2(0.0, 0.0);
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
+            for (int c = 0; c < NRW; ++c) {
                 const int n = lane + 32 * c;
                 if (n < N) {
                     const double2 v = cmulc(S.a[i][n], S.a[j][n]);
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_select(const double *__restrict_
         }
         double2 t = make_double2(0.0, 0.0);
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < NRW; ++c) {
             const int n = lane + 32 * c;
             if (n < N) {
                 const double2 v = cmulc(S.a[i][n], gv[c]);
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_select(const double *__restrict_
     }
     double g2 = 0.0;
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+    for (int c = 0; c < NRW; ++c)
         g2 += gv[c].x * gv[c].x + gv[c].y * gv[c].y;
     g2 = warp_sum_d(g2);
     const double pen = (a.penalty > 0.0) ? a.penalty : 3.0 * log(2.0 * (double)N);
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_select(const double *__restrict_
         }
         double r2 = 0.0;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < NRW; ++c) {
             const int n = lane + 32 * c;
             if (n < N) {
                 double2 r = gv[c];

@@ -1,5 +1,5 @@
-"""The C ABI library (CPU only): it loads, exports every function include/bpdn.h
-declares, and rejects bad arguments with error codes before touching the GPU."""
+"""The C ABI library (CPU only): it loads, exports every function the headers under
+include/ declare, and rejects bad arguments with error codes before touching the GPU."""
 import ctypes
 import os
 import re
@@ -10,13 +10,16 @@ import pytest
 from paper_1805_01759_gb300 import _lib
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "bpdn.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if h.endswith(".h")]
 
 
 def declared_functions():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"\b(bpdn_[a-z0-9_]+)\s*\(", src)
+    names = []
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"\b(bpdn_[a-z0-9_]+)\s*\(", src)
     return sorted(set(names))
 
 
@@ -37,14 +40,14 @@ def test_options_struct_layout(lib):
     opt = _lib.default_options()
     assert ctypes.sizeof(_lib.Options) == 64
     assert opt.max_iter == 500 and abs(opt.tol - 1e-6) < 1e-12 and opt.c_alpha == 0.5
-    assert opt.refit == 1 and opt.s_max == 16 and opt.precision == 0
+    assert opt.refit == 1 and opt.s_max == 32 and opt.precision == 0
 
 
 def test_workspace_sizes(lib):
     assert lib.bpdn_op_workspace_bytes(25, 400) > 25 * 400 * 16
     assert lib.bpdn_op_workspace_bytes(0, 400) == 0
     assert lib.bpdn_op_workspace_bytes(25, 0) == 0
-    assert lib.bpdn_op_workspace_bytes(65, 400) == 0
+    assert lib.bpdn_op_workspace_bytes(81, 400) == 0 and lib.bpdn_op_workspace_bytes(80, 400) > 0
     assert lib.bpdn_op_workspace_bytes(25, 1025) == 0
     assert lib.bpdn_op_workspace_bytes(25, 400) % 256 == 0
 

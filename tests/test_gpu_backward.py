@@ -135,7 +135,7 @@ def test_backward_edges(api, case):
     assert torch.all(dg == 0) and torch.all(dl == 0)
     # bad s_max is refused on the host
     lib = _lib.load()
-    rc = lib.bpdn_backward(op.handle, P, lam1.data_ptr(), 0, x.data_ptr(), sup.data_ptr(), nsupp.data_ptr(), None, 17,
+    rc = lib.bpdn_backward(op.handle, P, lam1.data_ptr(), 0, x.data_ptr(), sup.data_ptr(), nsupp.data_ptr(), None, 33,
                            x.data_ptr(), dg.data_ptr(), dl.data_ptr(), None, 0, None)
     assert rc == _lib.BPDN_EINVAL
 
@@ -181,13 +181,20 @@ def test_autograd_function_and_lambda_tuning(api):
     lr = 0.1 / abs(d.item() * lam0)
     lam_end, hist = api.tune_lambda(op, gd, gt, lam0, steps=5, lr=lr)
     assert min(h[1] for h in hist[1:]) < hist[0][1], hist
+    # from half the default weight (supports larger than the truth's, where the implicit
+    # gradient misses the support jumps) the line search still descends
+    lam_end, hist = api.tune_lambda(op, gd, gt, 0.5 * st.lam, steps=5, lr=lr)
+    errs = np.array([h[1] for h in hist])
+    assert np.all(np.diff(errs) <= 1e-7 * errs[:-1]) and errs[-1] < errs[0], hist
 
 
-def test_backward_full_support(api):
-    """16 nonzeros (the largest support the refit and the adjoint handle): orthogonal
-    columns (DFT geometry), lambda between the 16th and 17th largest |2 a_l^H g|."""
-    rng = np.random.default_rng(77)
-    N = 32
+@pytest.mark.parametrize("N,k", [(32, 16), (64, 32)])
+def test_backward_full_support(api, N, k):
+    """k nonzeros: 16 (the fast refit's and the fast adjoint's capacity) and 32 (the largest
+    support the library handles: the refit's wide pass and the adjoint's wide kernel, each
+    unknown pair of lanes then holding two of the 64 real unknowns).  Orthogonal columns (DFT
+    geometry), lambda between the k-th and (k+1)-th largest |2 a_l^H g|."""
+    rng = np.random.default_rng(77 + k)
     geom = synth.dft_geometry(N)
     A = oracle.operator(geom)
     P = 16
@@ -195,7 +202,7 @@ def test_backward_full_support(api):
     lam_v = np.empty(P, np.float32)
     for p in range(P):
         w = np.sort(np.abs(2 * A.conj().T @ G[p].astype(np.complex128)))[::-1]
-        lam_v[p] = np.float32(0.5 * (w[15] + w[16]))
+        lam_v[p] = np.float32(0.5 * (w[k - 1] + w[k]))
     op = api.Operator.from_geometry(geom)
     lam_t = torch.from_numpy(lam_v).cuda()
     res = api.solve(op, torch.from_numpy(G).cuda(), lam_t)
@@ -203,7 +210,7 @@ def test_backward_full_support(api):
     dg, dl = api.backward(op, res.x, res.support, res.nsupp, torch.from_numpy(c.astype(np.complex64)).cuda(),
                           lam_t, status=res.status)
     torch.cuda.synchronize()
-    assert torch.all(res.nsupp == 16) and torch.all((res.status & 64) != 0)
+    assert torch.all(res.nsupp == k) and torch.all((res.status & 64) != 0)
     dg, dl = dg.cpu().numpy(), dl.cpu().numpy()
     for p in range(P):
         xs = oracle.minimise(A, G[p].astype(np.complex128), float(lam_v[p]))["x"]

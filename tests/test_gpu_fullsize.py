@@ -52,7 +52,7 @@ def test_full_patch(patch, precision, tol):
     zero_bit = (status & 32) != 0
     assert bool(torch.equal(zero_bit, nnz == 0))
     cert = (status & 64) != 0
-    assert float(cert.float().mean()) >= 0.97
+    assert float(cert.float().mean()) >= 0.999, float(cert.float().mean())
     assert int(nsupp[cert].max()) <= support.shape[1]
     assert bool(torch.equal(nsupp[cert], nnz[cert]))
     # certified rows: the support lists exactly the nonzeros, ascending, -1 padded
@@ -70,9 +70,10 @@ def test_full_patch(patch, precision, tol):
     xs = x[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.complex128)
     st_s = status.cpu().numpy()[idx]
     checked = 0
+    assert np.all(ref["flags"] == 0), ref["flags"]  # the oracle resolves every sampled pixel
     for j, p in enumerate(idx):
-        if not (st_s[j] & 64) or ref["flags"][j] != 0:
-            continue
+        # every sampled pixel, certified or not, is compared with the oracle's minimiser
+        assert st_s[j] & 64, f"sampled pixel {p} is not certified (status {st_s[j]})"
         xr = ref["x"][j]
         if ref["margin"][j] <= 1e-6 or ref["min_abs_on"][j] <= 1e-6 * max(np.abs(xr).max(), 1e-300):
             continue
@@ -135,7 +136,7 @@ def test_full_ragged_batch():
             err = np.linalg.norm(xs[j] - xr) / nr if nr > 0 else np.linalg.norm(xs[j])
             assert err <= 1e-4, (i, idx[j], err)
             checked += 1
-    assert cert_n >= 0.97 * total, (cert_n, total)
+    assert cert_n >= 0.999 * total, (cert_n, total)
     assert checked >= 90, checked
 
 
@@ -162,7 +163,7 @@ def test_full_differentiation_workload():
     loss = (x - gt).abs().pow(2).sum()
     loss.backward()
     torch.cuda.synchronize()
-    assert float(((status & 64) != 0).float().mean()) >= 0.97
+    assert float(((status & 64) != 0).float().mean()) >= 0.999
 
     rng = np.random.default_rng(77)
     idx = np.sort(rng.choice(P_d, size=64, replace=False))
@@ -203,6 +204,10 @@ def test_full_differentiation_workload():
         checked += 1
     assert checked >= 48, checked
 
-    lam_end, hist = api.tune_lambda(op, g.detach(), gt, 1.5 * lam0, steps=50, lr=0.1)
-    errs = [h[1] for h in hist]
-    assert min(errs[1:]) < errs[0] and errs[-1] < errs[0], (hist[:3], hist[-3:])
+    # 50 steps from half the default lambda (the starting point of the differentiation
+    # workload), and from 1.5 times it: with the line search every accepted step lowers the
+    # error, so it never rises and ends below where it started
+    for start in (0.5, 1.5):
+        lam_end, hist = api.tune_lambda(op, g.detach(), gt, start * lam0, steps=50, lr=0.1)
+        errs = np.array([h[1] for h in hist])
+        assert np.all(np.diff(errs) <= 1e-7 * errs[:-1]) and errs[-1] < errs[0], (start, hist[:3], hist[-3:])

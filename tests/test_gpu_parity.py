@@ -87,6 +87,62 @@ def test_first_iterations_match_algorithm_1(api, small, k):
     assert checked >= (100 if k <= 3 else 50), checked
 
 
+@pytest.mark.parametrize("precision,tol,min_checked,min_stopped", [(0, 1e-2, 100, 90), (0, 3e-3, 150, 5),
+                                                                   (1, 1e-2, 100, 90)])
+def test_stopping_rule_on_the_gpu_iterates(api, small, precision, tol, min_checked, min_stopped):
+    """The stopping test of Algorithm 1 (stop at the first iteration whose candidate step
+    satisfies ||xbar - x^k|| <= tol ||xbar||, else at max_iter with NOT_CONVERGED), checked
+    on the kernel's own iterates: x^k for k = 1..K comes from runs with max_iter = k and
+    tol = 0 (the trajectory does not depend on max_iter), the stop iteration from a run
+    with the tolerance.  Accepted steps are evaluated in FP64 on the host; a step whose
+    ratio to tol lies within 2 % of 1 is not decided here (FP32 rounding of the sums)."""
+    op = api.Operator.from_geometry(small.geom)
+    g = torch.from_numpy(small.g).cuda()
+    K = 80
+    res = api.solve(op, g, small.lam, precision=precision, tol=tol, max_iter=K, refit=0)
+    it = res.iters.cpu().numpy()
+    stt = res.status.cpu().numpy()
+    x_stop = res.x.cpu().numpy().astype(np.complex128)
+    xs = [np.zeros_like(x_stop)]
+    for k in range(1, K + 1):
+        r = api.solve(op, g, small.lam, precision=precision, tol=0.0, max_iter=k, refit=0)
+        xs.append(r.x.cpu().numpy().astype(np.complex128))
+    checked = stopped = 0
+    for p in range(small.g.shape[0]):
+        k_stop = int(it[p])
+        # the tolerance run's output is the same trajectory's iterate at its stop
+        assert np.array_equal(x_stop[p], xs[k_stop][p]), p
+        if np.all(xs[k_stop][p] == 0):
+            continue  # the zero solution stops at k = 1 (tested elsewhere)
+        ok = True
+        verdicts = []
+        for k in range(1, k_stop + 1):
+            a, b = xs[k][p], xs[k - 1][p]
+            if np.array_equal(a, b):
+                verdicts.append(None)  # rejected candidate: its step is not visible here
+                continue
+            ratio = np.linalg.norm(a - b) / (tol * np.linalg.norm(a))
+            if abs(ratio - 1.0) < 0.02:
+                ok = False
+                break
+            verdicts.append(ratio <= 1.0)
+        if not ok:
+            continue
+        # no accepted step before the stop satisfied the rule
+        assert not any(v for v in verdicts[:-1] if v is not None), (p, k_stop, verdicts)
+        if k_stop < K:
+            stopped += 1
+            assert not (stt[p] & 1), p
+            if verdicts[-1] is not None:
+                assert verdicts[-1], (p, k_stop)
+        else:
+            assert (stt[p] & 1) or verdicts[-1], p  # at max_iter: NOT_CONVERGED unless the rule held
+        checked += 1
+    # about 30 % of the pixels are zero solutions; at tol 3e-3 most pixels run past K, which
+    # checks that no accepted step before the stop met the rule
+    assert checked >= min_checked and stopped >= min_stopped, (checked, stopped)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_solve_refit_small_workload(api, small, small_oracle, precision):
     """Full path (Algorithm 1 + FP64 refit) against the exact minimiser, N=25, L=200, P=256,
@@ -98,7 +154,7 @@ def test_solve_refit_small_workload(api, small, small_oracle, precision):
     x = res.x.cpu().numpy().astype(np.complex128)
     st = res.status.cpu().numpy()
     cert = (st & 64) != 0
-    assert cert.mean() >= 0.95, cert.mean()
+    assert cert.mean() >= 0.999, cert.mean()  # every pixel of the small workload
     degenerate = (ref["margin"] < 1e-6) | ((ref["nS"] > 0) & (ref["min_abs_on"] < 1e-6 * np.abs(ref["x"]).max(1)))
     sel = cert & ~degenerate
     assert np.array_equal(x[sel] != 0, ref["x"][sel] != 0)
@@ -219,13 +275,15 @@ def test_bf16_rejects_unsupported_sizes(api):
 
 
 @pytest.mark.parametrize("N,L,half_width,precision", [(60, 600, 250.0, 0), (40, 300, 120.0, 0), (12, 1000, 300.0, 0),
-                                                       (64, 1024, 300.0, 0), (32, 512, 200.0, 1)])
+                                                       (64, 1024, 300.0, 0), (32, 512, 200.0, 1),
+                                                       (78, 400, 200.0, 0), (80, 200, 100.0, 0)])
 def test_solve_refit_operator_sizes(api, N, L, half_width, precision):
     """Beyond the sizes of the benchmark stack: N > 32 (two rows per lane), L > 512, an
-    operator too large for shared memory (N=60, L=600: A is read from global memory), and
-    the library's maximum sizes (FP32: N = 64, L = 1024, one 1024-thread group per CTA;
-    BF16: 2N = 64 contraction terms, L = 512).  Same bar as the small workload against the
-    exact minimiser."""
+    operator too large for shared memory (N=60, L=600: A is read from global memory), the
+    78 acquisitions of the paper's Munich stack (three rows per lane, Sec. IV-C), and the
+    library's maximum sizes (FP32: N = 64, L = 1024, one 1024-thread group per CTA, and
+    N = 80; BF16: 2N = 64 contraction terms, L = 512).  Same bar as the small workload
+    against the exact minimiser."""
     rng = np.random.default_rng(1000 + N + L)
     geom = synth.make_geometry(rng, N, L, 250.0, half_width)
     st = synth.make_stack(geom, 48, rng, lam=synth.default_lambda(N, L), snr_db_range=(5.0, 20.0))
@@ -237,7 +295,7 @@ def test_solve_refit_operator_sizes(api, N, L, half_width, precision):
     x = res.x.cpu().numpy().astype(np.complex128)
     status = res.status.cpu().numpy()
     cert = (status & 64) != 0
-    assert cert.mean() >= 0.9, cert.mean()
+    assert cert.mean() >= 0.97, cert.mean()
     degenerate = (ref["margin"] < 1e-6) | ((ref["nS"] > 0) & (ref["min_abs_on"] < 1e-6 * np.abs(ref["x"]).max(1)))
     sel = cert & ~degenerate
     assert sel.sum() >= 30

@@ -122,3 +122,75 @@ def test_deal_stacks_by_cost():
     assert api.deal_stacks(costs, 1) == [0] * len(costs)
     assert api.deal_stacks([5, 1, 4, 2], 2) == [0, 0, 1, 1]  # 5 | 4, then 2 -> rank 1, 1 -> rank 0
 
+
+
+class _ClosedFormSolve:
+    """A CPU stand-in for BPDNFunction on an operator with orthogonal columns (A^H A = N I):
+    the minimiser of Eq. 6 is x = S_{lambda/2}(A^H g) / N (the complex soft threshold of the
+    matched filter), differentiable in lambda through torch's autograd."""
+
+    @staticmethod
+    def apply(g, lam, op, options=None):
+        A = op
+        c = g @ A.conj()  # (A^H g)_l for every pixel
+        mag = c.abs()
+        scale = torch.clamp(1.0 - lam.to(torch.float64) / (2.0 * mag.clamp_min(1e-300)), min=0.0)
+        return c * scale / A.shape[0], None
+
+
+def _dft_shards(world: int, per: int):
+    """Pixels with up to two on-grid scatterers and noise over the DFT geometry (N = L = 16),
+    split into `world` shards, with their on-grid ground truth."""
+    rng = np.random.default_rng(11)
+    N = 16
+    n = np.arange(N)
+    A = np.exp(-2j * np.pi * np.outer(n, n) / N)
+    P = world * per
+    gam = np.zeros((P, N), np.complex128)
+    for p in range(P):
+        for _ in range(int(rng.integers(0, 3))):
+            gam[p, rng.integers(0, N)] = np.exp(2j * np.pi * rng.uniform())
+    G = gam @ A.T + 0.4 * (rng.standard_normal((P, N)) + 1j * rng.standard_normal((P, N)))
+    lam_default = 2.0 * 0.4 * np.sqrt(N * np.log(N))
+    return A, G, gam, lam_default
+
+
+def _tune_full_rank(rank: int, world: int, port: int, out_dir: str) -> None:
+    sys.path.insert(0, ROOT)
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        from paper_1805_01759_gb300 import api
+        api.BPDNFunction = _ClosedFormSolve
+        A, G, gam, lam_d = _dft_shards(world, 32)
+        sl = slice(32 * rank, 32 * (rank + 1))
+        lam, hist = api.tune_lambda(torch.from_numpy(A), torch.from_numpy(G[sl]), torch.from_numpy(gam[sl]),
+                                    0.5 * lam_d, steps=12, lr=0.5)
+        np.save(os.path.join(out_dir, f"h{rank}.npy"), np.array([[l, e] for l, e in hist] + [[lam, 0.0]]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_lambda_tuning_end_to_end(tmp_path):
+    """tune_lambda with the pixels sharded over two gloo ranks: both ranks take identical
+    steps, the same steps as one process over all the pixels, and from half the default
+    lambda the line search lowers the error at every accepted step."""
+    world = 2
+    mp.spawn(_tune_full_rank, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    h = [np.load(tmp_path / f"h{r}.npy") for r in range(world)]
+    assert np.array_equal(h[0], h[1])
+    sys.path.insert(0, ROOT)
+    if dist.is_initialized():
+        pytest.skip("a process group is already initialised")
+    from paper_1805_01759_gb300 import api
+    saved = api.BPDNFunction
+    try:
+        api.BPDNFunction = _ClosedFormSolve
+        A, G, gam, lam_d = _dft_shards(world, 32)
+        lam, hist = api.tune_lambda(torch.from_numpy(A), torch.from_numpy(G), torch.from_numpy(gam),
+                                    0.5 * lam_d, steps=12, lr=0.5)
+    finally:
+        api.BPDNFunction = saved
+    one = np.array([[l, e] for l, e in hist] + [[lam, 0.0]])
+    np.testing.assert_allclose(h[0], one, rtol=1e-9, atol=0)
+    errs = one[:-1, 1]
+    assert np.all(np.diff(errs) <= 1e-12) and errs[-1] < errs[0], errs
