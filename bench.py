@@ -366,8 +366,8 @@ def precision_report(api, oracle_patch: "OracleSample", st_patch, op_patch, g_pa
     for cname, (o, op, g, lam) in {"small_N25_L200_P256": (o_small, op_small, g_small, small.lam),
                                    "patch_sample": (oracle_patch, op_patch, g_patch, lam_patch)}.items():
         rows = {}
-        for name, (prec, tol) in paths.items():
-            it = api.solve(op, g, lam, precision=prec, tol=tol, refit=0)
+        for name, (prec, tol, tile) in paths.items():
+            it = api.solve(op, g, lam, precision=prec, tol=tol, refit=0, tile_pixels=tile)
             x_it = it.x.cpu().numpy()
             x_rf, _, _, st_rf = api.refit(op, g, lam, it.x, status=it.status)
             torch.cuda.synchronize()
@@ -382,11 +382,11 @@ def precision_report(api, oracle_patch: "OracleSample", st_patch, op_patch, g_pa
 class PathRunner:
     """One configuration of the hot path (iteration kernel + refit) on resident inputs."""
 
-    def __init__(self, lib, _lib, op, g_dev, lam_t, P, precision, tol, stream):
+    def __init__(self, lib, _lib, op, g_dev, lam_t, P, precision, tol, stream, tile=0):
         import torch
         self.lib, self._lib, self.op, self.g_dev, self.lam_t, self.P = lib, _lib, op, g_dev, lam_t, P
         dev = g_dev.device
-        self.opt_solve = _lib.default_options(refit=0, precision=precision, tol=tol)
+        self.opt_solve = _lib.default_options(refit=0, precision=precision, tol=tol, tile_pixels=tile)
         self.opt_refit = _lib.default_options()
         L = op.L
         self.x = torch.empty((P, L), dtype=torch.complex64, device=dev)
@@ -468,7 +468,10 @@ def run_ours(args) -> None:
 
     # plain FP32 at its own tolerance, FP32 at the BF16 path's tolerance (the same stopping
     # rule, so that the two precisions are compared at equal work per pixel), and BF16
-    paths = {"fp32": (0, args.tol_fp32), "fp32_tol_bf16": (0, args.tol_bf16), "bf16": (1, args.tol_bf16)}
+    # (precision, tol, tile_pixels): tile_pixels 0 runs the pixel-per-thread BF16 kernel where it
+    # fits; bf16_gridpoint is the grid-point-per-thread BF16 kernel on the same solve
+    paths = {"fp32": (0, args.tol_fp32, 0), "fp32_tol_bf16": (0, args.tol_bf16, 0), "bf16": (1, args.tol_bf16, 0),
+             "bf16_gridpoint": (1, args.tol_bf16, 16)}
     if args.precision == "fp32":
         paths = {"fp32": paths["fp32"], "fp32_tol_bf16": paths["fp32_tol_bf16"]}
     elif args.precision == "bf16":
@@ -478,8 +481,8 @@ def run_ours(args) -> None:
     results = {}
     launches = 0
     with ClockSampler(dev.index) as clk:
-        for name, (prec, tol) in paths.items():
-            runner = PathRunner(lib, _lib, op, g_dev, lam_t, P, prec, tol, stream)
+        for name, (prec, tol, tile) in paths.items():
+            runner = PathRunner(lib, _lib, op, g_dev, lam_t, P, prec, tol, stream, tile)
             tm = runner.timed(args.steps, args.warmup, dev)
             launches += 2 * args.steps
             results[name] = (runner, tm)
@@ -513,7 +516,7 @@ def run_ours(args) -> None:
             "ms_per_sweep": statistics.mean(tm["rbpg_ms"]) / (sweeps / P),
             "alu_tflops": sweeps * alu_flops_per_sweep(name, N, L) / rbpg_avg_s / 1e12,
         }
-        if name == "bf16":
+        if name.startswith("bf16"):
             out_paths[name]["tensor_tflops"] = sweeps * 8.0 * N * L / rbpg_avg_s / 1e12
         out_paths[name]["alu_flops_per_sweep"] = alu_flops_per_sweep(name, N, L)
         if name == head:
@@ -575,10 +578,23 @@ def run_ours(args) -> None:
     rbpg_avg_s = statistics.mean(head_tm["rbpg_ms"]) / 1e3
     achieved = head_sweeps * alu_flops_per_sweep(head, N, L) / rbpg_avg_s / 1e12
     traffic = _traffic_per_launch(P, head)
+    # the survey's count for the same kernel: per pixel sweep 16 N L flops of contraction on the
+    # tensor cores (BF16; the FP32 path's contraction runs on the FP32 pipe) and 20 L of FP32
+    # elementwise work; roofline time = the slowest of the pipes and HBM (3.4 kB per pixel)
+    peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    mp = json.load(open(peaks_file)) if os.path.exists(peaks_file) else {}
+    bf16_peak = float(mp.get("bf16_tflops", 1900.0))
+    hbm_gbs = float(mp.get("hbm_gbs", 6800.0))
+    if head.startswith("bf16"):
+        t_pipe = max(head_sweeps * 16.0 * N * L / (bf16_peak * 1e12), head_sweeps * 20.0 * L / (peak_tflops * 1e12))
+    else:
+        t_pipe = head_sweeps * (16.0 * N * L + 20.0 * L) / (peak_tflops * 1e12)
+    t_hbm = P * (8.0 * N + 8.0 * L + 16.0) / (hbm_gbs * 1e9)
+    survey_frac = max(t_pipe, t_hbm) / rbpg_avg_s
 
     if rank != 0:
         return
-    kname = "k_rbpg<BF16>" if head == "bf16" else "k_rbpg<FP32>"
+    kname = "k_rbpg_px (BF16, one pixel per thread)" if head == "bf16" else "k_rbpg<FP32>"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_head, "higher_is_better": True,
@@ -596,6 +612,9 @@ def run_ours(args) -> None:
         "paths": out_paths,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic, "kernel": kname,
+                     "frac_survey_count": survey_frac,
+                     "survey_count": "16 N L tensor (BF16 peak %s) + 20 L FP32 per sweep, HBM 3.4 kB per pixel" % (
+                         "measured" if mp else "fallback 1.9 PFLOP/s"),
                      "peak_source": "measured: FFMA/FFMA2 loops of bpdn_bench_peak on this GPU",
                      "peak_unit_count": unit_count_tflops, "peaks_measured": pk,
                      "note": "the fused iteration (Algorithm 1); see kernels for the refit's share. "

@@ -110,8 +110,10 @@ static int check_options(const bpdn_options *o)
         return set_error(BPDN_EINVAL, "max_bt must be >= 0");
     if (o->refit_rounds < 0 || o->refit_rounds > 64)
         return set_error(BPDN_EINVAL, "refit_rounds must lie in [0, 64]");
-    if (o->tile_pixels != 0 && o->tile_pixels != 8 && o->tile_pixels != 16)
-        return set_error(BPDN_EINVAL, "tile_pixels must be 0 (library choice), 8 or 16");
+    if (o->tile_pixels != 0 && o->tile_pixels != 8 && o->tile_pixels != 16 && o->tile_pixels != 128)
+        return set_error(BPDN_EINVAL, "tile_pixels must be 0 (library choice), 8, 16 or 128");
+    if (o->tile_pixels == 128 && o->precision != 1)
+        return set_error(BPDN_EINVAL, "tile_pixels 128 (one pixel per thread) is the BF16 kernel: precision 1");
     if (o->blocks < 0 || o->blocks > 8)
         return set_error(BPDN_EINVAL, "blocks must lie in [0, 8]");
     if (o->blocks >= 2 && o->precision != 0)
@@ -131,6 +133,16 @@ size_t solve_min_workspace_bytes(const bpdn_options *opt)
     // a 64-bit work counter, an error word and the block draw table, padded; with
     // randomized blocks, A_j A_j^H of every block after that
     return 256 + block_scratch_bytes(opt ? opt->blocks : 0);
+}
+
+// scratch of the pixel-per-thread BF16 iteration kernel for this solve (0: the solve runs the
+// grid-point-per-thread kernel): precision 1, one block per pixel, tile_pixels 0 or 128, and
+// sizes the kernel takes
+static size_t px_scratch_for(const OpHandle *op, int64_t P, const bpdn_options *opt)
+{
+    if (!op || !opt || opt->precision != 1 || opt->blocks >= 2 || opt->tile_pixels != 128)
+        return 0;
+    return rbpg_px_scratch_bytes(*op, P, num_sms(op->device), max_smem_optin(op->device));
 }
 
 static int check_solve_buffers(const OpHandle *op, const void *d_g, int64_t P, const float *d_lambda,
@@ -178,7 +190,15 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
         return set_error(BPDN_EALIGN, "solve workspace must be 256-byte aligned");
     if (opt->refit && d_support && !aligned(d_support, 4))
         return set_error(BPDN_EALIGN, "support must be 4-byte aligned");
+    // the pixel-per-thread BF16 kernel when it suits the sizes and the workspace holds its scratch
+    const size_t base = solve_min_workspace_bytes(opt);
+    const size_t pxb = px_scratch_for(op, P, opt);
+    const bool use_px = pxb > 0 && workspace_bytes >= base + pxb;
+    if (opt->tile_pixels == 128 && !use_px)
+        return set_error(BPDN_ESIZE, pxb ? "tile_pixels 128: the workspace does not hold the kernel's scratch"
+                                         : "tile_pixels 128 needs 2N <= 64 and the operator within shared memory");
     const char *why = (opt->blocks >= 2) ? rbpg_block_check(*op, opt->blocks, max_smem_optin(op->device))
+                      : use_px           ? ""
                                          : rbpg_check(*op, opt->precision, opt->tile_pixels / 8,
                                                       max_smem_optin(op->device));
     if (why[0] != '\0')
@@ -209,6 +229,7 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     a.blip = (double *)((char *)d_workspace + 16);
     a.cum = (double *)((char *)d_workspace + 16 + 8 * 8);
     a.bscratch = a.blocks ? (double2 *)((char *)d_workspace + 256) : nullptr;
+    a.px_scratch = use_px ? (unsigned char *)d_workspace + base : nullptr;
     sp->refit = opt->refit != 0;
     RefitLaunch &r = sp->r;
     r.g = a.g;
@@ -222,9 +243,10 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     r.status = d_status;
     r.s_max = opt->s_max;
     r.rounds = opt->refit_rounds;
-    // the split refit (three launches) when the workspace holds its scratch, else one launch
-    const size_t base = solve_min_workspace_bytes(opt);
-    r.split = (workspace_bytes >= base + refit_scratch_bytes(P)) ? (unsigned char *)d_workspace + base : nullptr;
+    // the split refit when the workspace holds its scratch (after the iteration kernel's), else
+    // the fused refit
+    const size_t rbase = base + (use_px ? pxb : 0);
+    r.split = (workspace_bytes >= rbase + refit_scratch_bytes(P)) ? (unsigned char *)d_workspace + rbase : nullptr;
     return BPDN_OK;
 }
 
@@ -248,6 +270,8 @@ int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
         if (rc)
             return rc;
         rc = check_cuda(launch_rbpg_block(*sp.op, sp.a, s), "block iteration kernel");
+    } else if (sp.a.px_scratch) {
+        rc = check_cuda(launch_rbpg_px(*sp.op, sp.a, num_sms(sp.op->device), s), "iteration kernel (pixel per thread)");
     } else {
         rc = check_cuda(launch_rbpg(*sp.op, sp.a, num_sms(sp.op->device), s), "iteration kernel");
     }
@@ -492,10 +516,12 @@ int bpdn_op_export(bpdn_op_t h, int32_t what, void *d_dst, size_t dst_bytes, voi
 
 size_t bpdn_solve_workspace_bytes(bpdn_op_t h, int64_t P, const bpdn_options *opt)
 {
-    (void)h;
-    // the least workspace, then the scratch of the split refit (a smaller workspace,
-    // down to the least one, runs the refit in a single launch)
-    return solve_min_workspace_bytes(opt) + ((opt && opt->refit) ? refit_scratch_bytes(P) : 0);
+    // the least workspace, the pixel-per-thread kernel's scratch when the solve would run it,
+    // then the scratch of the split refit (a smaller workspace, down to the least one, runs
+    // the other iteration kernel and the fused refit)
+    const OpHandle *op = reinterpret_cast<const OpHandle *>(h);
+    const size_t pxb = (op && op->magic == kOpMagic && P > 0) ? px_scratch_for(op, P, opt) : 0;
+    return solve_min_workspace_bytes(opt) + pxb + ((opt && opt->refit) ? refit_scratch_bytes(P) : 0);
 }
 
 

@@ -96,9 +96,16 @@ struct SolveLaunch {
     double2 *bscratch;  // [blocks][N][N]: A_j A_j^H
     double *blip;       // [blocks]: lambda_max(A_j A_j^H)
     double *cum;        // [blocks]: cumulative draw probabilities, last = 1
+    // pixel-per-thread BF16 kernel (k_rbpg_px): per-slot iterate lists and residual state,
+    // or NULL when the solve runs the grid-point-per-thread kernel
+    unsigned char *px_scratch;
 };
 // iteration kernel (a.precision 0: FP32 CUDA cores, 1: BF16 tensor cores)
 cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
+// the pixel-per-thread BF16 iteration kernel: bytes of its per-slot scratch on this device
+// (0 when the operator's sizes do not suit it), and its launch
+size_t rbpg_px_scratch_bytes(const OpHandle &op, int64_t P, int num_sms, int max_smem);
+cudaError_t launch_rbpg_px(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
 // many stacks in persistent launches, one per kernel variant present (at most 64 stacks each)
 cudaError_t launch_rbpg_batch(const OpHandle *const *ops, const SolveLaunch *as, int n, int num_sms,
                               cudaStream_t s);

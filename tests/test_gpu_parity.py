@@ -236,6 +236,72 @@ def test_bitwise_deterministic_across_runs(api, precision):
     assert torch.equal(torch.view_as_real(r1.x), torch.view_as_real(r2.x))
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 10])
+def test_bf16_kernels_agree(api, small, k):
+    """The two BF16 iteration kernels -- one pixel per thread (tile_pixels 128, the default
+    where it fits) and one grid point per thread (tile_pixels 16) -- run the same Algorithm 1
+    with the same BF16-rounded residuals; they differ only in FP32 summation order and in
+    how the residual is formed (from A x - g kept per pixel, or from A x and A y), which can
+    move a BF16 rounding by one unit.  After k iterations: identical iteration counts, and
+    relative differences of x below 1e-5 on 90 % of the pixels and below 1e-2 on all."""
+    op = api.Operator.from_geometry(small.geom)
+    g = torch.from_numpy(small.g).cuda()
+    r_px = api.solve(op, g, small.lam, max_iter=k, tol=0.0, refit=0, precision=1, tile_pixels=128)
+    r_gp = api.solve(op, g, small.lam, max_iter=k, tol=0.0, refit=0, precision=1, tile_pixels=16)
+    torch.cuda.synchronize()
+    assert torch.equal(r_px.iters, r_gp.iters)
+    assert torch.equal(r_px.status & ~64, r_gp.status & ~64)
+    a, b = r_px.x.cpu().numpy(), r_gp.x.cpu().numpy()
+    nb = np.linalg.norm(b, axis=1)
+    d = np.linalg.norm(a - b, axis=1) / np.where(nb > 0, nb, 1.0)
+    assert np.quantile(d, 0.9) <= 1e-5 and d.max() <= 1e-2, (np.quantile(d, 0.9), d.max())
+
+
+@pytest.mark.parametrize("tile", [16, 128])
+def test_bf16_kernels_full_path(api, small, small_oracle, tile):
+    """Both BF16 iteration kernels followed by the refit reach the exact minimiser."""
+    A, ref = small_oracle
+    op = api.Operator.from_geometry(small.geom)
+    g = torch.from_numpy(small.g).cuda()
+    res = api.solve(op, g, small.lam, precision=1, tol=1e-3, tile_pixels=tile)
+    x = res.x.cpu().numpy().astype(np.complex128)
+    cert = (res.status.cpu().numpy() & 64) != 0
+    assert cert.mean() >= 0.999, cert.mean()
+    degenerate = (ref["margin"] < 1e-6) | ((ref["nS"] > 0) & (ref["min_abs_on"] < 1e-6 * np.abs(ref["x"]).max(1)))
+    sel = cert & ~degenerate
+    assert np.array_equal(x[sel] != 0, ref["x"][sel] != 0)
+    assert _rel(x[sel], ref["x"][sel]).max() <= 1e-4
+
+
+def test_bf16_pixel_kernel_edges(api, small):
+    """The pixel-per-thread kernel on a ragged count (not a multiple of its 256 slots per CTA),
+    a non-finite pixel, per-pixel lambda with a zero solution, max_iter = 0, and its
+    refusals (FP32, an operator beyond its sizes)."""
+    op = api.Operator.from_geometry(small.geom)
+    G = small.g[:37].copy()
+    G[5, 3] = np.nan
+    lam = np.full(37, small.lam, np.float32)
+    lam[7] = 1e4
+    g = torch.from_numpy(G).cuda()
+    res = api.solve(op, g, torch.from_numpy(lam).cuda(), max_iter=50, refit=0, precision=1, tile_pixels=128)
+    x, st, it = res.x.cpu().numpy(), res.status.cpu().numpy(), res.iters.cpu().numpy()
+    assert st[5] == 4 and it[5] == 0 and np.all(x[5] == 0)
+    assert np.all(x[7] == 0) and it[7] == 1 and (st[7] & 32)
+    ok = np.ones(37, bool)
+    ok[5] = False
+    assert np.all(np.isfinite(x[ok])) and np.all(it[ok] >= 1)
+    r0 = api.solve(op, g, small.lam, max_iter=0, refit=0, precision=1, tile_pixels=128)
+    assert np.all(r0.x.cpu().numpy() == 0) and np.all(r0.iters.cpu().numpy() == 0)
+    from paper_1805_01759_gb300 import _lib
+    with pytest.raises(_lib.BPDNError):
+        api.solve(op, g, small.lam, precision=0, tile_pixels=128)
+    geom = synth.make_geometry(np.random.default_rng(3), 40, 200, 250.0, 100.0)
+    op40 = api.Operator.from_geometry(geom)
+    with pytest.raises(_lib.BPDNError):
+        api.solve(op40, torch.zeros((4, 40), dtype=torch.complex64, device="cuda"), 1.0, precision=1,
+                  tile_pixels=128)
+
+
 @pytest.mark.parametrize("k", [1, 2])
 def test_bf16_first_iterations(api, small, k):
     """Algorithm 1 with the gradient from BF16 operands (FP32 accumulation) against the
