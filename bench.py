@@ -468,10 +468,10 @@ def run_ours(args) -> None:
 
     # plain FP32 at its own tolerance, FP32 at the BF16 path's tolerance (the same stopping
     # rule, so that the two precisions are compared at equal work per pixel), and BF16
-    # (precision, tol, tile_pixels): tile_pixels 0 runs the pixel-per-thread BF16 kernel where it
-    # fits; bf16_gridpoint is the grid-point-per-thread BF16 kernel on the same solve
+    # (precision, tol, tile_pixels): bf16 is the grid-point-per-thread BF16 kernel (the default);
+    # bf16_pixel_per_thread the alternative layout (tile_pixels 128) on the same solve
     paths = {"fp32": (0, args.tol_fp32, 0), "fp32_tol_bf16": (0, args.tol_bf16, 0), "bf16": (1, args.tol_bf16, 0),
-             "bf16_gridpoint": (1, args.tol_bf16, 16)}
+             "bf16_pixel_per_thread": (1, args.tol_bf16, 128)}
     if args.precision == "fp32":
         paths = {"fp32": paths["fp32"], "fp32_tol_bf16": paths["fp32_tol_bf16"]}
     elif args.precision == "bf16":
@@ -594,7 +594,7 @@ def run_ours(args) -> None:
 
     if rank != 0:
         return
-    kname = "k_rbpg_px (BF16, one pixel per thread)" if head == "bf16" else "k_rbpg<FP32>"
+    kname = "k_rbpg<BF16>" if head == "bf16" else "k_rbpg<FP32>"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_head, "higher_is_better": True,

@@ -44,13 +44,14 @@ STATUS_ZERO_SOLUTION = 32
 
 
 def build(force: bool = False) -> str:
-    """Compile bpdn_oracle.c into oracle/_build/liboracle.so (gcc, -O2, OpenMP)."""
+    """Compile bpdn_oracle.c into oracle/_build/liboracle.so (gcc -O3, ISO C11: no FP contraction,
+    the same results on x86-64 and aarch64; OpenMP)."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+    cmd = ["gcc", "-O3", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
            "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)

@@ -172,15 +172,18 @@ __host__ __device__ inline SmemLayout smem_layout(int N, int L)
 // per-slot scratch in global memory: A x - g for the two kept iterates (2 x 2N floats),
 // then three iterate lists (indices uint16 [L], values float2 [L] each)
 struct SlotLayout {
-    size_t U, LI, LV, bytes;
+    size_t U, LM, LV, bytes;
 };
 
+// per-slot scratch in global memory: A x - g of the two kept iterates ([2][N] complex), then
+// three sparse iterates, each a 32-bit mask per 32-point chunk of the grid (bit j: grid point
+// 32 c + j is nonzero) and its nonzero values packed in ascending order
 __host__ __device__ inline SlotLayout slot_layout(int N, int L)
 {
     SlotLayout s;
     size_t o = 0;
-    s.U = o;  o = al16(o + sizeof(float) * 4 * (size_t)N);
-    s.LI = o; o = al16(o + sizeof(uint16_t) * 3 * (size_t)L);
+    s.U = o;  o = al16(o + sizeof(float2) * 2 * (size_t)N);
+    s.LM = o; o = al16(o + sizeof(uint32_t) * 3 * (size_t)chunks_of(L));
     s.LV = o; o = al16(o + sizeof(float2) * 3 * (size_t)L);
     s.bytes = (o + 255) & ~(size_t)255;
     return s;
@@ -264,17 +267,19 @@ __global__ void __launch_bounds__(kTiles * kSlots, 1) k_rbpg_px(const __grid_con
     const uint32_t mbar0 = smem_u32(sbar + 2 * tile), mbar1 = smem_u32(sbar + 2 * tile + 1);
     int *tflag = sflag + 8 * tile;
 
-    // the slot's scratch: A x - g of the two kept iterates, three iterate lists
+    // the slot's scratch (this thread's, and any slot of the warp for the cooperative parts)
     const SlotLayout SL = slot_layout(N, L);
-    unsigned char *slot = a.px_scratch + (size_t)(blockIdx.x * (kTiles * kSlots) + tid) * prm.slot_bytes;
+    unsigned char *const slot0 = a.px_scratch + (size_t)(blockIdx.x * (kTiles * kSlots) + tid - lane) * prm.slot_bytes;
+    auto slot_of = [&](int t) -> unsigned char * { return slot0 + (size_t)t * prm.slot_bytes; };
+    unsigned char *slot = slot_of(lane);
     float2 *U = (float2 *)(slot + SL.U);        // [2][N]
-    uint16_t *LI = (uint16_t *)(slot + SL.LI);  // [3][L]
+    uint32_t *LM = (uint32_t *)(slot + SL.LM);  // [3][NC]
     float2 *LV = (float2 *)(slot + SL.LV);      // [3][L]
 
     long long pix = -1;
     int k = 0, nbt = 0, nbt_it = 0, st = 0, nnz = 0;
     float alpha = 0.f, Fx = 0.f, lam = 0.f, beta = 0.f;
-    int bx = 0, bxp = 0, nx = 0, nxp = 0;  // list buffers and lengths of x^k and x^{k-1}
+    int bx = 0, bxp = 0, nx = 0, nxp = 0;  // buffers and nonzero counts of x^k and x^{k-1}
     int ub = 0, upb = 0;                   // U buffers of A x^k - g and A x^{k-1} - g
     bool aborted = false;                  // this tile's tensor-core wait ran out
 
@@ -338,10 +343,9 @@ __global__ void __launch_bounds__(kTiles * kSlots, 1) k_rbpg_px(const __grid_con
             break;
         const bool act = pix >= 0;
 
-        // ---- 1. residual r = (1 + beta)(A x^k - g) - beta (A x^{k-1} - g) as this thread's BF16 row
+        // ---- 1. residual r = (1 + beta)(A x^k - g) - beta (A x^{k-1} - g) as this thread's BF16 row:
+        // element kk = Re r_kk (kk < N), Im r_{kk-N} (N <= kk < 2N), 0 beyond
         {
-            // element kk of the row: Re r_kk (kk < N), Im r_{kk-N} (N <= kk < 2N), 0 beyond;
-            // r from the slot's A x^k - g and A x^{k-1} - g (L1-resident)
             uint32_t rw[32];
 #pragma unroll
             for (int p = 0; p < 32; ++p) {
@@ -373,22 +377,19 @@ __global__ void __launch_bounds__(kTiles * kSlots, 1) k_rbpg_px(const __grid_con
 
         // ---- 2. gradient chunks: prox and sums, grid points in ascending order
         const float a2 = 2.f * alpha, tau = alpha * lam;
-        // next entries of the x^k and x^{k-1} lists
-        const uint16_t *lix = LI + bx * L, *lip = LI + bxp * L;
-        const float2 *lvx = LV + bx * L, *lvp = LV + bxp * L;
-        int px = 0, pp = 0;
-        int lx = (act && nx > 0) ? (int)lix[0] : (int)kEnd;
-        int lp = (act && nxp > 0) ? (int)lip[0] : (int)kEnd;
-        float2 vx = (act && nx > 0) ? lvx[0] : make_float2(0.f, 0.f);
-        float2 vp = (act && nxp > 0) ? lvp[0] : make_float2(0.f, 0.f);
-        const int bb = (bx == bxp) ? (bx + 1) % 3 : 3 - bx - bxp;  // the free list buffer: xbar
-        uint16_t *lib = LI + bb * L;
-        float2 *lvb = LV + bb * L;
-        int nb = 0;
+        const uint32_t *mkx = LM + bx * NC, *mkp = LM + bxp * NC;
+        const float2 *vlx = LV + bx * L, *vlp = LV + bxp * L;
+        const int bb = (bx == bxp) ? (bx + 1) % 3 : 3 - bx - bxp;  // the free buffer: xbar
+        uint32_t *mkb = LM + bb * NC;
+        float2 *vlb = LV + bb * L;
+        int ox = 0, op = 0, nb = 0;  // values consumed / written so far
         float dd = 0.f, l1 = 0.f, dx = 0.f, xn = 0.f;
         for (int c = 0; c < NC; ++c) {
             const int buf = c & 1;
             const uint32_t mb = buf ? mbar1 : mbar0;
+            // this chunk's nonzero masks of x^k and x^{k-1} (loaded before the wait)
+            const uint32_t mx = (act && nx > 0) ? mkx[c] : 0u;
+            const uint32_t mp = (act && nxp > 0) ? mkp[c] : 0u;
             if (!aborted && tflag[4] == 0) {  // no wait for MMAs that a timed-out tile never issued
                 if (!mbar_wait(mb, buf ? ph1 : ph0)) {
                     atomicExch(tflag + 4, 1);
@@ -413,73 +414,72 @@ __global__ void __launch_bounds__(kTiles * kSlots, 1) k_rbpg_px(const __grid_con
                 issue_chunk(tbase, bbase, mb, c + 2, buf);
             if (!act)
                 continue;
+            uint32_t mnew = 0;
+            // every point of the chunk: past L the operator rows are zero, so the gradient and
+            // the iterates are zero there and v = 0 gives xbar = 0 and no contribution
 #pragma unroll
             for (int j = 0; j < kChunkPts; ++j) {
-                const int l = kChunkPts * c + j;
-                if (l >= L)
-                    break;
                 const float gre = (j < 16) ? d0[2 * j] : d1[2 * (j - 16)];
                 const float gim = (j < 16) ? d0[2 * j + 1] : d1[2 * (j - 16) + 1];
+                // x^k_l and x^{k-1}_l from the packed values (addresses from the masks alone)
+                const bool hx = (mx >> j) & 1u, hp = (mp >> j) & 1u;
                 float2 xv = make_float2(0.f, 0.f), xpv = make_float2(0.f, 0.f);
-                if (lx == l) {
-                    xv = vx;
-                    ++px;
-                    const bool more = px < nx;
-                    lx = more ? (int)lix[px] : (int)kEnd;
-                    vx = more ? lvx[px] : make_float2(0.f, 0.f);
-                }
-                if (lp == l) {
-                    xpv = vp;
-                    ++pp;
-                    const bool more = pp < nxp;
-                    lp = more ? (int)lip[pp] : (int)kEnd;
-                    vp = more ? lvp[pp] : make_float2(0.f, 0.f);
-                }
+                if (hx)
+                    xv = vlx[ox];
+                if (hp)
+                    xpv = vlp[op];
+                ox += hx;
+                op += hp;
                 // y = x + beta (x - x^{k-1}); v = y - 2 alpha grad; xbar = soft threshold of v at tau
                 const float yx = fmaf(beta, xv.x - xpv.x, xv.x), yy = fmaf(beta, xv.y - xpv.y, xv.y);
                 const float vre = fmaf(-a2, gre, yx), vim = fmaf(-a2, gim, yy);
                 const float m2 = fmaf(vre, vre, vim * vim);
                 const float rs = rsqrtf(m2);
                 const float sc = fmaf(-tau, rs, 1.f);
-                float bre = 0.f, bim = 0.f;
-                if (sc > 0.f) {
-                    bre = vre * sc;
-                    bim = vim * sc;
-                    l1 += fmaf(m2, rs, -tau);
-                    lib[nb] = (uint16_t)l;
-                    lvb[nb] = make_float2(bre, bim);
-                    ++nb;
-                }
+                const bool nz = sc > 0.f;
+                const float bre = nz ? vre * sc : 0.f, bim = nz ? vim * sc : 0.f;
+                if (nz)
+                    vlb[nb] = make_float2(bre, bim);
+                nb += nz;
+                mnew |= (uint32_t)nz << j;
+                l1 += nz ? fmaf(m2, rs, -tau) : 0.f;
                 const float ex = bre - yx, ey = bim - yy;
                 dd = fmaf(ex, ex, fmaf(ey, ey, dd));
                 const float fx = bre - xv.x, fy = bim - xv.y;
                 dx = fmaf(fx, fx, fmaf(fy, fy, dx));
                 xn = fmaf(bre, bre, fmaf(bim, bim, xn));
             }
+            mkb[c] = mnew;
         }
 
-        // ---- 3. A xbar over the nonzeros of xbar (ascending l), Eq. 15, accept, stop
+        // ---- 3. A xbar over the nonzeros of xbar (ascending l, FP32 A in shared memory), then
+        // ||A xbar - A y||^2 = ||(A xbar - g) - r|| ^2 and F's ||A xbar - g||^2 with r = A y - g
+        const bool dead = aborted || (tflag[4] != 0);  // the gradient of this sweep is stale
+        float my_lhs = 0.f, my_res = 0.f;
+        float2 acc[32];
         if (act) {
-            float2 acc[32];
 #pragma unroll
             for (int n = 0; n < 32; ++n)
                 acc[n] = make_float2(0.f, 0.f);
-            for (int j = 0; j < nb; ++j) {
-                const int l = lib[j];
-                const float2 v = lvb[j];
-                const float2 *Al = sA + l * N;
+            int q = 0;
+            for (int c = 0; c < NC; ++c) {
+                uint32_t m = mkb[c];
+                while (m) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1u;
+                    const float2 v = vlb[q++];
+                    const float2 *Al = sA + (kChunkPts * c + j) * N;
 #pragma unroll
-                for (int n = 0; n < 32; ++n) {
-                    if (n < N) {
-                        const float2 av = Al[n];
-                        acc[n].x = fmaf(av.x, v.x, fmaf(-av.y, v.y, acc[n].x));
-                        acc[n].y = fmaf(av.x, v.y, fmaf(av.y, v.x, acc[n].y));
+                    for (int n = 0; n < 32; ++n) {
+                        if (n < N) {
+                            const float2 av = Al[n];
+                            acc[n].x = fmaf(av.x, v.x, fmaf(-av.y, v.y, acc[n].x));
+                            acc[n].y = fmaf(av.x, v.y, fmaf(av.y, v.x, acc[n].y));
+                        }
                     }
                 }
             }
-            // with r = A y - g:  ||A xbar - A y||^2 = ||(A xbar - g) - r||^2,  F = ||A xbar - g||^2 + lam |xbar|_1
             const float2 *gp = a.g + (size_t)pix * N;
-            float lhs = 0.f, res = 0.f;
 #pragma unroll
             for (int n = 0; n < 32; ++n) {
                 if (n < N) {
@@ -487,13 +487,16 @@ __global__ void __launch_bounds__(kTiles * kSlots, 1) k_rbpg_px(const __grid_con
                     const float rx = fmaf(beta, u.x - up.x, u.x), ry = fmaf(beta, u.y - up.y, u.y);
                     acc[n].x -= gv.x;  // A xbar - g
                     acc[n].y -= gv.y;
-                    const float d0 = acc[n].x - rx, d1 = acc[n].y - ry;
-                    lhs = fmaf(d0, d0, fmaf(d1, d1, lhs));
-                    res = fmaf(acc[n].x, acc[n].x, fmaf(acc[n].y, acc[n].y, res));
+                    const float e0 = acc[n].x - rx, e1 = acc[n].y - ry;
+                    my_lhs = fmaf(e0, e0, fmaf(e1, e1, my_lhs));
+                    my_res = fmaf(acc[n].x, acc[n].x, fmaf(acc[n].y, acc[n].y, my_res));
                 }
             }
-            const bool dead = aborted || (tflag[4] != 0);  // the gradient of this sweep is stale
-            const bool bt_ok = dead || lhs <= dd / (2.f * alpha);
+        }
+
+        // ---- 4. this thread's pixel: the same decision, the state update, output and refill
+        if (act) {
+            const bool bt_ok = dead || my_lhs <= dd / (2.f * alpha);
             if (!bt_ok && nbt_it < a.max_bt) {
                 // Eq. 15 failed: the next sweep redoes the prox with the smaller step and the
                 // same residual (the same rows give the same gradient)
@@ -501,7 +504,7 @@ __global__ void __launch_bounds__(kTiles * kSlots, 1) k_rbpg_px(const __grid_con
                 ++nbt;
                 ++nbt_it;
             } else {
-                const float Fb = fmaf(lam, l1, res);
+                const float Fb = fmaf(lam, l1, my_res);
                 const bool accepted = !dead && (Fb <= Fx);
                 const bool conv = !dead && ((dx <= a.tol * a.tol * xn) || (dx == 0.f));
                 const bool fin = dead || conv || (k >= a.max_iter);
@@ -515,7 +518,7 @@ __global__ void __launch_bounds__(kTiles * kSlots, 1) k_rbpg_px(const __grid_con
                     Fx = Fb;
                     nnz = nb;
                 }
-                // x^{k-1} <- x^k; x^k <- xbar when accepted (list buffers and A x - g)
+                // x^{k-1} <- x^k; x^k <- xbar when accepted (buffers of the lists and of A x - g)
                 if (accepted && !fin) {
                     const int nu = 1 - ub;
 #pragma unroll
@@ -534,20 +537,22 @@ __global__ void __launch_bounds__(kTiles * kSlots, 1) k_rbpg_px(const __grid_con
                     nx = nb;
                 }
                 if (fin) {
-                    // write x^k (ascending list) into the output row
+                    // write x^k into the output row
                     float2 *xq = a.x + (size_t)pix * L;
-                    const uint16_t *li = LI + bx * L;
-                    const float2 *lv = LV + bx * L;
+                    const uint32_t *mk = LM + bx * NC;
+                    const float2 *vl = LV + bx * L;
                     int q = 0;
-                    int nxt = (nx > 0) ? (int)li[0] : (int)kEnd;
-                    for (int l = 0; l < L; ++l) {
-                        float2 v = make_float2(0.f, 0.f);
-                        if (nxt == l) {
-                            v = lv[q];
-                            ++q;
-                            nxt = (q < nx) ? (int)li[q] : (int)kEnd;
+                    for (int c = 0; c < NC; ++c) {
+                        const uint32_t m = (nx > 0) ? mk[c] : 0u;
+                        for (int j = 0; j < kChunkPts; ++j) {
+                            const int l = kChunkPts * c + j;
+                            if (l >= L)
+                                break;
+                            float2 v = make_float2(0.f, 0.f);
+                            if ((m >> j) & 1u)
+                                v = vl[q++];
+                            xq[l] = v;
                         }
-                        xq[l] = v;
                     }
                     a.status[pix] = (nnz == 0) ? (st | BPDN_PX_ZERO_SOLUTION) : st;
                     a.iters[pix] = k;
