@@ -11,11 +11,14 @@ Functions and what they follow:
   gram_toeplitz, aah      A^H A and A A^H of the Eq. 5 operator
   lipschitz               the step constant of Eq. 14's remark, read as 2*lambda_max(A^H A)
   soft                    Eq. 10 read for complex values (complex soft threshold)
-  rbpg / rbpg_batch       Algorithm 1 with Eqs. 11-15 (the readings are listed in the C file)
+  rbpg / rbpg_batch       Algorithm 1 with Eqs. 11-15 (the readings are listed in the C file);
+                          optionally with the gradient's operands rounded to bfloat16
+  bf16_round              rounding to bfloat16 (binary32 first, ties to even), from its definition
   rbpg_block(_batch)      Algorithm 1 with randomized blocks of one pixel's grid (Eqs. 13-14);
   block_probabilities     Eq. 14's P_j from the block Lipschitz constants;
   splitmix64              the counter-based generator of the block draws
-  minimise(_batch)        the exact minimiser of Eq. 6 (coordinate descent + Newton + certificate)
+  minimise(_batch)        the exact minimiser of Eq. 6 (coordinate descent + Newton + certificate;
+                          a working-set loop from 0 for grids beyond 4096 points: minimise_ws)
   newton_polish           Newton on the smooth optimality system of Eq. 6 on a given support
   kkt, objective          optimality certificate and F of Eq. 6
   select (module)         SL1MMER steps (2)-(3) of Sec. III-A: scatterer candidates from the
@@ -81,7 +84,9 @@ def _configure(lib):
     lib.orc_objective.argtypes = [dp, c_int, c_int, dp, c_double, dp]
     lib.orc_objective.restype = c_double
     lib.orc_rbpg.argtypes = [dp, c_int, c_int, dp, c_double, c_double, c_double, c_double,
-                             c_int, c_int, dp, ip, dp, ip, ip, dp, dp, dp]
+                             c_int, c_int, c_int, dp, ip, dp, ip, ip, dp, dp, dp]
+    lib.orc_bf16_round.argtypes = [c_double, dp]
+    lib.orc_bf16_round.restype = c_double
     lib.orc_rbpg.restype = c_int
     lib.orc_cd.argtypes = [dp, c_int, c_int, dp, c_double, c_double, c_long, dp, lp]
     lib.orc_cd.restype = c_int
@@ -94,6 +99,8 @@ def _configure(lib):
     lib.orc_min.restype = c_int
     lib.orc_rbpg_batch.argtypes = [dp, c_int, c_int, dp, c_i64, dp, c_double, c_double,
                                    c_double, c_int, c_int, dp, ip, ip]
+    lib.orc_min_ws.argtypes = [dp, c_int, c_int, dp, c_double, dp, dp, dp, dp, ip]
+    lib.orc_min_ws.restype = c_int
     lib.orc_min_batch.argtypes = [dp, c_int, c_int, dp, c_i64, dp, c_double, c_long, dp, dp,
                                   dp, dp, ip, lp, ip]
     lib.orc_adjoint.argtypes = [dp, c_int, c_int, c_double, dp, dp, dp, dp]
@@ -213,8 +220,10 @@ def default_alpha0(A: np.ndarray) -> float:
 
 
 def rbpg(A, g, lam: float, *, alpha0: float | None = None, c_alpha: float = 0.5,
-         tol: float = 1e-6, max_iter: int = 500, max_bt: int = 64, trace: bool = False):
-    """Algorithm 1 for one pixel in FP64.  Returns dict(x, iters, status[, trace arrays])."""
+         tol: float = 1e-6, max_iter: int = 500, max_bt: int = 64, trace: bool = False,
+         bf16_operands: bool = False):
+    """Algorithm 1 for one pixel in FP64.  Returns dict(x, iters, status[, trace arrays]).
+    bf16_operands: the gradient's operands A and A y - g rounded to bfloat16 first."""
     A, g = _c128(A), _c128(g)
     N, L = A.shape
     a0 = default_alpha0(A) if alpha0 is None else float(alpha0)
@@ -224,7 +233,7 @@ def rbpg(A, g, lam: float, *, alpha0: float | None = None, c_alpha: float = 0.5,
     ta, tacc, tn, tF, tm, ts = (np.zeros(T), np.zeros(T, np.int32), np.zeros(T, np.int32),
                                 np.zeros(T), np.zeros(T), np.zeros(T))
     st = _load().orc_rbpg(_dp(A), N, L, _dp(g), float(lam), a0, float(c_alpha), float(tol),
-                          int(max_iter), int(max_bt), _dp(x), _ip(it), _dp(ta), _ip(tacc),
+                          int(max_iter), int(max_bt), 1 if bf16_operands else 0, _dp(x), _ip(it), _dp(ta), _ip(tacc),
                           _ip(tn), _dp(tF), _dp(tm), _dp(ts))
     out = {"x": x, "iters": int(it[0]), "status": int(st)}
     if trace:
@@ -232,6 +241,14 @@ def rbpg(A, g, lam: float, *, alpha0: float | None = None, c_alpha: float = 0.5,
         out.update(alpha=ta[:k].copy(), accepted=tacc[:k].astype(bool), n_bt=tn[:k].copy(),
                    F=tF[:k].copy(), margin=tm[:k].copy(), step=ts[:k].copy())
     return out
+
+
+def bf16_round(v: float) -> tuple[float, float]:
+    """v rounded to bfloat16 (through binary32, ties to even) and its distance from the
+    nearest rounding boundary in bfloat16 steps."""
+    d = np.zeros(1)
+    r = _load().orc_bf16_round(float(v), _dp(d))
+    return float(r), float(d[0])
 
 
 def rbpg_batch(A, G, lam, *, alpha0: float | None = None, c_alpha: float = 0.5,
@@ -352,6 +369,20 @@ def kkt(A, g, lam: float, x):
 def minimise(A, g, lam: float, *, cd_tol: float = 1e-14, max_sweeps: int = 200000):
     r = minimise_batch(A, np.asarray(g)[None, :], lam, cd_tol=cd_tol, max_sweeps=max_sweeps)
     return {k: v[0] for k, v in r.items()}
+
+
+def minimise_ws(A, g, lam: float):
+    """The exact minimiser of Eq. 6 by the working-set loop from x = 0 (no full-grid
+    coordinate descent; minimise_batch takes this path by itself for grids beyond 4096
+    points).  Returns dict(x, on_res, off_max, min_abs_on, nS, flags)."""
+    A, g = _c128(A), _c128(g)
+    N, L = A.shape
+    x = np.empty(L, np.complex128)
+    on, off, mn = np.zeros(1), np.zeros(1), np.zeros(1)
+    nS = np.zeros(1, np.int32)
+    fl = _load().orc_min_ws(_dp(A), N, L, _dp(g), float(lam), _dp(x), _dp(on), _dp(off), _dp(mn), _ip(nS))
+    return {"x": x, "on_res": float(on[0]), "off_max": float(off[0]), "min_abs_on": float(mn[0]),
+            "nS": int(nS[0]), "flags": int(fl)}
 
 
 def minimise_batch(A, G, lam, *, cd_tol: float = 1e-14, max_sweeps: int = 200000):

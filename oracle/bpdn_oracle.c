@@ -177,6 +177,37 @@ static int all_finite(const cplx *v, int n)
     return 1;
 }
 
+/*
+ * Round v to bfloat16 (the upper 16 bits of IEEE binary32), the operand format of the
+ * tensor-core contraction: v is first rounded to binary32, then to the nearest
+ * bfloat16, ties to even (add 0x7FFF plus the lowest kept bit, drop the low 16 bits).
+ * *dist (may be NULL) receives the distance of the binary32 value from the nearest
+ * bfloat16 rounding boundary, in units of one bfloat16 step (0: on a boundary, 0.5: on
+ * a bfloat16 value).  Finite inputs only.
+ */
+double orc_bf16_round(double v, double *dist)
+{
+    float f = (float)v;
+    uint32_t b;
+    memcpy(&b, &f, sizeof b);
+    const uint32_t rem = b & 0xFFFFu;
+    if (dist)
+        *dist = fabs((double)rem - 32768.0) / 65536.0;
+    b += 0x7FFFu + ((b >> 16) & 1u);
+    b &= 0xFFFF0000u;
+    memcpy(&f, &b, sizeof f);
+    return (double)f;
+}
+
+static cplx bf16_c(cplx v, double *dist)
+{
+    double d1, d2;
+    cplx r = orc_bf16_round(creal(v), &d1) + I * orc_bf16_round(cimag(v), &d2);
+    if (dist)
+        *dist = fmin(d1, d2);
+    return r;
+}
+
 /* --------------------------------------------------------- Algorithm 1 */
 
 /*
@@ -207,9 +238,13 @@ static int all_finite(const cplx *v, int n)
  * margin of any discrete decision taken in the iteration (prox thresholds,
  * line-search test, accept test) and the relative candidate step
  * ||xbar - x^k|| / max(||xbar||, 1e-30) that the stopping test compares with tol.
+ * bf16_operands != 0: the gradient's two operands, A and r = A y - g, are rounded to
+ * bfloat16 (orc_bf16_round) before the products, which are summed in FP64 -- the
+ * arithmetic of a BF16 tensor-core contraction up to its FP32 accumulation; the distance of
+ * every rounded r_n from its rounding boundary then enters the trace's margin.
  */
 int orc_rbpg(const cplx *A, int N, int L, const cplx *g, double lam, double alpha0,
-             double c_alpha, double tol, int max_iter, int max_bt, cplx *x_out,
+             double c_alpha, double tol, int max_iter, int max_bt, int bf16_operands, cplx *x_out,
              int *iters_out, double *tr_alpha, int *tr_acc, int *tr_nbt, double *tr_F,
              double *tr_margin, double *tr_step)
 {
@@ -225,6 +260,7 @@ int orc_rbpg(const cplx *A, int N, int L, const cplx *g, double lam, double alph
     cplx *r = (cplx *)calloc(Nz, sizeof(cplx));
     cplx *Axb = (cplx *)calloc(Nz, sizeof(cplx));
     cplx *tmp = (cplx *)calloc(Nz, sizeof(cplx));
+    cplx *Ab = NULL; /* A rounded to bfloat16 (bf16_operands) */
     int k = 0;
 
     if (!all_finite(g, N)) {
@@ -235,6 +271,11 @@ int orc_rbpg(const cplx *A, int N, int L, const cplx *g, double lam, double alph
     double alpha = alpha0;
     double Fx = norm2sq(g, N); /* F(0) */
     int stopped = 0;
+    if (bf16_operands) {
+        Ab = (cplx *)malloc(sizeof(cplx) * Nz * Lz);
+        for (size_t i = 0; i < Nz * Lz; ++i)
+            Ab[i] = bf16_c(A[i], NULL);
+    }
     for (k = 1; k <= max_iter; ++k) {
         double beta = (double)(k - 2) / (double)(k + 1);
         for (int l = 0; l < L; ++l)
@@ -242,7 +283,17 @@ int orc_rbpg(const cplx *A, int N, int L, const cplx *g, double lam, double alph
         matvec(A, N, L, y, Ay);
         for (int n = 0; n < N; ++n)
             r[n] = Ay[n] - g[n];
-        matvec_h(A, N, L, r, grad);
+        double rmargin = INFINITY;
+        if (bf16_operands) {
+            for (int n = 0; n < N; ++n) {
+                double dn;
+                r[n] = bf16_c(r[n], &dn);
+                rmargin = fmin(rmargin, dn);
+            }
+            matvec_h(Ab, N, L, r, grad);
+        } else {
+            matvec_h(A, N, L, r, grad);
+        }
         for (int l = 0; l < L; ++l)
             grad[l] *= 2.0;
 
@@ -269,7 +320,7 @@ int orc_rbpg(const cplx *A, int N, int L, const cplx *g, double lam, double alph
             }
             double rhs = dd / (2.0 * alpha);
             double bm = (lhs + rhs > 0.0) ? fabs(rhs - lhs) / fmax(lhs, rhs) : INFINITY;
-            margin = fmin(pm, bm);
+            margin = fmin(fmin(pm, bm), rmargin);
             if (lhs <= rhs)
                 break;
             if (nbt >= max_bt) {
@@ -333,6 +384,7 @@ done:
         x_out[l] = x[l];
     if (iters_out)
         *iters_out = k;
+    free(Ab);
     free(x); free(xp); free(y); free(grad); free(v); free(xb);
     free(Ay); free(r); free(Axb); free(tmp);
     return status;
@@ -923,6 +975,31 @@ static int repair_working_set(const cplx *A, int N, int L, const cplx *g, double
 }
 
 /*
+ * Exact minimiser of Eq. 6 from x = 0 by the working-set loop above alone (restricted
+ * coordinate descent on the support and the largest dual violators, Newton on the
+ * nonzeros, until the certificate holds): for grids whose full L x L Gram matrix, which
+ * coordinate descent over the whole grid keeps, is too large.  Flags as orc_min (bit2 when
+ * the certificate fails, bit3 for non-finite input).
+ */
+int orc_min_ws(const cplx *A, int N, int L, const cplx *g, double lam, cplx *x, double *on_res,
+               double *off_max, double *min_abs_on, int *nS)
+{
+    for (int l = 0; l < L; ++l)
+        x[l] = 0.0;
+    if (!all_finite(g, N)) {
+        *on_res = *off_max = *min_abs_on = 0.0;
+        *nS = 0;
+        return 8;
+    }
+    const int rc = repair_working_set(A, N, L, g, lam, x, 400);
+    orc_kkt(A, N, L, g, lam, x, on_res, off_max, min_abs_on, nS);
+    return rc ? 4 : 0;
+}
+
+/* grids beyond this many points skip the full-grid coordinate descent of orc_min */
+#define ORC_CD_MAX_L 4096
+
+/*
  * Exact minimiser of Eq. 6 for one pixel: coordinate descent, then Newton on
  * the support CD found (when CD stops, its support is the minimiser's unless
  * a component sits at a tie), then the certificate.  When the certificate fails
@@ -945,6 +1022,11 @@ int orc_min(const cplx *A, int N, int L, const cplx *g, double lam, double cd_to
         if (sweeps)
             *sweeps = 0;
         return 8;
+    }
+    if (L > ORC_CD_MAX_L) {
+        if (sweeps)
+            *sweeps = 0;
+        return orc_min_ws(A, N, L, g, lam, x, on_res, off_max, min_abs_on, nS);
     }
     if (orc_cd(A, N, L, g, lam, cd_tol, max_sweeps, x, sweeps))
         flags |= 1;
@@ -1071,7 +1153,7 @@ void orc_rbpg_batch(const cplx *A, int N, int L, const cplx *g, int64_t P, const
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t p = 0; p < P; ++p)
         status[p] = orc_rbpg(A, N, L, g + (size_t)p * N, lam[p], alpha0, c_alpha, tol, max_iter,
-                             max_bt, x + (size_t)p * L, iters + p, NULL, NULL, NULL, NULL, NULL, NULL);
+                             max_bt, 0, x + (size_t)p * L, iters + p, NULL, NULL, NULL, NULL, NULL, NULL);
 }
 
 void orc_rbpg_block_batch(const cplx *A, int N, int L, const cplx *g, int64_t P, const double *lam,

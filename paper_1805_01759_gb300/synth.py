@@ -47,6 +47,7 @@ __all__ = [
     "MotionGeometry",
     "make_stack_md",
     "workload_motion",
+    "workload_motion4d",
 ]
 
 
@@ -340,3 +341,22 @@ def workload_motion(P: int = 1 << 18, seed: int = 7, L_s: int = 32, L_v: int = 1
                           L_p=np.array([L_v]))
     return make_stack_md(geom, P, rng, lam=default_lambda(N, geom.L_total))
 
+
+
+def workload_motion4d(P: int = 1 << 12, seed: int = 8, L_s: int = 64, L_v: int = 16, L_a: int = 16) -> Stack:
+    """The 4-D reading of Eqs. 3-4 (elevation, linear velocity and the amplitude of a
+    seasonal motion): N = 25 acquisitions, baselines U[-250, 250] m, times U[0, 4] years,
+    elevation grid L_s on [-100, 100] m, velocity grid L_v on [-0.02, 0.02] m/yr, seasonal
+    amplitude grid L_a on [-0.01, 0.01] m with the base function sin(2 pi t) (t in years):
+    eta_1 = 2 t_n / wavelength, eta_2 = 2 sin(2 pi t_n) / wavelength.  The default grid has
+    64 x 16 x 16 = 16,384 points.  SNR U[5, 20] dB; lambda by the rule of the other
+    workloads with the whole grid's size."""
+    rng = np.random.default_rng(seed)
+    N = 25
+    b = rng.uniform(-250.0, 250.0, N)
+    t = rng.uniform(0.0, 4.0, N)
+    eta = np.stack([2.0 * t / 0.031, 2.0 * np.sin(2.0 * np.pi * t) / 0.031])
+    geom = MotionGeometry(np.asarray(b, np.float64), 0.031, 7.0e5, -100.0, 100.0, L_s, eta=eta,
+                          p_min=np.array([-0.02, -0.01]), p_max=np.array([0.02, 0.01]),
+                          L_p=np.array([L_v, L_a]))
+    return make_stack_md(geom, P, rng, lam=default_lambda(N, geom.L_total))

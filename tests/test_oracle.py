@@ -643,3 +643,74 @@ def test_oracle_reproduces_stored_minimiser():
             want[int(row[0]), int(row[1])] = float(row[2]) + 1j * float(row[3])
     assert np.array_equal(r["x"] != 0, want != 0)
     np.testing.assert_allclose(r["x"], want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+def _torch_bf16(a):
+    """bfloat16 rounding by torch's own conversion (binary32 first), as float64."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(torch.float32)
+    return t.to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def test_bf16_rounding_matches_torch():
+    """The oracle's bfloat16 rounding against torch's conversion on random values, on exact
+    ties (low 16 bits 0x8000: ties to even) and on bfloat16 values themselves."""
+    rng = np.random.default_rng(0)
+    v = np.concatenate([rng.standard_normal(2000) * 10.0 ** rng.integers(-6, 6, 2000),
+                        [0.0, -0.0, 1.0, -3.5, 1e-30, 3e30]])
+    bits = rng.integers(0, 1 << 16, 200).astype(np.uint32) << 16
+    ties = (bits | 0x8000).view(np.float32).astype(np.float64)
+    exact = bits.view(np.float32).astype(np.float64)
+    for arr, dist in ((v, None), (ties, 0.0), (exact, 0.5)):
+        arr = arr[np.isfinite(arr)]
+        ref = _torch_bf16(arr)
+        for a, r in zip(arr, ref):
+            got, d = oracle.bf16_round(float(a))
+            assert got == r, (a, got, r)
+            if dist is not None:
+                assert d == dist, (a, d)
+
+
+def test_bf16_operand_first_iteration_closed_form():
+    """Algorithm 1 with BF16 operands at k = 1 (x = 0, y = 0, r = -g): x^1 is the soft
+    threshold of -2 alpha Ab^H bf16(-g) at alpha lambda (alpha after the step cuts of that
+    iteration), or 0 if the step was rejected, with the rounding taken by torch."""
+    st = synth.workload_small(P=24, seed=2)
+    A = oracle.operator(st.geom)
+    Ab = _torch_bf16(A.real) + 1j * _torch_bf16(A.imag)
+    for p in range(st.g.shape[0]):
+        g = st.g[p].astype(np.complex128)
+        r = oracle.rbpg(A, g, st.lam, max_iter=1, tol=0.0, trace=True, bf16_operands=True)
+        alpha = r["alpha"][0]
+        gb = _torch_bf16(-g.real) + 1j * _torch_bf16(-g.imag)
+        ref = oracle.soft(-2.0 * alpha * (Ab.conj().T @ gb), alpha * st.lam)
+        if not r["accepted"][0]:
+            ref = np.zeros_like(ref)
+        np.testing.assert_allclose(r["x"], ref, atol=1e-12 * max(1.0, np.abs(ref).max()))
+        # and it differs from the FP64-operand iteration by the BF16 rounding only
+        r64 = oracle.rbpg(A, g, st.lam, max_iter=1, tol=0.0)
+        assert np.linalg.norm(r["x"] - r64["x"]) <= 2e-2 * max(np.linalg.norm(r64["x"]), 1e-12)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_working_set_minimiser_from_zero(seed):
+    """The working-set minimiser from x = 0 (the path for large grids) against brute-force
+    supports on tiny problems and against coordinate descent on the small workload."""
+    rng = np.random.default_rng(700 + seed)
+    N = int(rng.integers(3, 5))
+    L = 8
+    b = rng.uniform(-250, 250, N)
+    A = oracle.operator(_geom(b, -40.0, 40.0, L))
+    g = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    lam = rng.uniform(0.3, 0.6) * np.max(np.abs(2 * A.conj().T @ g))
+    xb, Fb = bruteforce_min(A, g, lam)
+    r = oracle.minimise_ws(A, g, lam)
+    assert r["flags"] == 0 and np.isfinite(Fb)
+    np.testing.assert_allclose(r["x"], xb, atol=1e-9 * max(1.0, np.abs(xb).max()))
+    st = synth.workload_small(P=4, seed=10 + seed)
+    A = oracle.operator(st.geom)
+    for p in range(4):
+        a = oracle.minimise(A, st.g[p], st.lam)
+        w = oracle.minimise_ws(A, st.g[p], st.lam)
+        assert w["flags"] == 0
+        np.testing.assert_allclose(w["x"], a["x"], atol=1e-9 * max(1.0, np.abs(a["x"]).max()))

@@ -37,6 +37,8 @@ MUTANTS = {
                                 "Gij += A[(size_t)n * L + S[i]] * conj(A[(size_t)n * L + S[j]]);"),
     "adjoint_dg_factor": ("dLdg[n] = 2.0 * acc;", "dLdg[n] = acc;"),
     "adjoint_lambda_sign": ("*dLdlam = -dl;", "*dLdlam = dl;"),
+    "bf16_truncation": ("b += 0x7FFFu + ((b >> 16) & 1u);", "b += 0u;"),
+    "bf16_residual_unrounded": ("                r[n] = bf16_c(r[n], &dn);", "                (void)bf16_c(r[n], &dn);"),
     "splitmix_shift": ("z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;", "z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ULL;"),
     "block_extrapolate_everywhere": ("y[l] = (l >= lo && l < hi) ? x[l] + beta * (x[l] - xp[l]) : x[l];",
                                      "y[l] = x[l] + beta * (x[l] - xp[l]);"),
