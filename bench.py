@@ -990,11 +990,51 @@ def run_motion(args) -> None:
                      "mean_iterations": float(res.iters.double().mean())}
         if not args.no_cpu_baseline:
             out[name]["oracle_sample"] = _motion_sample(st, res, 32)
+    if args.motion4d_pixels > 0:
+        out["fp32_4d_64x16x16"] = _motion4d(args)
     print(json.dumps({"metric": "certified pixels/s, multi-component operator (elevation x velocity)",
                       "value": out["bf16_32x16"]["certified_pixels_per_s"], "unit": "pixels/s",
                       "workload": f"N=25, times U[0,4] yr, linear velocity grid 16 points on [-0.02,0.02] m/yr, "
                                   f"elevation on [-100,100] m, {args.motion_pixels} pixels, seed 7",
                       "runs": out}), flush=True)
+
+
+def _motion4d(args) -> dict:
+    """The 4-D grid (elevation x velocity x seasonal amplitude, 64 x 16 x 16 = 16,384 points)
+    through the split-grid FP32 kernel and the refit: the whole solve, the iterations alone,
+    and the gradient's FP32 rate (8 N L flops per sweep of a pixel) over the iteration time."""
+    import torch
+    from paper_1805_01759_gb300 import api, synth
+    st = synth.workload_motion4d(P=args.motion4d_pixels, seed=8)
+    op = api.Operator.from_geometry(st.geom)
+    g = torch.from_numpy(st.g).cuda()
+    row = {"L": op.L, "N": op.N, "pixels": int(g.shape[0])}
+    for key, kw in (("solve", dict(precision=0, tol=args.tol_fp32)),
+                    ("iterations_only", dict(precision=0, tol=args.tol_fp32, refit=0))):
+        for _ in range(max(1, min(args.warmup, 2))):
+            api.solve(op, g, st.lam, **kw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = max(1, min(args.steps, 3))
+        e0.record()
+        for _ in range(steps):
+            res = api.solve(op, g, st.lam, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        if key == "solve":
+            cert = (res.status & 64) != 0
+            row.update(ms_per_step=ms, certified_frac=float(cert.float().mean()),
+                       certified_pixels_per_s=float(cert.sum()) / (ms / 1e3),
+                       mean_iterations=float(res.iters.double().mean()))
+            keep = res
+        else:
+            sweeps = float((res.iters.double() + res.nbt.double()).sum())
+            row.update(ms_iterations=ms, sweeps=sweeps,
+                       gradient_tflops=sweeps * 8.0 * op.N * op.L / (ms / 1e3) / 1e12)
+    if not args.no_cpu_baseline:
+        row["oracle_sample"] = _motion_sample(st, keep, 16)
+    return row
 
 
 def _motion_sample(st, res, n):
@@ -1027,6 +1067,8 @@ def main(argv=None) -> None:
     ap.add_argument("--cpu-sample", type=int, default=2048, help="pixels of the CPU baseline leg")
     ap.add_argument("--ref-sample", type=int, default=1024, help="pixels per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--motion4d-pixels", type=int, default=1 << 14,
+                    help="pixels of the 4-D grid run of the motion leg (0: skip)")
     ap.add_argument("--no-precision-report", action="store_true",
                     help="skip the error-before/after-refit report (small stack and patch sample)")
     ap.add_argument("--precision", choices=["fp32", "bf16", "both"], default="both")

@@ -59,7 +59,7 @@ enum bpdn_status {
 
 /* limits */
 #define BPDN_MAX_N 80
-#define BPDN_MAX_L 1024
+#define BPDN_MAX_L 65536 /* grids of more than 1024 points: see bpdn_solve */
 #define BPDN_MAX_SMAX 32
 #define BPDN_MAX_KSEL 4  /* scatterers per pixel bpdn_select considers */
 #define BPDN_MAX_MOTION 2 /* motion dimensions of bpdn_make_operator_md */
@@ -157,7 +157,11 @@ int bpdn_op_export(bpdn_op_t op, int32_t what, void *d_dst, size_t dst_bytes, vo
  * (256 bytes), A_j A_j^H per block when opt->blocks >= 2, and, with the refit, 460 bytes
  * per pixel of scratch for the refit in three launches (the FP32 support search of every
  * pixel, the FP64 finish and certificate, further rounds for the pixels that need them).  A workspace smaller than this, down to the first two parts,
- * is accepted too: the refit then runs in a single launch, with the same results. */
+ * is accepted too: the refit then runs in a single launch, with the same results.
+ * Operators of more than 1024 grid points add the split-grid kernel's scratch, which
+ * bpdn_solve cannot do without: the operator transposed in FP32 (8 N L bytes) and three
+ * rows of L complex values per pixel in flight (at most 4 per CTA, as many CTAs as the
+ * device holds at once and P needs). */
 size_t bpdn_solve_workspace_bytes(bpdn_op_t op, int64_t P, const bpdn_options *opt);
 
 /*
@@ -175,6 +179,11 @@ size_t bpdn_solve_workspace_bytes(bpdn_op_t op, int64_t P, const bpdn_options *o
  * d_nbt      device int32 [P] out (may be NULL): total step cuts (Eq. 15 failures)
  * d_workspace  >= bpdn_solve_workspace_bytes(op, P, opt) bytes, 256-byte aligned
  * The operator's workspace must be resident on the current device.
+ * Grids of more than 1024 points (L up to BPDN_MAX_L, e.g. the multi-component grids of
+ * Eq. 4) run Algorithm 1 in a split-grid FP32 kernel: they need precision 0,
+ * tile_pixels 0 and blocks <= 1, and a workspace of at least
+ * bpdn_solve_workspace_bytes(op, P, opt) bytes; otherwise BPDN_ESIZE before any launch.
+ * bpdn_solve_ragged and bpdn_solve_noalloc refuse such operators (BPDN_ESIZE).
  */
 int bpdn_solve(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda,
                int32_t lambda_per_pixel, const bpdn_options *opt, void *d_x, int32_t *d_support,

@@ -24,7 +24,7 @@ PX_CERTIFIED = 64
 PX_DEVICE_TIMEOUT = 128
 
 MAX_N = 80
-MAX_L = 1024
+MAX_L = 65536
 MAX_SMAX = 32
 MAX_KSEL = 4
 MAX_MOTION = 2

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbpdn.so")
-SOURCES = ["api.cu", "operator.cu", "rbpg.cu", "refit.cu", "backward.cu", "ragged.cu", "noalloc.cu", "select.cu", "rbpg_block.cu", "peaks.cu", "preclass.cu", "rbpg_px.cu"]
+SOURCES = ["api.cu", "operator.cu", "rbpg.cu", "refit.cu", "backward.cu", "ragged.cu", "noalloc.cu", "select.cu", "rbpg_block.cu", "peaks.cu", "preclass.cu", "rbpg_px.cu", "rbpg_split.cu"]
 HEADERS = ["bpdn_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -145,6 +145,19 @@ static size_t px_scratch_for(const OpHandle *op, int64_t P, const bpdn_options *
     return rbpg_px_scratch_bytes(*op, P, num_sms(op->device), max_smem_optin(op->device));
 }
 
+// grids of more than 1024 points run the split-grid FP32 kernel
+static bool split_grid(const OpHandle *op) { return op && op->L > 1024; }
+
+// scratch of the split-grid kernel for this solve (0 when the grid does not need it or the
+// options or sizes rule it out: solve_plan then names the reason)
+static size_t split_scratch_for(const OpHandle *op, int64_t P, const bpdn_options *opt)
+{
+    if (!split_grid(op) || !opt || opt->tile_pixels != 0 ||
+        rbpg_split_check(*op, opt->precision, opt->blocks, max_smem_optin(op->device))[0] != '\0')
+        return 0;
+    return rbpg_split_scratch_bytes(*op, P, num_sms(op->device));
+}
+
 static int check_solve_buffers(const OpHandle *op, const void *d_g, int64_t P, const float *d_lambda,
                                const void *d_x, const int32_t *d_status)
 {
@@ -192,17 +205,25 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
         return set_error(BPDN_EALIGN, "support must be 4-byte aligned");
     // the pixel-per-thread BF16 kernel when it suits the sizes and the workspace holds its scratch
     const size_t base = solve_min_workspace_bytes(opt);
-    const size_t pxb = px_scratch_for(op, P, opt);
+    const bool split = split_grid(op);
+    const size_t pxb = split ? 0 : px_scratch_for(op, P, opt);
     const bool use_px = pxb > 0 && workspace_bytes >= base + pxb;
-    if (opt->tile_pixels == 128 && !use_px)
+    const size_t spb = split_scratch_for(op, P, opt);
+    if (opt->tile_pixels == 128 && !use_px && !split)
         return set_error(BPDN_ESIZE, pxb ? "tile_pixels 128: the workspace does not hold the kernel's scratch"
                                          : "tile_pixels 128 needs 2N <= 64 and the operator within shared memory");
-    const char *why = (opt->blocks >= 2) ? rbpg_block_check(*op, opt->blocks, max_smem_optin(op->device))
-                      : use_px           ? ""
-                                         : rbpg_check(*op, opt->precision, opt->tile_pixels / 8,
-                                                      max_smem_optin(op->device));
+    const char *why = split ? (opt->tile_pixels != 0 ? "grids of more than 1024 points take tile_pixels 0"
+                                                     : rbpg_split_check(*op, opt->precision, opt->blocks,
+                                                                        max_smem_optin(op->device)))
+                      : (opt->blocks >= 2) ? rbpg_block_check(*op, opt->blocks, max_smem_optin(op->device))
+                      : use_px             ? ""
+                                           : rbpg_check(*op, opt->precision, opt->tile_pixels / 8,
+                                                        max_smem_optin(op->device));
     if (why[0] != '\0')
         return set_error(BPDN_ESIZE, "N = %d, L = %d, precision %d: %s", op->N, op->L, opt->precision, why);
+    if (split && (spb == 0 || workspace_bytes < base + spb))
+        return set_error(BPDN_ESIZE, "L = %d: the workspace does not hold the split-grid kernel's scratch "
+                                     "(bpdn_solve_workspace_bytes gives the size)", op->L);
     SolveLaunch &a = sp->a;
     a.g = (const float2 *)d_g;
     a.P = P;
@@ -230,6 +251,7 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     a.cum = (double *)((char *)d_workspace + 16 + 8 * 8);
     a.bscratch = a.blocks ? (double2 *)((char *)d_workspace + 256) : nullptr;
     a.px_scratch = use_px ? (unsigned char *)d_workspace + base : nullptr;
+    a.split_scratch = split ? (unsigned char *)d_workspace + base : nullptr;
     sp->refit = opt->refit != 0;
     RefitLaunch &r = sp->r;
     r.g = a.g;
@@ -245,7 +267,7 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     r.rounds = opt->refit_rounds;
     // the split refit when the workspace holds its scratch (after the iteration kernel's), else
     // the fused refit
-    const size_t rbase = base + (use_px ? pxb : 0);
+    const size_t rbase = base + (use_px ? pxb : 0) + (split ? spb : 0);
     r.split = (workspace_bytes >= rbase + refit_scratch_bytes(P)) ? (unsigned char *)d_workspace + rbase : nullptr;
     return BPDN_OK;
 }
@@ -270,6 +292,8 @@ int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
         if (rc)
             return rc;
         rc = check_cuda(launch_rbpg_block(*sp.op, sp.a, s), "block iteration kernel");
+    } else if (sp.a.split_scratch) {
+        rc = check_cuda(launch_rbpg_split(*sp.op, sp.a, num_sms(sp.op->device), s), "iteration kernel (split grid)");
     } else if (sp.a.px_scratch) {
         rc = check_cuda(launch_rbpg_px(*sp.op, sp.a, num_sms(sp.op->device), s), "iteration kernel (pixel per thread)");
     } else {
@@ -520,7 +544,8 @@ size_t bpdn_solve_workspace_bytes(bpdn_op_t h, int64_t P, const bpdn_options *op
     // then the scratch of the split refit (a smaller workspace, down to the least one, runs
     // the other iteration kernel and the fused refit)
     const OpHandle *op = reinterpret_cast<const OpHandle *>(h);
-    const size_t pxb = (op && op->magic == kOpMagic && P > 0) ? px_scratch_for(op, P, opt) : 0;
+    const bool ok = op && op->magic == kOpMagic && P > 0;
+    const size_t pxb = ok ? (split_grid(op) ? split_scratch_for(op, P, opt) : px_scratch_for(op, P, opt)) : 0;
     return solve_min_workspace_bytes(opt) + pxb + ((opt && opt->refit) ? refit_scratch_bytes(P) : 0);
 }
 

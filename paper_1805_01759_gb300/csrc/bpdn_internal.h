@@ -99,6 +99,9 @@ struct SolveLaunch {
     // pixel-per-thread BF16 kernel (k_rbpg_px): per-slot iterate lists and residual state,
     // or NULL when the solve runs the grid-point-per-thread kernel
     unsigned char *px_scratch;
+    // split-grid FP32 kernel (k_rbpg_split, grids of more than 1024 points): the transposed
+    // operator and the per-CTA row buffers, or NULL
+    unsigned char *split_scratch;
 };
 // iteration kernel (a.precision 0: FP32 CUDA cores, 1: BF16 tensor cores)
 cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
@@ -106,6 +109,11 @@ cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, c
 // (0 when the operator's sizes do not suit it), and its launch
 size_t rbpg_px_scratch_bytes(const OpHandle &op, int64_t P, int num_sms, int max_smem);
 cudaError_t launch_rbpg_px(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
+// the split-grid FP32 iteration kernel (L > 1024): "" when it takes the operator, else the
+// reason; bytes of its scratch for P pixels on this device (0: it cannot launch); its launch
+const char *rbpg_split_check(const OpHandle &op, int precision, int blocks, int max_smem);
+size_t rbpg_split_scratch_bytes(const OpHandle &op, int64_t P, int num_sms);
+cudaError_t launch_rbpg_split(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
 // many stacks in persistent launches, one per kernel variant present (at most 64 stacks each)
 cudaError_t launch_rbpg_batch(const OpHandle *const *ops, const SolveLaunch *as, int n, int num_sms,
                               cudaStream_t s);

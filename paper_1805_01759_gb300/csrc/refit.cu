@@ -860,19 +860,21 @@ __device__ __forceinline__ void refit_pixel(PixelSmem<KW> &P, const long long p,
         if (lane == 0)
             P.m = m;
     } else {
-        // cap rounds of a warp arg-max over |x_l|^2 excluding points already taken
-        uint32_t taken = 0;  // bit j: l = lane + 32 j taken (L <= 1024)
+        // cap rounds of a warp arg-max over |x_l|^2 in the order (|x_l|^2 descending, l
+        // ascending): round k takes the largest point after the one round k-1 took
+        float prev_a2 = INFINITY;
+        int prev_l = -1;
         for (int k = 0; k < cap; ++k) {
             float best = -1.f;
             int bl = -1;
-            for (int j = 0; lane + 32 * j < L; ++j) {
-                if (taken & (1u << j))
-                    continue;
-                const float2 v = xin[lane + 32 * j];
+            for (int l = lane; l < L; l += 32) {
+                const float2 v = xin[l];
                 const float a2 = v.x * v.x + v.y * v.y;
+                if (a2 > prev_a2 || (a2 == prev_a2 && l <= prev_l))
+                    continue;  // taken in an earlier round
                 if (a2 > best) {
                     best = a2;
-                    bl = lane + 32 * j;
+                    bl = l;
                 }
             }
 #pragma unroll
@@ -886,8 +888,8 @@ __device__ __forceinline__ void refit_pixel(PixelSmem<KW> &P, const long long p,
             }
             if (bl < 0)
                 break;  // cannot happen: more than cap grid points are nonzero
-            if ((bl & 31) == lane)
-                taken |= 1u << (bl >> 5);
+            prev_a2 = best;
+            prev_l = bl;
             if (lane == 0)
                 P.W[k] = bl;
         }
@@ -995,15 +997,7 @@ __device__ __forceinline__ void refit_pixel(PixelSmem<KW> &P, const long long p,
         const float near = (float)lam * (1.0f - 1e-4f);
         double worst = 0.0;
         int worst_l = -1;
-        uint32_t inW = 0;  // bit j: l = lane + 32 j is in W (L <= 1024)
-        for (int i = 0; i < m; ++i) {
-            const int w = P.W[i];
-            if ((w & 31) == lane)
-                inW |= 1u << (w >> 5);
-        }
         for (int l = lane; l < L; l += 32) {
-            if ((inW >> (l >> 5)) & 1u)
-                continue;
             float ux = 0.f, uy = 0.f;
             for (int n = 0; n < N; ++n) {
                 const float ar = A_re[n * lda + l], ai = A_im[n * lda + l];
@@ -1021,8 +1015,15 @@ __device__ __forceinline__ void refit_pixel(PixelSmem<KW> &P, const long long p,
             }
             const double u = 2.0 * sqrt(vx * vx + vy * vy);
             if (u > lam * (1.0 + 1e-9) && u > worst) {
-                worst = u;
-                worst_l = l;
+                // a point of W is never a violator (the scan over W is rare: only points
+                // past the threshold reach it)
+                bool inW = false;
+                for (int i = 0; i < m; ++i)
+                    inW = inW || (P.W[i] == l);
+                if (!inW) {
+                    worst = u;
+                    worst_l = l;
+                }
             }
         }
         // violators join W, largest first, at most 4 per round

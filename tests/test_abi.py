@@ -48,7 +48,8 @@ def test_workspace_sizes(lib):
     assert lib.bpdn_op_workspace_bytes(0, 400) == 0
     assert lib.bpdn_op_workspace_bytes(25, 0) == 0
     assert lib.bpdn_op_workspace_bytes(81, 400) == 0 and lib.bpdn_op_workspace_bytes(80, 400) > 0
-    assert lib.bpdn_op_workspace_bytes(25, 1025) == 0
+    assert lib.bpdn_op_workspace_bytes(25, 65537) == 0
+    assert lib.bpdn_op_workspace_bytes(25, 1025) > 0
     assert lib.bpdn_op_workspace_bytes(25, 400) % 256 == 0
 
 

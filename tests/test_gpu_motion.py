@@ -94,8 +94,8 @@ def test_motion_operator_refusals(api):
     with pytest.raises(_lib.BPDNError):
         op.export("h")
     # a grid larger than the library's maximum is refused before any launch
-    big = synth.MotionGeometry(st.geom.baselines_m, 0.031, 7e5, -100.0, 100.0, 512, eta=st.geom.eta,
-                               p_min=st.geom.p_min, p_max=st.geom.p_max, L_p=np.array([4]))
+    big = synth.MotionGeometry(st.geom.baselines_m, 0.031, 7e5, -100.0, 100.0, 1024, eta=st.geom.eta,
+                               p_min=st.geom.p_min, p_max=st.geom.p_max, L_p=np.array([65]))
     with pytest.raises(_lib.BPDNError) as e:
         api.Operator.from_geometry(big)
     assert e.value.code == _lib.BPDN_ESIZE
