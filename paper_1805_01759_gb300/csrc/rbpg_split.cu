@@ -1,17 +1,19 @@
 // Split-grid iteration kernel: Algorithm 1 (RBPG with backtracking, Eqs. 11-15) in FP32 for
 // grids too large for one thread per grid point in a CTA (the multi-component grids of Eq. 4,
-// L up to BPDN_MAX_L).  A CTA holds kSlots pixels; its eight warps walk the grid in 32-point
-// chunks (warp w takes chunks w, w + 8, ...), and every operator load of the gradient
-// serves all slots.  x^k, x^{k-1} and xbar of a slot are rows of the CTA's scratch in
-// global memory, gated by per-chunk nonzero masks in shared memory: only nonzeros are read
-// or written, so the rows cost traffic in proportion to the support, not to L.
+// L up to BPDN_MAX_L).  A CTA holds KS pixels (slots); its eight warps walk the grid in
+// 32-point chunks (warp w takes chunks w, w + 8, ...), and every operator load of the
+// gradient serves all KS slots.  x^k, x^{k-1} and xbar of a slot are rows of the CTA's
+// scratch in global memory, gated by per-chunk nonzero masks in shared memory: only nonzeros
+// are read or written, so the rows cost traffic in proportion to the support, not to L.
 //
 // One sweep:
 //   1. per chunk and lane (one grid point l): the gradient sum_n conj(A_nl) r_n of every
 //      slot from the FP32 tables (coalesced over l; r in shared memory), then per slot the
-//      extrapolation y = x + beta (x - x^{k-1}), the complex soft threshold of
-//      v = y - 2 alpha grad, the sums of Eq. 15, F and the stopping test, and A xbar over
-//      the chunk's nonzeros (ascending l) from the transposed table (coalesced over n);
+//      extrapolation y = x + beta (x - x^{k-1}) and the complex soft threshold of
+//      v = y - 2 alpha grad.  Only chunks where xbar, x^k or x^{k-1} has a nonzero go on to
+//      the sums of Eq. 15, F and the stopping test (a warp sum per chunk, added to the
+//      warp's running sums in chunk order) and to A xbar over the chunk's nonzeros
+//      (ascending l, from the transposed table, coalesced over n);
 //   2. warp p decides slot p: the warps' sums and A xbar added in warp order, Eq. 15, the
 //      monotone accept, the stopping test, the N-space update (A x^k, A x^{k-1}, A y and the
 //      next residual); a finished pixel's x goes to its output row and the slot is refilled.
@@ -28,16 +30,14 @@ namespace bpdn {
 
 namespace {
 
-constexpr int kWarps = 8;   // warps per CTA
-constexpr int kSlots = 4;   // pixels per CTA
-constexpr int kNCH = 3;     // rows n = lane + 32 c per lane (N <= 96)
+constexpr int kWarps = 8;  // warps per CTA
 constexpr int kThreads = 32 * kWarps;
 
 struct SplitParams {
     const float *A_re, *A_im;  // planar FP32 tables [N][lda]
     const float2 *AT;          // transposed FP32 table [L][N]
     int N, L, lda, NC;
-    float2 *rows;              // [ctas][kSlots][3][L]
+    float2 *rows;              // [ctas][KS][3][L]
     SolveLaunch a;
 };
 
@@ -45,7 +45,7 @@ struct SplitParams {
 struct SlotSt {
     long long pix;  // -1: the slot is empty
     int k, nbt, nbt_it, status, nnz;
-    float alpha, Fx, lam, beta;
+    float alpha, Fx, lam;
     int bx, bxp, bb;  // row buffers of x^k, x^{k-1} and xbar (bx == bxp after a rejected step)
 };
 
@@ -57,54 +57,74 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-// shared memory carve-up (float2 / float4 / uint32 sections, 16-byte aligned)
+// packed FP32 pair FMA: d = a * b + c on both halves (each half rounded as fmaf)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<unsigned long long *>(&a)), "l"(*reinterpret_cast<unsigned long long *>(&b)),
+          "l"(*reinterpret_cast<unsigned long long *>(&c)));
+    return *reinterpret_cast<float2 *>(&d);
+}
+
+// sweep parameters of a slot: beta, 2 alpha, tau = alpha lambda, and the three row buffers
+// (x^k | x^{k-1} << 2 | xbar << 4) as an int
+__device__ __forceinline__ float4 slot_par(float beta, float alpha, float lam, int bx, int bxp, int bb)
+{
+    return make_float4(beta, 2.f * alpha, alpha * lam, __int_as_float(bx | (bxp << 2) | (bb << 4)));
+}
+
+// shared memory carve-up (16-byte aligned sections)
 struct SplitSmem {
-    float2 *G, *Ax, *Axp, *Ay;  // [kSlots][N]
-    float2 *R;                  // [N][kSlots]: r_n of every slot, slot-minor
-    float2 *Wacc;               // [kSlots][kWarps][N]
-    float4 *Wsum;               // [kSlots][kWarps]: dd, l1, dx, xn
-    int *Wnnz;                  // [kSlots][kWarps]
-    uint32_t *M;                // [kSlots][3][NC] nonzero masks of the row buffers
-    SlotSt *S;                  // [kSlots]
+    float2 *G, *Ax, *Axp, *Ay;  // [KS][N]
+    float *R;                   // [N][2][KS]: Re r_n of every slot, then Im r_n (slot-minor)
+    float2 *Wacc;               // [KS][kWarps][N]
+    float4 *Wsum;               // [KS][kWarps]: dd, l1, dx, xn
+    float4 *Par;                // [KS]: slot_par
+    int *Wnnz;                  // [KS][kWarps]
+    uint32_t *M;                // [KS][3][NC] nonzero masks of the row buffers
+    SlotSt *S;                  // [KS]
 };
 
-__host__ __device__ inline size_t split_smem_bytes(int N, int NC)
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) / 16 * 16; }
+
+__host__ __device__ inline size_t split_smem_bytes(int KS, int N, int NC)
 {
     size_t b = 0;
-    b += (size_t)4 * kSlots * N * sizeof(float2);
-    b += (size_t)N * kSlots * sizeof(float2);
-    b += (size_t)kSlots * kWarps * N * sizeof(float2);
-    b += (size_t)kSlots * kWarps * sizeof(float4);
-    b += (size_t)kSlots * kWarps * sizeof(int);
-    b += (size_t)kSlots * 3 * NC * sizeof(uint32_t);
-    b = (b + 15) / 16 * 16;
-    b += (size_t)kSlots * sizeof(SlotSt);
+    b += align16((size_t)4 * KS * N * sizeof(float2));
+    b += align16((size_t)N * KS * sizeof(float2));
+    b += align16((size_t)KS * kWarps * N * sizeof(float2));
+    b += (size_t)KS * kWarps * sizeof(float4);
+    b += (size_t)KS * sizeof(float4);
+    b += align16((size_t)KS * kWarps * sizeof(int));
+    b += align16((size_t)KS * 3 * NC * sizeof(uint32_t));
+    b += (size_t)KS * sizeof(SlotSt);
     return b;
 }
 
+template <int KS>
 __device__ __forceinline__ SplitSmem carve(unsigned char *base, int N, int NC)
 {
     SplitSmem s;
     unsigned char *p = base;
     s.G = (float2 *)p;
-    p += (size_t)kSlots * N * sizeof(float2);
-    s.Ax = (float2 *)p;
-    p += (size_t)kSlots * N * sizeof(float2);
-    s.Axp = (float2 *)p;
-    p += (size_t)kSlots * N * sizeof(float2);
-    s.Ay = (float2 *)p;
-    p += (size_t)kSlots * N * sizeof(float2);
-    s.R = (float2 *)p;
-    p += (size_t)N * kSlots * sizeof(float2);
+    s.Ax = s.G + KS * N;
+    s.Axp = s.Ax + KS * N;
+    s.Ay = s.Axp + KS * N;
+    p += align16((size_t)4 * KS * N * sizeof(float2));
+    s.R = (float *)p;
+    p += align16((size_t)N * KS * sizeof(float2));
     s.Wacc = (float2 *)p;
-    p += (size_t)kSlots * kWarps * N * sizeof(float2);
+    p += align16((size_t)KS * kWarps * N * sizeof(float2));
     s.Wsum = (float4 *)p;
-    p += (size_t)kSlots * kWarps * sizeof(float4);
+    p += (size_t)KS * kWarps * sizeof(float4);
+    s.Par = (float4 *)p;
+    p += (size_t)KS * sizeof(float4);
     s.Wnnz = (int *)p;
-    p += (size_t)kSlots * kWarps * sizeof(int);
+    p += align16((size_t)KS * kWarps * sizeof(int));
     s.M = (uint32_t *)p;
-    p += (size_t)kSlots * 3 * NC * sizeof(uint32_t);
-    p = base + ((size_t)(p - base) + 15) / 16 * 16;
+    p += align16((size_t)KS * 3 * NC * sizeof(uint32_t));
     s.S = (SlotSt *)p;
     return s;
 }
@@ -124,6 +144,7 @@ __global__ void k_transpose_a(const float *__restrict__ A_re, const float *__res
 // Pixels with a non-finite g (or a solve with max_iter <= 0) get x = 0 at once.  With no
 // pixel left the slot is marked empty and its residual column zeroed, so that the shared
 // gradient loop adds nothing for it.
+template <int KS>
 __device__ void refill_slot(const SplitParams &prm, const SplitSmem &sm, int p, int lane)
 {
     const SolveLaunch &a = prm.a;
@@ -135,8 +156,10 @@ __device__ void refill_slot(const SplitParams &prm, const SplitSmem &sm, int p, 
             q = atomicAdd(a.counter, 1ULL);
         q = __shfl_sync(0xffffffffu, q, 0);
         if (q >= (unsigned long long)a.P) {
-            for (int n = lane; n < N; n += 32)
-                sm.R[n * kSlots + p] = make_float2(0.f, 0.f);
+            for (int n = lane; n < N; n += 32) {
+                sm.R[n * 2 * KS + p] = 0.f;
+                sm.R[n * 2 * KS + KS + p] = 0.f;
+            }
             if (lane == 0)
                 S.pix = -1;
             __syncwarp();
@@ -170,7 +193,8 @@ __device__ void refill_slot(const SplitParams &prm, const SplitSmem &sm, int p, 
             sm.Ax[p * N + n] = make_float2(0.f, 0.f);
             sm.Axp[p * N + n] = make_float2(0.f, 0.f);
             sm.Ay[p * N + n] = make_float2(0.f, 0.f);
-            sm.R[n * kSlots + p] = make_float2(-v.x, -v.y);
+            sm.R[n * 2 * KS + p] = -v.x;
+            sm.R[n * 2 * KS + KS + p] = -v.y;
             gg2 = fmaf(v.x, v.x, fmaf(v.y, v.y, gg2));
         }
         gg2 = warp_sum(gg2);
@@ -180,6 +204,7 @@ __device__ void refill_slot(const SplitParams &prm, const SplitSmem &sm, int p, 
             sm.M[(p * 3 + 1) * NC + c] = 0u;
         }
         if (lane == 0) {
+            const float lam = a.lam_pp ? a.lam[q] : a.lam[0];
             S.pix = (long long)q;
             S.k = 1;
             S.nbt = 0;
@@ -188,11 +213,11 @@ __device__ void refill_slot(const SplitParams &prm, const SplitSmem &sm, int p, 
             S.nnz = 0;
             S.alpha = a.alpha0;
             S.Fx = gg2;  // F(0) = ||g||^2
-            S.lam = a.lam_pp ? a.lam[q] : a.lam[0];
-            S.beta = 0.f;  // x^0 - x^{-1} = 0
+            S.lam = lam;
             S.bx = 0;
             S.bxp = 1;
             S.bb = 2;
+            sm.Par[p] = slot_par(0.f, a.alpha0, lam, 0, 1, 2);  // x^0 - x^{-1} = 0: beta unused
         }
         __syncwarp();
         return;
@@ -200,6 +225,7 @@ __device__ void refill_slot(const SplitParams &prm, const SplitSmem &sm, int p, 
 }
 
 // Warp p: the end of slot p's sweep (Eq. 15, accept, stopping test, N-space update).
+template <int KS, int NCH>
 __device__ void decide_slot(const SplitParams &prm, const SplitSmem &sm, float2 *rows, int p, int lane)
 {
     const SolveLaunch &a = prm.a;
@@ -216,10 +242,10 @@ __device__ void decide_slot(const SplitParams &prm, const SplitSmem &sm, float2 
         xn += t.w;
         nnz += sm.Wnnz[p * kWarps + v];
     }
-    float2 axb[kNCH], gg[kNCH];
+    float2 axb[NCH], gg[NCH];
     float lhs = 0.f, res = 0.f;
 #pragma unroll
-    for (int c = 0; c < kNCH; ++c) {
+    for (int c = 0; c < NCH; ++c) {
         axb[c] = make_float2(0.f, 0.f);
         gg[c] = make_float2(0.f, 0.f);
         const int n = lane + 32 * c;
@@ -240,16 +266,19 @@ __device__ void decide_slot(const SplitParams &prm, const SplitSmem &sm, float2 
     lhs = warp_sum(lhs);
     res = warp_sum(res);
     const float al = S.alpha, lam = S.lam, Fx = S.Fx;
-    const int nbt_it = S.nbt_it, k = S.k, obx = S.bx, obb = S.bb;
+    const int nbt_it = S.nbt_it, k = S.k, obx = S.bx, obxp = S.bxp, obb = S.bb;
     const long long q = S.pix;
+    const float beta_o = sm.Par[p].x;
     const bool bt_ok = lhs <= dd / (2.f * al);
     __syncwarp();  // every lane has read the slot state lane 0 updates below
     if (!bt_ok && nbt_it < a.max_bt) {
         // Eq. 15 failed: the next sweep redoes the prox with the smaller step
         if (lane == 0) {
-            S.alpha = al * a.c_alpha;
+            const float an = al * a.c_alpha;
+            S.alpha = an;
             S.nbt += 1;
             S.nbt_it = nbt_it + 1;
+            sm.Par[p] = slot_par(beta_o, an, lam, obx, obxp, obb);
         }
         __syncwarp();
         return;
@@ -265,7 +294,7 @@ __device__ void decide_slot(const SplitParams &prm, const SplitSmem &sm, float2 
     const float beta_n = (float)(k - 1) / (float)(k + 2);
     if (!fin) {
 #pragma unroll
-        for (int c = 0; c < kNCH; ++c) {
+        for (int c = 0; c < NCH; ++c) {
             const int n = lane + 32 * c;
             if (n < N) {
                 const float2 axo = sm.Ax[p * N + n];
@@ -275,7 +304,8 @@ __device__ void decide_slot(const SplitParams &prm, const SplitSmem &sm, float2 
                 const float2 ayn =
                     make_float2(fmaf(beta_n, axn.x - axo.x, axn.x), fmaf(beta_n, axn.y - axo.y, axn.y));
                 sm.Ay[p * N + n] = ayn;
-                sm.R[n * kSlots + p] = make_float2(ayn.x - gg[c].x, ayn.y - gg[c].y);
+                sm.R[n * 2 * KS + p] = ayn.x - gg[c].x;
+                sm.R[n * 2 * KS + KS + p] = ayn.y - gg[c].y;
             }
         }
     }
@@ -294,10 +324,10 @@ __device__ void decide_slot(const SplitParams &prm, const SplitSmem &sm, float2 
                 S.Fx = Fb;
             S.k = k + 1;
             S.nbt_it = 0;
-            S.beta = beta_n;
             S.bx = nbx;
             S.bxp = obx;
             S.bb = nbb;
+            sm.Par[p] = slot_par(beta_n, al, lam, nbx, obx, nbb);
         }
         __syncwarp();
         return;
@@ -320,111 +350,127 @@ __device__ void decide_slot(const SplitParams &prm, const SplitSmem &sm, float2 
             a.nsupp[q] = nz;
     }
     __syncwarp();
-    refill_slot(prm, sm, p, lane);
+    refill_slot<KS>(prm, sm, p, lane);
 }
 
+template <int KS, int NCH>
 __global__ void __launch_bounds__(kThreads, 2) k_rbpg_split(const __grid_constant__ SplitParams prm)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = prm.N, L = prm.L, lda = prm.lda, NC = prm.NC;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const SplitSmem sm = carve(smem_raw, N, NC);
-    float2 *rows = prm.rows + (size_t)blockIdx.x * kSlots * 3 * L;
+    const SplitSmem sm = carve<KS>(smem_raw, N, NC);
+    float2 *rows = prm.rows + (size_t)blockIdx.x * KS * 3 * L;
     const float *__restrict__ A_re = prm.A_re;
     const float *__restrict__ A_im = prm.A_im;
-    if (w < kSlots)
-        refill_slot(prm, sm, w, lane);
+    for (int p = w; p < KS; p += kWarps)
+        refill_slot<KS>(prm, sm, p, lane);
     __syncthreads();
     for (;;) {
-        // this sweep's slot parameters
-        bool act[kSlots];
-        float beta[kSlots], a2[kSlots], tau[kSlots];
-        int bx[kSlots], bxp[kSlots], bb[kSlots];
-        bool any = false;
+        // this sweep's slots; each warp's running sums start at zero
+        unsigned actm = 0;
 #pragma unroll
-        for (int p = 0; p < kSlots; ++p) {
-            const SlotSt &S = sm.S[p];
-            act[p] = S.pix >= 0;
-            any = any || act[p];
-            beta[p] = S.beta;
-            a2[p] = 2.f * S.alpha;
-            tau[p] = S.alpha * S.lam;
-            bx[p] = S.bx;
-            bxp[p] = S.bxp;
-            bb[p] = S.bb;
-        }
-        if (!any)
+        for (int p = 0; p < KS; ++p)
+            actm |= (sm.S[p].pix >= 0) ? (1u << p) : 0u;
+        if (!actm)
             break;
-        float sdd[kSlots], sl1[kSlots], sdx[kSlots], sxn[kSlots];
-        int snz[kSlots];
-        float2 acc[kSlots][kNCH];
-#pragma unroll
-        for (int p = 0; p < kSlots; ++p) {
-            sdd[p] = sl1[p] = sdx[p] = sxn[p] = 0.f;
-            snz[p] = 0;
-#pragma unroll
-            for (int c = 0; c < kNCH; ++c)
-                acc[p][c] = make_float2(0.f, 0.f);
+        if (lane < KS) {
+            sm.Wsum[lane * kWarps + w] = make_float4(0.f, 0.f, 0.f, 0.f);
+            sm.Wnnz[lane * kWarps + w] = 0;
         }
+        __syncwarp();  // lane 0 adds to these below
+        float2 acc[KS][NCH];
+#pragma unroll
+        for (int p = 0; p < KS; ++p)
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+                acc[p][c] = make_float2(0.f, 0.f);
         for (int c = w; c < NC; c += kWarps) {
             const int l = 32 * c + lane;
             const bool inl = l < L;
-            // gradient of every slot: one pair of operator loads feeds all of them
-            float gx[kSlots], gy[kSlots];
+            // gradient of every slot: one pair of operator loads feeds all of them; slot
+            // pairs (2q, 2q+1) in packed FP32 FMAs
+            float2 gx2[KS / 2], gy2[KS / 2];
 #pragma unroll
-            for (int p = 0; p < kSlots; ++p)
-                gx[p] = gy[p] = 0.f;
+            for (int q = 0; q < KS / 2; ++q)
+                gx2[q] = gy2[q] = make_float2(0.f, 0.f);
             if (inl) {
+                const float *pr = A_re + l, *pi = A_im + l;
 #pragma unroll 4
                 for (int n = 0; n < N; ++n) {
-                    const float ar = __ldg(A_re + (size_t)n * lda + l), ai = __ldg(A_im + (size_t)n * lda + l);
+                    const float ar = __ldg(pr + (size_t)n * lda), ai = __ldg(pi + (size_t)n * lda);
+                    const float2 ar2 = make_float2(ar, ar), ai2 = make_float2(ai, ai), nai2 = make_float2(-ai, -ai);
+                    const float4 *rre = (const float4 *)(sm.R + n * 2 * KS);
+                    const float4 *rim = (const float4 *)(sm.R + n * 2 * KS + KS);
 #pragma unroll
-                    for (int p = 0; p < kSlots; p += 2) {
-                        const float4 r2 = *(const float4 *)(sm.R + n * kSlots + p);  // r_n of slots p, p+1
+                    for (int h = 0; h < KS / 4; ++h) {
+                        const float4 rx = rre[h], ry = rim[h];  // slots 4h .. 4h+3
+                        const float2 rx0 = make_float2(rx.x, rx.y), rx1 = make_float2(rx.z, rx.w);
+                        const float2 ry0 = make_float2(ry.x, ry.y), ry1 = make_float2(ry.z, ry.w);
                         // conj(a) r = (ar r.x + ai r.y) + j (ar r.y - ai r.x)
-                        gx[p] = fmaf(ar, r2.x, fmaf(ai, r2.y, gx[p]));
-                        gy[p] = fmaf(ar, r2.y, fmaf(-ai, r2.x, gy[p]));
-                        gx[p + 1] = fmaf(ar, r2.z, fmaf(ai, r2.w, gx[p + 1]));
-                        gy[p + 1] = fmaf(ar, r2.w, fmaf(-ai, r2.z, gy[p + 1]));
+                        gx2[2 * h] = ffma2(ar2, rx0, ffma2(ai2, ry0, gx2[2 * h]));
+                        gy2[2 * h] = ffma2(ar2, ry0, ffma2(nai2, rx0, gy2[2 * h]));
+                        gx2[2 * h + 1] = ffma2(ar2, rx1, ffma2(ai2, ry1, gx2[2 * h + 1]));
+                        gy2[2 * h + 1] = ffma2(ar2, ry1, ffma2(nai2, rx1, gy2[2 * h + 1]));
                     }
                 }
             }
+            float gx[KS], gy[KS];
 #pragma unroll
-            for (int p = 0; p < kSlots; ++p) {
-                if (!act[p])
+            for (int q = 0; q < KS / 2; ++q) {
+                gx[2 * q] = gx2[q].x;
+                gx[2 * q + 1] = gx2[q].y;
+                gy[2 * q] = gy2[q].x;
+                gy[2 * q + 1] = gy2[q].y;
+            }
+#pragma unroll
+            for (int p = 0; p < KS; ++p) {
+                if (!((actm >> p) & 1u))
                     continue;  // the same for the whole CTA
-                const uint32_t mx = sm.M[(p * 3 + bx[p]) * NC + c];
-                const uint32_t mxp = sm.M[(p * 3 + bxp[p]) * NC + c];
-                float xbx = 0.f, xby = 0.f;
-                bool nz = false;
-                if (inl) {
-                    const float2 xv =
-                        ((mx >> lane) & 1u) ? rows[((size_t)p * 3 + bx[p]) * L + l] : make_float2(0.f, 0.f);
-                    const float2 xpv =
-                        ((mxp >> lane) & 1u) ? rows[((size_t)p * 3 + bxp[p]) * L + l] : make_float2(0.f, 0.f);
-                    const float yx = fmaf(beta[p], xv.x - xpv.x, xv.x), yy = fmaf(beta[p], xv.y - xpv.y, xv.y);
-                    const float vx = fmaf(-a2[p], gx[p], yx), vy = fmaf(-a2[p], gy[p], yy);
-                    const float m2 = fmaf(vx, vx, vy * vy);
-                    // soft threshold (Eq. 12): scale 1 - tau / |v| where that is positive
-                    const float rs = rsqrtf(m2);
-                    const float sc = fmaf(-tau[p], rs, 1.f);
-                    nz = sc > 0.f;
-                    if (nz) {
-                        xbx = vx * sc;
-                        xby = vy * sc;
-                        sl1[p] += fmaf(m2, rs, -tau[p]);
-                        rows[((size_t)p * 3 + bb[p]) * L + l] = make_float2(xbx, xby);
-                    }
-                    const float ex = xbx - yx, ey = xby - yy;
-                    sdd[p] = fmaf(ex, ex, fmaf(ey, ey, sdd[p]));
-                    const float fx = xbx - xv.x, fy = xby - xv.y;
-                    sdx[p] = fmaf(fx, fx, fmaf(fy, fy, sdx[p]));
-                    sxn[p] = fmaf(xbx, xbx, fmaf(xby, xby, sxn[p]));
-                }
+                const float4 par = sm.Par[p];
+                const int bits = __float_as_int(par.w);
+                const int bx = bits & 3, bxp = (bits >> 2) & 3, bb = (bits >> 4) & 3;
+                const uint32_t mx = sm.M[(p * 3 + bx) * NC + c];
+                const uint32_t mxp = sm.M[(p * 3 + bxp) * NC + c];
+                float2 xv = make_float2(0.f, 0.f), xpv = make_float2(0.f, 0.f);
+                if ((mx >> lane) & 1u)
+                    xv = rows[((size_t)p * 3 + bx) * L + l];
+                if ((mxp >> lane) & 1u)
+                    xpv = rows[((size_t)p * 3 + bxp) * L + l];
+                const float yx = fmaf(par.x, xv.x - xpv.x, xv.x), yy = fmaf(par.x, xv.y - xpv.y, xv.y);
+                const float vx = fmaf(-par.y, gx[p], yx), vy = fmaf(-par.y, gy[p], yy);
+                const float m2 = fmaf(vx, vx, vy * vy);
+                // soft threshold (Eq. 12): scale 1 - tau / |v| where that is positive
+                const float rs = rsqrtf(m2);
+                const float sc = fmaf(-par.z, rs, 1.f);
+                const bool nz = inl && sc > 0.f;
                 const unsigned bal = __ballot_sync(0xffffffffu, nz);
                 if (lane == 0)
-                    sm.M[(p * 3 + bb[p]) * NC + c] = bal;
-                snz[p] += __popc(bal);
+                    sm.M[(p * 3 + bb) * NC + c] = bal;
+                if ((bal | mx | mxp) == 0u)
+                    continue;  // xbar = y = 0 on the whole chunk: nothing to add
+                float xbx = 0.f, xby = 0.f, l1 = 0.f;
+                if (nz) {
+                    xbx = vx * sc;
+                    xby = vy * sc;
+                    l1 = fmaf(m2, rs, -par.z);
+                    rows[((size_t)p * 3 + bb) * L + l] = make_float2(xbx, xby);
+                }
+                const float ex = xbx - yx, ey = xby - yy;
+                const float fx = xbx - xv.x, fy = xby - xv.y;
+                const float dd = warp_sum(fmaf(ex, ex, ey * ey));
+                const float s1 = warp_sum(l1);
+                const float dx = warp_sum(fmaf(fx, fx, fy * fy));
+                const float xn = warp_sum(fmaf(xbx, xbx, xby * xby));
+                if (lane == 0) {
+                    float4 t = sm.Wsum[p * kWarps + w];
+                    t.x += dd;
+                    t.y += s1;
+                    t.z += dx;
+                    t.w += xn;
+                    sm.Wsum[p * kWarps + w] = t;
+                    sm.Wnnz[p * kWarps + w] += __popc(bal);
+                }
                 // this chunk's share of A xbar, ascending l; lane n owns rows n + 32 c
                 unsigned m = bal;
                 while (m) {
@@ -433,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rbpg_split(const __grid_constan
                     const float xr = __shfl_sync(0xffffffffu, xbx, j), xi = __shfl_sync(0xffffffffu, xby, j);
                     const float2 *at = prm.AT + (size_t)(32 * c + j) * N;
 #pragma unroll
-                    for (int cc = 0; cc < kNCH; ++cc) {
+                    for (int cc = 0; cc < NCH; ++cc) {
                         const int n = lane + 32 * cc;
                         if (n < N) {
                             const float2 av = __ldg(at + n);
@@ -445,45 +491,86 @@ __global__ void __launch_bounds__(kThreads, 2) k_rbpg_split(const __grid_constan
             }
         }
 #pragma unroll
-        for (int p = 0; p < kSlots; ++p) {
-            if (!act[p])
+        for (int p = 0; p < KS; ++p) {
+            if (!((actm >> p) & 1u))
                 continue;
-            const float dd = warp_sum(sdd[p]), l1 = warp_sum(sl1[p]);
-            const float dx = warp_sum(sdx[p]), xn = warp_sum(sxn[p]);
-            if (lane == 0) {
-                sm.Wsum[p * kWarps + w] = make_float4(dd, l1, dx, xn);
-                sm.Wnnz[p * kWarps + w] = snz[p];
-            }
 #pragma unroll
-            for (int cc = 0; cc < kNCH; ++cc) {
+            for (int cc = 0; cc < NCH; ++cc) {
                 const int n = lane + 32 * cc;
                 if (n < N)
                     sm.Wacc[(p * kWarps + w) * N + n] = acc[p][cc];
             }
         }
         __syncthreads();
-        if (w < kSlots && sm.S[w].pix >= 0)  // the slots of this sweep: unchanged since its start
-            decide_slot(prm, sm, rows, w, lane);
+        for (int p = w; p < KS; p += kWarps)
+            if ((actm >> p) & 1u)
+                decide_slot<KS, NCH>(prm, sm, rows, p, lane);
         __syncthreads();
     }
 }
 
-}  // namespace
+template <int KS, int NCH>
+void *split_fn()
+{
+    return (void *)k_rbpg_split<KS, NCH>;
+}
 
-// CTAs of a split launch on this device: as many as fit (at most one per kSlots pixels)
-static int split_ctas(const OpHandle &op, int64_t P, int num_sms, size_t smem)
+// the variant for these sizes: 8 slots when their shared memory fits the device, else 4;
+// NCH = rows of A per lane in the gather (N <= 32 NCH)
+struct SplitVariant {
+    void *fn;
+    int ks;
+    size_t smem;
+};
+
+SplitVariant split_variant(const OpHandle &op, int max_smem)
+{
+    const int NC = (op.L + 31) / 32;
+    const int nch = (op.N + 31) / 32;
+    SplitVariant v{nullptr, 0, 0};
+    for (int ks : {8, 4}) {
+        const size_t smem = split_smem_bytes(ks, op.N, NC);
+        if (smem > (size_t)max_smem)
+            continue;
+        v.ks = ks;
+        v.smem = smem;
+        if (ks == 8)
+            v.fn = nch == 1 ? split_fn<8, 1>() : nch == 2 ? split_fn<8, 2>() : split_fn<8, 3>();
+        else
+            v.fn = nch == 1 ? split_fn<4, 1>() : nch == 2 ? split_fn<4, 2>() : split_fn<4, 3>();
+        return v;
+    }
+    return v;
+}
+
+int max_smem_dev(int dev)
+{
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 48 * 1024;
+    }
+    return v;
+}
+
+// CTAs of a split launch on this device: as many as fit (at most one per KS pixels)
+int split_ctas(const SplitVariant &v, int64_t P, int num_sms)
 {
     int per_sm = 0;
-    if (cudaFuncSetAttribute(k_rbpg_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbpg_split, kThreads, smem) != cudaSuccess ||
+    if (!v.fn ||
+        cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, kThreads, v.smem) != cudaSuccess ||
         per_sm < 1) {
         (void)cudaGetLastError();
         return 0;
     }
-    (void)op;
-    const int64_t want = (P + kSlots - 1) / kSlots;
+    const int64_t want = (P + v.ks - 1) / v.ks;
     return (int)std::min<int64_t>((int64_t)per_sm * num_sms, want);
 }
+
+size_t at_bytes(const OpHandle &op) { return ((size_t)op.L * op.N * sizeof(float2) + 255) / 256 * 256; }
+
+}  // namespace
 
 const char *rbpg_split_check(const OpHandle &op, int precision, int blocks, int max_smem)
 {
@@ -491,10 +578,9 @@ const char *rbpg_split_check(const OpHandle &op, int precision, int blocks, int 
         return "grids of more than 1024 points run in FP32 only (precision 0)";
     if (blocks >= 2)
         return "randomized blocks handle grids of at most 1024 points";
-    if (op.N > 32 * kNCH)
+    if (op.N > 96)
         return "the split kernel handles N <= 96";
-    const int NC = (op.L + 31) / 32;
-    if (split_smem_bytes(op.N, NC) > (size_t)max_smem)
+    if (!split_variant(op, max_smem).fn)
         return "the split kernel's shared memory exceeds the device limit";
     return "";
 }
@@ -503,19 +589,17 @@ size_t rbpg_split_scratch_bytes(const OpHandle &op, int64_t P, int num_sms)
 {
     if (P <= 0)
         return 0;
-    const int NC = (op.L + 31) / 32;
-    const int ctas = split_ctas(op, P, num_sms, split_smem_bytes(op.N, NC));
+    const SplitVariant v = split_variant(op, max_smem_dev(op.device));
+    const int ctas = split_ctas(v, P, num_sms);
     if (ctas < 1)
         return 0;
-    const size_t at = ((size_t)op.L * op.N * sizeof(float2) + 255) / 256 * 256;
-    return at + (size_t)ctas * kSlots * 3 * op.L * sizeof(float2);
+    return at_bytes(op) + (size_t)ctas * v.ks * 3 * op.L * sizeof(float2);
 }
 
 cudaError_t launch_rbpg_split(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s)
 {
-    const int NC = (op.L + 31) / 32;
-    const size_t smem = split_smem_bytes(op.N, NC);
-    const int ctas = split_ctas(op, a.P, num_sms, smem);
+    const SplitVariant v = split_variant(op, max_smem_dev(op.device));
+    const int ctas = split_ctas(v, a.P, num_sms);
     if (ctas < 1)
         return cudaErrorInvalidConfiguration;
     SplitParams prm;
@@ -525,14 +609,15 @@ cudaError_t launch_rbpg_split(const OpHandle &op, const SolveLaunch &a, int num_
     prm.N = op.N;
     prm.L = op.L;
     prm.lda = op.lda;
-    prm.NC = NC;
-    prm.rows = (float2 *)(a.split_scratch + ((size_t)op.L * op.N * sizeof(float2) + 255) / 256 * 256);
+    prm.NC = (op.L + 31) / 32;
+    prm.rows = (float2 *)(a.split_scratch + at_bytes(op));
     prm.a = a;
     const long long tot = (long long)op.N * op.L;
     k_transpose_a<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(op.A_re, op.A_im, op.N, op.L, op.lda,
                                                                 (float2 *)a.split_scratch);
-    k_rbpg_split<<<(unsigned)ctas, kThreads, smem, s>>>(prm);
-    return cudaGetLastError();
+    void *args[] = {(void *)&prm};
+    cudaError_t e = cudaLaunchKernel(v.fn, dim3((unsigned)ctas), dim3(kThreads), args, v.smem, s);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace bpdn
