@@ -999,6 +999,19 @@ def run_motion(args) -> None:
                       "runs": out}), flush=True)
 
 
+def run_motion4d(args) -> None:
+    """The 4-D grid run of the motion leg on its own (one JSON line)."""
+    import torch
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    row = _motion4d(args)
+    print(json.dumps({"metric": "certified pixels/s, 4-D grid (elevation x velocity x seasonal amplitude)",
+                      "value": row["certified_pixels_per_s"], "unit": "pixels/s",
+                      "workload": "N=25, 64 x 16 x 16 = 16,384 grid points, seed 8", "run": row}), flush=True)
+
+
 def _motion4d(args) -> dict:
     """The 4-D grid (elevation x velocity x seasonal amplitude, 64 x 16 x 16 = 16,384 points)
     through the split-grid FP32 kernel and the refit: the whole solve, the iterations alone,
@@ -1077,7 +1090,7 @@ def main(argv=None) -> None:
                     help="stopping tolerance of the BF16 path: BF16 operands carry 2^-9 relative error, "
                          "so smaller steps are not resolved")
     ap.add_argument("--e2e-chunks", type=int, default=8, help="chunks of the end-to-end leg")
-    ap.add_argument("--workload", choices=["patch", "ragged", "detection", "blocks", "motion", "peaks", "hybrid"], default="patch",
+    ap.add_argument("--workload", choices=["patch", "ragged", "detection", "blocks", "motion", "motion4d", "peaks", "hybrid"], default="patch",
                     help="patch: the headline line; ragged: the 64-stack ragged batch; detection: the "
                          "detection-rate Monte Carlo through solve + model selection (separate lines)")
     ap.add_argument("--det-per", type=int, default=5000, help="realisations per (SNR, kappa)")
@@ -1098,6 +1111,8 @@ def main(argv=None) -> None:
         run_blocks(args)
     elif args.workload == "motion":
         run_motion(args)
+    elif args.workload == "motion4d":
+        run_motion4d(args)
     elif args.workload == "peaks":
         run_peaks(args)
     elif args.workload == "hybrid":
