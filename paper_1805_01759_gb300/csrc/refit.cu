@@ -1007,6 +1007,13 @@ __device__ __forceinline__ void refit_pixel(PixelSmem<KW> &P, const long long p,
             }
             if (2.f * sqrtf(ux * ux + uy * uy) <= near)
                 continue;
+            // the points of W sit at the threshold: they pass the screen, and skip the FP64
+            // recheck here (only points past the screen pay for the scan over W)
+            bool inW = false;
+            for (int i = 0; i < m; ++i)
+                inW = inW || (P.W[i] == l);
+            if (inW)
+                continue;
             double vx = 0.0, vy = 0.0;
             for (int n = 0; n < N; ++n) {
                 const double2 av = A64[(size_t)n * L + l], rv = P.rr[n];
@@ -1015,15 +1022,8 @@ __device__ __forceinline__ void refit_pixel(PixelSmem<KW> &P, const long long p,
             }
             const double u = 2.0 * sqrt(vx * vx + vy * vy);
             if (u > lam * (1.0 + 1e-9) && u > worst) {
-                // a point of W is never a violator (the scan over W is rare: only points
-                // past the threshold reach it)
-                bool inW = false;
-                for (int i = 0; i < m; ++i)
-                    inW = inW || (P.W[i] == l);
-                if (!inW) {
-                    worst = u;
-                    worst_l = l;
-                }
+                worst = u;
+                worst_l = l;
             }
         }
         // violators join W, largest first, at most 4 per round

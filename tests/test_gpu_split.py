@@ -167,3 +167,42 @@ def test_split_grid_edges(api, grid4d):
         assert e.value.code == _lib.BPDN_ESIZE, bad
     with pytest.raises(_lib.BPDNError):
         api.solve_ragged([(op, g, grid4d.lam)])
+
+
+def _max_stack():
+    """The library's largest sizes: N = 80 acquisitions on the 4-D grid 64 x 32 x 32 =
+    65,536 points (BPDN_MAX_N, BPDN_MAX_L), 12 pixels."""
+    rng = np.random.default_rng(11)
+    N = 80
+    b = rng.uniform(-250.0, 250.0, N)
+    t = rng.uniform(0.0, 4.0, N)
+    eta = np.stack([2.0 * t / 0.031, 2.0 * np.sin(2.0 * np.pi * t) / 0.031])
+    geom = synth.MotionGeometry(b, 0.031, 7.0e5, -100.0, 100.0, 64, eta=eta, p_min=np.array([-0.02, -0.01]),
+                                p_max=np.array([0.02, 0.01]), L_p=np.array([32, 32]))
+    return synth.make_stack_md(geom, 12, rng, lam=synth.default_lambda(N, geom.L_total))
+
+
+def test_split_grid_maximum_sizes(api):
+    from paper_1805_01759_gb300 import _lib
+    st = _max_stack()
+    A = oracle.operator_md(st.geom)
+    op = api.Operator.from_geometry(st.geom)
+    assert (op.N, op.L) == (_lib.MAX_N, _lib.MAX_L) == A.shape
+    g = torch.from_numpy(st.g).cuda()
+    for k, need in ((1, 5), (3, 3)):
+        res = api.solve(op, g, st.lam, max_iter=k, tol=0.0, refit=0)
+        x = res.x.cpu().numpy()
+        checked = 0
+        for p in range(12):
+            r = oracle.rbpg(A, st.g[p], st.lam, max_iter=k, tol=0.0, trace=True)
+            if np.min(r["margin"]) < 1e-5:
+                continue
+            assert int(res.iters[p]) == r["iters"], (k, p)
+            assert np.linalg.norm(x[p] - r["x"]) <= 2e-4 * max(np.linalg.norm(r["x"]), 1e-6), (k, p)
+            assert np.array_equal(x[p] != 0, r["x"] != 0), (k, p)
+            checked += 1
+        assert checked >= need, (k, checked)
+    res = api.solve(op, g, st.lam)
+    ref = _exact(A, st.g, st.lam)
+    cert = _check_minimiser(res, ref, 10)
+    assert cert.sum() >= 11, cert
