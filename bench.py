@@ -651,8 +651,8 @@ def run_ours(args) -> None:
 
 def run_ragged(args) -> None:
     """The ragged batch (64 stacks: N 10..60, L 100..600, 2^12..2^16 pixels each) through
-    one bpdn_solve_ragged call replayed as a CUDA graph, with and without the tile
-    autotuner, next to the same stacks solved one after another on one stream."""
+    one bpdn_solve_ragged call replayed as a CUDA graph, next to the same stacks solved one
+    after another on one stream."""
     import torch
     import torch.distributed as dist
     rank, world, local = dist_env()
@@ -693,20 +693,19 @@ def run_ragged(args) -> None:
 
     out = {}
     # per-stack precision differs, so the stacks are grouped into one solver per option set
-    for mode in ("graph", "graph_autotuned"):
+    for mode in ("graph",):
         solvers = []
         for key in sorted({tuple(sorted(opts(op).items())) for op, _, _ in items}):
             sub = [it for it in items if tuple(sorted(opts(it[0]).items())) == key]
-            solvers.append(api.RaggedSolver(sub, autotune=(mode == "graph_autotuned"), **dict(key)))
+            solvers.append(api.RaggedSolver(sub, **dict(key)))
         for sv in solvers:
             sv.capture()
         ms = timed(lambda: [sv.replay() for sv in solvers], args.steps, args.warmup)
         cert = sum(int(((r.status & 64) != 0).sum().item()) for sv in solvers for r in sv.results)
-        out[mode] = {"ms": ms, "pixels_per_s_certified": cert / (ms / 1e3), "certified_frac": cert / P_total,
-                     "tiles": [t for sv in solvers for t in sv.tiles]}
+        out[mode] = {"ms": ms, "pixels_per_s_certified": cert / (ms / 1e3), "certified_frac": cert / P_total}
     ms = timed(lambda: [api.solve(op, g, lam, **opts(op)) for op, g, lam in items], args.steps, args.warmup)
     out["sequential_one_stream"] = {"ms": ms}
-    best = min(("graph", "graph_autotuned"), key=lambda k: out[k]["ms"])
+    best = "graph"
     # whole job: certified pixels of every rank over the slowest rank's time
     cert_all = reduce_sum(out[best]["pixels_per_s_certified"] * out[best]["ms"] / 1e3, dev)
     P_all = int(reduce_sum(float(P_total), dev))

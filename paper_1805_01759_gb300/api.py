@@ -461,54 +461,21 @@ def tune_lambda(op: Operator, g: torch.Tensor, gamma_true: torch.Tensor, lam0: f
     return float(log_lam.exp().item()), history
 
 
-_TILE_CACHE: dict = {}
-
-
-def autotune_tile(op: Operator, g: torch.Tensor, lam, *, candidates=(8, 16), repeats: int = 2,
-                  **options) -> int:
-    """Pick tile_pixels (pixels in flight per SM) for this operator and batch by timing
-    bpdn_solve with each candidate on g itself.  Results are cached by
-    (N, L, precision, P); candidates the kernel cannot run at these sizes are skipped."""
-    P = g.shape[0]
-    prec = int(options.get("precision", 0))
-    key = (op.N, op.L, prec, P)
-    if key in _TILE_CACHE:
-        return _TILE_CACHE[key]
-    best, best_ms = 0, float("inf")
-    for t in candidates:
-        try:
-            solve(op, g, lam, tile_pixels=t, **options)  # warm-up, and checks that it runs
-        except _lib.BPDNError:
-            continue
-        ms = float("inf")
-        for _ in range(repeats):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            solve(op, g, lam, tile_pixels=t, **options)
-            e1.record()
-            torch.cuda.synchronize()
-            ms = min(ms, e0.elapsed_time(e1))
-        if ms < best_ms:
-            best, best_ms = t, ms
-    _TILE_CACHE[key] = best
-    return best
-
-
 class RaggedSolver:
     """Many stacks, each with its own operator and pixel count, through bpdn_solve_ragged.
 
-    items: list of (Operator, g [P_s, N_s] complex64 CUDA tensor, lambda).  With
-    autotune=True each stack's tile_pixels is chosen by autotune_tile first.  Outputs are
-    allocated once (`results`, one SolveResult per stack).  run() launches on the current
-    (or given) stream; capture() records one call into a CUDA graph and replay()
-    relaunches it: the graph reads the same g tensors, so new data is copied into them."""
+    items: list of (Operator, g [P_s, N_s] complex64 CUDA tensor, lambda); tiles (optional):
+    each stack's tile_pixels (0 = the options' value).  Outputs are allocated once
+    (`results`, one SolveResult per stack).  run() launches on the current (or given) stream;
+    capture() records one call into a CUDA graph and replay() relaunches it: the graph reads
+    the same g tensors, so new data is copied into them."""
 
-    def __init__(self, items, *, autotune: bool = False, **options):
+    def __init__(self, items, *, tiles=None, **options):
         lib = _lib.load()
         self.opt = _lib.default_options(**options)
-        self.tiles = [autotune_tile(op, _check_g(op, g), lam, **options) if autotune else 0
-                      for op, g, lam in items]
+        self.tiles = [0] * len(items) if tiles is None else [int(t) for t in tiles]
+        if len(self.tiles) != len(items):
+            raise ValueError("tiles must name one tile_pixels per stack")
         self.items = []
         self.results = []
         self._keep = []
