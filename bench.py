@@ -1088,7 +1088,7 @@ def main(argv=None) -> None:
     ap.add_argument("--tol-bf16", type=float, default=1e-3,
                     help="stopping tolerance of the BF16 path: BF16 operands carry 2^-9 relative error, "
                          "so smaller steps are not resolved")
-    ap.add_argument("--e2e-chunks", type=int, default=8, help="chunks of the end-to-end leg")
+    ap.add_argument("--e2e-chunks", type=int, default=2, help="chunks of the end-to-end leg")
     ap.add_argument("--workload", choices=["patch", "ragged", "detection", "blocks", "motion", "motion4d", "peaks", "hybrid"], default="patch",
                     help="patch: the headline line; ragged: the 64-stack ragged batch; detection: the "
                          "detection-rate Monte Carlo through solve + model selection (separate lines)")

@@ -554,9 +554,13 @@ class HostSolver:
     The batch is cut into `chunks` pieces on two streams with two sets of device buffers:
     while one piece is solved, the next one's g is copied in and the previous one's x
     is copied out, so the transfers hide behind the solves.  Results go straight into
-    the host tensors passed to run()."""
+    the host tensors passed to run().  Two chunks are the default: the copies run at about
+    200 GB/s, so one chunk's x (1.7 GB for half of 2^20 pixels at L = 400) hides behind the
+    other's solve, while every further chunk adds the tails of its own launches (2^20
+    pixels, N = 25, L = 400, BF16: 869 ms per step with 2 chunks, 913 with 8, 991 with 16,
+    against 860 for the device-resident solve)."""
 
-    def __init__(self, op: Operator, P: int, *, chunks: int = 8, device=None, **options):
+    def __init__(self, op: Operator, P: int, *, chunks: int = 2, device=None, **options):
         self.op = op
         self.P = P
         self.chunks = max(1, min(chunks, P)) if P else 1
@@ -613,6 +617,6 @@ class HostSolver:
 
 
 def solve_host(op: Operator, g_host: torch.Tensor, lam, x_host: torch.Tensor, status_host: torch.Tensor,
-               *, chunks: int = 8, **options) -> None:
+               *, chunks: int = 2, **options) -> None:
     """One-shot HostSolver: solve the pixels of g_host into x_host / status_host."""
     HostSolver(op, g_host.shape[0], chunks=chunks, **options).run(g_host, lam, x_host, status_host)
