@@ -159,8 +159,8 @@ int bpdn_op_export(bpdn_op_t op, int32_t what, void *d_dst, size_t dst_bytes, vo
  * pixel, the FP64 finish and certificate, further rounds for the pixels that need them).  A workspace smaller than this, down to the first two parts,
  * is accepted too: the refit then runs in a single launch, with the same results.
  * Operators of more than 1024 grid points add the split-grid kernel's scratch, which
- * bpdn_solve cannot do without: the operator transposed in FP32 (8 N L bytes) and three
- * rows of L complex values per pixel in flight (at most 4 per CTA, as many CTAs as the
+ * bpdn_solve cannot do without: two FP32 copies of the operator (16 N L bytes) and three
+ * rows of L complex values per pixel in flight (at most 8 per CTA, as many CTAs as the
  * device holds at once and P needs). */
 size_t bpdn_solve_workspace_bytes(bpdn_op_t op, int64_t P, const bpdn_options *opt);
 

@@ -8,7 +8,8 @@
 //
 // One sweep:
 //   1. per chunk and lane (one grid point l): the gradient sum_n conj(A_nl) r_n of every
-//      slot from the FP32 tables (coalesced over l; r in shared memory), then per slot the
+//      slot from an interleaved copy of the FP32 operator (one 8-byte load per lane and
+//      row, coalesced over l; r in shared memory), then per slot the
 //      extrapolation y = x + beta (x - x^{k-1}) and the complex soft threshold of
 //      v = y - 2 alpha grad.  Only chunks where xbar, x^k or x^{k-1} has a nonzero go on to
 //      the sums of Eq. 15, F and the stopping test (a warp sum per chunk, added to the
@@ -34,9 +35,9 @@ constexpr int kWarps = 8;  // warps per CTA
 constexpr int kThreads = 32 * kWarps;
 
 struct SplitParams {
-    const float *A_re, *A_im;  // planar FP32 tables [N][lda]
     const float2 *AT;          // transposed FP32 table [L][N]
-    int N, L, lda, NC;
+    const float2 *A2;          // interleaved FP32 table [N][L]: (Re A_nl, Im A_nl)
+    int N, L, NC;
     float2 *rows;              // [ctas][KS][3][L]
     SolveLaunch a;
 };
@@ -129,15 +130,19 @@ __device__ __forceinline__ SplitSmem carve(unsigned char *base, int N, int NC)
     return s;
 }
 
-// A^T in FP32: AT[l][n] = A_nl, for the gather of A xbar (lanes over n)
-__global__ void k_transpose_a(const float *__restrict__ A_re, const float *__restrict__ A_im, int N, int L, int lda,
-                              float2 *__restrict__ AT)
+// The launch's two copies of the FP32 operator: AT[l][n] = A_nl for the gather of A xbar
+// (lanes over n), and A2[n][l] = A_nl for the gradient (one 8-byte load per lane and row,
+// lanes over l)
+__global__ void k_operator_copies(const float *__restrict__ A_re, const float *__restrict__ A_im, int N, int L,
+                                  int lda, float2 *__restrict__ AT, float2 *__restrict__ A2)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)N * L)
         return;
     const int l = (int)(i / N), n = (int)(i % N);
-    AT[i] = make_float2(A_re[(size_t)n * lda + l], A_im[(size_t)n * lda + l]);
+    const float2 v = make_float2(A_re[(size_t)n * lda + l], A_im[(size_t)n * lda + l]);
+    AT[i] = v;
+    A2[(size_t)n * L + l] = v;
 }
 
 // Refill slot p (warp p) from the work counter: x^0 = x^{-1} = 0, so A y = 0 and r = -g.
@@ -354,15 +359,13 @@ __device__ void decide_slot(const SplitParams &prm, const SplitSmem &sm, float2 
 }
 
 template <int KS, int NCH>
-__global__ void __launch_bounds__(kThreads, 2) k_rbpg_split(const __grid_constant__ SplitParams prm)
+__global__ void __launch_bounds__(kThreads, 3) k_rbpg_split(const __grid_constant__ SplitParams prm)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = prm.N, L = prm.L, lda = prm.lda, NC = prm.NC;
+    const int N = prm.N, L = prm.L, NC = prm.NC;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const SplitSmem sm = carve<KS>(smem_raw, N, NC);
     float2 *rows = prm.rows + (size_t)blockIdx.x * KS * 3 * L;
-    const float *__restrict__ A_re = prm.A_re;
-    const float *__restrict__ A_im = prm.A_im;
     for (int p = w; p < KS; p += kWarps)
         refill_slot<KS>(prm, sm, p, lane);
     __syncthreads();
@@ -395,11 +398,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_rbpg_split(const __grid_constan
             for (int q = 0; q < KS / 2; ++q)
                 gx2[q] = gy2[q] = make_float2(0.f, 0.f);
             if (inl) {
-                const float *pr = A_re + l, *pi = A_im + l;
+                const float2 *pa = prm.A2 + l;
 #pragma unroll 4
                 for (int n = 0; n < N; ++n) {
-                    const float ar = __ldg(pr + (size_t)n * lda), ai = __ldg(pi + (size_t)n * lda);
-                    const float2 ar2 = make_float2(ar, ar), ai2 = make_float2(ai, ai), nai2 = make_float2(-ai, -ai);
+                    const float2 av = __ldg(pa + (size_t)n * L);
+                    const float2 ar2 = make_float2(av.x, av.x), ai2 = make_float2(av.y, av.y);
+                    const float2 nai2 = make_float2(-av.y, -av.y);
                     const float4 *rre = (const float4 *)(sm.R + n * 2 * KS);
                     const float4 *rim = (const float4 *)(sm.R + n * 2 * KS + KS);
 #pragma unroll
@@ -568,7 +572,9 @@ int split_ctas(const SplitVariant &v, int64_t P, int num_sms)
     return (int)std::min<int64_t>((int64_t)per_sm * num_sms, want);
 }
 
+// bytes of each of the two operator copies at the start of the scratch (AT, then A2)
 size_t at_bytes(const OpHandle &op) { return ((size_t)op.L * op.N * sizeof(float2) + 255) / 256 * 256; }
+
 
 }  // namespace
 
@@ -593,7 +599,7 @@ size_t rbpg_split_scratch_bytes(const OpHandle &op, int64_t P, int num_sms)
     const int ctas = split_ctas(v, P, num_sms);
     if (ctas < 1)
         return 0;
-    return at_bytes(op) + (size_t)ctas * v.ks * 3 * op.L * sizeof(float2);
+    return 2 * at_bytes(op) + (size_t)ctas * v.ks * 3 * op.L * sizeof(float2);
 }
 
 cudaError_t launch_rbpg_split(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s)
@@ -603,18 +609,17 @@ cudaError_t launch_rbpg_split(const OpHandle &op, const SolveLaunch &a, int num_
     if (ctas < 1)
         return cudaErrorInvalidConfiguration;
     SplitParams prm;
-    prm.A_re = op.A_re;
-    prm.A_im = op.A_im;
     prm.AT = (const float2 *)a.split_scratch;
+    prm.A2 = (const float2 *)(a.split_scratch + at_bytes(op));
     prm.N = op.N;
     prm.L = op.L;
-    prm.lda = op.lda;
     prm.NC = (op.L + 31) / 32;
-    prm.rows = (float2 *)(a.split_scratch + at_bytes(op));
+    prm.rows = (float2 *)(a.split_scratch + 2 * at_bytes(op));
     prm.a = a;
     const long long tot = (long long)op.N * op.L;
-    k_transpose_a<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(op.A_re, op.A_im, op.N, op.L, op.lda,
-                                                                (float2 *)a.split_scratch);
+    k_operator_copies<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+        op.A_re, op.A_im, op.N, op.L, op.lda, (float2 *)a.split_scratch,
+        (float2 *)(a.split_scratch + at_bytes(op)));
     void *args[] = {(void *)&prm};
     cudaError_t e = cudaLaunchKernel(v.fn, dim3((unsigned)ctas), dim3(kThreads), args, v.smem, s);
     return e != cudaSuccess ? e : cudaGetLastError();

@@ -206,3 +206,36 @@ def test_split_grid_maximum_sizes(api):
     ref = _exact(A, st.g, st.lam)
     cert = _check_minimiser(res, ref, 10)
     assert cert.sum() >= 11, cert
+
+
+def test_split_grid_adjoint(api, grid4d):
+    """dL/dg and dL/dlambda through the adjoint on the 16,384-point grid, against the
+    oracle's adjoint of its own minimiser (pixels with a slack dual margin and the oracle's
+    support), to 1e-3 relative."""
+    A = oracle.operator_md(grid4d.geom)
+    op = api.Operator.from_geometry(grid4d.geom)
+    P = 32
+    g = torch.from_numpy(grid4d.g[:P]).cuda()
+    res = api.solve(op, g, grid4d.lam)
+    rng = np.random.default_rng(21)
+    c = rng.standard_normal((P, op.L)) + 1j * rng.standard_normal((P, op.L))
+    lam = torch.full((P,), grid4d.lam, dtype=torch.float32, device="cuda")
+    dg, dl = api.backward(op, res.x, res.support, res.nsupp, torch.from_numpy(c.astype(np.complex64)).cuda(), lam,
+                          status=res.status)
+    torch.cuda.synchronize()
+    ref = _exact(A, grid4d.g[:P], grid4d.lam)
+    r = oracle.adjoint_batch(A, np.full(P, grid4d.lam), ref["x"], c)
+    x = res.x.cpu().numpy()
+    cert = (res.status.cpu().numpy() & 64) != 0
+    dg, dl = dg.cpu().numpy(), dl.cpu().numpy()
+    checked = 0
+    for p in range(P):
+        if not cert[p] or ref["flags"][p] != 0 or ref["margin"][p] < 1e-3 or r["flags"][p] != 0:
+            continue
+        if not np.array_equal(x[p] != 0, ref["x"][p] != 0):
+            continue
+        scale = max(np.linalg.norm(r["dLdg"][p]), 1e-12)
+        assert np.linalg.norm(dg[p] - r["dLdg"][p]) <= 1e-3 * scale, p
+        assert abs(dl[p] - r["dLdlam"][p]) <= 1e-3 * max(abs(r["dLdlam"][p]), 1e-9 * scale), p
+        checked += 1
+    assert checked >= 16, checked
