@@ -158,10 +158,10 @@ int bpdn_op_export(bpdn_op_t op, int32_t what, void *d_dst, size_t dst_bytes, vo
  * per pixel of scratch for the refit in three launches (the FP32 support search of every
  * pixel, the FP64 finish and certificate, further rounds for the pixels that need them).  A workspace smaller than this, down to the first two parts,
  * is accepted too: the refit then runs in a single launch, with the same results.
- * Operators of more than 1024 grid points add the split-grid kernel's scratch, which
- * bpdn_solve cannot do without: two FP32 copies of the operator (16 N L bytes) and three
- * rows of L complex values per pixel in flight (at most 8 per CTA, as many CTAs as the
- * device holds at once and P needs). */
+ * Solves that run the split-grid kernel (see bpdn_solve) add its scratch, which they cannot
+ * do without: two FP32 copies of the operator (16 N L bytes) and three rows of L complex
+ * values per pixel in flight (at most 8 per CTA, as many CTAs as the device holds at once
+ * and P needs). */
 size_t bpdn_solve_workspace_bytes(bpdn_op_t op, int64_t P, const bpdn_options *opt);
 
 /*
@@ -179,11 +179,14 @@ size_t bpdn_solve_workspace_bytes(bpdn_op_t op, int64_t P, const bpdn_options *o
  * d_nbt      device int32 [P] out (may be NULL): total step cuts (Eq. 15 failures)
  * d_workspace  >= bpdn_solve_workspace_bytes(op, P, opt) bytes, 256-byte aligned
  * The operator's workspace must be resident on the current device.
- * Grids of more than 1024 points (L up to BPDN_MAX_L, e.g. the multi-component grids of
- * Eq. 4) run Algorithm 1 in a split-grid FP32 kernel: they need precision 0,
- * tile_pixels 0 and blocks <= 1, and a workspace of at least
- * bpdn_solve_workspace_bytes(op, P, opt) bytes; otherwise BPDN_ESIZE before any launch.
- * bpdn_solve_ragged and bpdn_solve_noalloc refuse such operators (BPDN_ESIZE).
+ * Algorithm 1 runs in a split-grid FP32 kernel (a CTA's warps walk the grid in 32-point
+ * chunks, the iterate in the workspace) for grids of more than 1024 points (L up to
+ * BPDN_MAX_L, e.g. the multi-component grids of Eq. 4), which need precision 0,
+ * tile_pixels 0 and blocks <= 1, and for FP32 solves of 513..1024 points with
+ * tile_pixels 0 and blocks <= 1 (tile_pixels 8 keeps the grid-point kernel there).  The
+ * choice depends on the operator and the options only.  Such a solve needs a workspace of
+ * at least bpdn_solve_workspace_bytes(op, P, opt) bytes; otherwise BPDN_ESIZE before any
+ * launch (bpdn_solve_noalloc refuses them).
  */
 int bpdn_solve(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda,
                int32_t lambda_per_pixel, const bpdn_options *opt, void *d_x, int32_t *d_support,
@@ -233,12 +236,15 @@ typedef struct {
 } bpdn_stack;
 
 /* Least workspace of bpdn_solve_ragged: 256 bytes per stack (the refits then run as single
- * launches). */
+ * launches).  A batch with stacks that run the split-grid kernel (see bpdn_solve) needs
+ * bpdn_solve_ragged_workspace_bytes_for. */
 size_t bpdn_solve_ragged_workspace_bytes(int32_t n_stacks);
 
 /* Workspace with which bpdn_solve_ragged runs each stack's refit in three launches (as
- * bpdn_solve does): 256 bytes per stack, then, when opt->refit, 460 bytes per pixel of every
- * stack.  Same results either way.  0 if stacks is NULL with n_stacks > 0. */
+ * bpdn_solve does): 256 bytes per stack, the split-grid kernel's scratch of the stacks that
+ * run it (bpdn_solve_workspace_bytes's part for it), then, when opt->refit, 460 bytes per
+ * pixel of every stack.  Same results with or without the last part.  0 if stacks is NULL
+ * with n_stacks > 0. */
 size_t bpdn_solve_ragged_workspace_bytes_for(const bpdn_stack *stacks, int32_t n_stacks,
                                              const bpdn_options *opt);
 
@@ -248,7 +254,9 @@ size_t bpdn_solve_ragged_workspace_bytes_for(const bpdn_stack *stacks, int32_t n
  * stack's arguments are checked first; on any error nothing is launched and the
  * message names the stack.  Algorithm 1 runs for all stacks in one persistent launch
  * per kernel variant present (BF16 or FP32, A in shared or global memory; 64 stacks
- * per launch): every CTA works through the stacks while they have pixels left.  The
+ * per launch): every CTA works through the stacks while they have pixels left.  Stacks
+ * that bpdn_solve would give the split-grid kernel run it in their own launches after
+ * that one, on the library's streams.  The
  * refits follow, one launch per stack, on a few library-owned streams that fork from
  * and join back into cuda_stream through events, so the whole call can be captured
  * into one CUDA graph.  The streams and events are created by the first call on a

@@ -145,14 +145,27 @@ static size_t px_scratch_for(const OpHandle *op, int64_t P, const bpdn_options *
     return rbpg_px_scratch_bytes(*op, P, num_sms(op->device), max_smem_optin(op->device));
 }
 
-// grids of more than 1024 points run the split-grid FP32 kernel
-static bool split_grid(const OpHandle *op) { return op && op->L > 1024; }
+// The split-grid FP32 kernel runs grids of more than 1024 points, and FP32 solves of
+// 513..1024 points with the library's choice of tile (tile_pixels 0, no randomized
+// blocks): there the grid-point kernel fits only one group of slots per CTA, and the
+// split kernel is faster (1.2-1.7x on such stacks).  The choice depends on the operator and
+// the options only, never on the workspace, so that results do not depend on it.
+bool solve_uses_split(const OpHandle *op, const bpdn_options *opt)
+{
+    if (!op)
+        return false;
+    if (op->L > 1024)
+        return true;
+    return opt && op->L > 512 && opt->precision == 0 && opt->tile_pixels == 0 && opt->blocks < 2;
+}
+
+static bool split_grid(const OpHandle *op, const bpdn_options *opt) { return solve_uses_split(op, opt); }
 
 // scratch of the split-grid kernel for this solve (0 when the grid does not need it or the
 // options or sizes rule it out: solve_plan then names the reason)
 static size_t split_scratch_for(const OpHandle *op, int64_t P, const bpdn_options *opt)
 {
-    if (!split_grid(op) || !opt || opt->tile_pixels != 0 ||
+    if (!split_grid(op, opt) || !opt || opt->tile_pixels != 0 ||
         rbpg_split_check(*op, opt->precision, opt->blocks, max_smem_optin(op->device))[0] != '\0')
         return 0;
     return rbpg_split_scratch_bytes(*op, P, num_sms(op->device));
@@ -178,7 +191,8 @@ static int check_solve_buffers(const OpHandle *op, const void *d_g, int64_t P, c
 // Checks every argument of a solve; launches it when `launch` is true.
 int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, int32_t lambda_per_pixel,
                const bpdn_options *opt, void *d_x, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
-               int32_t *d_iters, int32_t *d_nbt, void *d_workspace, size_t workspace_bytes, SolvePlan *sp)
+               int32_t *d_iters, int32_t *d_nbt, void *d_workspace, size_t workspace_bytes, SolvePlan *sp,
+               unsigned char *split_at)
 {
     OpHandle *op = nullptr;
     int rc = check_op(h, &op);
@@ -205,7 +219,7 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
         return set_error(BPDN_EALIGN, "support must be 4-byte aligned");
     // the pixel-per-thread BF16 kernel when it suits the sizes and the workspace holds its scratch
     const size_t base = solve_min_workspace_bytes(opt);
-    const bool split = split_grid(op);
+    const bool split = split_grid(op, opt);
     const size_t pxb = split ? 0 : px_scratch_for(op, P, opt);
     const bool use_px = pxb > 0 && workspace_bytes >= base + pxb;
     const size_t spb = split_scratch_for(op, P, opt);
@@ -221,7 +235,7 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
                                                         max_smem_optin(op->device));
     if (why[0] != '\0')
         return set_error(BPDN_ESIZE, "N = %d, L = %d, precision %d: %s", op->N, op->L, opt->precision, why);
-    if (split && (spb == 0 || workspace_bytes < base + spb))
+    if (split && (spb == 0 || (!split_at && workspace_bytes < base + spb)))
         return set_error(BPDN_ESIZE, "L = %d: the workspace does not hold the split-grid kernel's scratch "
                                      "(bpdn_solve_workspace_bytes gives the size)", op->L);
     SolveLaunch &a = sp->a;
@@ -251,7 +265,7 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     a.cum = (double *)((char *)d_workspace + 16 + 8 * 8);
     a.bscratch = a.blocks ? (double2 *)((char *)d_workspace + 256) : nullptr;
     a.px_scratch = use_px ? (unsigned char *)d_workspace + base : nullptr;
-    a.split_scratch = split ? (unsigned char *)d_workspace + base : nullptr;
+    a.split_scratch = !split ? nullptr : split_at ? split_at : (unsigned char *)d_workspace + base;
     sp->refit = opt->refit != 0;
     RefitLaunch &r = sp->r;
     r.g = a.g;
@@ -267,7 +281,7 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     r.rounds = opt->refit_rounds;
     // the split refit when the workspace holds its scratch (after the iteration kernel's), else
     // the fused refit
-    const size_t rbase = base + (use_px ? pxb : 0) + (split ? spb : 0);
+    const size_t rbase = base + (use_px ? pxb : 0) + (split && !split_at ? spb : 0);
     r.split = (workspace_bytes >= rbase + refit_scratch_bytes(P)) ? (unsigned char *)d_workspace + rbase : nullptr;
     return BPDN_OK;
 }
@@ -545,7 +559,7 @@ size_t bpdn_solve_workspace_bytes(bpdn_op_t h, int64_t P, const bpdn_options *op
     // the other iteration kernel and the fused refit)
     const OpHandle *op = reinterpret_cast<const OpHandle *>(h);
     const bool ok = op && op->magic == kOpMagic && P > 0;
-    const size_t pxb = ok ? (split_grid(op) ? split_scratch_for(op, P, opt) : px_scratch_for(op, P, opt)) : 0;
+    const size_t pxb = ok ? (split_grid(op, opt) ? split_scratch_for(op, P, opt) : px_scratch_for(op, P, opt)) : 0;
     return solve_min_workspace_bytes(opt) + pxb + ((opt && opt->refit) ? refit_scratch_bytes(P) : 0);
 }
 

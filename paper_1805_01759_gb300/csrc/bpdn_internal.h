@@ -63,9 +63,14 @@ cudaError_t launch_make_operator_md(const OpHandle &op, const double *d_b, const
 
 struct SolvePlan;
 // bpdn_solve's argument checks and launch records (sp->a.P == 0: nothing to launch)
+// (split_at: the split-grid kernel's scratch outside the workspace, for bpdn_solve_ragged)
 int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, int32_t lambda_per_pixel,
                const bpdn_options *opt, void *d_x, int32_t *d_support, int32_t *d_nsupp, int32_t *d_status,
-               int32_t *d_iters, int32_t *d_nbt, void *d_workspace, size_t workspace_bytes, SolvePlan *sp);
+               int32_t *d_iters, int32_t *d_nbt, void *d_workspace, size_t workspace_bytes, SolvePlan *sp,
+               unsigned char *split_at = nullptr);
+// whether a solve with these options runs the split-grid FP32 kernel (it then needs that
+// kernel's scratch: rbpg_split_scratch_bytes)
+bool solve_uses_split(const OpHandle *op, const bpdn_options *opt);
 int device_sms(int dev);
 // bpdn_solve's argument checks, followed by its launches when `launch` is true
 int solve_impl(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, int32_t lambda_per_pixel,

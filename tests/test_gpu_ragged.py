@@ -44,10 +44,11 @@ def test_ragged_equals_single_stack_solves(api, stacks):
     torch.cuda.synchronize()
     for i, (r, s) in enumerate(zip(out, singles)):
         assert _same(r, s), i
-    # the sizes span the kernel's shapes: N above and below 32, L above and below 512
+    # the sizes span the kernels' shapes: N above and below 32, L above and below 512 (the
+    # FP32 stacks beyond 512 points run the split-grid kernel in both calls)
     Ns = [st.geom.N for st in sts]
     Ls = [st.geom.L for st in sts]
-    assert max(Ns) > 32 and min(Ns) <= 32 and max(Ls) > 400
+    assert max(Ns) > 32 and min(Ns) <= 32 and max(Ls) > 512 and min(Ls) <= 512
 
 
 def test_ragged_against_oracle(api, stacks):
@@ -137,12 +138,12 @@ def test_tile_pixels_do_not_change_results(api, stacks):
 
 def test_per_stack_tiles_equal_default(api, stacks):
     """A stack's own tile_pixels (here 8: one group of slots per CTA, which fits wherever the
-    default does) changes the launch shape, not the arithmetic: the outputs equal the default
-    call's bit for bit."""
+    default does; for FP32 stacks beyond 512 points it also selects the grid-point kernel
+    over the split-grid one) gives exactly what bpdn_solve gives with that tile_pixels."""
     sts, items = stacks
     tiles = [8 if i % 2 else 0 for i in range(len(items))]
     out = api.RaggedSolver(items, tiles=tiles).run()
-    ref = api.solve_ragged(items)
+    ref = [api.solve(op, g, lam, tile_pixels=t) for (op, g, lam), t in zip(items, tiles)]
     torch.cuda.synchronize()
     for r, e in zip(out, ref):
         assert _same(r, e)

@@ -9,7 +9,7 @@ one-CTA grids' 1e-3 would leave no pixel; the FP32 error of |v| and of the sums 
 Eq. 15 over the few nonzero terms is ~1e-6 relative, well inside 1e-5);
 the certified solution equal to the exact minimiser (identical support, relative l2
 error <= 1e-4) on every certified, non-degenerate pixel; the edges (ragged P, a
-non-finite pixel, max_iter 0, options the kernel does not take).
+non-finite pixel, max_iter 0, options the kernel does not take, the ragged batch).
 """
 import numpy as np
 import pytest
@@ -165,8 +165,18 @@ def test_split_grid_edges(api, grid4d):
         with pytest.raises(_lib.BPDNError) as e:
             api.solve(op, g, grid4d.lam, **bad)
         assert e.value.code == _lib.BPDN_ESIZE, bad
-    with pytest.raises(_lib.BPDNError):
-        api.solve_ragged([(op, g, grid4d.lam)])
+    # the ragged batch runs such a stack in its own launch: bpdn_solve's results bit for bit,
+    # next to a stack of the batch launch
+    small = synth.workload_small(P=40, seed=5)
+    op_s = api.Operator.from_geometry(small.geom)
+    g_s = torch.from_numpy(small.g).cuda()
+    gg = torch.from_numpy(grid4d.g[:9]).cuda()
+    out = api.solve_ragged([(op_s, g_s, small.lam), (op, gg, grid4d.lam)])
+    refs = [api.solve(op_s, g_s, small.lam), api.solve(op, gg, grid4d.lam)]
+    torch.cuda.synchronize()
+    for r, e in zip(out, refs):
+        assert torch.equal(torch.view_as_real(r.x), torch.view_as_real(e.x))
+        assert torch.equal(r.status, e.status) and torch.equal(r.iters, e.iters)
 
 
 def _max_stack():
