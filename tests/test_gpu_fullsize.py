@@ -211,3 +211,43 @@ def test_full_differentiation_workload():
         lam_end, hist = api.tune_lambda(op, g.detach(), gt, start * lam0, steps=50, lr=0.1)
         errs = np.array([h[1] for h in hist])
         assert np.all(np.diff(errs) <= 1e-7 * errs[:-1]) and errs[-1] < errs[0], (start, hist[:3], hist[-3:])
+
+
+def test_full_4d_grid():
+    """The 4-D grid (64 x 16 x 16 = 16,384 points) at the size `bench.py --workload motion4d`
+    times (16,384 pixels, FP32 split-grid kernel + refit): whole-output properties, and 24
+    seeded pixels against the oracle's exact minimiser (working-set loop, certificate over
+    all 16,384 points)."""
+    from paper_1805_01759_gb300 import api, _lib
+    _lib.load()
+    P4 = 1 << 14
+    st = synth.workload_motion4d(P=P4, seed=8)
+    op = api.Operator.from_geometry(st.geom)
+    res = api.solve(op, torch.from_numpy(st.g).cuda(), st.lam)
+    torch.cuda.synchronize()
+    x, status, nsupp = res.x, res.status, res.nsupp
+    assert bool(torch.isfinite(torch.view_as_real(x)).all())
+    assert int((status & ~DEFINED_BITS).abs().sum()) == 0
+    nnz = (x != 0).sum(dim=1).to(torch.int32)
+    assert bool(torch.equal((status & 32) != 0, nnz == 0))
+    cert = (status & 64) != 0
+    assert float(cert.float().mean()) >= 0.999, float(cert.float().mean())
+    assert bool(torch.equal(nsupp[cert], nnz[cert]))
+    idx = np.sort(np.random.default_rng(4096).choice(P4, size=24, replace=False))
+    A = oracle.operator_md(st.geom)
+    xs = x[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.complex128)
+    st_s = status.cpu().numpy()[idx]
+    checked = 0
+    for j, p in enumerate(idx):
+        r = oracle.minimise_ws(A, st.g[p], st.lam)
+        assert r["flags"] == 0, p
+        assert st_s[j] & 64, f"sampled pixel {p} is not certified (status {st_s[j]})"
+        xr = r["x"]
+        if 1.0 - r["off_max"] <= 1e-6 or r["min_abs_on"] <= 1e-6 * max(np.abs(xr).max(), 1e-300):
+            continue
+        assert np.array_equal(xs[j] != 0, xr != 0), p
+        nr = np.linalg.norm(xr)
+        err = np.linalg.norm(xs[j] - xr) / nr if nr > 0 else np.linalg.norm(xs[j])
+        assert err <= 1e-4, (p, err)
+        checked += 1
+    assert checked >= 20, checked
