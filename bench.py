@@ -651,8 +651,9 @@ def run_ours(args) -> None:
 
 def run_ragged(args) -> None:
     """The ragged batch (64 stacks: N 10..60, L 100..600, 2^12..2^16 pixels each) through
-    one bpdn_solve_ragged call replayed as a CUDA graph, next to the same stacks solved one
-    after another on one stream."""
+    one bpdn_solve_ragged call replayed as a CUDA graph, with the library's kernel choice and
+    with each stack's kernel and tile picked by timing (api.autotune_stack), next to the same
+    stacks solved one after another on one stream."""
     import torch
     import torch.distributed as dist
     rank, world, local = dist_env()
@@ -693,19 +694,20 @@ def run_ragged(args) -> None:
 
     out = {}
     # per-stack precision differs, so the stacks are grouped into one solver per option set
-    for mode in ("graph",):
+    for mode in ("graph", "graph_autotuned"):
         solvers = []
         for key in sorted({tuple(sorted(opts(op).items())) for op, _, _ in items}):
             sub = [it for it in items if tuple(sorted(opts(it[0]).items())) == key]
-            solvers.append(api.RaggedSolver(sub, **dict(key)))
+            solvers.append(api.RaggedSolver(sub, autotune=(mode == "graph_autotuned"), **dict(key)))
         for sv in solvers:
             sv.capture()
         ms = timed(lambda: [sv.replay() for sv in solvers], args.steps, args.warmup)
         cert = sum(int(((r.status & 64) != 0).sum().item()) for sv in solvers for r in sv.results)
-        out[mode] = {"ms": ms, "pixels_per_s_certified": cert / (ms / 1e3), "certified_frac": cert / P_total}
+        out[mode] = {"ms": ms, "pixels_per_s_certified": cert / (ms / 1e3), "certified_frac": cert / P_total,
+                     "kernel_tile": [[k, t] for sv in solvers for k, t in zip(sv.kernels, sv.tiles)]}
     ms = timed(lambda: [api.solve(op, g, lam, **opts(op)) for op, g, lam in items], args.steps, args.warmup)
     out["sequential_one_stream"] = {"ms": ms}
-    best = "graph"
+    best = min(("graph", "graph_autotuned"), key=lambda k: out[k]["ms"])
     # whole job: certified pixels of every rank over the slowest rank's time
     cert_all = reduce_sum(out[best]["pixels_per_s_certified"] * out[best]["ms"] / 1e3, dev)
     P_all = int(reduce_sum(float(P_total), dev))

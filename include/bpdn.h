@@ -80,7 +80,12 @@ typedef struct {
                           /* iteration with probability L_j / sum L_j (Eqs. 13-14); FP32 only */
     uint32_t seed;        /* stream of the block draws: pixel p uses SplitMix64 from state     */
                           /* seed + p * 2^40 (default 0)                                       */
-    int32_t reserved[4];
+    int32_t kernel;       /* iteration kernel: 0 = library choice (the split-grid kernel for    */
+                          /* grids of more than 1024 points, and for FP32 grids of more than  */
+                          /* 512 with tile_pixels 0; else the grid-point kernel); 1 = the      */
+                          /* grid-point kernel (L <= 1024); 2 = the split-grid kernel (FP32,   */
+                          /* tile_pixels 0, blocks <= 1) (default 0)                           */
+    int32_t reserved[3];
 } bpdn_options;
 
 /* Fill *opt with the defaults above. */
@@ -183,8 +188,9 @@ size_t bpdn_solve_workspace_bytes(bpdn_op_t op, int64_t P, const bpdn_options *o
  * chunks, the iterate in the workspace) for grids of more than 1024 points (L up to
  * BPDN_MAX_L, e.g. the multi-component grids of Eq. 4), which need precision 0,
  * tile_pixels 0 and blocks <= 1, and for FP32 solves of 513..1024 points with
- * tile_pixels 0 and blocks <= 1 (tile_pixels 8 keeps the grid-point kernel there).  The
- * choice depends on the operator and the options only.  Such a solve needs a workspace of
+ * tile_pixels 0 and blocks <= 1; opt->kernel overrides that choice (1: the grid-point
+ * kernel, 2: the split-grid kernel at any L).  The choice depends on the operator and the
+ * options only.  Such a solve needs a workspace of
  * at least bpdn_solve_workspace_bytes(op, P, opt) bytes; otherwise BPDN_ESIZE before any
  * launch (bpdn_solve_noalloc refuses them).
  */
@@ -233,6 +239,7 @@ typedef struct {
     int32_t *d_iters;          /* device int32 [P] out */
     int32_t *d_nbt;            /* device int32 [P] out, or NULL */
     int32_t tile_pixels;       /* this stack's tile_pixels (0 = the options' value) */
+    int32_t kernel;            /* this stack's kernel option (0 = the options' value) */
 } bpdn_stack;
 
 /* Least workspace of bpdn_solve_ragged: 256 bytes per stack (the refits then run as single

@@ -55,7 +55,8 @@ class Options(ctypes.Structure):
         ("refit_rounds", ctypes.c_int32),
         ("blocks", ctypes.c_int32),
         ("seed", ctypes.c_uint32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("kernel", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -83,6 +84,7 @@ class Stack(ctypes.Structure):
         ("d_iters", ctypes.c_void_p),
         ("d_nbt", ctypes.c_void_p),
         ("tile_pixels", ctypes.c_int32),
+        ("kernel", ctypes.c_int32),
     ]
 
 

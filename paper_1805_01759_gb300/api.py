@@ -461,21 +461,64 @@ def tune_lambda(op: Operator, g: torch.Tensor, gamma_true: torch.Tensor, lam0: f
     return float(log_lam.exp().item()), history
 
 
+_TUNE_CACHE: dict = {}
+
+
+def autotune_stack(op: Operator, g: torch.Tensor, lam, *, repeats: int = 2, **options):
+    """Pick the iteration kernel and tile for this operator and batch by timing bpdn_solve
+    on g itself: (kernel, tile_pixels) among the grid-point kernel with 16 or 8 pixels per
+    slot group and, in FP32, the split-grid kernel.  Cached by (N, L, precision, P);
+    candidates the library refuses at these sizes are skipped.  Returns (0, 0), the
+    library's own choice, when nothing could be timed."""
+    P = g.shape[0]
+    prec = int(options.get("precision", 0))
+    key = (op.N, op.L, prec, P, int(options.get("blocks", 0)))
+    if key in _TUNE_CACHE:
+        return _TUNE_CACHE[key]
+    cands = [(1, 16), (1, 8)] + ([(2, 0)] if prec == 0 else [])
+    opts = {k: v for k, v in options.items() if k not in ("kernel", "tile_pixels")}
+    best, best_ms = (0, 0), float("inf")
+    for kern, tile in cands:
+        try:
+            solve(op, g, lam, kernel=kern, tile_pixels=tile, **opts)  # warm-up, and checks that it runs
+        except _lib.BPDNError:
+            continue
+        ms = float("inf")
+        for _ in range(repeats):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            solve(op, g, lam, kernel=kern, tile_pixels=tile, **opts)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = min(ms, e0.elapsed_time(e1))
+        if ms < best_ms:
+            best, best_ms = (kern, tile), ms
+    _TUNE_CACHE[key] = best
+    return best
+
+
 class RaggedSolver:
     """Many stacks, each with its own operator and pixel count, through bpdn_solve_ragged.
 
-    items: list of (Operator, g [P_s, N_s] complex64 CUDA tensor, lambda); tiles (optional):
-    each stack's tile_pixels (0 = the options' value).  Outputs are allocated once
-    (`results`, one SolveResult per stack).  run() launches on the current (or given) stream;
-    capture() records one call into a CUDA graph and replay() relaunches it: the graph reads
-    the same g tensors, so new data is copied into them."""
+    items: list of (Operator, g [P_s, N_s] complex64 CUDA tensor, lambda); tiles and kernels
+    (optional): each stack's tile_pixels and kernel options (0 = the options' value); with
+    autotune=True each stack's (kernel, tile_pixels) is chosen by autotune_stack first.
+    Outputs are allocated once (`results`, one SolveResult per stack).  run() launches on the
+    current (or given) stream; capture() records one call into a CUDA graph and replay()
+    relaunches it: the graph reads the same g tensors, so new data is copied into them."""
 
-    def __init__(self, items, *, tiles=None, **options):
+    def __init__(self, items, *, tiles=None, kernels=None, autotune: bool = False, **options):
         lib = _lib.load()
         self.opt = _lib.default_options(**options)
+        if autotune:
+            picks = [autotune_stack(op, _check_g(op, g), lam, **options) for op, g, lam in items]
+            kernels = [k for k, _ in picks]
+            tiles = [t for _, t in picks]
         self.tiles = [0] * len(items) if tiles is None else [int(t) for t in tiles]
-        if len(self.tiles) != len(items):
-            raise ValueError("tiles must name one tile_pixels per stack")
+        self.kernels = [0] * len(items) if kernels is None else [int(k) for k in kernels]
+        if len(self.tiles) != len(items) or len(self.kernels) != len(items):
+            raise ValueError("tiles and kernels must name one value per stack")
         self.items = []
         self.results = []
         self._keep = []
@@ -496,7 +539,7 @@ class RaggedSolver:
             )
             arr[i] = _lib.Stack(op.handle.value, g.data_ptr(), P, lam_t.data_ptr(), pp, res.x.data_ptr(),
                                 _ptr(res.support), res.nsupp.data_ptr(), res.status.data_ptr(),
-                                res.iters.data_ptr(), res.nbt.data_ptr(), self.tiles[i])
+                                res.iters.data_ptr(), res.nbt.data_ptr(), self.tiles[i], self.kernels[i])
             self.items.append((op, g, lam_t))
             self.results.append(res)
         self._arr = arr

@@ -114,6 +114,10 @@ static int check_options(const bpdn_options *o)
         return set_error(BPDN_EINVAL, "tile_pixels must be 0 (library choice), 8, 16 or 128");
     if (o->tile_pixels == 128 && o->precision != 1)
         return set_error(BPDN_EINVAL, "tile_pixels 128 (one pixel per thread) is the BF16 kernel: precision 1");
+    if (o->kernel < 0 || o->kernel > 2)
+        return set_error(BPDN_EINVAL, "kernel must be 0 (library choice), 1 (grid-point) or 2 (split-grid)");
+    if (o->kernel == 2 && (o->precision != 0 || o->tile_pixels != 0 || o->blocks >= 2))
+        return set_error(BPDN_EINVAL, "kernel 2 (split-grid) runs FP32 with tile_pixels 0 and blocks <= 1");
     if (o->blocks < 0 || o->blocks > 8)
         return set_error(BPDN_EINVAL, "blocks must lie in [0, 8]");
     if (o->blocks >= 2 && o->precision != 0)
@@ -154,8 +158,12 @@ bool solve_uses_split(const OpHandle *op, const bpdn_options *opt)
 {
     if (!op)
         return false;
-    if (op->L > 1024)
+    if (opt && opt->kernel == 2)
         return true;
+    if (op->L > 1024)
+        return true;  // (kernel 1 is then refused by the plan)
+    if (opt && opt->kernel == 1)
+        return false;
     return opt && op->L > 512 && opt->precision == 0 && opt->tile_pixels == 0 && opt->blocks < 2;
 }
 
@@ -226,7 +234,8 @@ int solve_plan(bpdn_op_t h, const void *d_g, int64_t P, const float *d_lambda, i
     if (opt->tile_pixels == 128 && !use_px && !split)
         return set_error(BPDN_ESIZE, pxb ? "tile_pixels 128: the workspace does not hold the kernel's scratch"
                                          : "tile_pixels 128 needs 2N <= 64 and the operator within shared memory");
-    const char *why = split ? (opt->tile_pixels != 0 ? "grids of more than 1024 points take tile_pixels 0"
+    const char *why = (opt->kernel == 1 && op->L > 1024) ? "the grid-point kernel (kernel 1) handles L <= 1024"
+                      : split ? (opt->tile_pixels != 0 ? "grids of more than 1024 points take tile_pixels 0"
                                                      : rbpg_split_check(*op, opt->precision, opt->blocks,
                                                                         max_smem_optin(op->device)))
                       : (opt->blocks >= 2) ? rbpg_block_check(*op, opt->blocks, max_smem_optin(op->device))

@@ -66,13 +66,16 @@ size_t stack_split_bytes(const bpdn_stack &st, const bpdn_options &o)
     return (rbpg_split_scratch_bytes(*op, st.P, device_sms(op->device)) + 255) / 256 * 256;
 }
 
-// each stack's options: the call's, with the stack's tile_pixels when it names one
+// each stack's options: the call's, with the stack's tile_pixels and kernel when it names them
 std::vector<bpdn_options> stack_options(const bpdn_stack *stacks, int n, const bpdn_options &opt)
 {
     std::vector<bpdn_options> sopt(n, opt);
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i) {
         if (stacks[i].tile_pixels)
             sopt[i].tile_pixels = stacks[i].tile_pixels;
+        if (stacks[i].kernel)
+            sopt[i].kernel = stacks[i].kernel;
+    }
     return sopt;
 }
 

@@ -149,6 +149,44 @@ def test_per_stack_tiles_equal_default(api, stacks):
         assert _same(r, e)
 
 
+def test_autotuned_ragged_equals_per_stack_solves(api, stacks):
+    """The autotuner's per-stack (kernel, tile_pixels) choice: the batch gives exactly what
+    bpdn_solve gives each stack with those options, and every choice is a valid one."""
+    sts, items = stacks
+    tuned = api.RaggedSolver(items, autotune=True)
+    assert all((k, t) in ((1, 16), (1, 8), (2, 0), (0, 0)) for k, t in zip(tuned.kernels, tuned.tiles))
+    out = tuned.run()
+    ref = [api.solve(op, g, lam, kernel=k, tile_pixels=t)
+           for (op, g, lam), k, t in zip(items, tuned.kernels, tuned.tiles)]
+    torch.cuda.synchronize()
+    for r, e in zip(out, ref):
+        assert _same(r, e)
+
+
+def test_kernel_option(api, stacks):
+    """kernel 1 (grid-point) and 2 (split-grid) on the same FP32 stack both reach the exact
+    minimiser; kernel 2 is refused with BF16 or a tile, kernel 1 beyond 1024 points."""
+    from paper_1805_01759_gb300 import _lib
+    sts, items = stacks
+    st, (op, g, lam) = sts[0], items[0]
+    A = oracle.operator(st.geom)
+    ref = oracle.minimise_batch(A, st.g, st.lam)
+    for kern in (1, 2):
+        res = api.solve(op, g, lam, kernel=kern)
+        x = res.x.cpu().numpy().astype(np.complex128)
+        cert = (res.status.cpu().numpy() & 64) != 0
+        sel = cert & (ref["flags"] == 0) & (ref["margin"] > 1e-6)
+        assert cert.mean() >= 0.99 and sel.sum() >= 0.9 * len(sel), (kern, cert.mean(), sel.sum())
+        assert np.array_equal(x[sel] != 0, ref["x"][sel] != 0), kern
+        nr = np.linalg.norm(ref["x"][sel], axis=1)
+        err = np.linalg.norm(x[sel] - ref["x"][sel], axis=1) / np.where(nr > 0, nr, 1.0)
+        assert err.max() <= 1e-4, (kern, err.max())
+    for bad in (dict(kernel=2, precision=1), dict(kernel=2, tile_pixels=8), dict(kernel=3)):
+        with pytest.raises(_lib.BPDNError) as e:
+            api.solve(op, g, lam, **bad)
+        assert e.value.code == _lib.BPDN_EINVAL, bad
+
+
 def test_host_solver_equals_device_solve(api):
     """Chunked solve from pinned host memory (copies overlapped on two streams) returns
     the device solve's results bit for bit, with lambda shared or per pixel."""
