@@ -10,7 +10,7 @@
 // refits follow, one launch per stack, spread over a small pool of library-owned streams
 // that fork from and join back into the caller's stream through events, so the call can
 // be captured into one CUDA graph.  A stack may carry its own tile_pixels (pixels in
-// flight per SM).
+// flight per SM) and kernel option, as the autotuner of the Python binding picks them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
