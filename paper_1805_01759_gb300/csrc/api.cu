@@ -116,8 +116,8 @@ static int check_options(const bpdn_options *o)
         return set_error(BPDN_EINVAL, "tile_pixels 128 (one pixel per thread) is the BF16 kernel: precision 1");
     if (o->kernel < 0 || o->kernel > 2)
         return set_error(BPDN_EINVAL, "kernel must be 0 (library choice), 1 (grid-point) or 2 (split-grid)");
-    if (o->kernel == 2 && (o->precision != 0 || o->tile_pixels != 0 || o->blocks >= 2))
-        return set_error(BPDN_EINVAL, "kernel 2 (split-grid) runs FP32 with tile_pixels 0 and blocks <= 1");
+    if (o->kernel == 2 && (o->tile_pixels != 0 || o->blocks >= 2))
+        return set_error(BPDN_EINVAL, "kernel 2 (split-grid) runs with tile_pixels 0 and blocks <= 1");
     if (o->blocks < 0 || o->blocks > 8)
         return set_error(BPDN_EINVAL, "blocks must lie in [0, 8]");
     if (o->blocks >= 2 && o->precision != 0)
@@ -162,9 +162,11 @@ bool solve_uses_split(const OpHandle *op, const bpdn_options *opt)
         return true;
     if (op->L > 1024)
         return true;  // (kernel 1 is then refused by the plan)
-    if (opt && opt->kernel == 1)
+    if (!opt || opt->kernel == 1 || opt->tile_pixels != 0 || opt->blocks >= 2)
         return false;
-    return opt && op->L > 512 && opt->precision == 0 && opt->tile_pixels == 0 && opt->blocks < 2;
+    if (opt->precision == 1)  // the grid-point BF16 kernel takes 2N <= 64 and L <= 512
+        return op->L > 512 || 2 * op->N > 64;
+    return op->L > 512;
 }
 
 static bool split_grid(const OpHandle *op, const bpdn_options *opt) { return solve_uses_split(op, opt); }
@@ -176,7 +178,7 @@ static size_t split_scratch_for(const OpHandle *op, int64_t P, const bpdn_option
     if (!split_grid(op, opt) || !opt || opt->tile_pixels != 0 ||
         rbpg_split_check(*op, opt->precision, opt->blocks, max_smem_optin(op->device))[0] != '\0')
         return 0;
-    return rbpg_split_scratch_bytes(*op, P, num_sms(op->device));
+    return rbpg_split_scratch_bytes(*op, opt->precision, P, num_sms(op->device));
 }
 
 static int check_solve_buffers(const OpHandle *op, const void *d_g, int64_t P, const float *d_lambda,

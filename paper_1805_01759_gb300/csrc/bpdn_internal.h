@@ -114,10 +114,11 @@ cudaError_t launch_rbpg(const OpHandle &op, const SolveLaunch &a, int num_sms, c
 // (0 when the operator's sizes do not suit it), and its launch
 size_t rbpg_px_scratch_bytes(const OpHandle &op, int64_t P, int num_sms, int max_smem);
 cudaError_t launch_rbpg_px(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
-// the split-grid FP32 iteration kernel (L > 1024): "" when it takes the operator, else the
-// reason; bytes of its scratch for P pixels on this device (0: it cannot launch); its launch
+// the split-grid iteration kernel (FP32 CUDA cores, or BF16 tensor cores with precision 1):
+// "" when it takes the operator, else the reason; bytes of its scratch for P pixels on this
+// device (0: it cannot launch); its launch (the variant follows a.precision)
 const char *rbpg_split_check(const OpHandle &op, int precision, int blocks, int max_smem);
-size_t rbpg_split_scratch_bytes(const OpHandle &op, int64_t P, int num_sms);
+size_t rbpg_split_scratch_bytes(const OpHandle &op, int precision, int64_t P, int num_sms);
 cudaError_t launch_rbpg_split(const OpHandle &op, const SolveLaunch &a, int num_sms, cudaStream_t s);
 // many stacks in persistent launches, one per kernel variant present (at most 64 stacks each)
 cudaError_t launch_rbpg_batch(const OpHandle *const *ops, const SolveLaunch *as, int n, int num_sms,

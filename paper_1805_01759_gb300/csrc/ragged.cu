@@ -63,7 +63,7 @@ size_t stack_split_bytes(const bpdn_stack &st, const bpdn_options &o)
     const OpHandle *op = reinterpret_cast<const OpHandle *>(st.op);
     if (!op || op->magic != kOpMagic || st.P <= 0 || !solve_uses_split(op, &o))
         return 0;
-    return (rbpg_split_scratch_bytes(*op, st.P, device_sms(op->device)) + 255) / 256 * 256;
+    return (rbpg_split_scratch_bytes(*op, o.precision, st.P, device_sms(op->device)) + 255) / 256 * 256;
 }
 
 // each stack's options: the call's, with the stack's tile_pixels and kernel when it names them

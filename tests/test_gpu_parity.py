@@ -307,18 +307,20 @@ def test_bf16_pixel_kernel_edges(api, small):
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 10])
-@pytest.mark.parametrize("tile", [16, 128])
+@pytest.mark.parametrize("tile", [16, 128, "split"])
 def test_bf16_iterations_match_algorithm_1_element_wise(api, small, k, tile):
     """Algorithm 1 with the BF16 tensor-core contraction against the oracle's Algorithm 1 with
     the same BF16 operands (A and r = A y - g rounded to bfloat16, products summed in FP64):
     element by element, relative ||x - x_oracle|| <= 2e-4 ||x_oracle||, identical supports and
     iteration counts, on pixels where no discrete decision (prox threshold, Eq. 15, accept, or
     the bfloat16 rounding of a residual entry) lies within 1e-3 of its boundary.  Both BF16
-    kernels (tile 16: grid point per thread; 128: pixel per thread)."""
+    kernels (tile 16: grid point per thread; 128: pixel per thread; split: the split-grid
+    kernel on tensor cores, its two 128-point tiles the second one partial)."""
     A = oracle.operator(small.geom)
     op = api.Operator.from_geometry(small.geom)
     g = torch.from_numpy(small.g).cuda()
-    res = api.solve(op, g, small.lam, max_iter=k, tol=0.0, refit=0, precision=1, tile_pixels=tile)
+    kw = dict(kernel=2) if tile == "split" else dict(tile_pixels=tile)
+    res = api.solve(op, g, small.lam, max_iter=k, tol=0.0, refit=0, precision=1, **kw)
     x = res.x.cpu().numpy()
     iters = res.iters.cpu().numpy()
     checked = 0
@@ -365,27 +367,35 @@ def test_bf16_first_iterations(api, small, k):
     assert np.percentile(errs, 90) <= 3e-2, np.percentile(errs, 90)
 
 
-def test_bf16_rejects_unsupported_sizes(api):
-    """The tensor-core path holds 2N <= 64 contraction terms; larger N is refused up front."""
+def test_bf16_beyond_the_grid_kernel(api):
+    """The grid-point BF16 kernel holds 2N <= 64 contraction terms: with the library's choice
+    a larger N runs the tensor-core split-grid kernel, while asking for the grid-point kernel
+    (a tile of 8 or 16 pixels, or kernel 1) is refused up front."""
     from paper_1805_01759_gb300 import _lib
     geom = synth.make_geometry(np.random.default_rng(0), 40, 100)
     op = api.Operator.from_geometry(geom)
     g = torch.zeros((4, 40), dtype=torch.complex64, device="cuda")
-    with pytest.raises(_lib.BPDNError) as ei:
-        api.solve(op, g, 1.0, precision=1)
-    assert ei.value.code == -3
+    res = api.solve(op, g, 1.0, precision=1)
+    assert torch.all(res.x == 0) and torch.all((res.status & 32) != 0)
+    for bad in (dict(tile_pixels=16), dict(tile_pixels=8), dict(kernel=1)):
+        with pytest.raises(_lib.BPDNError) as ei:
+            api.solve(op, g, 1.0, precision=1, **bad)
+        assert ei.value.code == -3, bad
 
 
 @pytest.mark.parametrize("N,L,half_width,precision", [(60, 600, 250.0, 0), (40, 300, 120.0, 0), (12, 1000, 300.0, 0),
                                                        (64, 1024, 300.0, 0), (32, 512, 200.0, 1),
-                                                       (78, 400, 200.0, 0), (80, 200, 100.0, 0)])
+                                                       (78, 400, 200.0, 0), (80, 200, 100.0, 0),
+                                                       (78, 400, 200.0, 1), (60, 600, 250.0, 1),
+                                                       (12, 1000, 300.0, 1), (80, 1024, 300.0, 1)])
 def test_solve_refit_operator_sizes(api, N, L, half_width, precision):
     """Beyond the sizes of the benchmark stack: N > 32 (two rows per lane), L > 512, an
     operator too large for shared memory (N=60, L=600: A is read from global memory), the
     78 acquisitions of the paper's Munich stack (three rows per lane, Sec. IV-C), and the
     library's maximum sizes (FP32: N = 64, L = 1024, one 1024-thread group per CTA, and
-    N = 80; BF16: 2N = 64 contraction terms, L = 512).  Same bar as the small workload
-    against the exact minimiser."""
+    N = 80; BF16: 2N = 64 contraction terms, L = 512, on the grid-point kernel, and beyond
+    that, up to N = 80 and L = 1024, on the tensor-core split-grid kernel).  Same bar as the
+    small workload against the exact minimiser."""
     rng = np.random.default_rng(1000 + N + L)
     geom = synth.make_geometry(rng, N, L, 250.0, half_width)
     st = synth.make_stack(geom, 48, rng, lam=synth.default_lambda(N, L), snr_db_range=(5.0, 20.0))

@@ -165,7 +165,7 @@ def test_autotuned_ragged_equals_per_stack_solves(api, stacks):
 
 def test_kernel_option(api, stacks):
     """kernel 1 (grid-point) and 2 (split-grid) on the same FP32 stack both reach the exact
-    minimiser; kernel 2 is refused with BF16 or a tile, kernel 1 beyond 1024 points."""
+    minimiser; kernel 2 is refused with a tile or randomized blocks."""
     from paper_1805_01759_gb300 import _lib
     sts, items = stacks
     st, (op, g, lam) = sts[0], items[0]
@@ -181,7 +181,7 @@ def test_kernel_option(api, stacks):
         nr = np.linalg.norm(ref["x"][sel], axis=1)
         err = np.linalg.norm(x[sel] - ref["x"][sel], axis=1) / np.where(nr > 0, nr, 1.0)
         assert err.max() <= 1e-4, (kern, err.max())
-    for bad in (dict(kernel=2, precision=1), dict(kernel=2, tile_pixels=8), dict(kernel=3)):
+    for bad in (dict(kernel=2, tile_pixels=8), dict(kernel=2, blocks=2), dict(kernel=3)):
         with pytest.raises(_lib.BPDNError) as e:
             api.solve(op, g, lam, **bad)
         assert e.value.code == _lib.BPDN_EINVAL, bad

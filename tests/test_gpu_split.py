@@ -161,7 +161,7 @@ def test_split_grid_edges(api, grid4d):
     r0 = api.solve(op, g[3:6], grid4d.lam, max_iter=0, refit=0)
     assert torch.all(r0.x == 0) and torch.all(r0.iters == 0) and torch.all(r0.status == 33)
     # options the split-grid kernel does not take are refused before any launch
-    for bad in (dict(precision=1), dict(tile_pixels=16), dict(blocks=2)):
+    for bad in (dict(precision=1, tile_pixels=16), dict(tile_pixels=16), dict(blocks=2), dict(kernel=1)):
         with pytest.raises(_lib.BPDNError) as e:
             api.solve(op, g, grid4d.lam, **bad)
         assert e.value.code == _lib.BPDN_ESIZE, bad
@@ -249,3 +249,39 @@ def test_split_grid_adjoint(api, grid4d):
         assert abs(dl[p] - r["dLdlam"][p]) <= 1e-3 * max(abs(r["dLdlam"][p]), 1e-9 * scale), p
         checked += 1
     assert checked >= 16, checked
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_split_grid_bf16_first_iterations(api, grid4d, k):
+    """The tensor-core split-grid kernel on the 16,384-point grid against the oracle's
+    Algorithm 1 with the same BF16 operands, element by element (2e-4), on pixels with no
+    decision (including the bfloat16 rounding of a residual entry) within 1e-5 of its
+    boundary."""
+    A = oracle.operator_md(grid4d.geom)
+    op = api.Operator.from_geometry(grid4d.geom)
+    g = torch.from_numpy(grid4d.g).cuda()
+    res = api.solve(op, g, grid4d.lam, max_iter=k, tol=0.0, refit=0, precision=1)
+    x = res.x.cpu().numpy()
+    iters = res.iters.cpu().numpy()
+    checked = 0
+    for p in range(grid4d.g.shape[0]):
+        r = oracle.rbpg(A, grid4d.g[p], grid4d.lam, max_iter=k, tol=0.0, trace=True, bf16_operands=True)
+        if np.min(r["margin"]) < 1e-5:
+            continue
+        assert iters[p] == r["iters"], p
+        ref = r["x"]
+        assert np.linalg.norm(x[p] - ref) <= 2e-4 * max(np.linalg.norm(ref), 1e-6), p
+        assert np.array_equal(x[p] != 0, ref != 0), p
+        checked += 1
+    assert checked >= 12, checked
+
+
+def test_split_grid_bf16_solve_refit_4d(api, grid4d):
+    """BF16 (tol 1e-3) on the tensor-core split-grid kernel, then the FP64 refit: the exact
+    minimiser on every certified, non-degenerate pixel."""
+    A = oracle.operator_md(grid4d.geom)
+    op = api.Operator.from_geometry(grid4d.geom)
+    res = api.solve(op, torch.from_numpy(grid4d.g).cuda(), grid4d.lam, precision=1, tol=1e-3)
+    ref = _exact(A, grid4d.g, grid4d.lam)
+    cert = _check_minimiser(res, ref, 48)
+    assert cert.mean() >= 0.9, cert.mean()
