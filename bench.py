@@ -674,9 +674,11 @@ def run_ragged(args) -> None:
     # the BF16 path needs 2N <= 64 and L <= 512: other stacks run in FP32 in either mode; in the
     # BF16 mode they stop at the same tolerance as the BF16 stacks (the refit certifies both)
     def opts(op):
-        # in the BF16 mode every stack runs on tensor cores (the grid-point kernel where
-        # 2N <= 64 and L <= 512, the tensor-core split-grid kernel elsewhere)
-        return dict(precision=prec, tol=tol)
+        # BF16 where the grid-point tensor-core kernel takes the stack (2N <= 64, L <= 512);
+        # the other stacks run in FP32 (at the same tolerance in the BF16 mode), which is
+        # faster there than the tensor-core split-grid kernel
+        ok = prec == 1 and 2 * op.N <= 64 and op.L <= 512
+        return dict(precision=1 if ok else 0, tol=tol)
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
@@ -972,7 +974,8 @@ def run_motion(args) -> None:
     from paper_1805_01759_gb300 import api, synth
     out = {}
     for name, L_s, kw in (("bf16_32x16", 32, dict(precision=1, tol=args.tol_bf16)),
-                          ("fp32_64x16", 64, dict(precision=0, tol=args.tol_fp32))):
+                          ("fp32_64x16", 64, dict(precision=0, tol=args.tol_fp32)),
+                          ("bf16_64x16", 64, dict(precision=1, tol=args.tol_bf16))):
         st = synth.workload_motion(P=args.motion_pixels, seed=7, L_s=L_s, L_v=16)
         op = api.Operator.from_geometry(st.geom)
         g = torch.from_numpy(st.g).cuda()
@@ -993,7 +996,8 @@ def run_motion(args) -> None:
         if not args.no_cpu_baseline:
             out[name]["oracle_sample"] = _motion_sample(st, res, 32)
     if args.motion4d_pixels > 0:
-        out["fp32_4d_64x16x16"] = _motion4d(args)
+        out["fp32_4d_64x16x16"] = _motion4d(args, 0)
+        out["bf16_4d_64x16x16"] = _motion4d(args, 1)
     print(json.dumps({"metric": "certified pixels/s, multi-component operator (elevation x velocity)",
                       "value": out["bf16_32x16"]["certified_pixels_per_s"], "unit": "pixels/s",
                       "workload": f"N=25, times U[0,4] yr, linear velocity grid 16 points on [-0.02,0.02] m/yr, "
@@ -1002,30 +1006,32 @@ def run_motion(args) -> None:
 
 
 def run_motion4d(args) -> None:
-    """The 4-D grid run of the motion leg on its own (one JSON line)."""
+    """The 4-D grid runs of the motion leg on their own (one JSON line)."""
     import torch
     rank, world, local = dist_env()
     if rank != 0:
         return
     torch.cuda.set_device(local)
-    row = _motion4d(args)
+    runs = {"fp32": _motion4d(args, 0), "bf16": _motion4d(args, 1)}
     print(json.dumps({"metric": "certified pixels/s, 4-D grid (elevation x velocity x seasonal amplitude)",
-                      "value": row["certified_pixels_per_s"], "unit": "pixels/s",
-                      "workload": "N=25, 64 x 16 x 16 = 16,384 grid points, seed 8", "run": row}), flush=True)
+                      "value": max(r["certified_pixels_per_s"] for r in runs.values()), "unit": "pixels/s",
+                      "workload": "N=25, 64 x 16 x 16 = 16,384 grid points, seed 8", "runs": runs}), flush=True)
 
 
-def _motion4d(args) -> dict:
+def _motion4d(args, precision: int = 0) -> dict:
     """The 4-D grid (elevation x velocity x seasonal amplitude, 64 x 16 x 16 = 16,384 points)
-    through the split-grid FP32 kernel and the refit: the whole solve, the iterations alone,
-    and the gradient's FP32 rate (8 N L flops per sweep of a pixel) over the iteration time."""
+    through the split-grid kernel (FP32 CUDA cores at tol 1e-6, or BF16 tensor cores at
+    tol 1e-3) and the refit: the whole solve, the iterations alone, and the contraction's rate
+    (8 N L flops per sweep of a pixel) over the iteration time."""
     import torch
     from paper_1805_01759_gb300 import api, synth
     st = synth.workload_motion4d(P=args.motion4d_pixels, seed=8)
     op = api.Operator.from_geometry(st.geom)
     g = torch.from_numpy(st.g).cuda()
-    row = {"L": op.L, "N": op.N, "pixels": int(g.shape[0])}
-    for key, kw in (("solve", dict(precision=0, tol=args.tol_fp32)),
-                    ("iterations_only", dict(precision=0, tol=args.tol_fp32, refit=0))):
+    row = {"L": op.L, "N": op.N, "pixels": int(g.shape[0]), "precision": "bf16" if precision else "fp32"}
+    tol = args.tol_bf16 if precision else args.tol_fp32
+    for key, kw in (("solve", dict(precision=precision, tol=tol)),
+                    ("iterations_only", dict(precision=precision, tol=tol, refit=0))):
         for _ in range(max(1, min(args.warmup, 2))):
             api.solve(op, g, st.lam, **kw)
         torch.cuda.synchronize()

@@ -562,8 +562,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_rbpg_split(const __grid_constan
 // The same sweep with the gradient from tcgen05 MMAs (BF16 operands, FP32 accumulators): per
 // 128-point tile of the grid D[l, j] = sum_k Aop[l, k] B[j, k], Aop[l, :] = (Re A_.l, Im A_.l)
 // (K = 2N padded to 16) from the launch's BF16 tiled copy of the operator, staged in shared
-// memory by cp.async into two buffers, and B = the residual rows (put_r).  The MMA of tile c+1
-// runs while the warps work on tile c.  Four warps: warp w holds tensor-memory lanes 32w ..
+// memory by cp.async into three buffers (the copy of tile c+2 and the MMA of tile c+1 run
+// while the warps work on tile c), and B = the residual rows (put_r).  Four warps: warp w holds tensor-memory lanes 32w ..
 // 32w+31 = grid points 128c + 32w + lane = 32-point block 4c + w.  Every wait for the tensor
 // cores is bounded; after one runs out the CTA ends its pixels with DEVICE_TIMEOUT.
 
@@ -653,7 +653,7 @@ __device__ __forceinline__ void issue_tile_mma(uint32_t d, const unsigned char *
 // bytes of the tensor-core variant's dynamic shared memory
 __host__ __device__ inline size_t split_tc_smem_bytes(int N, int NC, int Kp)
 {
-    return (size_t)2 * 256 * Kp + align16((size_t)2 * kTcKS * Kp * 2) + split_smem_bytes(kTcKS, N, NC, kTcWarps);
+    return (size_t)3 * 256 * Kp + align16((size_t)2 * kTcKS * Kp * 2) + split_smem_bytes(kTcKS, N, NC, kTcWarps);
 }
 
 template <int NCH>
@@ -667,8 +667,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rbpg_split_tc(const __grid_co
     const int N = prm.N, L = prm.L, NC = prm.NC, Kp = prm.Kp, NCT = prm.NCT;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const size_t tb = (size_t)256 * Kp;
-    unsigned char *abuf0 = smem_raw, *abuf1 = smem_raw + tb;
-    unsigned char *bop = smem_raw + 2 * tb;
+    // three operator buffers: tile t sits in abuf(t % 3); its copy is issued two tiles ahead
+    auto abuf = [&](long long tt) -> unsigned char * { return smem_raw + (size_t)(tt % 3) * tb; };
+    unsigned char *bop = smem_raw + 3 * tb;
     SplitSmem sm = carve<KS>(bop + align16((size_t)2 * KS * Kp * 2), N, NC, kTcWarps);
     sm.Bop = bop;
     float2 *rows = prm.rows + (size_t)blockIdx.x * KS * 3 * L;
@@ -692,7 +693,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rbpg_split_tc(const __grid_co
     const uint32_t tlane = tmem + ((uint32_t)(32 * w) << 16);
     for (int p = w; p < KS; p += kTcWarps)
         refill_slot<KS, true>(prm, sm, p, lane);
-    stage_tile(prm, abuf0, 0, tid);
+    stage_tile(prm, abuf(0), 0, tid);
+    stage_tile(prm, abuf(1), NCT > 1 ? 1 : 0, tid);
     asm volatile("cp.async.wait_all;" ::: "memory");
     proxy_fence();  // the operator tile and the B rows, for the first MMA
     tc_before();
@@ -722,12 +724,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rbpg_split_tc(const __grid_co
             for (int cc = 0; cc < NCH; ++cc)
                 acc[p][cc] = make_float2(0.f, 0.f);
         if (tid == 0)
-            issue_tile_mma(tmem + 16u * (uint32_t)(t & 1), (t & 1) ? abuf1 : abuf0, bop, Kp, (t & 1) ? mb1 : mb0);
+            issue_tile_mma(tmem + 16u * (uint32_t)(t & 1), abuf(t), bop, Kp, (t & 1) ? mb1 : mb0);
         for (int c = 0; c < NCT; ++c, ++t) {
             const int b = (int)(t & 1);
-            // the next tile (this sweep's, or the next sweep's first) into the other buffer:
-            // its last MMA (tile t - 1) was waited for in the previous step
-            stage_tile(prm, b ? abuf0 : abuf1, (c + 1 < NCT) ? c + 1 : 0, tid);
             const uint32_t ph = b ? ph1 : ph0;
             const bool ok = tc_wait(b ? mb1 : mb0, ph);
             if (b)
@@ -744,6 +743,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rbpg_split_tc(const __grid_co
                 pend = b;
                 pend_ph = ph;
             }
+            // the copy of tile t + 1, issued a step ago, is in place for its MMA
             asm volatile("cp.async.wait_all;" ::: "memory");
             proxy_fence();
             tc_before();
@@ -756,7 +756,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rbpg_split_tc(const __grid_co
                 break;
             }
             if (c + 1 < NCT && tid == 0)
-                issue_tile_mma(tmem + 16u * (uint32_t)(b ^ 1), b ? abuf0 : abuf1, bop, Kp, b ? mb0 : mb1);
+                issue_tile_mma(tmem + 16u * (uint32_t)(b ^ 1), abuf(t + 1), bop, Kp, b ? mb0 : mb1);
+            // tile t + 2 (of this sweep or the next) into the buffer of tile t - 1, whose MMA
+            // was waited for a step ago; the copy runs while the warps work on tile t
+            stage_tile(prm, abuf(t + 2), (int)((c + 2) % NCT), tid);
             float gx[KS], gy[KS];
 #pragma unroll
             for (int p = 0; p < KS; ++p) {
@@ -835,7 +838,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rbpg_split_tc(const __grid_co
         }
     }
     // retire the barriers and the tensor memory: no MMA is in flight, except the one a wait
-    // gave up on, which gets one more bounded wait first
+    // gave up on, which gets one more bounded wait first; the last operator copies land
+    asm volatile("cp.async.wait_all;" ::: "memory");
     tc_before();
     __syncthreads();
     tc_after();
