@@ -70,6 +70,8 @@ typedef struct {
     float c_alpha;        /* step reduction factor C_alpha of Eq. 15, in (0,1) (default 0.5)    */
     float alpha0_scale;   /* alpha_0 = alpha0_scale / (2N)  (default 1)                         */
     int32_t precision;    /* 0: FP32 contraction (CUDA cores); 1: BF16 operands, FP32 accumulate */
+                          /* (tensor cores: the grid-point kernel for 2N <= 64 and L <= 512,  */
+                          /* the split-grid kernel for 2N <= 160 at any L)                    */
     int32_t refit;        /* 0: none; 1: FP64 restricted solve on the support + certificate     */
     int32_t s_max;        /* largest support the refit handles (<= BPDN_MAX_SMAX, default 32)   */
     int32_t max_bt;       /* step cuts allowed per iteration before BT_LIMIT (default 64)        */
