@@ -186,15 +186,15 @@ size_t bpdn_solve_workspace_bytes(bpdn_op_t op, int64_t P, const bpdn_options *o
  * d_nbt      device int32 [P] out (may be NULL): total step cuts (Eq. 15 failures)
  * d_workspace  >= bpdn_solve_workspace_bytes(op, P, opt) bytes, 256-byte aligned
  * The operator's workspace must be resident on the current device.
- * Algorithm 1 runs in a split-grid FP32 kernel (a CTA's warps walk the grid in 32-point
- * chunks, the iterate in the workspace) for grids of more than 1024 points (L up to
- * BPDN_MAX_L, e.g. the multi-component grids of Eq. 4), which need precision 0,
- * tile_pixels 0 and blocks <= 1, and for FP32 solves of 513..1024 points with
+ * Algorithm 1 runs in a split-grid kernel (a CTA's warps walk the grid in 32-point chunks,
+ * the iterate in the workspace; FP32 CUDA cores, or BF16 tensor cores with precision 1)
+ * for grids of more than 1024 points (L up to BPDN_MAX_L, e.g. the multi-component grids
+ * of Eq. 4), which need tile_pixels 0 and blocks <= 1, for FP32 solves of 513..1024 points
+ * and for BF16 solves beyond the grid-point kernel's sizes (2N > 64 or L > 512), both with
  * tile_pixels 0 and blocks <= 1; opt->kernel overrides that choice (1: the grid-point
  * kernel, 2: the split-grid kernel at any L).  The choice depends on the operator and the
- * options only.  Such a solve needs a workspace of
- * at least bpdn_solve_workspace_bytes(op, P, opt) bytes; otherwise BPDN_ESIZE before any
- * launch (bpdn_solve_noalloc refuses them).
+ * options only.  Such a solve needs a workspace of at least
+ * bpdn_solve_workspace_bytes(op, P, opt) bytes; otherwise BPDN_ESIZE before any launch.
  */
 int bpdn_solve(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda,
                int32_t lambda_per_pixel, const bpdn_options *opt, void *d_x, int32_t *d_support,
@@ -417,7 +417,10 @@ int bpdn_classify_merge(int64_t P_c, const int64_t *d_idx, int32_t kmax, const i
  * on that device again (the kept address would be stale).  All calls share the array and
  * each clears what it uses, so calls whose work overlaps on the GPU race and must
  * be serialised by the caller.  A solve whose scratch would exceed 256 bytes is
- * rejected with BPDN_ESIZE.  No device memory is allocated or freed.
+ * rejected with BPDN_ESIZE: randomized blocks, the pixel-per-thread kernel and every solve
+ * that runs the split-grid kernel (see bpdn_solve; kernel 1 keeps FP32 solves of up to
+ * 1024 points on the grid-point kernel, which needs none).  No device memory is allocated
+ * or freed.
  */
 int bpdn_solve_noalloc(bpdn_op_t op, const void *d_g, int64_t P, const float *d_lambda,
                        int32_t lambda_per_pixel, const bpdn_options *opt, void *d_x,
