@@ -649,6 +649,7 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
                 }
                 mma_phase ^= 1u;
             }
+            __syncwarp();  // lanes leave the polling loop apart: reconverge before tcgen05.ld
             tc_fence_after();
         } else {
 #pragma unroll

@@ -401,6 +401,7 @@ __global__ void __launch_bounds__(kTiles * kSlots, 1) k_rbpg_px(const __grid_con
                 else
                     ph0 ^= 1u;
             }
+            __syncwarp();  // lanes leave the polling loop apart: reconverge before tcgen05.ld
             tc_fence_after();
             float d0[32], d1[32];
             tmem_ld32(lbase + kColD + kChunkCols * buf, d0);

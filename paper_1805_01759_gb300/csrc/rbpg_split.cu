@@ -728,7 +728,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rbpg_split_tc(const __grid_co
         for (int c = 0; c < NCT; ++c, ++t) {
             const int b = (int)(t & 1);
             const uint32_t ph = b ? ph1 : ph0;
-            const bool ok = tc_wait(b ? mb1 : mb0, ph);
+            // every lane polls the barrier on its own: vote, which also reconverges the warp
+            // before the warp-wide (.sync.aligned) tensor-memory loads below
+            const bool ok = __all_sync(0xffffffffu, tc_wait(b ? mb1 : mb0, ph));
             if (b)
                 ph1 ^= 1u;
             else
