@@ -164,8 +164,8 @@ bool solve_uses_split(const OpHandle *op, const bpdn_options *opt)
         return true;  // (kernel 1 is then refused by the plan)
     if (!opt || opt->kernel == 1 || opt->tile_pixels != 0 || opt->blocks >= 2)
         return false;
-    if (opt->precision == 1)  // the grid-point BF16 kernel takes 2N <= 64 and L <= 512
-        return op->L > 512 || 2 * op->N > 64;
+    if (opt->precision == 1)  // the grid-point BF16 kernel takes 2N <= 128 and L <= 512
+        return op->L > 512 || 2 * op->N > 128;
     return op->L > 512;
 }
 

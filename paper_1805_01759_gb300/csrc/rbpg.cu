@@ -5,7 +5,7 @@
 //   FP32  CUDA cores, packed f32x2 FMAs against the FP32 residuals in shared memory;
 //   BF16  tcgen05 MMAs from BF16 operands into FP32 accumulators in tensor memory,
 //         D[l, j] = sum_k Aop[l, k] B[j, k] per 128-row tile of the grid, K = 64
-//         (2N <= 64, zero padded), N = 16, with the constant operator rows
+//         (2N <= 64) or 128 (2N <= 128), zero padded, N = 16, with the constant operator rows
 //         Aop[l, :] = (Re A[:, l], Im A[:, l]) in tensor memory for the whole launch and
 //         B[p, :] = (Re r_p, Im r_p), B[8 + p, :] = (Im r_p, -Re r_p) in shared memory,
 //         so that D[l, p] = Re sum_n conj(A_nl) r_n and D[l, 8 + p] its imaginary part.
@@ -48,7 +48,9 @@ namespace {
 
 constexpr int TPG = 8;          // pixel slots per group
 constexpr int kMaxGroups = 2;   // groups per CTA (named barriers 1..kMaxGroups)
-constexpr int kK = 64;          // BF16 contraction length 2N padded to a multiple of 16
+// BF16 contraction length 2N zero padded: 64 with one row per lane (N <= 32), 128 with two
+constexpr int kK1 = 64, kK2 = 128;
+__host__ __device__ constexpr int tc_k(int nch) { return nch == 1 ? kK1 : kK2; }
 constexpr int kTmemCols = 512;
 constexpr int kMaxNW = 32;      // 32-point blocks of the grid per group: Lpad <= 1024
 
@@ -76,14 +78,14 @@ struct GroupLayout {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline GroupLayout group_layout(int N, int Lpad, bool tc)
+__host__ __device__ inline GroupLayout group_layout(int N, int Lpad, bool tc, int kk)
 {
     GroupLayout s;
     const int NW = Lpad / 32;
     size_t o = 0;
     s.Bop = s.Rre = s.Rim = s.mbar = 0;
     if (tc) {
-        s.Bop = o;  o = align16(o + 16 * kK * 2);  // B: 16 rows x K bf16, core-matrix layout
+        s.Bop = o;  o = align16(o + 16 * kk * 2);  // B: 16 rows x K bf16, core-matrix layout
         s.mbar = o; o = align16(o + 8);
     } else {
         s.Rre = o;  o = align16(o + sizeof(float) * (size_t)N * TPG);  // [N][TPG]
@@ -173,11 +175,11 @@ int warps_for(int Lpad, int G)
     return W;
 }
 
-// tensor-memory columns: [BF16 operator rows][BF16 accumulators per group][x^{k-1} per
-// group][xbar per group], 16 columns per tile for each per-group table
-__host__ __device__ inline int tmem_cols_used(int T, int G, bool tc)
+// tensor-memory columns: [BF16 operator rows, K/2 per tile][BF16 accumulators per group]
+// [x^{k-1} per group][xbar per group], 16 columns per tile for each per-group table
+__host__ __device__ inline int tmem_cols_used(int T, int G, bool tc, int kk)
 {
-    return (tc ? 32 * T + 16 * T * G : 0) + 32 * T * G;
+    return (tc ? kk / 2 * T + 16 * T * G : 0) + 32 * T * G;
 }
 
 // one stack of a launch: its operator, sizes and solve
@@ -248,12 +250,12 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return l | (h << 16);
 }
 
-// byte offset of element (row, k) of a K-major operand with kK columns, no swizzle:
+// byte offset of element (row, k) of a K-major operand with kk columns, no swizzle:
 // core matrices of 8 rows x 16 bytes; the K-adjacent core matrix 128 bytes on (LBO),
-// the next 8-row group kK/8 * 128 bytes on (SBO)
-__host__ __device__ inline int kmaj_off(int row, int k)
+// the next 8-row group kk/8 * 128 bytes on (SBO)
+__host__ __device__ inline int kmaj_off(int row, int k, int kk)
 {
-    return (row >> 3) * (kK / 8) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+    return (row >> 3) * (kk / 8) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
 // shared-memory matrix descriptor of tcgen05 (no swizzle)
@@ -353,8 +355,9 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
     const int G = prm.groups;
     const int N = prm.N, L = prm.L, Lpad = prm.Lpad, lda = prm.lda;
     const int NW = Lpad / 32;  // warps (blocks of 32 grid points) per group
-    // rows n = lane + 32 c, c < NCH, per lane (BF16: N <= 32; FP32: N <= 64, or N <= 96 for three)
-    static_assert(!TC || NCH == 1, "the BF16 contraction holds 2N <= 64 terms");
+    // rows n = lane + 32 c, c < NCH, per lane (BF16: N <= 32 or 64; FP32: N <= 64, or N <= 96 for three)
+    static_assert(!TC || NCH <= 2, "the BF16 contraction holds 2N <= 128 terms");
+    constexpr int KK = TC ? tc_k(NCH) : 0;  // BF16 contraction length
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q4 = w & 3;
     int grp = 0, blk = 0, tile = 0;
@@ -362,7 +365,7 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
     const int l = 32 * blk + lane;  // grid index owned by this thread
     const SolveLaunch &a = prm.a;
     float2 *sA = (float2 *)smem_raw;  // [N][lda] when SA
-    const GroupLayout lay = group_layout(N, Lpad, TC);
+    const GroupLayout lay = group_layout(N, Lpad, TC, KK);
     unsigned char *gbase = smem_raw + (SA ? a_bytes(N, lda) : 0) + (size_t)grp * lay.bytes;
     unsigned char *sBop = gbase + lay.Bop;  // BF16
     float *sRre = (float *)(gbase + lay.Rre), *sRim = (float *)(gbase + lay.Rim);  // FP32: [N][TPG]
@@ -388,10 +391,10 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
         if constexpr (TC) {
             const __nv_bfloat16 bre = __float2bfloat16_rn(re), bim = __float2bfloat16_rn(im);
             const __nv_bfloat16 nre = __float2bfloat16_rn(-re);
-            *(__nv_bfloat16 *)(sBop + kmaj_off(p, n)) = bre;
-            *(__nv_bfloat16 *)(sBop + kmaj_off(p, N + n)) = bim;
-            *(__nv_bfloat16 *)(sBop + kmaj_off(TPG + p, n)) = bim;
-            *(__nv_bfloat16 *)(sBop + kmaj_off(TPG + p, N + n)) = nre;
+            *(__nv_bfloat16 *)(sBop + kmaj_off(p, n, KK)) = bre;
+            *(__nv_bfloat16 *)(sBop + kmaj_off(p, N + n, KK)) = bim;
+            *(__nv_bfloat16 *)(sBop + kmaj_off(TPG + p, n, KK)) = bim;
+            *(__nv_bfloat16 *)(sBop + kmaj_off(TPG + p, N + n, KK)) = nre;
         } else {
             sRre[n * TPG + p] = re;
             sRim[n * TPG + p] = im;
@@ -406,7 +409,7 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
         if (lane == 0)
             S.abort = 0;
         if constexpr (TC) {
-            for (int i = lane; i < 16 * kK * 2 / 4; i += 32)
+            for (int i = lane; i < 16 * KK * 2 / 4; i += 32)
                 ((uint32_t *)sBop)[i] = 0u;  // K padding of B stays zero
             if (lane == 0) {
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar));
@@ -424,7 +427,7 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
     tc_fence_after();
     const uint32_t lane_base = tmem + ((uint32_t)(32 * q4) << 16);
     const int T = (Lpad + 127) / 128;
-    const int colD = TC ? 32 * T : 0;
+    const int colD = TC ? KK / 2 * T : 0;
     const int colXp = colD + (TC ? 16 * T * G : 0);
     const int colXb = colXp + 16 * T * G;
     const uint32_t taD = lane_base + colD + 16 * T * grp + 16 * tile;
@@ -435,9 +438,9 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
             // operator rows of this thread's grid index into its tensor-memory lane: full
             // tiles by group 0, the partial tile by every group at its own quadrants
             if (grp == 0 || tile == T - 1) {
-                const uint32_t ta = lane_base + 32 * tile;
+                const uint32_t ta = lane_base + KK / 2 * tile;
 #pragma unroll
-                for (int part = 0; part < 4; ++part) {
+                for (int part = 0; part < KK / 16; ++part) {
                     uint32_t v[8];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
@@ -596,10 +599,10 @@ __device__ __forceinline__ void run_stack(const StackDesc &prm, uint32_t tmem, u
                 const uint32_t b0 = smem_u32(sBop);
                 for (int t = 0; t < T; ++t) {
                     const uint32_t d = tmem + colD + 16 * T * grp + 16 * t;
-                    const uint32_t arow = tmem + 32 * t;
+                    const uint32_t arow = tmem + KK / 2 * t;
 #pragma unroll
-                    for (int j = 0; j < kK / 16; ++j)
-                        tc_mma_ts(d, arow + 8 * j, smem_desc(b0 + 256 * j, 128, (kK / 8) * 128), j > 0);
+                    for (int j = 0; j < KK / 16; ++j)
+                        tc_mma_ts(d, arow + 8 * j, smem_desc(b0 + 256 * j, 128, (KK / 8) * 128), j > 0);
                 }
                 tc_commit(mbar);
             }
@@ -1000,38 +1003,53 @@ __global__ void __launch_bounds__(MAXT, 1) k_rbpg(const __grid_constant__ Params
 struct Plan {
     int groups, threads;
     bool smem_a;
+    int nch;  // BF16: rows per lane (contraction length 64 or 128)
     size_t smem;
 };
 
-// Pick groups per CTA and where A lives: two groups before one (or the groups asked
-// for), A in shared memory before A in global memory.  Returns an empty string on
-// success, else the reason.
+// Pick groups per CTA and where A lives.  FP32: A in shared memory before A in global
+// memory (its contraction reads A every sweep), then two groups before one.  BF16 (A only
+// feeds A xbar): two groups before one, then A in shared memory before global memory.  A
+// fixed groups count is taken when asked for.  BF16 solves with N <= 32 use K = 64 where A
+// fits in shared memory, else K = 128 (the zero padding adds exact zeros: same results).
+// Returns an empty string on success, else the reason.
 const char *make_plan(const OpHandle &op, bool tc, int groups, int max_smem, Plan *pl)
 {
     if (op.Lpad > 32 * kMaxNW)
         return "the iteration kernel handles L <= 1024";
-    if (tc && (2 * op.N > kK || op.Lpad > 512))
-        return "precision 1 (BF16 tensor cores) needs 2N <= 64 and L <= 512";
+    if (tc && (2 * op.N > kK2 || op.Lpad > 512))
+        return "precision 1 (BF16 tensor cores) needs 2N <= 128 and L <= 512";
     const int T = (op.Lpad + 127) / 128;
-    const GroupLayout lay = group_layout(op.N, op.Lpad, tc);
     const size_t abytes = a_bytes(op.N, op.lda);
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool sa = (pass == 0);
-        if (!sa && tc)
-            break;
-        for (int g = kMaxGroups; g >= 1; --g) {
+    // candidates (groups, A in shared memory) in order of preference
+    int cg[2 * kMaxGroups];
+    bool csa[2 * kMaxGroups];
+    int nc = 0;
+    for (int i = 0; i < 2 * kMaxGroups; ++i) {
+        cg[nc] = tc ? kMaxGroups - i / 2 : kMaxGroups - i % kMaxGroups;
+        csa[nc] = tc ? (i % 2 == 0) : (i < kMaxGroups);
+        ++nc;
+    }
+    for (int c = 0; c < nc; ++c) {
+        {
+            const int g = cg[c];
+            const bool smem_a = csa[c];
             if (groups && g != groups)
                 continue;
+            const int nch = tc ? ((2 * op.N <= kK1 && smem_a) ? 1 : 2) : 0;
+            const int kk = tc ? tc_k(nch) : 0;
+            const GroupLayout lay = group_layout(op.N, op.Lpad, tc, kk);
             const int W = warps_for(op.Lpad, g);
             // the BF16 variant is built for at most 832 threads, the FP32 ones for 1024
-            if (32 * W > (tc ? 832 : 1024) || tmem_cols_used(T, g, tc) > kTmemCols)
+            if (32 * W > (tc ? 832 : 1024) || tmem_cols_used(T, g, tc, kk) > kTmemCols)
                 continue;
-            const size_t smem = (sa ? abytes : 0) + (size_t)g * lay.bytes;
+            const size_t smem = (smem_a ? abytes : 0) + (size_t)g * lay.bytes;
             if (smem > (size_t)max_smem)
                 continue;
             pl->groups = g;
             pl->threads = 32 * W;
-            pl->smem_a = sa;
+            pl->smem_a = smem_a;
+            pl->nch = nch;
             pl->smem = smem;
             return "";
         }
@@ -1074,7 +1092,6 @@ cudaError_t launch_rbpg_batch(const OpHandle *const *ops, const SolveLaunch *as,
         int i;
         Plan pl;
     };
-    // kernel variant of a stack: precision, where A lives, launch bound
     // kernel variant: precision, rows per lane, where A lives, launch bound
     std::vector<Item> byvar[16];
     for (int i = 0; i < n; ++i) {
@@ -1085,7 +1102,8 @@ cudaError_t launch_rbpg_batch(const OpHandle *const *ops, const SolveLaunch *as,
         const bool tc = (as[i].precision == 1);
         if (make_plan(*ops[i], tc, as[i].groups, max_smem, &it.pl)[0] != '\0')
             return cudaErrorInvalidValue;
-        const bool wide = ops[i]->N > 64;
+        // FP32: three rows per lane beyond N = 64; BF16: two rows per lane (K = 128)
+        const bool wide = tc ? it.pl.nch == 2 : ops[i]->N > 64;
         byvar[(tc ? 8 : 0) + (wide ? 4 : 0) + (it.pl.smem_a ? 2 : 0) + (it.pl.threads > 832 ? 1 : 0)].push_back(it);
     }
     std::unique_ptr<Params> prm(new Params);
@@ -1123,8 +1141,11 @@ cudaError_t launch_rbpg_batch(const OpHandle *const *ops, const SolveLaunch *as,
             if (smem < (size_t)max_smem / 2 + 1024)
                 smem = (size_t)max_smem / 2 + 1024;
             const bool tc = (v & 8) != 0, wide = (v & 4) != 0, sa = (v & 2) != 0, big = (v & 1) != 0;
-            if (tc)
+            if (tc && !wide)
                 e = launch_variant<true, true, 832, 1>(*prm, threads, grid, smem, s);
+            else if (tc)
+                e = sa ? launch_variant<true, true, 832, 2>(*prm, threads, grid, smem, s)
+                       : launch_variant<true, false, 832, 2>(*prm, threads, grid, smem, s);
             else if (!wide && sa)
                 e = big ? launch_variant<false, true, 1024, 2>(*prm, threads, grid, smem, s)
                         : launch_variant<false, true, 832, 2>(*prm, threads, grid, smem, s);

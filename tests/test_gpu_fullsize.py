@@ -95,7 +95,7 @@ def test_full_ragged_batch():
     items = [(api.Operator.from_geometry(st.geom), torch.from_numpy(st.g).cuda(), st.lam) for st in sts]
 
     def opts(op):
-        ok = 2 * op.N <= 64 and op.L <= 512
+        ok = 2 * op.N <= 128 and op.L <= 512
         return dict(precision=1 if ok else 0, tol=1e-3 if ok else 1e-6)
 
     results = {}

@@ -340,6 +340,37 @@ def test_bf16_iterations_match_algorithm_1_element_wise(api, small, k, tile):
     assert checked >= {1: 120, 2: 100, 3: 80, 10: 30}[k], checked
 
 
+@pytest.mark.parametrize("k", [1, 3])
+@pytest.mark.parametrize("N,L,tile", [(48, 300, 16), (48, 300, 8), (64, 512, 0)])
+def test_bf16_grid_kernel_k128_element_wise(api, N, L, tile, k):
+    """The grid-point BF16 kernel with 2N > 64 (contraction length K = 128, two rows per
+    lane) against the oracle's Algorithm 1 with the same BF16 operands, element by element
+    under the bar of the test above: two groups with A in shared memory (tile 16), one group
+    (tile 8), and N = 64, L = 512 (the largest stack it takes; A in global memory)."""
+    rng = np.random.default_rng(7000 + N + L)
+    geom = synth.make_geometry(rng, N, L, 250.0, 120.0)
+    st = synth.make_stack(geom, 128, rng, lam=synth.default_lambda(N, L), snr_db_range=(5.0, 20.0))
+    A = oracle.operator(st.geom)
+    op = api.Operator.from_geometry(st.geom)
+    res = api.solve(op, torch.from_numpy(st.g).cuda(), st.lam, max_iter=k, tol=0.0, refit=0, precision=1,
+                    tile_pixels=tile)
+    x = res.x.cpu().numpy()
+    iters = res.iters.cpu().numpy()
+    checked = 0
+    for p in range(st.g.shape[0]):
+        r = oracle.rbpg(A, st.g[p], st.lam, max_iter=k, tol=0.0, trace=True, bf16_operands=True)
+        if np.min(r["margin"]) < 1e-3:
+            continue
+        assert iters[p] == r["iters"], p
+        ref = r["x"]
+        nr = np.linalg.norm(ref)
+        err = np.linalg.norm(x[p] - ref)
+        assert err <= 2e-4 * max(nr, 1e-6), (p, err, nr)
+        assert np.array_equal(x[p] != 0, ref != 0), p
+        checked += 1
+    assert checked >= {1: 24, 3: 12}[k], checked
+
+
 @pytest.mark.parametrize("k", [1, 2])
 def test_bf16_first_iterations(api, small, k):
     """Algorithm 1 with the gradient from BF16 operands (FP32 accumulation) against the
@@ -368,13 +399,13 @@ def test_bf16_first_iterations(api, small, k):
 
 
 def test_bf16_beyond_the_grid_kernel(api):
-    """The grid-point BF16 kernel holds 2N <= 64 contraction terms: with the library's choice
+    """The grid-point BF16 kernel holds 2N <= 128 contraction terms: with the library's choice
     a larger N runs the tensor-core split-grid kernel, while asking for the grid-point kernel
     (a tile of 8 or 16 pixels, or kernel 1) is refused up front."""
     from paper_1805_01759_gb300 import _lib
-    geom = synth.make_geometry(np.random.default_rng(0), 40, 100)
+    geom = synth.make_geometry(np.random.default_rng(0), 70, 100)
     op = api.Operator.from_geometry(geom)
-    g = torch.zeros((4, 40), dtype=torch.complex64, device="cuda")
+    g = torch.zeros((4, 70), dtype=torch.complex64, device="cuda")
     res = api.solve(op, g, 1.0, precision=1)
     assert torch.all(res.x == 0) and torch.all((res.status & 32) != 0)
     for bad in (dict(tile_pixels=16), dict(tile_pixels=8), dict(kernel=1)):
@@ -387,15 +418,18 @@ def test_bf16_beyond_the_grid_kernel(api):
                                                        (64, 1024, 300.0, 0), (32, 512, 200.0, 1),
                                                        (78, 400, 200.0, 0), (80, 200, 100.0, 0),
                                                        (78, 400, 200.0, 1), (60, 600, 250.0, 1),
-                                                       (12, 1000, 300.0, 1), (80, 1024, 300.0, 1)])
+                                                       (12, 1000, 300.0, 1), (80, 1024, 300.0, 1),
+                                                       (40, 300, 120.0, 1), (48, 400, 200.0, 1),
+                                                       (64, 512, 200.0, 1), (60, 200, 100.0, 1)])
 def test_solve_refit_operator_sizes(api, N, L, half_width, precision):
     """Beyond the sizes of the benchmark stack: N > 32 (two rows per lane), L > 512, an
     operator too large for shared memory (N=60, L=600: A is read from global memory), the
     78 acquisitions of the paper's Munich stack (three rows per lane, Sec. IV-C), and the
     library's maximum sizes (FP32: N = 64, L = 1024, one 1024-thread group per CTA, and
-    N = 80; BF16: 2N = 64 contraction terms, L = 512, on the grid-point kernel, and beyond
-    that, up to N = 80 and L = 1024, on the tensor-core split-grid kernel).  Same bar as the
-    small workload against the exact minimiser."""
+    N = 80; BF16 on the grid-point kernel: 2N = 64 contraction terms at L = 512, and 2N up to
+    128 (K = 128, two rows per lane: N = 40, 48, 60 and 64, the last at L = 512 with A in
+    global memory); beyond that, up to N = 80 and L = 1024, on the tensor-core split-grid
+    kernel).  Same bar as the small workload against the exact minimiser."""
     rng = np.random.default_rng(1000 + N + L)
     geom = synth.make_geometry(rng, N, L, 250.0, half_width)
     st = synth.make_stack(geom, 48, rng, lam=synth.default_lambda(N, L), snr_db_range=(5.0, 20.0))
