@@ -70,7 +70,7 @@ typedef struct {
     float c_alpha;        /* step reduction factor C_alpha of Eq. 15, in (0,1) (default 0.5)    */
     float alpha0_scale;   /* alpha_0 = alpha0_scale / (2N)  (default 1)                         */
     int32_t precision;    /* 0: FP32 contraction (CUDA cores); 1: BF16 operands, FP32 accumulate */
-                          /* (tensor cores: the grid-point kernel for 2N <= 64 and L <= 512,  */
+                          /* (tensor cores: the grid-point kernel for 2N <= 128 and L <= 512, */
                           /* the split-grid kernel for 2N <= 160 at any L)                    */
     int32_t refit;        /* 0: none; 1: FP64 restricted solve on the support + certificate     */
     int32_t s_max;        /* largest support the refit handles (<= BPDN_MAX_SMAX, default 32)   */
@@ -190,7 +190,7 @@ size_t bpdn_solve_workspace_bytes(bpdn_op_t op, int64_t P, const bpdn_options *o
  * the iterate in the workspace; FP32 CUDA cores, or BF16 tensor cores with precision 1)
  * for grids of more than 1024 points (L up to BPDN_MAX_L, e.g. the multi-component grids
  * of Eq. 4), which need tile_pixels 0 and blocks <= 1, for FP32 solves of 513..1024 points
- * and for BF16 solves beyond the grid-point kernel's sizes (2N > 64 or L > 512), both with
+ * and for BF16 solves beyond the grid-point kernel's sizes (2N > 128 or L > 512), both with
  * tile_pixels 0 and blocks <= 1; opt->kernel overrides that choice (1: the grid-point
  * kernel, 2: the split-grid kernel at any L).  The choice depends on the operator and the
  * options only.  Such a solve needs a workspace of at least
