@@ -75,7 +75,8 @@ typedef struct {
     int32_t refit;        /* 0: none; 1: FP64 restricted solve on the support + certificate     */
     int32_t s_max;        /* largest support the refit handles (<= BPDN_MAX_SMAX, default 32)   */
     int32_t max_bt;       /* step cuts allowed per iteration before BT_LIMIT (default 64)        */
-    int32_t tile_pixels;  /* pixels in flight per SM: 8 or 16 (0 = library choice, 16 when it fits) */
+    int32_t tile_pixels;  /* pixels in flight per SM: 8 or 16; 0 = library choice: groups of 8 */
+                          /* pixels, as many as fit (16 at L = 400, up to 64 on small grids)   */
     int32_t refit_rounds; /* working-set rounds of the refit (default 4)                         */
     int32_t blocks;       /* 0 or 1: Algorithm 1 on each pixel's whole grid (default); 2..8:     */
                           /* the grid split into that many contiguous blocks, one drawn per    */

@@ -466,8 +466,9 @@ _TUNE_CACHE: dict = {}
 
 def autotune_stack(op: Operator, g: torch.Tensor, lam, *, repeats: int = 2, **options):
     """Pick the iteration kernel and tile for this operator and batch by timing bpdn_solve
-    on g itself: (kernel, tile_pixels) among the grid-point kernel with 16 or 8 pixels per
-    slot group and the split-grid kernel (CUDA cores in FP32, tensor cores with BF16).
+    on g itself: (kernel, tile_pixels) among the grid-point kernel with the library's number
+    of slot groups, with 16 or with 8 pixels per CTA, and the split-grid kernel (CUDA cores in
+    FP32, tensor cores with BF16).
     Cached by (N, L, precision, P);
     candidates the library refuses at these sizes are skipped.  Returns (0, 0), the
     library's own choice, when nothing could be timed."""
@@ -476,7 +477,7 @@ def autotune_stack(op: Operator, g: torch.Tensor, lam, *, repeats: int = 2, **op
     key = (op.N, op.L, prec, P, int(options.get("blocks", 0)))
     if key in _TUNE_CACHE:
         return _TUNE_CACHE[key]
-    cands = [(1, 16), (1, 8), (2, 0)]
+    cands = [(1, 0), (1, 16), (1, 8), (2, 0)]
     opts = {k: v for k, v in options.items() if k not in ("kernel", "tile_pixels")}
     best, best_ms = (0, 0), float("inf")
     for kern, tile in cands:

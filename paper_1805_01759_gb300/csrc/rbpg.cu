@@ -47,7 +47,7 @@ namespace bpdn {
 namespace {
 
 constexpr int TPG = 8;          // pixel slots per group
-constexpr int kMaxGroups = 2;   // groups per CTA (named barriers 1..kMaxGroups)
+constexpr int kMaxGroups = 8;   // groups per CTA (named barriers 1..kMaxGroups)
 // BF16 contraction length 2N zero padded: 64 with one row per lane (N <= 32), 128 with two
 constexpr int kK1 = 64, kK2 = 128;
 __host__ __device__ constexpr int tc_k(int nch) { return nch == 1 ? kK1 : kK2; }
@@ -1008,9 +1008,12 @@ struct Plan {
 };
 
 // Pick groups per CTA and where A lives.  FP32: A in shared memory before A in global
-// memory (its contraction reads A every sweep), then two groups before one.  BF16 (A only
-// feeds A xbar): two groups before one, then A in shared memory before global memory.  A
-// fixed groups count is taken when asked for.  BF16 solves with N <= 32 use K = 64 where A
+// memory (its contraction reads A every sweep), then more groups before fewer.  BF16 (A only
+// feeds A xbar): two or more groups with A in shared memory, then two or more with A in
+// global memory (more before fewer), then one group.
+// Threads (832 BF16, 1024 FP32), tensor-memory columns and shared memory bound the groups:
+// two at L = 400, up to eight on grids of at most 128 points.  A fixed groups count is taken
+// when asked for.  BF16 solves with N <= 32 use K = 64 where A
 // fits in shared memory, else K = 128 (the zero padding adds exact zeros: same results).
 // Returns an empty string on success, else the reason.
 const char *make_plan(const OpHandle &op, bool tc, int groups, int max_smem, Plan *pl)
@@ -1026,8 +1029,16 @@ const char *make_plan(const OpHandle &op, bool tc, int groups, int max_smem, Pla
     bool csa[2 * kMaxGroups];
     int nc = 0;
     for (int i = 0; i < 2 * kMaxGroups; ++i) {
-        cg[nc] = tc ? kMaxGroups - i / 2 : kMaxGroups - i % kMaxGroups;
-        csa[nc] = tc ? (i % 2 == 0) : (i < kMaxGroups);
+        if (tc) {
+            // two or more groups with A in shared memory, then with A in global memory,
+            // then one group
+            const int j = i < 2 * (kMaxGroups - 1) ? i % (kMaxGroups - 1) : 0;
+            cg[nc] = i < 2 * (kMaxGroups - 1) ? kMaxGroups - j : 1;
+            csa[nc] = i < 2 * (kMaxGroups - 1) ? (i < kMaxGroups - 1) : (i == 2 * (kMaxGroups - 1));
+        } else {
+            cg[nc] = kMaxGroups - i % kMaxGroups;
+            csa[nc] = i < kMaxGroups;
+        }
         ++nc;
     }
     for (int c = 0; c < nc; ++c) {

@@ -341,12 +341,13 @@ def test_bf16_iterations_match_algorithm_1_element_wise(api, small, k, tile):
 
 
 @pytest.mark.parametrize("k", [1, 3])
-@pytest.mark.parametrize("N,L,tile", [(48, 300, 16), (48, 300, 8), (64, 512, 0)])
+@pytest.mark.parametrize("N,L,tile", [(48, 300, 16), (48, 300, 8), (64, 512, 0), (48, 120, 0)])
 def test_bf16_grid_kernel_k128_element_wise(api, N, L, tile, k):
     """The grid-point BF16 kernel with 2N > 64 (contraction length K = 128, two rows per
     lane) against the oracle's Algorithm 1 with the same BF16 operands, element by element
     under the bar of the test above: two groups with A in shared memory (tile 16), one group
-    (tile 8), and N = 64, L = 512 (the largest stack it takes; A in global memory)."""
+    (tile 8), N = 64, L = 512 (the largest stack it takes; A in global memory), and L = 120
+    (six slot groups per CTA)."""
     rng = np.random.default_rng(7000 + N + L)
     geom = synth.make_geometry(rng, N, L, 250.0, 120.0)
     st = synth.make_stack(geom, 128, rng, lam=synth.default_lambda(N, L), snr_db_range=(5.0, 20.0))
@@ -420,7 +421,9 @@ def test_bf16_beyond_the_grid_kernel(api):
                                                        (78, 400, 200.0, 1), (60, 600, 250.0, 1),
                                                        (12, 1000, 300.0, 1), (80, 1024, 300.0, 1),
                                                        (40, 300, 120.0, 1), (48, 400, 200.0, 1),
-                                                       (64, 512, 200.0, 1), (60, 200, 100.0, 1)])
+                                                       (64, 512, 200.0, 1), (60, 200, 100.0, 1),
+                                                       (20, 100, 60.0, 0), (20, 100, 60.0, 1),
+                                                       (48, 120, 80.0, 1), (30, 200, 100.0, 0)])
 def test_solve_refit_operator_sizes(api, N, L, half_width, precision):
     """Beyond the sizes of the benchmark stack: N > 32 (two rows per lane), L > 512, an
     operator too large for shared memory (N=60, L=600: A is read from global memory), the
@@ -429,7 +432,8 @@ def test_solve_refit_operator_sizes(api, N, L, half_width, precision):
     N = 80; BF16 on the grid-point kernel: 2N = 64 contraction terms at L = 512, and 2N up to
     128 (K = 128, two rows per lane: N = 40, 48, 60 and 64, the last at L = 512 with A in
     global memory); beyond that, up to N = 80 and L = 1024, on the tensor-core split-grid
-    kernel).  Same bar as the small workload against the exact minimiser."""
+    kernel); grids of at most 200 points, where a CTA holds three to eight slot groups.  Same
+    bar as the small workload against the exact minimiser."""
     rng = np.random.default_rng(1000 + N + L)
     geom = synth.make_geometry(rng, N, L, 250.0, half_width)
     st = synth.make_stack(geom, 48, rng, lam=synth.default_lambda(N, L), snr_db_range=(5.0, 20.0))
