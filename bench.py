@@ -578,7 +578,7 @@ def run_ours(args) -> None:
     rbpg_avg_s = statistics.mean(head_tm["rbpg_ms"]) / 1e3
     achieved = head_sweeps * alu_flops_per_sweep(head, N, L) / rbpg_avg_s / 1e12
     traffic = _traffic_per_launch(P, head)
-    # the survey's count for the same kernel: per pixel sweep 16 N L flops of contraction on the
+    # a second count for the same kernel: per pixel sweep 16 N L flops of contraction on the
     # tensor cores (BF16; the FP32 path's contraction runs on the FP32 pipe) and 20 L of FP32
     # elementwise work; roofline time = the slowest of the pipes and HBM (3.4 kB per pixel)
     peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -590,7 +590,7 @@ def run_ours(args) -> None:
     else:
         t_pipe = head_sweeps * (16.0 * N * L + 20.0 * L) / (peak_tflops * 1e12)
     t_hbm = P * (8.0 * N + 8.0 * L + 16.0) / (hbm_gbs * 1e9)
-    survey_frac = max(t_pipe, t_hbm) / rbpg_avg_s
+    frac_16nl = max(t_pipe, t_hbm) / rbpg_avg_s
 
     if rank != 0:
         return
@@ -612,8 +612,8 @@ def run_ours(args) -> None:
         "paths": out_paths,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic, "kernel": kname,
-                     "frac_survey_count": survey_frac,
-                     "survey_count": "16 N L tensor (BF16 peak %s) + 20 L FP32 per sweep, HBM 3.4 kB per pixel" % (
+                     "frac_count_16NL_20L": frac_16nl,
+                     "count_16NL_20L": "16 N L tensor (BF16 peak %s) + 20 L FP32 per sweep, HBM 3.4 kB per pixel" % (
                          "measured" if mp else "fallback 1.9 PFLOP/s"),
                      "peak_source": "measured: FFMA/FFMA2 loops of bpdn_bench_peak on this GPU",
                      "peak_unit_count": unit_count_tflops, "peaks_measured": pk,
