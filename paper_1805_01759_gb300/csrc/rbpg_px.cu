@@ -48,7 +48,6 @@ constexpr int kColD = 32;
 constexpr int kTileCols = 32 + 2 * kChunkCols;  // 160
 constexpr int kTmemCols = 512;
 static_assert(kTiles * kTileCols <= kTmemCols, "tensor memory of the tiles");
-constexpr uint16_t kEnd = 0xFFFFu;  // list sentinel (L <= 1024)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
 
